@@ -1,0 +1,260 @@
+"""Seeded synthetic dual-way streams of planted PARAFAC2 tensors (inputs only).
+
+This module produces the *inputs* that both the FP64 oracle and the CUDA
+library consume: the irregular tensor {X_k} revealed over time as new rows of
+existing slices plus whole new slices (the dual-way streaming setting of §2.2,
+Problem 1, and the time terms of Figure 3).  It holds none of Dash's
+arithmetic: it only draws random factors and multiplies them out.
+
+Planted model (one recipe for every workload):
+  * H (R×R), V (J×R) and the slice weights W (K_total×R) have U(0,1) entries;
+  * Q_k (I_k,final×R) is the Q factor of a QR of a standard Gaussian matrix,
+    with its columns' signs fixed so that diag(R̃) > 0, drawn at the slice's
+    *final* length and revealed by row prefix, so new rows continue the same
+    planted slice;
+  * X_k = Q_k H diag(w_k) Vᵀ + σ·N(0,1)  (absolute noise level σ).
+
+Row counts are drawn up front from the workload's distributions, so the
+stream is a pure function of (workload, seed, device).  The CPU and CUDA
+torch generators give different draws for the same seed; every comparison
+therefore generates on one device and copies, never regenerates elsewhere.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence, Tuple
+
+import torch
+
+BASE_SEED = 2305183760
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """Shape and arrival recipe of one synthetic stream."""
+    name: str
+    K0: int                    # slices in the initial tensor
+    J: int                     # columns shared by every slice
+    R: int                     # target rank
+    init_rows: Tuple           # distribution of initial I_k
+    steps: int                 # number of updates in the stream
+    rows_per_step: Tuple       # rows added to every existing slice per update
+    new_slices_per_step: int   # L per update
+    new_slice_rows: Tuple      # distribution of a new slice's initial rows
+    sigma: float               # absolute Gaussian noise level
+    lam: float                 # forgetting factor used by this workload
+    seed: int
+
+
+def _w(name, idx, **kw):
+    return Workload(name=name, seed=BASE_SEED + idx, **kw)
+
+
+# The five dual-way workloads.  Stock-like shapes: J ∈ {85, 96, 144} in the
+# paper's Table 2 are matched by J = 88 (c2) and 64–256 (serving); the row
+# growth per update mirrors the update cycle of §4.1.
+WORKLOADS = {
+    "c1": _w("c1", 0, K0=50, J=100, R=10, init_rows=("uniform", 50, 200), steps=10,
+             rows_per_step=("const", 10), new_slices_per_step=5,
+             new_slice_rows=("uniform", 50, 200), sigma=0.01, lam=1.0),
+    "c2": _w("c2", 1, K0=3000, J=88, R=10, init_rows=("uniform", 500, 3000), steps=200,
+             rows_per_step=("const", 1), new_slices_per_step=10,
+             new_slice_rows=("uniform", 500, 1000), sigma=0.05, lam=0.98),
+    "c3": _w("c3", 2, K0=20000, J=256, R=20, init_rows=("lognormal", 400, 1.0, 1, 20000),
+             steps=50, rows_per_step=("uniform", 1, 64), new_slices_per_step=100,
+             new_slice_rows=("lognormal", 400, 1.0, 1, 20000), sigma=0.1, lam=0.95),
+    "c4": _w("c4", 3, K0=50000, J=512, R=32, init_rows=("lognormal", 400, 1.0, 1, 20000),
+             steps=20, rows_per_step=("uniform", 1, 64), new_slices_per_step=100,
+             new_slice_rows=("lognormal", 400, 1.0, 1, 20000), sigma=0.1, lam=0.95),
+}
+
+
+def scaled(w: Workload, **changes) -> Workload:
+    """A copy of a workload with some fields replaced (e.g. fewer slices)."""
+    return dataclasses.replace(w, **changes)
+
+
+def _draw_counts(dist: Tuple, n: int, gen: torch.Generator) -> torch.Tensor:
+    kind = dist[0]
+    if n == 0:
+        return torch.zeros(0, dtype=torch.int64)
+    if kind == "const":
+        return torch.full((n,), int(dist[1]), dtype=torch.int64)
+    if kind == "uniform":                      # integers lo..hi inclusive
+        lo, hi = int(dist[1]), int(dist[2])
+        return torch.randint(lo, hi + 1, (n,), generator=gen, dtype=torch.int64)
+    if kind == "lognormal":                    # median, sigma_ln, clip lo, clip hi
+        med, s, lo, hi = dist[1], dist[2], int(dist[3]), int(dist[4])
+        z = torch.randn(n, generator=gen, dtype=torch.float64)
+        v = torch.round(torch.exp(math.log(med) + s * z))
+        return v.clamp(lo, hi).to(torch.int64)
+    raise ValueError(f"unknown row distribution {dist!r}")
+
+
+@dataclasses.dataclass
+class Batch:
+    """New data of one update in CSR form: segment s covers rows
+    row_ptr[s]..row_ptr[s+1] of X and belongs to slice slice_ids[s].
+
+    Slices with id >= K_before are new; they are numbered consecutively
+    K_before .. K_before+n_new-1 and each has exactly one segment.
+    """
+    slice_ids: torch.Tensor     # (n_seg,) int64, ascending
+    row_ptr: torch.Tensor       # (n_seg+1,) int64
+    X: torch.Tensor             # (N, J)
+    K_before: int
+    n_new: int
+
+    @property
+    def n_rows(self) -> int:
+        return int(self.X.shape[0])
+
+    def segments(self):
+        """(slice id, rows) pairs, in order."""
+        rp = self.row_ptr.tolist()
+        for s, k in enumerate(self.slice_ids.tolist()):
+            yield k, self.X[rp[s]:rp[s + 1]]
+
+
+class PlantedStream:
+    """A planted PARAFAC2 stream for one workload.
+
+    batch(0) is the initial tensor (K0 slices, all their initial rows);
+    batch(t), t = 1..steps, is update t: rows_per_step new rows for every
+    slice that exists before it, then new_slices_per_step new slices.
+    """
+
+    def __init__(self, w: Workload, device="cpu", dtype=torch.float64,
+                 seed: Optional[int] = None):
+        self.w = w
+        self.device = torch.device(device)
+        self.dtype = dtype
+        seed = w.seed if seed is None else seed
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        L, T = w.new_slices_per_step, w.steps
+        self.K_total = w.K0 + L * T
+        # ---- row counts (host, int64) --------------------------------------
+        born = torch.zeros(self.K_total, dtype=torch.int64)   # arrival update
+        first = torch.empty(self.K_total, dtype=torch.int64)  # rows at arrival
+        first[: w.K0] = _draw_counts(w.init_rows, w.K0, g)
+        self.step_rows: List[torch.Tensor] = [first[: w.K0].clone()]
+        for t in range(1, T + 1):
+            k_exist = w.K0 + L * (t - 1)
+            grow = _draw_counts(w.rows_per_step, k_exist, g)
+            lo = k_exist
+            first[lo: lo + L] = _draw_counts(w.new_slice_rows, L, g)
+            born[lo: lo + L] = t
+            self.step_rows.append(torch.cat([grow, first[lo: lo + L]]))
+        self.born = born
+        final = torch.zeros(self.K_total, dtype=torch.int64)
+        for t, rows in enumerate(self.step_rows):
+            final[: rows.numel()] += rows
+        self.final_len = final
+        # prefix offsets of each slice's planted rows inside the flat Q store
+        self.q_off = torch.zeros(self.K_total + 1, dtype=torch.int64)
+        self.q_off[1:] = torch.cumsum(final, 0)
+        # rows of each slice revealed before update t
+        self._revealed = torch.zeros(self.K_total, dtype=torch.int64)
+        # ---- planted factors (drawn on the target device) -------------------
+        dg = torch.Generator(device=self.device).manual_seed(seed + 7919)
+        self._dgen = dg
+        R, J = w.R, w.J
+        kw = dict(generator=dg, device=self.device, dtype=dtype)
+        self.H = torch.rand(R, R, **kw)
+        self.V = torch.rand(J, R, **kw)
+        self.W = torch.rand(self.K_total, R, **kw)
+        self.Q = self._planted_q(final, dg)
+        self._next = 0
+
+    # -- planted orthonormal Q_k, bucketed by length for batched QR ----------
+    def _planted_q(self, final: torch.Tensor, dg: torch.Generator) -> torch.Tensor:
+        R = self.w.R
+        total = int(final.sum())
+        Q = torch.zeros(total, R, device=self.device, dtype=self.dtype)
+        G = torch.randn(total, R, generator=dg, device=self.device, dtype=self.dtype)
+        lens = final.tolist()
+        offs = self.q_off.tolist()
+        order = sorted(range(len(lens)), key=lambda k: lens[k])
+        i = 0
+        while i < len(order):
+            lmax_lo = max(lens[order[i]], 1)
+            cap = max(int(lmax_lo * 1.25) + 1, lmax_lo + 8)
+            j = i
+            while j < len(order) and lens[order[j]] <= cap and j - i < 4096:
+                j += 1
+            ids = order[i:j]
+            lmax = max(lens[k] for k in ids)
+            if lmax > 0:
+                pad = torch.zeros(len(ids), lmax, R, device=self.device, dtype=self.dtype)
+                for b, k in enumerate(ids):
+                    pad[b, : lens[k]] = G[offs[k]: offs[k] + lens[k]]
+                q, r = torch.linalg.qr(pad, mode="reduced")
+                sgn = torch.sign(torch.diagonal(r, dim1=-2, dim2=-1))
+                sgn[sgn == 0] = 1
+                q = q * sgn.unsqueeze(-2)
+                for b, k in enumerate(ids):
+                    Q[offs[k]: offs[k] + lens[k]] = q[b, : lens[k]]
+            i = j
+        return Q
+
+    def batch(self, t: int) -> Batch:
+        """Update t's new data (t = 0: the initial tensor).  Batches must be
+        drawn in order 0, 1, 2, ... because rows are revealed by prefix."""
+        if t != self._next:
+            raise ValueError(f"batches must be drawn in order (next is {self._next})")
+        self._next += 1
+        w = self.w
+        rows = self.step_rows[t]
+        k_count = rows.numel()
+        K_before = 0 if t == 0 else w.K0 + w.new_slices_per_step * (t - 1)
+        n_new = w.K0 if t == 0 else w.new_slices_per_step
+        ids = torch.arange(k_count, dtype=torch.int64)
+        row_ptr = torch.zeros(k_count + 1, dtype=torch.int64)
+        row_ptr[1:] = torch.cumsum(rows, 0)
+        N = int(row_ptr[-1])
+        # gather the planted Q rows revealed at this update
+        start = self.q_off[:k_count] + self._revealed[:k_count]
+        seg_of_row = torch.repeat_interleave(ids, rows)
+        within = torch.arange(N, dtype=torch.int64) - row_ptr[:-1].repeat_interleave(rows)
+        src = (start.repeat_interleave(rows) + within).to(self.device)
+        self._revealed[:k_count] += rows
+        q = self.Q.index_select(0, src)
+        wk = self.W.index_select(0, seg_of_row.to(self.device))
+        X = ((q @ self.H) * wk) @ self.V.T
+        if w.sigma:
+            X = X + w.sigma * torch.randn(N, w.J, generator=self._dgen,
+                                          device=self.device, dtype=self.dtype)
+        return Batch(slice_ids=ids, row_ptr=row_ptr, X=X.contiguous(),
+                     K_before=K_before, n_new=n_new)
+
+
+def workload(name: str, **changes) -> Workload:
+    w = WORKLOADS[name]
+    return scaled(w, **changes) if changes else w
+
+
+def tiny(K0=4, J=6, R=3, steps=3, rows=("uniform", 1, 4), new=2,
+         new_rows=("uniform", 2, 6), init_rows=("uniform", 4, 9),
+         sigma=0.0, lam=1.0, seed=11) -> Workload:
+    """A small stream for exact checks on the CPU."""
+    return Workload(name="tiny", K0=K0, J=J, R=R, init_rows=init_rows, steps=steps,
+                    rows_per_step=rows, new_slices_per_step=new,
+                    new_slice_rows=new_rows, sigma=sigma, lam=lam, seed=seed)
+
+
+def ragged_batch(K_before: int, n_new: int, J: int, rows: Sequence[int],
+                 seed: int, dtype=torch.float64, device="cpu",
+                 slice_ids: Optional[Sequence[int]] = None) -> Batch:
+    """An unstructured batch with the given per-segment row counts (Gaussian
+    entries): for edge cases (empty segments, 1-row slices, ragged tails)."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    rows_t = torch.tensor(list(rows), dtype=torch.int64)
+    if slice_ids is None:
+        slice_ids = list(range(len(rows)))
+    row_ptr = torch.zeros(len(rows) + 1, dtype=torch.int64)
+    row_ptr[1:] = torch.cumsum(rows_t, 0)
+    X = torch.randn(int(row_ptr[-1]), J, generator=g, dtype=torch.float64)
+    return Batch(slice_ids=torch.tensor(list(slice_ids), dtype=torch.int64),
+                 row_ptr=row_ptr, X=X.to(device=device, dtype=dtype),
+                 K_before=K_before, n_new=n_new)

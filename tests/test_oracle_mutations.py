@@ -1,0 +1,61 @@
+"""Planted mistakes in the oracle must fail its pins.
+
+Each case patches one plausible slip into the oracle (on the CPU only) and
+checks that at least one pin in test_oracle_pins.py then fails.
+"""
+import numpy as np
+import pytest
+
+from oracle import dash_oracle as O
+import tests.test_oracle_pins as P
+
+
+def _dropped_s_in_lemma1(X_new, V, w, rtol=None):
+    return X_new @ V @ O.pinv(V.T @ V, rtol)                  # S_k dropped
+
+
+def _sum_not_hadamard(c, D, V, rtol=None):
+    return c @ O.pinv((V.T @ V) + D, rtol)                    # ∗ read as +
+
+
+def _transposed_c_term(X, V, U):
+    if X.shape[0] == 0:
+        return np.zeros(V.shape[1])
+    return O.vec(X) @ O.khatri_rao(U, V)                       # operands swapped
+
+
+def _u_without_pinv_cutoff(X_new, V, w, rtol=None):
+    S = np.diag(w)
+    return X_new @ V @ S @ np.linalg.inv(S @ V.T @ V @ S + 1e-3 * np.eye(len(w)))
+
+
+def _lambda_dropped_on_old_f_g(state, segments, n_new, lam, **kw):
+    undo = state.copy()
+    if lam > 0:
+        undo.F = state.F / lam                                 # λ·F_old becomes F_old
+        undo.G = state.G / lam
+    return _ORIG_UPDATE(undo, segments, n_new, lam, **kw)
+
+
+_ORIG_UPDATE = O.dash_update_p
+
+CASES = [
+    ("update_u_new", _dropped_s_in_lemma1, [P.test_lemma1_u_new_is_the_least_squares_solution]),
+    ("solve_w_row", _sum_not_hadamard,
+     [lambda: P.test_lemma2_w_minimises_weighted_loss_with_v_frozen(1.0)]),
+    ("c_term", _transposed_c_term, [P.test_c_term_equals_explicit_triple_sum]),
+    ("update_u_new", _u_without_pinv_cutoff, [P.test_lemma1_u_new_is_the_least_squares_solution]),
+    ("dash_update_p", _lambda_dropped_on_old_f_g, [P.test_worked_example_rank_one_exact_fractions]),
+]
+
+
+@pytest.mark.parametrize("name,fake,pins", CASES, ids=[f"{c[0]}:{c[1].__name__}" for c in CASES])
+def test_planted_mistake_is_caught(monkeypatch, name, fake, pins):
+    monkeypatch.setattr(O, name, fake)
+    failed = 0
+    for pin in pins:
+        try:
+            pin()
+        except (AssertionError, ValueError, np.linalg.LinAlgError):
+            failed += 1
+    assert failed > 0, f"no pin caught the planted mistake in {name}"
