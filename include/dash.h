@@ -1,0 +1,201 @@
+/*
+ * dash.h — C ABI of the GB300 (sm_103a) Dash streaming PARAFAC2 library.
+ *
+ * Dash (Jang, Jang and Kang, KDD'23) keeps a PARAFAC2 model X_k ≈ U_k S_k Vᵀ
+ * of an irregular tensor {X_k} up to date while new rows of existing slices
+ * and whole new slices arrive (§2.2, Problem 1).  Each call to dash_update()
+ * is one "update" of Figure 3: it absorbs every row staged since the previous
+ * update with one pass of Algorithm 1, touching only the new rows and the
+ * λ-weighted helper summaries c_k, D_k, F, G (§3.2, Eqs. 11-21).
+ *
+ * Two model forms share the interface:
+ *   DASH_MODE_P  Algorithm 1 as written (U_k free).
+ *   DASH_MODE_Q  the constrained form U_k = Q_k H S_k with column-orthonormal
+ *                Q_k (the reparameterisation mentioned in §2.1), streamed
+ *                with the same old/new split (see dash_update()).
+ *
+ * Conventions for every entry point
+ *   - All matrices are row-major, dense, 0-based.  V is J×R, W is K×R
+ *     (row k = diagonal of S_k), D_k is R×R, F is J×R, G and H are R×R,
+ *     Z_k is R×J.  Row block X_k,new is I_k,new×J with leading dimension ld
+ *     (elements, >= J).
+ *   - Host pointers are read or written before the call returns; device
+ *     pointers (`where == DASH_DEVICE`) are read in stream order on the
+ *     model's stream.  The library never frees caller memory.
+ *   - Every call returns a dash_status.  On an error the model keeps its
+ *     previous state (argument and capacity errors are found on the host
+ *     before any device work) and dash_last_error() describes the cause.
+ *     A CUDA error (DASH_ECUDA) leaves the model unusable: destroy it.
+ *   - A model is not thread-safe; calls on one model must be serialised.
+ */
+#ifndef DASH_H
+#define DASH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dash_model dash_model;
+
+typedef enum dash_status {
+    DASH_OK = 0,
+    DASH_EINVAL = 1,     /* bad argument (shape, id, dtype, null pointer)   */
+    DASH_ENOMEM = 2,     /* device allocation failed or a capacity exceeded */
+    DASH_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed      */
+    DASH_ESTATE = 4,     /* call not valid now (e.g. V never set)            */
+    DASH_ENUMERIC = 5,   /* a non-finite value reached the factors           */
+    DASH_ETIMEOUT = 6    /* a bounded device wait gave up                    */
+} dash_status;
+
+enum { DASH_MODE_P = 0, DASH_MODE_Q = 1 };
+
+/* Arithmetic of the bulk products X_new·V and X_newᵀ(U S) (Theorem 1's
+ * dominant terms).  R×R solves, summaries and fitness are FP64 in all three. */
+enum {
+    DASH_PREC_FP64 = 0,  /* FP64 products                                      */
+    DASH_PREC_FP32 = 1,  /* FP32 products, FP32 accumulation                   */
+    DASH_PREC_BF16X3 = 2 /* tensor cores: BF16 hi/lo split, 3 products, FP32 acc */
+};
+
+enum { DASH_F64 = 0, DASH_F32 = 1 };        /* element type of staged X   */
+enum { DASH_HOST = 0, DASH_DEVICE = 1 };    /* where a caller pointer lives */
+
+typedef struct dash_config {
+    int32_t J;              /* columns of every slice (> 0)                      */
+    int32_t R;              /* target rank, 1..64                                */
+    double lambda;          /* forgetting factor λ, 0 < λ <= 1 (Eq. 5)           */
+    int32_t mode;           /* DASH_MODE_P or DASH_MODE_Q                        */
+    int32_t precision;      /* DASH_PREC_*                                       */
+    int32_t input_dtype;    /* DASH_F64 or DASH_F32: element type of X           */
+    int32_t n_sweeps;       /* passes of Algorithm 1 per update; must be 1       */
+    double pinv_rtol;       /* pseudo-inverse cut-off relative to the largest
+                               singular value; <= 0 selects R·DBL_EPSILON      */
+    int64_t max_slices;     /* capacity K_max of slices over the model's life    */
+    int64_t max_rows;       /* capacity of staged rows per update                */
+    int64_t max_segments;   /* capacity of staged segments per update            */
+    void *stream;           /* cudaStream_t to run on; NULL = a private stream   */
+} dash_config;
+
+/* Fill *cfg with defaults for (J, R, λ): mode P, FP32 products, FP32 input,
+ * one sweep, capacities 1<<16 slices / 1<<20 rows / 1<<17 segments. */
+void dash_config_default(dash_config *cfg, int32_t J, int32_t R, double lambda);
+
+/* init(K, J, R, λ) of the problem statement: create a model with no slices.
+ * Allocates all device memory for the capacities in cfg (DASH_ENOMEM if it
+ * does not fit).  V must be set with dash_set_factors() or dash_set_state()
+ * before the first update. */
+dash_status dash_init(const dash_config *cfg, dash_model **out);
+void dash_destroy(dash_model *m);
+const char *dash_last_error(const dash_model *m);
+const char *dash_status_string(dash_status s);
+
+/* Set the shared factors from host FP64 arrays: V (J×R) and, in mode Q,
+ * H (R×R; NULL = identity).  Used for a fresh model (the starting V of the
+ * static fit, §3.2.1). */
+dash_status dash_set_factors(dash_model *m, const double *V, const double *H);
+
+/* Replace the whole mode-P state (host FP64): K slices with factors V, W and
+ * helpers c (K×R), D (K×R×R), F (J×R), G (R×R) of §3.2.1 (Eqs. 6-9).  This
+ * is how a model resumes from saved or externally initialised helpers. */
+dash_status dash_set_state_p(dash_model *m, int64_t K, const double *V, const double *W,
+                             const double *c, const double *D, const double *F,
+                             const double *G);
+/* Read the mode-P state into host FP64 arrays sized for the current K
+ * (dash_num_slices()).  Any pointer may be NULL to skip that array. */
+dash_status dash_get_state_p(const dash_model *m, double *V, double *W, double *c,
+                             double *D, double *F, double *G);
+
+/* Mode-Q state: V, H, W and the λ-weighted per-slice summaries
+ * B_k = Σ λ^age A_kᵀA_k (R×R) and Z_k = Σ λ^age A_kᵀX_k (R×J). */
+dash_status dash_set_state_q(dash_model *m, int64_t K, const double *V, const double *H,
+                             const double *W, const double *B, const double *Z);
+dash_status dash_get_state_q(const dash_model *m, double *V, double *H, double *W,
+                             double *B, double *Z);
+
+int64_t dash_num_slices(const dash_model *m);
+
+/* append_rows(k, X_k,new): stage I_new new rows of existing slice k (or of a
+ * slice staged by dash_append_slices() in this update).  Rows are appended
+ * after the slice's existing rows, in call order.  X has input_dtype
+ * elements, I_new×J with leading dimension ld, at `where`; it is copied. */
+dash_status dash_append_rows(dash_model *m, int64_t k, const void *X, int64_t I_new,
+                             int64_t ld, int32_t where);
+
+/* append_slices({X_k}): stage L new slices with I[l] rows each (0 allowed);
+ * they get ids K..K+L-1 (K = slices before this call plus earlier staged
+ * new slices), returned in *first_new_id.  X[l] has leading dimension ld[l]
+ * (NULL = J for all). */
+dash_status dash_append_slices(dash_model *m, int64_t L, const int64_t *I,
+                               const void *const *X, const int64_t *ld, int32_t where,
+                               int64_t *first_new_id);
+
+/* Stage a whole batch in CSR form in one call: segment s covers rows
+ * row_ptr[s]..row_ptr[s+1]-1 of X (row-major, ld = J) and belongs to slice
+ * slice_ids[s]; ids >= the current slice count (plus staged new slices)
+ * create new slices, which must be numbered consecutively and appear in
+ * ascending order.  slice_ids and row_ptr are host arrays; X is at `where`
+ * and is copied (host → device with cudaMemcpyAsync; pinned memory lets
+ * it overlap). */
+dash_status dash_append_batch(dash_model *m, int64_t n_seg, const int64_t *slice_ids,
+                              const int64_t *row_ptr, const void *X, int32_t where);
+
+/* One update of Algorithm 1 (mode P) or of the constrained stream (mode Q)
+ * over everything staged since the last update, then clear the staging.
+ * Mode P, in the order of Algorithm 1:
+ *   U_k,new = X_k,new V S_k (S_k VᵀV S_k)⁺                 (Lemma 1, Eq. 11)
+ *   c_k ← λc_k + vec(X_k,new)ᵀ(V ⊙ U_k,new),  D_k ← λD_k + U_k,newᵀU_k,new
+ *   W(k,:) = c_kᵀ (VᵀV ∗ D_k)⁺  for every slice k        (Eqs. 15, 16, 12)
+ *   F ← λF + Σ X_k,newᵀU_k,newS_k,  G ← λG + Σ S_kU_k,newᵀU_k,newS_k
+ *   V = F G⁺                                              (Eqs. 20, 21, 17)
+ * A new slice uses S_k = I in Lemma 1.  ⁺ is the Moore-Penrose
+ * pseudo-inverse with cut-off pinv_rtol.
+ * Mode Q: A_new = X_new V S_k Hᵀ; B_k ← λB_k + A_newᵀA_new;
+ *   Z_k ← λZ_k + A_newᵀX_new; T_k = B_k^{-1/2}; Q_k,new = A_new T_k;
+ *   Y_k = T_k Z_k; one CP-ALS sweep H → V → W on {Y_k}.
+ * Runs asynchronously on the model's stream; results are read by the
+ * getters below, which synchronise. */
+dash_status dash_update(dash_model *m);
+
+/* The same update on a batch that already lives in device memory, read in
+ * place (no staging copy): slice_ids/row_ptr as in dash_append_batch (host
+ * arrays), X a device pointer of input_dtype, row-major with ld = J.  X must
+ * stay unchanged until the update has run on the model's stream.  Nothing
+ * may be staged when this is called. */
+dash_status dash_update_device(dash_model *m, int64_t n_seg, const int64_t *slice_ids,
+                               const int64_t *row_ptr, const void *X);
+
+/* Static fit of the initial tensor (§3.2.1): on an empty model with the
+ * staged batch made only of new slices, run n_iter ALS iterations from the
+ * current V (each = one update on empty helpers, which equals one static
+ * ALS iteration), then set the helpers from the final factors (Eqs. 6-9).
+ * Clears the staging. */
+dash_status dash_fit_initial(dash_model *m, int32_t n_iter);
+
+/* factors(): copy V (J×R), rows k_first..k_first+k_count-1 of W, and in mode
+ * Q H (R×R), to host FP64 arrays (NULL skips). */
+dash_status dash_factors(const dash_model *m, double *V, double *W, int64_t k_first,
+                         int64_t k_count, double *H);
+
+/* New factor rows of the last update, in staging row order: U_k,new (mode P)
+ * or Q_k,new (mode Q), N×R, to a host FP64 array.  *n_rows receives N. */
+dash_status dash_new_rows(const dash_model *m, double *out, int64_t *n_rows);
+
+/* fitness(): of the last update's batch with the updated factors,
+ * fit = 1 − ||X_new − X̂_new||_F / ||X_new||_F with X̂_new = U_new S_k Vᵀ
+ * (mode P) or Q_new H S_k Vᵀ (mode Q), from FP64 Gram terms.  x_norm2 (may
+ * be NULL) receives ||X_new||²_F. */
+dash_status dash_fitness(const dash_model *m, double *fit_batch, double *x_norm2);
+
+/* Wait for all work issued on the model's stream. */
+dash_status dash_sync(dash_model *m);
+
+/* Per-update device time of the last dash_update (CUDA events, ms). */
+dash_status dash_last_update_ms(const dash_model *m, float *ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DASH_H */

@@ -1,0 +1,246 @@
+"""ctypes binding of libdash_gb300.so (include/dash.h): argument marshalling
+only.  Every step of an update runs in the library's CUDA kernels; there is
+no Python or CPU fallback, and loading fails loudly when the library is
+missing."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdash_gb300.so")
+
+DASH_MODE_P, DASH_MODE_Q = 0, 1
+PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2}
+DTYPE = {"f64": 0, "f32": 1}
+HOST, DEVICE = 0, 1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory or capacity", 3: "CUDA error",
+          4: "invalid state", 5: "non-finite result", 6: "device wait timed out"}
+
+
+class DashError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("J", C.c_int32), ("R", C.c_int32), ("lambda_", C.c_double),
+                ("mode", C.c_int32), ("precision", C.c_int32), ("input_dtype", C.c_int32),
+                ("n_sweeps", C.c_int32), ("pinv_rtol", C.c_double),
+                ("max_slices", C.c_int64), ("max_rows", C.c_int64),
+                ("max_segments", C.c_int64), ("stream", C.c_void_p)]
+
+
+_lib = None
+
+# (name, restype, argtypes): every entry point declared in include/dash.h
+P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+PD = C.POINTER(C.c_double)
+PI64 = C.POINTER(C.c_int64)
+SIGNATURES = [
+    ("dash_config_default", None, [C.POINTER(Config), I32, I32, D]),
+    ("dash_init", C.c_int, [C.POINTER(Config), C.POINTER(P)]),
+    ("dash_destroy", None, [P]),
+    ("dash_last_error", C.c_char_p, [P]),
+    ("dash_status_string", C.c_char_p, [C.c_int]),
+    ("dash_set_factors", C.c_int, [P, PD, PD]),
+    ("dash_set_state_p", C.c_int, [P, I64, PD, PD, PD, PD, PD, PD]),
+    ("dash_get_state_p", C.c_int, [P, PD, PD, PD, PD, PD, PD]),
+    ("dash_set_state_q", C.c_int, [P, I64, PD, PD, PD, PD, PD]),
+    ("dash_get_state_q", C.c_int, [P, PD, PD, PD, PD, PD]),
+    ("dash_num_slices", I64, [P]),
+    ("dash_append_rows", C.c_int, [P, I64, P, I64, I64, I32]),
+    ("dash_append_slices", C.c_int, [P, I64, PI64, C.POINTER(P), PI64, I32, PI64]),
+    ("dash_append_batch", C.c_int, [P, I64, PI64, PI64, P, I32]),
+    ("dash_update", C.c_int, [P]),
+    ("dash_update_device", C.c_int, [P, I64, PI64, PI64, P]),
+    ("dash_fit_initial", C.c_int, [P, I32]),
+    ("dash_factors", C.c_int, [P, PD, PD, I64, I64, PD]),
+    ("dash_new_rows", C.c_int, [P, PD, PI64]),
+    ("dash_fitness", C.c_int, [P, PD, PD]),
+    ("dash_sync", C.c_int, [P]),
+    ("dash_last_update_ms", C.c_int, [P, C.POINTER(C.c_float)]),
+]
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once).  Raises if it is missing: there is no
+    fallback implementation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with "
+                          "`python -m paper_2305_18376_gb300.build` (needs nvcc)")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _pd(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(PD)
+
+
+def _f64(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _i64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+class DashModel:
+    """One streaming PARAFAC2 model behind the C ABI (dash_init ...)."""
+
+    def __init__(self, J: int, R: int, lam: float, mode: str = "P", precision: str = "fp32",
+                 input_dtype: str = "f32", max_slices: int = 1 << 16, max_rows: int = 1 << 20,
+                 max_segments: int = 1 << 17, pinv_rtol: float = 0.0, stream=None):
+        lib = load()
+        cfg = Config()
+        lib.dash_config_default(C.byref(cfg), J, R, lam)
+        cfg.mode = DASH_MODE_P if mode == "P" else DASH_MODE_Q
+        cfg.precision = PREC[precision]
+        cfg.input_dtype = DTYPE[input_dtype]
+        cfg.max_slices, cfg.max_rows, cfg.max_segments = max_slices, max_rows, max_segments
+        cfg.pinv_rtol = pinv_rtol
+        cfg.stream = stream
+        h = P()
+        st = lib.dash_init(C.byref(cfg), C.byref(h))
+        if st != 0:
+            raise DashError(st, "dash_init failed")
+        self._lib, self._h = lib, h
+        self.J, self.R, self.lam, self.mode = J, R, lam, mode
+        self.np_dtype = np.float64 if input_dtype == "f64" else np.float32
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dash_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st: int):
+        if st != 0:
+            raise DashError(st, self._lib.dash_last_error(self._h).decode())
+
+    # ---- factors / state ---------------------------------------------------
+    @property
+    def K(self) -> int:
+        return int(self._lib.dash_num_slices(self._h))
+
+    def set_factors(self, V, H=None):
+        V = _f64(V, (self.J, self.R))
+        Hh = None if H is None else _f64(H, (self.R, self.R))
+        self._ck(self._lib.dash_set_factors(self._h, _pd(V), _pd(Hh)))
+
+    def set_state_p(self, V, W, c, D, F, G):
+        K = int(np.asarray(W).shape[0])
+        R, J = self.R, self.J
+        V, W, c = _f64(V, (J, R)), _f64(W, (K, R)), _f64(c, (K, R))
+        D, F, G = _f64(D, (K, R, R)), _f64(F, (J, R)), _f64(G, (R, R))
+        self._ck(self._lib.dash_set_state_p(self._h, K, _pd(V), _pd(W), _pd(c), _pd(D),
+                                            _pd(F), _pd(G)))
+
+    def get_state_p(self) -> dict:
+        K, R, J = self.K, self.R, self.J
+        out = dict(V=np.empty((J, R)), W=np.empty((K, R)), c=np.empty((K, R)),
+                   D=np.empty((K, R, R)), F=np.empty((J, R)), G=np.empty((R, R)))
+        self._ck(self._lib.dash_get_state_p(self._h, *(_pd(out[k]) for k in "VWcDFG")))
+        return out
+
+    def factors(self, k_first: int = 0, k_count: Optional[int] = None):
+        if k_count is None:
+            k_count = self.K - k_first
+        V = np.empty((self.J, self.R))
+        W = np.empty((k_count, self.R))
+        self._ck(self._lib.dash_factors(self._h, _pd(V), _pd(W), k_first, k_count, None))
+        return V, W
+
+    def new_rows(self) -> np.ndarray:
+        n = C.c_int64()
+        self._ck(self._lib.dash_new_rows(self._h, None, C.byref(n)))
+        out = np.empty((n.value, self.R))
+        self._ck(self._lib.dash_new_rows(self._h, _pd(out), C.byref(n)))
+        return out
+
+    def fitness(self):
+        f, x = C.c_double(), C.c_double()
+        self._ck(self._lib.dash_fitness(self._h, C.byref(f), C.byref(x)))
+        return f.value, x.value
+
+    def last_update_ms(self) -> float:
+        ms = C.c_float()
+        self._ck(self._lib.dash_last_update_ms(self._h, C.byref(ms)))
+        return ms.value
+
+    def sync(self):
+        self._ck(self._lib.dash_sync(self._h))
+
+    # ---- staging -------------------------------------------------------------
+    def _ptr(self, X):
+        """(pointer, where, keepalive) of a host numpy array or a CUDA tensor."""
+        if hasattr(X, "is_cuda") and X.is_cuda:
+            want = {np.float64: "float64", np.float32: "float32"}[self.np_dtype]
+            if str(X.dtype).split(".")[-1] != want or not X.is_contiguous():
+                raise TypeError(f"device X must be a contiguous {want} tensor")
+            return C.c_void_p(X.data_ptr()), DEVICE, X
+        if hasattr(X, "numpy"):
+            X = X.numpy()
+        X = np.ascontiguousarray(np.asarray(X, dtype=self.np_dtype))
+        return C.c_void_p(X.ctypes.data), HOST, X
+
+    def append_rows(self, k: int, X):
+        ptr, where, keep = self._ptr(X)
+        n = int(keep.shape[0])
+        self._ck(self._lib.dash_append_rows(self._h, k, ptr, n, self.J, where))
+
+    def append_slices(self, Xs: Sequence) -> int:
+        ptrs, keeps, rows, where = [], [], [], HOST
+        for X in Xs:
+            p, where, keep = self._ptr(X)
+            ptrs.append(p.value or 0)
+            keeps.append(keep)
+            rows.append(int(keep.shape[0]))
+        L = len(rows)
+        I = _i64(rows)
+        arr = (C.c_void_p * max(L, 1))(*ptrs)
+        first = C.c_int64()
+        self._ck(self._lib.dash_append_slices(self._h, L, I.ctypes.data_as(PI64), arr, None,
+                                              where, C.byref(first)))
+        return first.value
+
+    def append_batch(self, slice_ids, row_ptr, X):
+        ids, rp = _i64(slice_ids), _i64(row_ptr)
+        ptr, where, keep = self._ptr(X)
+        self._ck(self._lib.dash_append_batch(self._h, len(ids), ids.ctypes.data_as(PI64),
+                                             rp.ctypes.data_as(PI64), ptr, where))
+
+    def update(self):
+        self._ck(self._lib.dash_update(self._h))
+
+    def update_device(self, slice_ids, row_ptr, X):
+        ids, rp = _i64(slice_ids), _i64(row_ptr)
+        ptr, where, keep = self._ptr(X)
+        if where != DEVICE:
+            raise TypeError("update_device needs a CUDA tensor")
+        self._ck(self._lib.dash_update_device(self._h, len(ids), ids.ctypes.data_as(PI64),
+                                              rp.ctypes.data_as(PI64), ptr))
+
+    def fit_initial(self, n_iter: int):
+        self._ck(self._lib.dash_fit_initial(self._h, n_iter))

@@ -1,0 +1,765 @@
+// C ABI of the Dash library (include/dash.h): model life cycle, staging of
+// new rows, per-update planning on the host, and the launch sequence of one
+// update on the model's CUDA stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dash.h"
+#include "dash_internal.cuh"
+
+using namespace dash;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static dash_status fail(dash_model *m, dash_status s, const char *fmt, ...) {
+    if (m) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        m->err = buf;
+    }
+    return s;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            m->broken = true;                                                            \
+            return fail(m, DASH_ECUDA, "%s failed: %s (%s:%d)", #call,                   \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+        }                                                                                \
+    } while (0)
+
+#define CKL()                                                                            \
+    do {                                                                                 \
+        cudaError_t e_ = cudaGetLastError();                                             \
+        if (e_ != cudaSuccess) {                                                         \
+            m->broken = true;                                                            \
+            return fail(m, DASH_ECUDA, "kernel launch failed: %s (%s:%d)",               \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+        }                                                                                \
+    } while (0)
+
+extern "C" const char *dash_status_string(dash_status s) {
+    switch (s) {
+    case DASH_OK: return "ok";
+    case DASH_EINVAL: return "invalid argument";
+    case DASH_ENOMEM: return "out of memory or capacity";
+    case DASH_ECUDA: return "CUDA error";
+    case DASH_ESTATE: return "invalid state";
+    case DASH_ENUMERIC: return "non-finite result";
+    case DASH_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *dash_last_error(const dash_model *m) {
+    return m ? m->err.c_str() : "null model";
+}
+
+extern "C" void dash_config_default(dash_config *cfg, int32_t J, int32_t R, double lambda) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->J = J;
+    cfg->R = R;
+    cfg->lambda = lambda;
+    cfg->mode = DASH_MODE_P;
+    cfg->precision = DASH_PREC_FP32;
+    cfg->input_dtype = DASH_F32;
+    cfg->n_sweeps = 1;
+    cfg->pinv_rtol = 0.0;
+    cfg->max_slices = 1 << 16;
+    cfg->max_rows = 1 << 20;
+    cfg->max_segments = 1 << 17;
+    cfg->stream = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// allocation helpers
+// ---------------------------------------------------------------------------
+static dash_status dalloc(dash_model *m, void **p, size_t bytes, const char *what) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(m, DASH_ENOMEM, "cudaMalloc of %zu bytes for %s failed: %s", bytes, what,
+                    cudaGetErrorString(e));
+    }
+    m->allocs.push_back(*p);
+    return DASH_OK;
+}
+
+#define DALLOC(ptr, bytes, what)                                                         \
+    do {                                                                                 \
+        dash_status s_ = dalloc(m, (void **)&(ptr), (bytes), (what));                    \
+        if (s_ != DASH_OK) return s_;                                                    \
+    } while (0)
+
+static void free_all(dash_model *m) {
+    for (void *p : m->allocs) cudaFree(p);
+    m->allocs.clear();
+    for (void *p : m->host_allocs) cudaFreeHost(p);
+    m->host_allocs.clear();
+}
+
+static dash_status halloc(dash_model *m, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocHost(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(m, DASH_ENOMEM, "cudaMallocHost of %zu bytes failed", bytes);
+    }
+    m->host_allocs.push_back(*p);
+    return DASH_OK;
+}
+
+static dash_status init_alloc(dash_model *m) {
+    const dash_config &c = m->cfg;
+    const int64_t J = c.J, R = c.R, Km = c.max_slices, Nm = c.max_rows, Sm = c.max_segments;
+    const size_t te = m->tsize;
+    const size_t ie = (c.input_dtype == DASH_F64) ? 8 : 4;
+    // state
+    DALLOC(m->st.V, J * R * 8, "V");
+    DALLOC(m->st.W, Km * R * 8, "W");
+    DALLOC(m->st.F, J * R * 8, "F");
+    DALLOC(m->st.G, R * R * 8, "G");
+    DALLOC(m->st.Gam, R * R * 8, "Gamma");
+    DALLOC(m->st.GamP, R * R * 8, "Gamma+");
+    DALLOC(m->st.gam_ok, sizeof(int), "flag");
+    DALLOC(m->VT, J * R * te, "V (compute type)");
+    DALLOC(m->GP, R * R * 8, "G+");
+    DALLOC(m->Finc, J * R * 8, "F_inc");
+    DALLOC(m->Ginc, R * R * 8, "G_inc");
+    DALLOC(m->fit, 4 * 8, "fitness");
+    if (c.mode == DASH_MODE_P) {
+        DALLOC(m->st.c, Km * R * 8, "c");
+        DALLOC(m->st.D, Km * R * R * 8, "D");
+    } else {
+        return fail(m, DASH_EINVAL, "mode Q is not available in this build");
+    }
+    // staging and batch metadata
+    DALLOC(m->Xs, Nm * J * ie, "staged X");
+    DALLOC(m->d_seg_slice, Sm * 4, "segment ids");
+    DALLOC(m->d_seg_row, (Sm + 1) * 8, "segment rows");
+    DALLOC(m->d_tslot, Km * 4, "slice slots");
+    DALLOC(m->d_tseg_ptr, (Sm + 1) * 4, "slice segment ptr");
+    DALLOC(m->d_tseg_idx, Sm * 4, "slice segment idx");
+    DALLOC(m->d_row_slice, Nm * 4, "row slice");
+    // scratch
+    DALLOC(m->P, Nm * R * te, "P = X V");
+    DALLOC(m->U, Nm * R * te, "U_new");
+    m->n_xn_max = (Nm + XV_ROWS - 1) / XV_ROWS;
+    DALLOC(m->xn_part, m->n_xn_max * 8, "||X|| partials");
+    m->n_fb_max = kFBlocksMax;
+    DALLOC(m->Fpart, (size_t)m->n_fb_max * J * R * te, "F partials");
+    m->n_gb_max = kSliceBlocksMax;
+    DALLOC(m->Gpart, (size_t)m->n_gb_max * R * R * 8, "G partials");
+    DALLOC(m->cross_part, ((J + 7) / 8) * 8, "cross partials");
+    // pinned host metadata (upload source)
+    dash_status s;
+    if ((s = halloc(m, (void **)&m->h_seg_slice, Sm * 4))) return s;
+    if ((s = halloc(m, (void **)&m->h_seg_row, (Sm + 1) * 8))) return s;
+    if ((s = halloc(m, (void **)&m->h_tslot, Km * 4))) return s;
+    if ((s = halloc(m, (void **)&m->h_tseg_ptr, (Sm + 1) * 4))) return s;
+    if ((s = halloc(m, (void **)&m->h_tseg_idx, Sm * 4))) return s;
+    if ((s = halloc(m, (void **)&m->h_fit, 4 * 8))) return s;
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_init(const dash_config *cfg, dash_model **out) {
+    if (!cfg || !out) return DASH_EINVAL;
+    *out = nullptr;
+    dash_model *m = new dash_model();
+    m->cfg = *cfg;
+    const dash_config &c = m->cfg;
+    auto bad = [&](const char *msg) {
+        fail(m, DASH_EINVAL, "%s", msg);
+        return DASH_EINVAL;
+    };
+    dash_status st = DASH_OK;
+    if (c.J <= 0) st = bad("J must be positive");
+    else if (c.R < 1 || c.R > kMaxR) st = bad("R must be in 1..64");
+    else if (!(c.lambda > 0.0 && c.lambda <= 1.0)) st = bad("lambda must be in (0, 1]");
+    else if (c.mode != DASH_MODE_P && c.mode != DASH_MODE_Q) st = bad("unknown mode");
+    else if (c.precision != DASH_PREC_FP64 && c.precision != DASH_PREC_FP32 &&
+             c.precision != DASH_PREC_BF16X3) st = bad("unknown precision");
+    else if (c.input_dtype != DASH_F64 && c.input_dtype != DASH_F32) st = bad("unknown input dtype");
+    else if (c.n_sweeps != 1) st = bad("only n_sweeps = 1 is supported");
+    else if (c.max_slices < 1 || c.max_rows < 1 || c.max_segments < 1) st = bad("capacities must be positive");
+    else if (c.max_slices > INT32_MAX / 2 || c.max_segments > INT32_MAX / 2) st = bad("capacity too large");
+    if (st != DASH_OK) {
+        // keep the message reachable through a static copy
+        static thread_local std::string last;
+        last = m->err;
+        delete m;
+        return st;
+    }
+    m->rtol = c.pinv_rtol > 0.0 ? c.pinv_rtol : (double)c.R * DBL_EPSILON;
+    m->tsize = (c.precision == DASH_PREC_FP64) ? 8 : 4;
+    m->st.J = c.J;
+    m->st.R = c.R;
+    m->st.lam = c.lambda;
+    m->st.rtol = m->rtol;
+    if (c.stream) {
+        m->stream = (cudaStream_t)c.stream;
+        m->own_stream = false;
+    } else {
+        if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete m;
+            return DASH_ECUDA;
+        }
+        m->own_stream = true;
+    }
+    cudaEventCreate(&m->ev0);
+    cudaEventCreate(&m->ev1);
+    st = init_alloc(m);
+    if (st != DASH_OK) {
+        fprintf(stderr, "dash_init: %s\n", m->err.c_str());
+        free_all(m);
+        if (m->own_stream) cudaStreamDestroy(m->stream);
+        delete m;
+        return st;
+    }
+    // zero the state so that get_state on an empty model is well defined
+    cudaMemsetAsync(m->st.F, 0, (size_t)c.J * c.R * 8, m->stream);
+    cudaMemsetAsync(m->st.G, 0, (size_t)c.R * c.R * 8, m->stream);
+    *out = m;
+    return DASH_OK;
+}
+
+extern "C" void dash_destroy(dash_model *m) {
+    if (!m) return;
+    cudaStreamSynchronize(m->stream);
+    free_all(m);
+    cudaEventDestroy(m->ev0);
+    cudaEventDestroy(m->ev1);
+    if (m->own_stream) cudaStreamDestroy(m->stream);
+    delete m;
+}
+
+extern "C" int64_t dash_num_slices(const dash_model *m) { return m ? m->K : -1; }
+
+extern "C" dash_status dash_sync(dash_model *m) {
+    if (!m) return DASH_EINVAL;
+    CK(cudaStreamSynchronize(m->stream));
+    return DASH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// factors / state
+// ---------------------------------------------------------------------------
+static dash_status refresh_gamma(dash_model *m) {
+    const int J = m->cfg.J, R = m->cfg.R;
+    const int64_t n = (int64_t)J * R;
+    if (m->tsize == 8)
+        k_cast<double><<<(n + 255) / 256, 256, 0, m->stream>>>(m->st.V, (double *)m->VT, n);
+    else
+        k_cast<float><<<(n + 255) / 256, 256, 0, m->stream>>>(m->st.V, (float *)m->VT, n);
+    CKL();
+    k_gamma<<<(R * R + 7) / 8, 256, 0, m->stream>>>(m->st.V, J, R, m->st.Gam);
+    CKL();
+    const size_t sm = (size_t)(3 * R * (R + 1) + (R + 1)) * 8;
+    k_pinv_small<<<1, 32, sm, m->stream>>>(m->st.Gam, R, m->rtol, m->st.GamP, m->st.gam_ok);
+    CKL();
+    return DASH_OK;
+}
+
+static bool finite_all(const double *a, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+extern "C" dash_status dash_set_factors(dash_model *m, const double *V, const double *H) {
+    if (!m) return DASH_EINVAL;
+    if (!V) return fail(m, DASH_EINVAL, "V is null");
+    const int J = m->cfg.J, R = m->cfg.R;
+    if (!finite_all(V, (size_t)J * R)) return fail(m, DASH_EINVAL, "V has non-finite entries");
+    (void)H;
+    CK(cudaMemcpyAsync(m->st.V, V, (size_t)J * R * 8, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    dash_status s = refresh_gamma(m);
+    if (s) return s;
+    m->v_set = true;
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_set_state_p(dash_model *m, int64_t K, const double *V,
+                                        const double *W, const double *c, const double *D,
+                                        const double *F, const double *G) {
+    if (!m) return DASH_EINVAL;
+    if (m->cfg.mode != DASH_MODE_P) return fail(m, DASH_ESTATE, "model is not in mode P");
+    if (K < 0 || K > m->cfg.max_slices) return fail(m, DASH_ENOMEM, "K = %lld exceeds capacity", (long long)K);
+    if (!V || !F || !G || (K > 0 && (!W || !c || !D)))
+        return fail(m, DASH_EINVAL, "null state array");
+    if (m->st_segs() > 0) return fail(m, DASH_ESTATE, "rows are staged; update or discard first");
+    const int64_t J = m->cfg.J, R = m->cfg.R;
+    CK(cudaMemcpyAsync(m->st.V, V, J * R * 8, cudaMemcpyHostToDevice, m->stream));
+    if (K > 0) {
+        CK(cudaMemcpyAsync(m->st.W, W, K * R * 8, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->st.c, c, K * R * 8, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->st.D, D, K * R * R * 8, cudaMemcpyHostToDevice, m->stream));
+    }
+    CK(cudaMemcpyAsync(m->st.F, F, J * R * 8, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaMemcpyAsync(m->st.G, G, R * R * 8, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    m->K = K;
+    dash_status s = refresh_gamma(m);
+    if (s) return s;
+    m->v_set = true;
+    m->has_last = false;
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_get_state_p(const dash_model *mc, double *V, double *W, double *c,
+                                        double *D, double *F, double *G) {
+    dash_model *m = const_cast<dash_model *>(mc);
+    if (!m) return DASH_EINVAL;
+    if (m->cfg.mode != DASH_MODE_P) return fail(m, DASH_ESTATE, "model is not in mode P");
+    const int64_t J = m->cfg.J, R = m->cfg.R, K = m->K;
+    CK(cudaStreamSynchronize(m->stream));
+    if (V) CK(cudaMemcpy(V, m->st.V, J * R * 8, cudaMemcpyDeviceToHost));
+    if (W && K) CK(cudaMemcpy(W, m->st.W, K * R * 8, cudaMemcpyDeviceToHost));
+    if (c && K) CK(cudaMemcpy(c, m->st.c, K * R * 8, cudaMemcpyDeviceToHost));
+    if (D && K) CK(cudaMemcpy(D, m->st.D, K * R * R * 8, cudaMemcpyDeviceToHost));
+    if (F) CK(cudaMemcpy(F, m->st.F, J * R * 8, cudaMemcpyDeviceToHost));
+    if (G) CK(cudaMemcpy(G, m->st.G, R * R * 8, cudaMemcpyDeviceToHost));
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_set_state_q(dash_model *m, int64_t, const double *, const double *,
+                                        const double *, const double *, const double *) {
+    if (!m) return DASH_EINVAL;
+    return fail(m, DASH_ESTATE, "model is not in mode Q");
+}
+
+extern "C" dash_status dash_get_state_q(const dash_model *mc, double *, double *, double *,
+                                        double *, double *) {
+    dash_model *m = const_cast<dash_model *>(mc);
+    if (!m) return DASH_EINVAL;
+    return fail(m, DASH_ESTATE, "model is not in mode Q");
+}
+
+extern "C" dash_status dash_factors(const dash_model *mc, double *V, double *W, int64_t k_first,
+                                    int64_t k_count, double *H) {
+    dash_model *m = const_cast<dash_model *>(mc);
+    if (!m) return DASH_EINVAL;
+    const int64_t J = m->cfg.J, R = m->cfg.R;
+    if (W && (k_first < 0 || k_count < 0 || k_first + k_count > m->K))
+        return fail(m, DASH_EINVAL, "slice range %lld+%lld outside 0..%lld", (long long)k_first,
+                    (long long)k_count, (long long)m->K);
+    CK(cudaStreamSynchronize(m->stream));
+    if (V) CK(cudaMemcpy(V, m->st.V, J * R * 8, cudaMemcpyDeviceToHost));
+    if (W && k_count)
+        CK(cudaMemcpy(W, m->st.W + k_first * R, k_count * R * 8, cudaMemcpyDeviceToHost));
+    if (H) return fail(m, DASH_ESTATE, "H exists only in mode Q");
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_new_rows(const dash_model *mc, double *out, int64_t *n_rows) {
+    dash_model *m = const_cast<dash_model *>(mc);
+    if (!m) return DASH_EINVAL;
+    if (n_rows) *n_rows = m->has_last ? m->last_N : 0;
+    if (!m->has_last || !out) return DASH_OK;
+    const int64_t n = m->last_N * m->cfg.R;
+    CK(cudaStreamSynchronize(m->stream));
+    if (m->tsize == 8) {
+        CK(cudaMemcpy(out, m->U, n * 8, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> tmp(n);
+        CK(cudaMemcpy(tmp.data(), m->U, n * 4, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n; ++i) out[i] = tmp[i];
+    }
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_fitness(const dash_model *mc, double *fit_batch, double *x_norm2) {
+    dash_model *m = const_cast<dash_model *>(mc);
+    if (!m) return DASH_EINVAL;
+    if (!m->has_last) return fail(m, DASH_ESTATE, "no update has run");
+    CK(cudaStreamSynchronize(m->stream));
+    if (fit_batch) *fit_batch = m->h_fit[0];
+    if (x_norm2) *x_norm2 = m->h_fit[1];
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_last_update_ms(const dash_model *mc, float *ms) {
+    dash_model *m = const_cast<dash_model *>(mc);
+    if (!m || !ms) return DASH_EINVAL;
+    if (!m->has_last) return fail(m, DASH_ESTATE, "no update has run");
+    CK(cudaEventSynchronize(m->ev1));
+    CK(cudaEventElapsedTime(ms, m->ev0, m->ev1));
+    return DASH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// staging
+// ---------------------------------------------------------------------------
+static dash_status stage_rows(dash_model *m, int64_t k, const void *X, int64_t I, int64_t ld,
+                              int32_t where) {
+    const int64_t J = m->cfg.J;
+    const size_t ie = (m->cfg.input_dtype == DASH_F64) ? 8 : 4;
+    if (I < 0) return fail(m, DASH_EINVAL, "negative row count");
+    if (I > 0 && !X) return fail(m, DASH_EINVAL, "X is null");
+    if (ld < J) return fail(m, DASH_EINVAL, "ld %lld < J %lld", (long long)ld, (long long)J);
+    if (where != DASH_HOST && where != DASH_DEVICE) return fail(m, DASH_EINVAL, "bad pointer location");
+    if (m->st_rows + I > m->cfg.max_rows)
+        return fail(m, DASH_ENOMEM, "staged rows would exceed max_rows = %lld", (long long)m->cfg.max_rows);
+    if (m->st_segs() + 1 > m->cfg.max_segments)
+        return fail(m, DASH_ENOMEM, "staged segments would exceed max_segments");
+    if (I > 0) {
+        char *dst = (char *)m->Xs + (size_t)m->st_rows * J * ie;
+        CK(cudaMemcpy2DAsync(dst, J * ie, X, ld * ie, J * ie, I,
+                             where == DASH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                             m->stream));
+    }
+    m->st_slice.push_back(k);
+    m->st_rows += I;
+    m->st_row.push_back(m->st_rows);
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_append_rows(dash_model *m, int64_t k, const void *X, int64_t I_new,
+                                        int64_t ld, int32_t where) {
+    if (!m) return DASH_EINVAL;
+    if (k < 0 || k >= m->K + m->st_new)
+        return fail(m, DASH_EINVAL, "slice %lld does not exist (K = %lld, staged new = %lld)",
+                    (long long)k, (long long)m->K, (long long)m->st_new);
+    return stage_rows(m, k, X, I_new, ld, where);
+}
+
+extern "C" dash_status dash_append_slices(dash_model *m, int64_t L, const int64_t *I,
+                                          const void *const *X, const int64_t *ld, int32_t where,
+                                          int64_t *first_new_id) {
+    if (!m) return DASH_EINVAL;
+    if (L < 0 || (L > 0 && (!I || !X))) return fail(m, DASH_EINVAL, "bad slice list");
+    if (m->K + m->st_new + L > m->cfg.max_slices)
+        return fail(m, DASH_ENOMEM, "slices would exceed max_slices = %lld", (long long)m->cfg.max_slices);
+    int64_t tot = 0;
+    for (int64_t l = 0; l < L; ++l) {
+        if (I[l] < 0) return fail(m, DASH_EINVAL, "negative row count for new slice %lld", (long long)l);
+        tot += I[l];
+    }
+    if (m->st_rows + tot > m->cfg.max_rows) return fail(m, DASH_ENOMEM, "staged rows would exceed max_rows");
+    if (m->st_segs() + L > m->cfg.max_segments) return fail(m, DASH_ENOMEM, "staged segments would exceed max_segments");
+    if (first_new_id) *first_new_id = m->K + m->st_new;
+    for (int64_t l = 0; l < L; ++l) {
+        const int64_t id = m->K + m->st_new;
+        m->st_new += 1;
+        dash_status s = stage_rows(m, id, X[l], I[l], ld ? ld[l] : m->cfg.J, where);
+        if (s) return s;
+    }
+    return DASH_OK;
+}
+
+// Check a CSR batch: ascending row_ptr from 0, ids in range, new ids
+// consecutive from K_base.  Returns the number of new slices in *n_new.
+static dash_status check_csr(dash_model *m, int64_t n_seg, const int64_t *ids, const int64_t *rp,
+                             int64_t K_base, int64_t *n_new) {
+    if (n_seg < 0 || (n_seg > 0 && (!ids || !rp))) return fail(m, DASH_EINVAL, "bad CSR arrays");
+    if (n_seg > 0 && rp[0] != 0) return fail(m, DASH_EINVAL, "row_ptr[0] must be 0");
+    int64_t next_new = K_base;
+    for (int64_t s = 0; s < n_seg; ++s) {
+        if (rp[s + 1] < rp[s]) return fail(m, DASH_EINVAL, "row_ptr not ascending at %lld", (long long)s);
+        const int64_t k = ids[s];
+        if (k < 0) return fail(m, DASH_EINVAL, "negative slice id");
+        if (k >= K_base) {
+            if (k == next_new) ++next_new;
+            else if (k >= next_new)
+                return fail(m, DASH_EINVAL, "new slice ids must be consecutive from %lld (got %lld)",
+                            (long long)K_base, (long long)k);
+        }
+    }
+    *n_new = next_new - K_base;
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_append_batch(dash_model *m, int64_t n_seg, const int64_t *slice_ids,
+                                         const int64_t *row_ptr, const void *X, int32_t where) {
+    if (!m) return DASH_EINVAL;
+    int64_t n_new = 0;
+    dash_status s = check_csr(m, n_seg, slice_ids, row_ptr, m->K + m->st_new, &n_new);
+    if (s) return s;
+    const int64_t N = n_seg ? row_ptr[n_seg] : 0;
+    if (m->st_rows + N > m->cfg.max_rows) return fail(m, DASH_ENOMEM, "staged rows would exceed max_rows");
+    if (m->st_segs() + n_seg > m->cfg.max_segments) return fail(m, DASH_ENOMEM, "staged segments would exceed max_segments");
+    if (m->K + m->st_new + n_new > m->cfg.max_slices) return fail(m, DASH_ENOMEM, "slices would exceed max_slices");
+    if (N > 0 && !X) return fail(m, DASH_EINVAL, "X is null");
+    const size_t ie = (m->cfg.input_dtype == DASH_F64) ? 8 : 4;
+    if (N > 0) {
+        char *dst = (char *)m->Xs + (size_t)m->st_rows * m->cfg.J * ie;
+        CK(cudaMemcpyAsync(dst, X, (size_t)N * m->cfg.J * ie,
+                           where == DASH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                           m->stream));
+    }
+    const int64_t base = m->st_rows;
+    for (int64_t q = 0; q < n_seg; ++q) {
+        m->st_slice.push_back(slice_ids[q]);
+        m->st_row.push_back(base + row_ptr[q + 1]);
+    }
+    m->st_rows += N;
+    m->st_new += n_new;
+    return DASH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one update
+// ---------------------------------------------------------------------------
+
+// Build and upload the device view of a batch: segments, touched slices and
+// their segment lists.  K_old is the slice count before the update.
+static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
+                              const int64_t *rp /* n_seg+1 absolute */, int64_t K_old,
+                              int64_t n_new, BatchDev *b) {
+    const int64_t K_all = K_old + n_new;
+    CK(cudaStreamSynchronize(m->stream));   // pinned metadata buffers are reused
+    int *tslot = m->h_tslot;
+    for (int64_t k = 0; k < K_all; ++k) tslot[k] = -1;
+    int n_touch = 0;
+    // count segments per slice, in first-appearance order of ascending id
+    std::vector<int> cnt;
+    cnt.reserve(1024);
+    for (int64_t s = 0; s < n_seg; ++s) {
+        const int64_t k = ids[s];
+        if (tslot[k] < 0) {
+            tslot[k] = n_touch++;
+            cnt.push_back(0);
+        }
+        cnt[tslot[k]] += 1;
+    }
+    // renumber touched slots in ascending slice order (fixed reduction order)
+    {
+        int t = 0;
+        std::vector<int> remap(n_touch);
+        for (int64_t k = 0; k < K_all; ++k)
+            if (tslot[k] >= 0) { remap[tslot[k]] = t; tslot[k] = t; ++t; }
+        std::vector<int> c2(n_touch);
+        for (int i = 0; i < n_touch; ++i) c2[remap[i]] = cnt[i];
+        cnt.swap(c2);
+    }
+    int *tp = m->h_tseg_ptr;
+    tp[0] = 0;
+    for (int i = 0; i < n_touch; ++i) tp[i + 1] = tp[i] + cnt[i];
+    std::vector<int> fillp(tp, tp + n_touch);
+    for (int64_t s = 0; s < n_seg; ++s) {
+        const int t = tslot[ids[s]];
+        m->h_tseg_idx[fillp[t]++] = (int)s;
+        m->h_seg_slice[s] = (int)ids[s];
+    }
+    for (int64_t s = 0; s <= n_seg; ++s) m->h_seg_row[s] = rp[s];
+    if (n_seg > 0) {
+        CK(cudaMemcpyAsync(m->d_seg_slice, m->h_seg_slice, n_seg * 4, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->d_tseg_idx, m->h_tseg_idx, n_seg * 4, cudaMemcpyHostToDevice, m->stream));
+    }
+    CK(cudaMemcpyAsync(m->d_seg_row, m->h_seg_row, (n_seg + 1) * 8, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaMemcpyAsync(m->d_tseg_ptr, m->h_tseg_ptr, (n_touch + 1) * 4, cudaMemcpyHostToDevice, m->stream));
+    if (K_all > 0) CK(cudaMemcpyAsync(m->d_tslot, m->h_tslot, K_all * 4, cudaMemcpyHostToDevice, m->stream));
+    b->n_seg = (int)n_seg;
+    b->n_touch = n_touch;
+    b->K_all = (int)K_all;
+    b->K_old = (int)K_old;
+    b->N = n_seg ? rp[n_seg] : 0;
+    b->seg_slice = m->d_seg_slice;
+    b->seg_row = m->d_seg_row;
+    b->tslot = m->d_tslot;
+    b->tseg_ptr = m->d_tseg_ptr;
+    b->tseg_idx = m->d_tseg_idx;
+    b->row_slice = m->d_row_slice;
+    return DASH_OK;
+}
+
+template <typename TI, typename T>
+static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void *Xv, double lam,
+                                   bool begin_new) {
+    const int J = m->cfg.J, R = m->cfg.R;
+    cudaStream_t st = m->stream;
+    const TI *X = (const TI *)Xv;
+    StateDev s = m->st;
+    s.lam = lam;
+    const int64_t N = b.N;
+    const int n_new = b.K_all - b.K_old;
+    if (begin_new && n_new > 0) {
+        const int64_t tot = (int64_t)n_new * R * (R + 2);
+        k_begin_new<<<(tot + 255) / 256, 256, 0, st>>>(s.W, s.c, s.D, b.K_old, n_new, R);
+        CKL();
+    }
+    int n_xn = 0;
+    if (N > 0) {
+        k_rowmap<<<(N + 255) / 256, 256, 0, st>>>(b);
+        CKL();
+        n_xn = (int)((N + XV_ROWS - 1) / XV_ROWS);
+        k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, N, J, R, (const T *)m->VT, (T *)m->P, m->xn_part);
+        CKL();
+    }
+    // per-slice work
+    const int nw = sl_warps(R);
+    const size_t smem = (size_t)nw * sl_warp_doubles(R) * 8;
+    int nsb = (int)std::min<int64_t>((b.K_all + nw - 1) / nw, kSliceBlocksMax);
+    if (nsb < 1) nsb = 1;
+    CK(cudaFuncSetAttribute(k_slices<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_slices<T><<<nsb, 32 * nw, smem, st>>>(b, s, (const T *)m->P, (T *)m->U, m->Gpart);
+    CKL();
+    // F partials
+    int nfb = 0;
+    if (N > 0) {
+        const int nby = (J + F_JB - 1) / F_JB;
+        nfb = (int)std::min<int64_t>(std::max<int64_t>(1, (2 * 152 * 4) / nby), (N + F_RC - 1) / F_RC);
+        nfb = std::min(nfb, m->n_fb_max);
+        int64_t rpc = (N + nfb - 1) / nfb;
+        rpc = (rpc + F_RC - 1) / F_RC * F_RC;
+        nfb = (int)((N + rpc - 1) / rpc);
+        dim3 grid(nfb, nby);
+        k_f<TI, T><<<grid, 256, 0, st>>>(X, b, J, R, (const T *)m->U, s.W, rpc, (T *)m->Fpart);
+        CKL();
+    }
+    k_f_reduce<T><<<((int64_t)J * R + 255) / 256, 256, 0, st>>>((const T *)m->Fpart, nfb, J, R, lam,
+                                                                s.F, m->Finc);
+    CKL();
+    k_g_reduce<<<(R * R + 7) / 8, 256, 0, st>>>(m->Gpart, nsb, R, lam, s.G, m->Ginc);
+    CKL();
+    const size_t psm = (size_t)(3 * R * (R + 1) + (R + 1)) * 8;
+    k_pinv_small<<<1, 32, psm, st>>>(s.G, R, m->rtol, m->GP, nullptr);
+    CKL();
+    k_vupdate<T><<<(J + 7) / 8, 256, 0, st>>>(s.F, m->GP, m->Finc, J, R, s.V, (T *)m->VT,
+                                               m->cross_part);
+    CKL();
+    k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(s.V, J, R, s.Gam);
+    CKL();
+    k_pinv_small<<<1, 32, psm, st>>>(s.Gam, R, m->rtol, s.GamP, s.gam_ok);
+    CKL();
+    k_fitness<<<1, 32, 0, st>>>(m->xn_part, n_xn, m->cross_part, (J + 7) / 8, s.Gam, m->Ginc, R,
+                                m->fit);
+    CKL();
+    CK(cudaMemcpyAsync(m->h_fit, m->fit, 3 * 8, cudaMemcpyDeviceToHost, st));
+    return DASH_OK;
+}
+
+template <typename TI, typename T>
+static dash_status launch_recompute_c(dash_model *m, const BatchDev &b, const void *Xv) {
+    const int J = m->cfg.J, R = m->cfg.R;
+    if (b.N > 0) {
+        const int n_xn = (int)((b.N + XV_ROWS - 1) / XV_ROWS);
+        k_xv<TI, T><<<n_xn, 256, 0, m->stream>>>((const TI *)Xv, b.N, J, R, (const T *)m->VT,
+                                                  (T *)m->P, m->xn_part);
+        CKL();
+    }
+    const int nb = (b.K_all + 7) / 8;
+    k_c_recompute<T><<<nb > 0 ? nb : 1, 256, 0, m->stream>>>(b, (const T *)m->P, (const T *)m->U, R,
+                                                            m->st.c);
+    CKL();
+    return DASH_OK;
+}
+
+static dash_status recompute_c(dash_model *m, const BatchDev &b, const void *X) {
+    const bool f64in = m->cfg.input_dtype == DASH_F64;
+    if (m->tsize == 8)
+        return f64in ? launch_recompute_c<double, double>(m, b, X) : launch_recompute_c<float, double>(m, b, X);
+    return f64in ? launch_recompute_c<double, float>(m, b, X) : launch_recompute_c<float, float>(m, b, X);
+}
+
+static dash_status run_update(dash_model *m, const BatchDev &b, const void *X, double lam,
+                              bool begin_new) {
+    const bool f64in = m->cfg.input_dtype == DASH_F64;
+    if (m->cfg.mode != DASH_MODE_P) return fail(m, DASH_ESTATE, "mode Q is not available");
+    if (m->tsize == 8) {
+        return f64in ? launch_update_p<double, double>(m, b, X, lam, begin_new)
+                     : launch_update_p<float, double>(m, b, X, lam, begin_new);
+    }
+    return f64in ? launch_update_p<double, float>(m, b, X, lam, begin_new)
+                 : launch_update_p<float, float>(m, b, X, lam, begin_new);
+}
+
+static dash_status update_common(dash_model *m, int64_t n_seg, const int64_t *ids,
+                                 const int64_t *rp, const void *X, int64_t n_new) {
+    if (!m->v_set) return fail(m, DASH_ESTATE, "V is not set (dash_set_factors)");
+    if (m->broken) return fail(m, DASH_ESTATE, "model is unusable after a CUDA error");
+    BatchDev b;
+    dash_status s = plan_batch(m, n_seg, ids, rp, m->K, n_new, &b);
+    if (s) return s;
+    CK(cudaEventRecord(m->ev0, m->stream));
+    s = run_update(m, b, X, m->cfg.lambda, true);
+    if (s) return s;
+    CK(cudaEventRecord(m->ev1, m->stream));
+    m->K += n_new;
+    m->last_N = b.N;
+    m->has_last = true;
+    return DASH_OK;
+}
+
+static void clear_staging(dash_model *m) {
+    m->st_slice.clear();
+    m->st_row.assign(1, 0);
+    m->st_rows = 0;
+    m->st_new = 0;
+}
+
+extern "C" dash_status dash_update(dash_model *m) {
+    if (!m) return DASH_EINVAL;
+    const int64_t n_seg = m->st_segs();
+    dash_status s = update_common(m, n_seg, m->st_slice.data(), m->st_row.data(), m->Xs, m->st_new);
+    if (s == DASH_OK) clear_staging(m);
+    return s;
+}
+
+extern "C" dash_status dash_update_device(dash_model *m, int64_t n_seg, const int64_t *slice_ids,
+                                          const int64_t *row_ptr, const void *X) {
+    if (!m) return DASH_EINVAL;
+    if (m->st_segs() > 0) return fail(m, DASH_ESTATE, "rows are staged; call dash_update first");
+    int64_t n_new = 0;
+    dash_status s = check_csr(m, n_seg, slice_ids, row_ptr, m->K, &n_new);
+    if (s) return s;
+    const int64_t N = n_seg ? row_ptr[n_seg] : 0;
+    if (N > m->cfg.max_rows) return fail(m, DASH_ENOMEM, "batch rows exceed max_rows");
+    if (n_seg > m->cfg.max_segments) return fail(m, DASH_ENOMEM, "batch segments exceed max_segments");
+    if (m->K + n_new > m->cfg.max_slices) return fail(m, DASH_ENOMEM, "slices would exceed max_slices");
+    if (N > 0 && !X) return fail(m, DASH_EINVAL, "X is null");
+    return update_common(m, n_seg, slice_ids, row_ptr, X, n_new);
+}
+
+extern "C" dash_status dash_fit_initial(dash_model *m, int32_t n_iter) {
+    if (!m) return DASH_EINVAL;
+    if (n_iter < 1) return fail(m, DASH_EINVAL, "n_iter must be >= 1");
+    if (m->K != 0) return fail(m, DASH_ESTATE, "fit_initial needs an empty model");
+    if (!m->v_set) return fail(m, DASH_ESTATE, "V is not set (dash_set_factors)");
+    const int64_t n_seg = m->st_segs();
+    const int64_t n_new = m->st_new;
+    for (int64_t s = 0; s < n_seg; ++s)
+        if (m->st_slice[s] < 0 || m->st_slice[s] >= n_new)
+            return fail(m, DASH_EINVAL, "fit_initial takes new slices only");
+    BatchDev b;
+    dash_status s = plan_batch(m, n_seg, m->st_slice.data(), m->st_row.data(), 0, n_new, &b);
+    if (s) return s;
+    CK(cudaEventRecord(m->ev0, m->stream));
+    // iteration 1: the slices are new (S_k = I); later iterations: the same
+    // rows with the helpers of the previous iteration dropped (λ = 0), which
+    // is one static ALS iteration each (single batch ≡ static ALS).
+    for (int it = 0; it < n_iter; ++it) {
+        BatchDev bi = b;
+        if (it > 0) bi.K_old = bi.K_all;     // no new slices any more
+        s = run_update(m, bi, m->Xs, 0.0, it == 0);
+        if (s) return s;
+    }
+    // c_k = vec(X_k)ᵀ(V ⊙ U_k) with the final V (Eq. 6)
+    s = recompute_c(m, b, m->Xs);
+    if (s) return s;
+    CK(cudaEventRecord(m->ev1, m->stream));
+    m->K = n_new;
+    m->last_N = b.N;
+    m->has_last = true;
+    clear_staging(m);
+    return DASH_OK;
+}

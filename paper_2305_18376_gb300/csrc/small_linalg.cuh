@@ -1,0 +1,249 @@
+// Warp-level FP64 routines for the small R×R systems of the Dash update:
+// (S_k VᵀV S_k)⁺ (Lemma 1, Eq. 11), (VᵀV ∗ D_k)⁺ (Lemma 2, Eq. 12), G⁺
+// (Lemma 3, Eq. 17) and, in mode Q, B_k^{-1/2}.
+//
+// All matrices live in shared memory, row-major with leading dimension ld,
+// and are handled by one warp (R <= 64, so each lane owns at most two rows).
+// "⁺" is the Moore-Penrose pseudo-inverse of a symmetric PSD matrix:
+// eigenvalues <= rtol · max|eigenvalue| count as zero.  The fast path is a
+// Cholesky factorisation, taken only when every pivot is far above that
+// cut-off; otherwise a cyclic Jacobi eigen-decomposition gives the exact
+// pseudo-inverse.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace dash {
+
+constexpr int kMaxR = 64;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// In-place lower Cholesky A = L Lᵀ of an n×n SPD matrix (lower triangle of A
+// is overwritten by L; the strict upper triangle is left untouched).
+// Returns false as soon as a pivot is not above `tol` (also for NaN).
+__device__ inline bool warp_cholesky(double *A, int n, int ld, double tol) {
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < n; ++j) {
+        __syncwarp();
+        const double d = A[j * ld + j];
+        if (!(d > tol)) return false;
+        const double l = sqrt(d);
+        const double inv = 1.0 / l;
+        for (int i = j + 1 + lane; i < n; i += 32) A[i * ld + j] *= inv;
+        __syncwarp();
+        if (lane == 0) A[j * ld + j] = l;
+        for (int i = j + 1 + lane; i < n; i += 32) {
+            const double lij = A[i * ld + j];
+            for (int k = j + 1; k <= i; ++k) A[i * ld + k] -= lij * A[k * ld + j];
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+// Solve L Lᵀ x = b with L from warp_cholesky; b (length n, shared) is
+// overwritten by x.
+__device__ inline void warp_cholesky_solve(const double *L, int n, int ld, double *b) {
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < n; ++j) {
+        __syncwarp();
+        const double yj = b[j] / L[j * ld + j];
+        __syncwarp();
+        if (lane == 0) b[j] = yj;
+        for (int i = j + 1 + lane; i < n; i += 32) b[i] -= L[i * ld + j] * yj;
+    }
+    for (int j = n - 1; j >= 0; --j) {
+        __syncwarp();
+        const double xj = b[j] / L[j * ld + j];
+        __syncwarp();
+        if (lane == 0) b[j] = xj;
+        for (int i = lane; i < j; i += 32) b[i] -= L[j * ld + i] * xj;
+    }
+    __syncwarp();
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric n×n matrix.  On return
+// the diagonal of A holds the eigenvalues and the columns of E the
+// eigenvectors (A_in = E diag(A_out) Eᵀ).  Off-diagonal entries of A are
+// destroyed.  Rotations follow the symmetric Schur 2×2 step of Golub and
+// Van Loan (Matrix Computations, §8.5).
+__device__ inline void warp_jacobi_eig(double *A, double *E, int n, int ld, int max_sweeps = 50) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < n * n; i += 32) {
+        const int r = i / n, c = i % n;
+        E[r * ld + c] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int i = lane; i < n * n; i += 32) {
+            const int r = i / n, c = i % n;
+            const double v = A[r * ld + c];
+            if (r == c) dia += v * v; else off += v * v;
+        }
+        off = warp_sum(off);
+        dia = warp_sum(dia);
+        if (off <= 1e-32 * dia || off == 0.0) break;
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                __syncwarp();
+                const double apq = A[p * ld + q];
+                const double app = A[p * ld + p];
+                const double aqq = A[q * ld + q];
+                if (fabs(apq) <= 1e-300 ||
+                    fabs(apq) <= 1e-18 * sqrt(fabs(app) * fabs(aqq))) {
+                    continue;
+                }
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) /
+                                 (fabs(theta) + sqrt(1.0 + theta * theta));
+                const double c = 1.0 / sqrt(1.0 + t * t);
+                const double s = t * c;
+                __syncwarp();
+                for (int k = lane; k < n; k += 32) {
+                    if (k != p && k != q) {
+                        const double akp = A[k * ld + p], akq = A[k * ld + q];
+                        const double nkp = c * akp - s * akq;
+                        const double nkq = s * akp + c * akq;
+                        A[k * ld + p] = nkp; A[p * ld + k] = nkp;
+                        A[k * ld + q] = nkq; A[q * ld + k] = nkq;
+                    }
+                    const double ekp = E[k * ld + p], ekq = E[k * ld + q];
+                    E[k * ld + p] = c * ekp - s * ekq;
+                    E[k * ld + q] = s * ekp + c * ekq;
+                }
+                if (lane == 0) {
+                    A[p * ld + p] = app - t * apq;
+                    A[q * ld + q] = aqq + t * apq;
+                    A[p * ld + q] = 0.0;
+                    A[q * ld + p] = 0.0;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+}
+
+// Spectral weights f(μ_i) after warp_jacobi_eig: power 1 → 1/μ, power 2 →
+// 1/sqrt(μ); eigenvalues <= rtol·max|μ| (and all of them when max|μ| = 0)
+// get weight 0.  f has length n (shared).
+__device__ inline void warp_spectral_weights(const double *A, int n, int ld, double rtol,
+                                             int power, double *f) {
+    const int lane = threadIdx.x & 31;
+    double mx = 0.0;
+    for (int i = lane; i < n; i += 32) mx = fmax(mx, fabs(A[i * ld + i]));
+    mx = warp_max(mx);
+    const double cut = rtol * mx;
+    for (int i = lane; i < n; i += 32) {
+        const double mu = A[i * ld + i];
+        double v = 0.0;
+        if (mx > 0.0 && mu > cut) v = (power == 1) ? 1.0 / mu : 1.0 / sqrt(mu);
+        f[i] = v;
+    }
+    __syncwarp();
+}
+
+// out = E diag(f) Eᵀ (n×n, shared, may not alias E).
+__device__ inline void warp_spectral_apply(const double *E, const double *f, int n, int ld,
+                                           double *out) {
+    const int lane = threadIdx.x & 31;
+    for (int idx = lane; idx < n * n; idx += 32) {
+        const int r = idx / n, c = idx % n;
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += E[r * ld + k] * f[k] * E[c * ld + k];
+        out[r * ld + c] = s;
+    }
+    __syncwarp();
+}
+
+// Pseudo-inverse (power 1) or pseudo-inverse square root (power 2) of the
+// symmetric PSD matrix in A, written to out.  A and E are destroyed (E is
+// workspace), f is length-n workspace.  When `try_cholesky` and power == 1,
+// a Cholesky inverse is used if every pivot exceeds 100·rtol·max(diag).
+__device__ inline void warp_psd_pinv(double *A, double *E, double *f, double *out, int n,
+                                     int ld, double rtol, int power, bool try_cholesky) {
+    const int lane = threadIdx.x & 31;
+    if (power == 1 && try_cholesky) {
+        double md = 0.0;
+        for (int i = lane; i < n; i += 32) md = fmax(md, fabs(A[i * ld + i]));
+        md = warp_max(md);
+        for (int i = lane; i < n * n; i += 32) E[(i / n) * ld + (i % n)] = A[(i / n) * ld + (i % n)];
+        __syncwarp();
+        if (md > 0.0 && warp_cholesky(E, n, ld, 100.0 * rtol * md)) {
+            // columns of the inverse: solve L Lᵀ x = e_c, one column per pass
+            for (int c = 0; c < n; ++c) {
+                for (int i = lane; i < n; i += 32) f[i] = (i == c) ? 1.0 : 0.0;
+                __syncwarp();
+                warp_cholesky_solve(E, n, ld, f);
+                for (int i = lane; i < n; i += 32) out[i * ld + c] = f[i];
+            }
+            __syncwarp();
+            // symmetrise
+            for (int idx = lane; idx < n * n; idx += 32) {
+                const int r = idx / n, c = idx % n;
+                if (r < c) {
+                    const double v = 0.5 * (out[r * ld + c] + out[c * ld + r]);
+                    out[r * ld + c] = v;
+                    out[c * ld + r] = v;
+                }
+            }
+            __syncwarp();
+            return;
+        }
+    }
+    warp_jacobi_eig(A, E, n, ld);
+    warp_spectral_weights(A, n, ld, rtol, power, f);
+    warp_spectral_apply(E, f, n, ld, out);
+}
+
+// x = A⁺ b for symmetric PSD A: Cholesky when all pivots exceed
+// 100·rtol·max(diag), else Jacobi pseudo-inverse.  A is destroyed; L and E
+// are n×ld workspaces; b (shared, length n) is overwritten with x; f is
+// length-n workspace.  Returns 0 for the Cholesky path, 1 for the eigen path.
+__device__ inline int warp_psd_solve(double *A, double *L, double *E, double *b, double *f,
+                                     int n, int ld, double rtol) {
+    const int lane = threadIdx.x & 31;
+    double md = 0.0;
+    for (int i = lane; i < n; i += 32) md = fmax(md, fabs(A[i * ld + i]));
+    md = warp_max(md);
+    for (int i = lane; i < n * n; i += 32) L[(i / n) * ld + (i % n)] = A[(i / n) * ld + (i % n)];
+    __syncwarp();
+    if (md > 0.0 && warp_cholesky(L, n, ld, 100.0 * rtol * md)) {
+        warp_cholesky_solve(L, n, ld, b);
+        return 0;
+    }
+    warp_jacobi_eig(A, E, n, ld);
+    warp_spectral_weights(A, n, ld, rtol, 1, f);
+    // x = E diag(f) Eᵀ b, using L's first row as scratch for y = Eᵀ b
+    double *y = L;
+    __syncwarp();
+    for (int k = lane; k < n; k += 32) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += E[i * ld + k] * b[i];
+        y[k] = s * f[k];
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += E[i * ld + k] * y[k];
+        f[i] = s;
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) b[i] = f[i];
+    __syncwarp();
+    return 1;
+}
+
+}  // namespace dash

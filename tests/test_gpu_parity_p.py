@@ -1,0 +1,220 @@
+"""Mode P (Algorithm 1) on the GPU against the FP64 oracle, element by
+element, through the C ABI.
+
+FP64 products: every factor and helper within 1e-10 (relative, normwise
+max); FP32 products: within 1e-4 and batch fitness within 1e-3.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dash_oracle as O
+from synth.planted import PlantedStream, ragged_batch, tiny, workload
+from tests._parity import (FIT_TOL, TOL, compare_state_p, gpu_rows_by_slice, oracle_batch_fitness_p,
+                           rel, segs_np)
+
+pytestmark = pytest.mark.gpu
+
+PREC_DTYPE = {"fp64": ("f64", torch.float64), "fp32": ("f32", torch.float32)}
+
+
+def _model(J, R, lam, prec, **kw):
+    from paper_2305_18376_gb300 import DashModel
+    idt, _ = PREC_DTYPE[prec]
+    return DashModel(J, R, lam, precision=prec, input_dtype=idt, **kw)
+
+
+def _run_stream(w, prec, n_steps, init_iters=3, via="batch", seed_v=1):
+    """Initialise both sides with the same static fit, then stream."""
+    _, tdt = PREC_DTYPE[prec]
+    s = PlantedStream(w)
+    rng = np.random.default_rng(seed_v)
+    V0 = rng.random((w.J, w.R))
+    b0 = s.batch(0)
+    X0 = [x for _, x in segs_np(b0, tdt)]
+    U, W, V = O.static_als_p(X0, V0, np.ones((len(X0), w.R)), init_iters)
+    st = O.init_helpers_p(X0, U, W, V)
+    m = _model(w.J, w.R, w.lam, prec, max_slices=w.K0 + w.new_slices_per_step * n_steps + 8,
+               max_rows=max(4096, b0.n_rows * 2), max_segments=4096)
+    m.set_factors(V0)
+    m.append_batch(b0.slice_ids.numpy(), b0.row_ptr.numpy(), b0.X.to(tdt).numpy())
+    m.fit_initial(init_iters)
+    compare_state_p(m.get_state_p(), st, TOL[prec] * (10 if prec == "fp64" else 1), "init")
+    worst = {}
+    for t in range(1, n_steps + 1):
+        b = s.batch(t)
+        segs = segs_np(b, tdt)
+        X = O._group(segs, st.K, b.n_new, w.J)
+        st, Uo = O.dash_update_p(st, list(X.items()), b.n_new, w.lam)
+        Xg = b.X.to(tdt)
+        if via == "batch":
+            m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), Xg.numpy())
+            m.update()
+        elif via == "device":
+            m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), Xg.cuda())
+        else:   # append_rows / append_slices
+            ids = b.slice_ids.tolist()
+            rp = b.row_ptr.tolist()
+            old = [(q, k) for q, k in enumerate(ids) if k < b.K_before]
+            for q, k in old:
+                m.append_rows(k, Xg[rp[q]:rp[q + 1]].numpy())
+            new = [Xg[rp[q]:rp[q + 1]].numpy() for q, k in enumerate(ids) if k >= b.K_before]
+            first = m.append_slices(new)
+            assert first == b.K_before
+            m.update()
+        g = m.get_state_p()
+        errs = compare_state_p(g, st, TOL[prec], f"update {t}")
+        rows = gpu_rows_by_slice(m.new_rows(), b)
+        errs["U"] = max(rel(rows[k], Uo[k]) for k in rows)
+        assert errs["U"] <= TOL[prec], errs
+        fit_g, xn = m.fitness()
+        fit_o = oracle_batch_fitness_p(st, Uo, X)
+        assert abs(fit_g - fit_o) <= FIT_TOL[prec], (fit_g, fit_o)
+        for k, v in errs.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+    m.close()
+    return worst
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_small_stream_parity(prec):
+    w = tiny(K0=6, J=9, R=3, steps=4, sigma=0.05, lam=0.9)
+    _run_stream(w, prec, 4)
+
+
+@pytest.mark.parametrize("via", ["rows", "device"])
+def test_staging_paths_agree(via):
+    w = tiny(K0=5, J=7, R=2, steps=3, sigma=0.05, lam=0.8)
+    _run_stream(w, "fp64", 3, via=via)
+
+
+def test_c1_workload_fp64():
+    """K0=50, J=100, R=10, λ=1, 10 updates of +10 rows / +5 slices, FP64."""
+    w = workload("c1")
+    worst = _run_stream(w, "fp64", 10, init_iters=5)
+    print("c1 fp64 worst relative errors:", worst)
+
+
+def test_c2_shaped_fp32():
+    """c2's shape (J=88, R=10, +1 row per slice, +10 slices) at K0=300."""
+    w = workload("c2", K0=300, init_rows=("uniform", 50, 300), new_slice_rows=("uniform", 50, 100),
+                 steps=5)
+    worst = _run_stream(w, "fp32", 5, init_iters=3)
+    print("c2-shaped fp32 worst relative errors:", worst)
+
+
+def _state_from_oracle(w, prec, lam):
+    """A fitted oracle state for a small planted tensor."""
+    _, tdt = PREC_DTYPE[prec]
+    s = PlantedStream(w)
+    b0 = s.batch(0)
+    X0 = [x for _, x in segs_np(b0, tdt)]
+    rng = np.random.default_rng(3)
+    U, W, V = O.static_als_p(X0, rng.random((w.J, w.R)), np.ones((len(X0), w.R)), 2)
+    return O.init_helpers_p(X0, U, W, V)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ragged_edge_batch_from_oracle_state(prec):
+    """One update from an oracle state with: a slice split in two segments,
+    untouched slices (λ decay only), a 1-row segment, a segment longer than
+    one tile (ragged tail), and new slices of 0 and 70 rows."""
+    _, tdt = PREC_DTYPE[prec]
+    w = tiny(K0=8, J=37, R=5, steps=0, sigma=0.05, init_rows=("uniform", 10, 20))
+    st = _state_from_oracle(w, prec, 0.7)
+    ids = [0, 2, 2, 5, 7, 8, 9]
+    rows = [3, 2, 1, 133, 1, 0, 70]
+    b = ragged_batch(8, 2, 37, rows, seed=9, slice_ids=ids, dtype=tdt)
+    segs = segs_np(b, tdt)
+    st2, Uo = O.dash_update_p(st, segs, 2, 0.7)
+    m = _model(37, 5, 0.7, prec, max_slices=16, max_rows=512, max_segments=64)
+    m.set_state_p(st.V, st.W, st.c, st.D, st.F, st.G)
+    m.append_batch(ids, b.row_ptr.numpy(), b.X.numpy())
+    m.update()
+    g = m.get_state_p()
+    compare_state_p(g, st2, TOL[prec], "ragged")
+    got = gpu_rows_by_slice(m.new_rows(), b)
+    for k in Uo:
+        assert rel(got[k], Uo[k]) <= TOL[prec]
+    assert np.all(g["W"][8] == 0.0)          # new slice without rows: w = 0
+
+
+def test_rank_deficient_gram_uses_the_pseudo_inverse():
+    """J < R: VᵀV is singular, Lemma 1 needs the pseudo-inverse (eigen path)."""
+    J, R = 3, 5
+    rng = np.random.default_rng(4)
+    V0 = rng.random((J, R))
+    b = ragged_batch(0, 4, J, [6, 2, 9, 4], seed=5)
+    segs = segs_np(b, torch.float64)
+    st, Uo = O.dash_update_p(O.empty_state_p(V0), segs, 4, 1.0)
+    m = _model(J, R, 1.0, "fp64", max_slices=8, max_rows=64, max_segments=8)
+    m.set_factors(V0)
+    m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.numpy())
+    m.update()
+    compare_state_p(m.get_state_p(), st, 1e-9, "J<R")
+    got = gpu_rows_by_slice(m.new_rows(), b)
+    for k in Uo:
+        assert rel(got[k], Uo[k]) <= 1e-9
+
+
+def test_zero_weight_entries_take_the_general_lemma1_path():
+    """A slice whose S_k has zero entries: S (S Γ S)⁺ ≠ Γ⁻¹ S⁻¹."""
+    w = tiny(K0=4, J=8, R=3, steps=0, sigma=0.05)
+    st = _state_from_oracle(w, "fp64", 1.0)
+    st.W[1, 0] = 0.0
+    st.W[2, :] = 0.0
+    b = ragged_batch(4, 0, 8, [5, 4, 3], seed=6, slice_ids=[0, 1, 2])
+    segs = segs_np(b, torch.float64)
+    st2, Uo = O.dash_update_p(st, segs, 0, 0.9)
+    m = _model(8, 3, 0.9, "fp64", max_slices=8, max_rows=64, max_segments=8)
+    m.set_state_p(st.V, st.W, st.c, st.D, st.F, st.G)
+    m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.numpy())
+    m.update()
+    compare_state_p(m.get_state_p(), st2, 1e-9, "zero w")
+    got = gpu_rows_by_slice(m.new_rows(), b)
+    for k in Uo:
+        assert rel(got[k], Uo[k]) <= 1e-9
+
+
+def test_empty_update_is_pure_decay():
+    w = tiny(K0=4, J=8, R=3, steps=0, sigma=0.05)
+    st = _state_from_oracle(w, "fp64", 0.5)
+    st2, _ = O.dash_update_p(st, [], 0, 0.5)
+    m = _model(8, 3, 0.5, "fp64", max_slices=8, max_rows=64, max_segments=8)
+    m.set_state_p(st.V, st.W, st.c, st.D, st.F, st.G)
+    m.update()
+    compare_state_p(m.get_state_p(), st2, 1e-10, "empty")
+
+
+def test_update_is_deterministic():
+    w = tiny(K0=30, J=40, R=6, steps=1, sigma=0.05)
+    st = _state_from_oracle(w, "fp32", 0.9)
+    s = PlantedStream(w)
+    s.batch(0)
+    b = s.batch(1)
+    outs = []
+    for _ in range(2):
+        m = _model(40, 6, 0.9, "fp32", max_slices=64, max_rows=4096, max_segments=128)
+        m.set_state_p(st.V, st.W, st.c, st.D, st.F, st.G)
+        m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.float().numpy())
+        m.update()
+        outs.append(m.get_state_p())
+        m.close()
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+def test_capacity_and_argument_errors_leave_state_unchanged():
+    from paper_2305_18376_gb300 import DashError
+    m = _model(6, 2, 0.9, "fp32", max_slices=4, max_rows=8, max_segments=4)
+    m.set_factors(np.ones((6, 2)))
+    with pytest.raises(DashError):
+        m.append_rows(0, np.zeros((2, 6), np.float32))        # slice 0 does not exist
+    with pytest.raises(DashError):
+        m.append_slices([np.zeros((9, 6), np.float32)])       # > max_rows
+    with pytest.raises(DashError):
+        m.append_batch([0, 2], [0, 1, 2], np.zeros((2, 6), np.float32))   # id gap
+    assert m.K == 0
+    m.append_slices([np.ones((3, 6), np.float32)])
+    m.update()
+    assert m.K == 1
