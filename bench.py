@@ -1,0 +1,459 @@
+#!/usr/bin/env python3
+"""Dash update throughput on GB300: rows absorbed per second and p50/p99
+update latency, mixed precision vs FP64, on a synthetic planted stream.
+
+    python bench.py [--gpus N --steps K --warmup W] [--workload c4] [--impl reference]
+
+One step = one dash_update (Algorithm 1) over one batch of new rows that is
+already resident in HBM.  N > 1 (torchrun) runs N independent replicas, one
+stream per GPU (the path has no exchange in this build), and reports the
+whole-job rows/s over the slowest rank.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Dash update rows/s & p50/p99 latency, mixed-prec vs FP64 on 1 GB300"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+FP64_FMA_TFLOPS = 1.20     # measured FMA-loop FP64 rate of this machine's GB300
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c4")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--init-iters", type=int, default=3)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-slices", type=int, default=200,
+                    help="slices in the oracle's bounded CPU sample")
+    ap.add_argument("--profile-out", default="", help="write the per-kernel profile here")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# nvidia-smi clock sampling during the timed region
+# ---------------------------------------------------------------------------
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx),
+                                          f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        mhz, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work ("Roofline")
+# ---------------------------------------------------------------------------
+def algorithmic(kernel: str, N: int, K_all: int, J: int, R: int, tsize: int, isize: int):
+    """(bytes, flops) one launch must move / do, by kernel."""
+    state = K_all * (R + R * (R + 1) // 2 + R) * 8 * 2      # c, D (sym.), W read + write
+    if kernel == "k_xv":
+        return N * J * isize + N * R * tsize, 2 * N * J * R
+    if kernel == "k_f":
+        return N * J * isize + N * R * tsize, 2 * N * J * R
+    if kernel == "k_slices":
+        return 2 * N * R * tsize + state, N * (2 * R * R + R * R) + K_all * (R ** 3 // 3)
+    if kernel == "k_rows":      # fused single-read pass
+        return N * J * isize + N * R * tsize + state, 4 * N * J * R
+    return None, None
+
+
+def step_bytes(N, K_all, J, R, isize):
+    """§8(d) algorithmic bytes of one update: X read once, U written, the
+    per-slice helpers read and written."""
+    return N * J * isize + N * R * 4 + K_all * (R + R * (R + 1) // 2 + R) * 8 * 2
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2305_18376_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken from the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel)
+    if not e or e.get("src_sha") != src_hash():
+        return None
+    return e.get("dram_bytes_per_launch_full")
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(wname: str, n_slices: int, n_updates: int, warm: int = 0):
+    import numpy as np
+    import torch
+    from oracle import dash_oracle as O
+    from synth.planted import PlantedStream, workload
+    try:
+        from threadpoolctl import threadpool_info
+        blas = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        blas = os.cpu_count() or 1
+    w = workload(wname)
+    # the update's cost depends on the new rows and on K, not on the history:
+    # the untimed initial tensor of the sample keeps R..2R rows per slice
+    w = type(w)(**{**w.__dict__, "K0": n_slices, "steps": warm + n_updates,
+                   "init_rows": ("uniform", w.R, 2 * w.R),
+                   "new_slices_per_step": max(1, w.new_slices_per_step * n_slices // w.K0)})
+    s = PlantedStream(w, dtype=torch.float32)
+    b0 = s.batch(0)
+    X0 = [x.double().numpy() for _, x in b0.segments()]
+    V0 = np.random.default_rng(0).random((w.J, w.R))
+    U, W, V = O.static_als_p(X0, V0, np.ones((len(X0), w.R)), 1)
+    st = O.init_helpers_p(X0, U, W, V)
+    times, rows = [], []
+    for t in range(1, warm + n_updates + 1):
+        b = s.batch(t)
+        segs = [(k, x.double().numpy()) for k, x in b.segments()]
+        t0 = time.perf_counter()
+        st, _ = O.dash_update_p(st, segs, b.n_new, w.lam)
+        dt = time.perf_counter() - t0
+        if t > warm:
+            times.append(dt)
+            rows.append(b.n_rows)
+    return {"rows": rows, "times": times, "cores": blas, "nproc": os.cpu_count(),
+            "sample": f"{wname} update recipe on K0={n_slices} slices (J={w.J}, R={w.R}; "
+                      f"untimed initial tensor of R..2R rows per slice), {n_updates} timed "
+                      f"updates, oracle mode P in numpy float64"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from synth.planted import workload
+    w = workload(a.workload)
+    r = oracle_sample(a.workload, a.cpu_slices, a.steps, warm=a.warmup)
+    tot_rows, tot_t = sum(r["rows"]), sum(r["times"])
+    v = tot_rows / tot_t
+    lat = sorted(r["times"])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "rows/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot_t / len(r["times"]),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(w, a),
+        "latency": {"p50_ms": 1e3 * statistics.median(lat), "p99_ms": 1e3 * lat[-1]},
+        "cpu_baseline": {"value": v, "unit": "rows/s", "cores": r["cores"], "kind": "oracle",
+                         "sample": r["sample"], "nproc": r["nproc"]},
+        "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(w, a):
+    return {"workload": f"{w.name}: planted PARAFAC2 stream, K0={w.K0}, J={w.J}, R={w.R}, "
+                        f"init rows {w.init_rows}, +{w.rows_per_step} rows per slice and "
+                        f"+{w.new_slices_per_step} slices {w.new_slice_rows} per update, "
+                        f"sigma={w.sigma}, lambda={w.lam}",
+            "mode": "P (Algorithm 1)", "precision": a.precision, "input": "f32",
+            "init": f"{a.init_iters} static ALS iterations on the GPU",
+            "l2": "inputs larger than L2 (each step's X_new is GBs)"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2305_18376_gb300 import DashModel
+    from synth.planted import PlantedStream, workload
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = workload(a.workload)
+    n_batches = a.warmup + a.steps
+    if n_batches > w.steps:
+        w = type(w)(**{**w.__dict__, "steps": n_batches})
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = PlantedStream(w, device="cuda", dtype=torch.float32, seed=w.seed + 1000 * rank)
+    b0 = s.batch(0)
+    batches = [s.batch(t) for t in range(1, n_batches + 1)]
+    del s
+    max_rows = max([b0.n_rows] + [b.n_rows for b in batches])
+    max_seg = max([b0.slice_ids.numel()] + [b.slice_ids.numel() for b in batches])
+    K_total = w.K0 + w.new_slices_per_step * n_batches
+    step_rows = max(b.n_rows for b in batches)
+    m = DashModel(w.J, w.R, w.lam, precision=a.precision, input_dtype="f32",
+                  max_slices=K_total + 8, max_rows=max_rows, max_segments=max_seg + 8,
+                  stream=stream.cuda_stream, max_staged_rows=step_rows)
+    V0 = np.random.default_rng(7).random((w.J, w.R))
+    m.set_factors(V0)
+    t0 = time.perf_counter()
+    m.fit_initial_device(b0.slice_ids.numpy(), b0.row_ptr.numpy(), b0.X, a.init_iters)
+    m.sync()
+    init_s = time.perf_counter() - t0
+    fit_init = m.fitness()[0]
+    del b0
+    torch.cuda.empty_cache()
+    for b in batches[: a.warmup]:
+        m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X)
+    m.sync()
+    snap = m.get_state_p() if (rank == 0 and not a.no_fp64) else None
+    timed = batches[a.warmup:]
+    # ---- timed region (device-resident inputs) ----------------------------
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in timed]
+    m.profile(True)
+    l0 = m.launch_count()
+    fits = []
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for (ea, eb), b in zip(evs, timed):
+        ea.record(stream)
+        m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X)
+        eb.record(stream)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = m.launch_count() - l0
+    prof = m.profile_report()
+    m.profile(False)
+    elapsed = e_start.elapsed_time(e_end) / 1e3
+    lat = sorted(ea.elapsed_time(eb) for ea, eb in evs)
+    rows = sum(b.n_rows for b in timed)
+    t_max = elapsed
+    if world > 1:
+        tt = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        rr = torch.tensor([float(rows)], device="cuda")
+        dist.all_reduce(rr)
+        rows_all = float(rr.item())
+    else:
+        rows_all = float(rows)
+    value = rows_all / t_max
+    fit_last = m.fitness()[0]
+    # ---- FP64 path on the same state and inputs (rank 0) -------------------
+    fp64 = None
+    if snap is not None:
+        m64 = DashModel(w.J, w.R, w.lam, precision="fp64", input_dtype="f32",
+                        max_slices=K_total + 8, max_rows=step_rows, max_segments=max_seg + 8,
+                        stream=stream.cuda_stream, max_staged_rows=1)
+        m64.set_state_p(**snap)
+        m_fit, d_fit = [], []
+        # replay the mixed model from the same snapshot for a per-step fitness diff
+        mm = DashModel(w.J, w.R, w.lam, precision=a.precision, input_dtype="f32",
+                       max_slices=K_total + 8, max_rows=step_rows, max_segments=max_seg + 8,
+                       stream=stream.cuda_stream, max_staged_rows=1)
+        mm.set_state_p(**snap)
+        ev64 = []
+        for b in timed:
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            m64.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X)
+            eb.record(stream)
+            ev64.append((ea, eb))
+            f64v = m64.fitness()[0]
+            mm.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X)
+            fmv = mm.fitness()[0]
+            m_fit.append(f64v)
+            d_fit.append(abs(fmv - f64v))
+        torch.cuda.synchronize()
+        l64 = sorted(ea.elapsed_time(eb) for ea, eb in ev64)
+        st64, stm = m64.get_state_p(), mm.get_state_p()
+        err = {k: float(np.max(np.abs(stm[k] - st64[k])) / max(np.max(np.abs(st64[k])), 1e-300))
+               for k in ("V", "W", "c", "D", "F", "G")}
+        fp64 = {"value": rows / (sum(l64) / 1e3), "unit": "rows/s",
+                "ms_per_step": sum(l64) / len(l64), "p50_ms": statistics.median(l64),
+                "p99_ms": l64[-1], "fitness_mean": float(np.mean(m_fit)),
+                "max_abs_fitness_diff_mixed_vs_fp64": float(max(d_fit)),
+                "max_rel_err_mixed_vs_fp64": err}
+        m64.close()
+        mm.close()
+    # ---- end to end through the C ABI with host buffers --------------------
+    e2e = None
+    if not a.no_e2e:
+        hosts = []
+        for b in timed[: min(2, len(timed))]:
+            hx = torch.empty(b.X.shape, dtype=b.X.dtype, pin_memory=True)
+            hx.copy_(b.X)
+            hosts.append((b, hx))
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        erows = 0
+        for i in range(len(timed)):
+            b, hx = hosts[i % len(hosts)]
+            m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), hx)
+            m.update()
+            m.fitness()                           # D2H read of the step's result
+            h2d += hx.numel() * hx.element_size() + 16 * b.slice_ids.numel()
+            d2h += 24
+            erows += b.n_rows
+        torch.cuda.synchronize()
+        et = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([et], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            et = float(tt.item())
+        e2e = {"value": erows * world / et, "unit": "rows/s",
+               "h2d_bytes_per_step": h2d // len(timed), "d2h_bytes_per_step": d2h // len(timed)}
+    # ---- roofline of the dominant kernel ------------------------------------
+    pk, pk_kind = peaks()
+    Nm = int(statistics.mean(b.n_rows for b in timed))
+    K_all = w.K0 + w.new_slices_per_step * (a.warmup + len(timed))
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    kernels = {}
+    for name, (n, ms) in prof.items():
+        by, fl = algorithmic(name, Nm, K_all, w.J, w.R, 4, 4)
+        d = {"launches": n, "ms_total": ms, "ms_per_launch": ms / n}
+        if by:
+            d["gbs"] = by / (ms / n / 1e3) / 1e9
+            d["gflops"] = fl / (ms / n / 1e3) / 1e9
+        kernels[name] = d
+    if top:
+        name, (n, ms) = top
+        by, fl = algorithmic(name, Nm, K_all, w.J, w.R, 4, 4)
+        if by:
+            per = ms / n / 1e3
+            ach = by / per / 1e9
+            hbm = pk["hbm_gbs"]
+            if name == "k_slices":
+                roof = {"bound": "alu", "achieved": fl / per / 1e12, "peak": FP64_FMA_TFLOPS,
+                        "unit": "TFLOP/s", "frac": fl / per / 1e12 / FP64_FMA_TFLOPS,
+                        "traffic": ncu_traffic(name), "kernel": name,
+                        "peak_source": "FP64 FMA-loop measurement (DESIGN.md)"}
+            else:
+                roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                        "frac": ach / hbm, "traffic": ncu_traffic(name), "kernel": name,
+                        "peak_source": f"{pk_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    sb = step_bytes(Nm, K_all, w.J, w.R, 4)
+    cpu = None
+    if rank == 0 and world == 1:
+        r = oracle_sample(a.workload, a.cpu_slices, 2)
+        cpu = {"value": sum(r["rows"]) / sum(r["times"]), "unit": "rows/s", "cores": r["cores"],
+               "kind": "oracle", "sample": r["sample"], "nproc": r["nproc"]}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_max / len(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if a.precision == "fp32" else "bf16x3",
+            "data": "synthetic", "config": workload_config(w, a),
+            "latency": {"p50_ms": statistics.median(lat), "p99_ms": lat[-1]},
+            "rows_per_step": Nm, "slices": K_all,
+            "fitness": {"init": fit_init, "last_step": fit_last},
+            "fp64": fp64, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof,
+            "step_roofline": {"bound": "hbm", "algorithmic_bytes": sb,
+                              "achieved": sb / (t_max / len(timed)) / 1e9, "peak": pk["hbm_gbs"],
+                              "unit": "GB/s", "frac": sb / (t_max / len(timed)) / 1e9 / pk["hbm_gbs"]},
+            "kernels": kernels, "cpu_baseline": cpu, "clocks": clocks,
+            "init_seconds": init_s, "src_sha": src_hash(),
+        }
+        print(json.dumps(line), flush=True)
+        if a.profile_out:
+            json.dump({"kernels": kernels, "config": line["config"]}, open(a.profile_out, "w"),
+                      indent=1)
+    m.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

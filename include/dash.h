@@ -74,9 +74,11 @@ typedef struct dash_config {
     double pinv_rtol;       /* pseudo-inverse cut-off relative to the largest
                                singular value; <= 0 selects R·DBL_EPSILON      */
     int64_t max_slices;     /* capacity K_max of slices over the model's life    */
-    int64_t max_rows;       /* capacity of staged rows per update                */
-    int64_t max_segments;   /* capacity of staged segments per update            */
+    int64_t max_rows;       /* capacity of rows per update (scratch sizing)      */
+    int64_t max_segments;   /* capacity of segments per update                   */
     void *stream;           /* cudaStream_t to run on; NULL = a private stream   */
+    int64_t max_staged_rows;/* rows the append_* staging buffer holds; 0 = max_rows
+                               (device-resident batches need no staging)       */
 } dash_config;
 
 /* Fill *cfg with defaults for (J, R, λ): mode P, FP32 products, FP32 input,
@@ -174,6 +176,11 @@ dash_status dash_update_device(dash_model *m, int64_t n_seg, const int64_t *slic
  * Clears the staging. */
 dash_status dash_fit_initial(dash_model *m, int32_t n_iter);
 
+/* dash_fit_initial() on a batch of new slices that lives in device memory,
+ * read in place (same contract as dash_update_device()). */
+dash_status dash_fit_initial_device(dash_model *m, int64_t n_seg, const int64_t *slice_ids,
+                                    const int64_t *row_ptr, const void *X, int32_t n_iter);
+
 /* factors(): copy V (J×R), rows k_first..k_first+k_count-1 of W, and in mode
  * Q H (R×R), to host FP64 arrays (NULL skips). */
 dash_status dash_factors(const dash_model *m, double *V, double *W, int64_t k_first,
@@ -194,6 +201,19 @@ dash_status dash_sync(dash_model *m);
 
 /* Per-update device time of the last dash_update (CUDA events, ms). */
 dash_status dash_last_update_ms(const dash_model *m, float *ms);
+
+/* Kernel accounting.  dash_launch_count(): kernels the library has launched
+ * on this model since dash_init.  With profiling on, every launch is
+ * bracketed by CUDA events on the model's stream and its device time is
+ * accumulated per kernel kind (enabling resets the counters).
+ * dash_profile_get() reads kind i < dash_profile_kinds(): its name, the
+ * launches and the total milliseconds since profiling was enabled; it
+ * synchronises the stream.  *name points to static storage. */
+int64_t dash_launch_count(const dash_model *m);
+dash_status dash_profile_enable(dash_model *m, int32_t on);
+int32_t dash_profile_kinds(void);
+dash_status dash_profile_get(const dash_model *m, int32_t i, const char **name,
+                             int64_t *launches, double *total_ms);
 
 #ifdef __cplusplus
 }

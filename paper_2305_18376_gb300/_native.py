@@ -33,7 +33,8 @@ class Config(C.Structure):
                 ("mode", C.c_int32), ("precision", C.c_int32), ("input_dtype", C.c_int32),
                 ("n_sweeps", C.c_int32), ("pinv_rtol", C.c_double),
                 ("max_slices", C.c_int64), ("max_rows", C.c_int64),
-                ("max_segments", C.c_int64), ("stream", C.c_void_p)]
+                ("max_segments", C.c_int64), ("stream", C.c_void_p),
+                ("max_staged_rows", C.c_int64)]
 
 
 _lib = None
@@ -60,11 +61,16 @@ SIGNATURES = [
     ("dash_update", C.c_int, [P]),
     ("dash_update_device", C.c_int, [P, I64, PI64, PI64, P]),
     ("dash_fit_initial", C.c_int, [P, I32]),
+    ("dash_fit_initial_device", C.c_int, [P, I64, PI64, PI64, P, I32]),
     ("dash_factors", C.c_int, [P, PD, PD, I64, I64, PD]),
     ("dash_new_rows", C.c_int, [P, PD, PI64]),
     ("dash_fitness", C.c_int, [P, PD, PD]),
     ("dash_sync", C.c_int, [P]),
     ("dash_last_update_ms", C.c_int, [P, C.POINTER(C.c_float)]),
+    ("dash_launch_count", I64, [P]),
+    ("dash_profile_enable", C.c_int, [P, I32]),
+    ("dash_profile_kinds", I32, []),
+    ("dash_profile_get", C.c_int, [P, I32, C.POINTER(C.c_char_p), PI64, PD]),
 ]
 
 
@@ -106,7 +112,8 @@ class DashModel:
 
     def __init__(self, J: int, R: int, lam: float, mode: str = "P", precision: str = "fp32",
                  input_dtype: str = "f32", max_slices: int = 1 << 16, max_rows: int = 1 << 20,
-                 max_segments: int = 1 << 17, pinv_rtol: float = 0.0, stream=None):
+                 max_segments: int = 1 << 17, pinv_rtol: float = 0.0, stream=None,
+                 max_staged_rows: int = 0):
         lib = load()
         cfg = Config()
         lib.dash_config_default(C.byref(cfg), J, R, lam)
@@ -116,6 +123,7 @@ class DashModel:
         cfg.max_slices, cfg.max_rows, cfg.max_segments = max_slices, max_rows, max_segments
         cfg.pinv_rtol = pinv_rtol
         cfg.stream = stream
+        cfg.max_staged_rows = max_staged_rows
         h = P()
         st = lib.dash_init(C.byref(cfg), C.byref(h))
         if st != 0:
@@ -189,6 +197,22 @@ class DashModel:
         self._ck(self._lib.dash_last_update_ms(self._h, C.byref(ms)))
         return ms.value
 
+    def launch_count(self) -> int:
+        return int(self._lib.dash_launch_count(self._h))
+
+    def profile(self, on: bool = True):
+        self._ck(self._lib.dash_profile_enable(self._h, 1 if on else 0))
+
+    def profile_report(self) -> dict:
+        """{kernel: (launches, total ms)} since profiling was enabled."""
+        out = {}
+        for i in range(self._lib.dash_profile_kinds()):
+            name, n, ms = C.c_char_p(), C.c_int64(), C.c_double()
+            self._ck(self._lib.dash_profile_get(self._h, i, C.byref(name), C.byref(n), C.byref(ms)))
+            if n.value:
+                out[name.value.decode()] = (n.value, ms.value)
+        return out
+
     def sync(self):
         self._ck(self._lib.dash_sync(self._h))
 
@@ -244,3 +268,11 @@ class DashModel:
 
     def fit_initial(self, n_iter: int):
         self._ck(self._lib.dash_fit_initial(self._h, n_iter))
+
+    def fit_initial_device(self, slice_ids, row_ptr, X, n_iter: int):
+        ids, rp = _i64(slice_ids), _i64(row_ptr)
+        ptr, where, keep = self._ptr(X)
+        if where != DEVICE:
+            raise TypeError("fit_initial_device needs a CUDA tensor")
+        self._ck(self._lib.dash_fit_initial_device(self._h, len(ids), ids.ctypes.data_as(PI64),
+                                                   rp.ctypes.data_as(PI64), ptr, n_iter))

@@ -52,6 +52,83 @@ static dash_status fail(dash_model *m, dash_status s, const char *fmt, ...) {
         }                                                                                \
     } while (0)
 
+// ---------------------------------------------------------------------------
+// launch accounting and the optional per-kernel profiler
+// ---------------------------------------------------------------------------
+static cudaEvent_t prof_event(dash_model *m) {
+    if (!m->prof.pool.empty()) {
+        cudaEvent_t e = m->prof.pool.back();
+        m->prof.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static void prof_collect(dash_model *m) {
+    if (m->prof.pending.empty()) return;
+    cudaStreamSynchronize(m->stream);
+    for (auto &mk : m->prof.pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, mk.a, mk.b) == cudaSuccess) {
+            m->prof.ms[mk.kind] += ms;
+            m->prof.launches[mk.kind] += 1;
+        }
+        m->prof.pool.push_back(mk.a);
+        m->prof.pool.push_back(mk.b);
+    }
+    m->prof.pending.clear();
+    cudaGetLastError();
+}
+
+// Launch a kernel on the model's stream; with profiling on, bracket it with
+// events.  Every launch is counted.
+#define LAUNCH(kind, ...)                                                                \
+    do {                                                                                 \
+        cudaEvent_t a_ = nullptr;                                                        \
+        if (m->prof.on) {                                                                \
+            a_ = prof_event(m);                                                          \
+            cudaEventRecord(a_, m->stream);                                              \
+        }                                                                                \
+        __VA_ARGS__;                                                                     \
+        CKL();                                                                           \
+        m->prof.launches_total += 1;                                                     \
+        if (m->prof.on) {                                                                \
+            cudaEvent_t b_ = prof_event(m);                                              \
+            cudaEventRecord(b_, m->stream);                                              \
+            m->prof.pending.push_back({(int)(kind), a_, b_});                            \
+        }                                                                                \
+    } while (0)
+
+extern "C" int64_t dash_launch_count(const dash_model *m) {
+    return m ? m->prof.launches_total : -1;
+}
+
+extern "C" dash_status dash_profile_enable(dash_model *m, int32_t on) {
+    if (!m) return DASH_EINVAL;
+    prof_collect(m);
+    m->prof.on = on != 0;
+    for (int i = 0; i < KK_COUNT; ++i) {
+        m->prof.ms[i] = 0.0;
+        m->prof.launches[i] = 0;
+    }
+    return DASH_OK;
+}
+
+extern "C" int32_t dash_profile_kinds(void) { return KK_COUNT; }
+
+extern "C" dash_status dash_profile_get(const dash_model *mc, int32_t i, const char **name,
+                                        int64_t *launches, double *total_ms) {
+    dash_model *m = const_cast<dash_model *>(mc);
+    if (!m || i < 0 || i >= KK_COUNT) return DASH_EINVAL;
+    prof_collect(m);
+    if (name) *name = kKernelNames[i];
+    if (launches) *launches = m->prof.launches[i];
+    if (total_ms) *total_ms = m->prof.ms[i];
+    return DASH_OK;
+}
+
 extern "C" const char *dash_status_string(dash_status s) {
     switch (s) {
     case DASH_OK: return "ok";
@@ -84,6 +161,7 @@ extern "C" void dash_config_default(dash_config *cfg, int32_t J, int32_t R, doub
     cfg->max_rows = 1 << 20;
     cfg->max_segments = 1 << 17;
     cfg->stream = nullptr;
+    cfg->max_staged_rows = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -151,7 +229,8 @@ static dash_status init_alloc(dash_model *m) {
         return fail(m, DASH_EINVAL, "mode Q is not available in this build");
     }
     // staging and batch metadata
-    DALLOC(m->Xs, Nm * J * ie, "staged X");
+    m->stage_cap = c.max_staged_rows > 0 ? std::min<int64_t>(c.max_staged_rows, Nm) : Nm;
+    DALLOC(m->Xs, m->stage_cap * J * ie, "staged X");
     DALLOC(m->d_seg_slice, Sm * 4, "segment ids");
     DALLOC(m->d_seg_row, (Sm + 1) * 8, "segment rows");
     DALLOC(m->d_tslot, Km * 4, "slice slots");
@@ -244,6 +323,8 @@ extern "C" dash_status dash_init(const dash_config *cfg, dash_model **out) {
 extern "C" void dash_destroy(dash_model *m) {
     if (!m) return;
     cudaStreamSynchronize(m->stream);
+    prof_collect(m);
+    for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
     free_all(m);
     cudaEventDestroy(m->ev0);
     cudaEventDestroy(m->ev1);
@@ -266,15 +347,12 @@ static dash_status refresh_gamma(dash_model *m) {
     const int J = m->cfg.J, R = m->cfg.R;
     const int64_t n = (int64_t)J * R;
     if (m->tsize == 8)
-        k_cast<double><<<(n + 255) / 256, 256, 0, m->stream>>>(m->st.V, (double *)m->VT, n);
+        LAUNCH(KK_CAST, k_cast<double><<<(n + 255) / 256, 256, 0, m->stream>>>(m->st.V, (double *)m->VT, n));
     else
-        k_cast<float><<<(n + 255) / 256, 256, 0, m->stream>>>(m->st.V, (float *)m->VT, n);
-    CKL();
-    k_gamma<<<(R * R + 7) / 8, 256, 0, m->stream>>>(m->st.V, J, R, m->st.Gam);
-    CKL();
+        LAUNCH(KK_CAST, k_cast<float><<<(n + 255) / 256, 256, 0, m->stream>>>(m->st.V, (float *)m->VT, n));
+    LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, m->stream>>>(m->st.V, J, R, m->st.Gam));
     const size_t sm = (size_t)(3 * R * (R + 1) + (R + 1)) * 8;
-    k_pinv_small<<<1, 32, sm, m->stream>>>(m->st.Gam, R, m->rtol, m->st.GamP, m->st.gam_ok);
-    CKL();
+    LAUNCH(KK_PINV, k_pinv_small<<<1, 32, sm, m->stream>>>(m->st.Gam, R, m->rtol, m->st.GamP, m->st.gam_ok));
     return DASH_OK;
 }
 
@@ -417,8 +495,8 @@ static dash_status stage_rows(dash_model *m, int64_t k, const void *X, int64_t I
     if (I > 0 && !X) return fail(m, DASH_EINVAL, "X is null");
     if (ld < J) return fail(m, DASH_EINVAL, "ld %lld < J %lld", (long long)ld, (long long)J);
     if (where != DASH_HOST && where != DASH_DEVICE) return fail(m, DASH_EINVAL, "bad pointer location");
-    if (m->st_rows + I > m->cfg.max_rows)
-        return fail(m, DASH_ENOMEM, "staged rows would exceed max_rows = %lld", (long long)m->cfg.max_rows);
+    if (m->st_rows + I > m->stage_cap)
+        return fail(m, DASH_ENOMEM, "staged rows would exceed the staging capacity %lld", (long long)m->stage_cap);
     if (m->st_segs() + 1 > m->cfg.max_segments)
         return fail(m, DASH_ENOMEM, "staged segments would exceed max_segments");
     if (I > 0) {
@@ -454,7 +532,7 @@ extern "C" dash_status dash_append_slices(dash_model *m, int64_t L, const int64_
         if (I[l] < 0) return fail(m, DASH_EINVAL, "negative row count for new slice %lld", (long long)l);
         tot += I[l];
     }
-    if (m->st_rows + tot > m->cfg.max_rows) return fail(m, DASH_ENOMEM, "staged rows would exceed max_rows");
+    if (m->st_rows + tot > m->stage_cap) return fail(m, DASH_ENOMEM, "staged rows would exceed the staging capacity");
     if (m->st_segs() + L > m->cfg.max_segments) return fail(m, DASH_ENOMEM, "staged segments would exceed max_segments");
     if (first_new_id) *first_new_id = m->K + m->st_new;
     for (int64_t l = 0; l < L; ++l) {
@@ -495,7 +573,7 @@ extern "C" dash_status dash_append_batch(dash_model *m, int64_t n_seg, const int
     dash_status s = check_csr(m, n_seg, slice_ids, row_ptr, m->K + m->st_new, &n_new);
     if (s) return s;
     const int64_t N = n_seg ? row_ptr[n_seg] : 0;
-    if (m->st_rows + N > m->cfg.max_rows) return fail(m, DASH_ENOMEM, "staged rows would exceed max_rows");
+    if (m->st_rows + N > m->stage_cap) return fail(m, DASH_ENOMEM, "staged rows would exceed the staging capacity");
     if (m->st_segs() + n_seg > m->cfg.max_segments) return fail(m, DASH_ENOMEM, "staged segments would exceed max_segments");
     if (m->K + m->st_new + n_new > m->cfg.max_slices) return fail(m, DASH_ENOMEM, "slices would exceed max_slices");
     if (N > 0 && !X) return fail(m, DASH_EINVAL, "X is null");
@@ -594,16 +672,13 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     const int n_new = b.K_all - b.K_old;
     if (begin_new && n_new > 0) {
         const int64_t tot = (int64_t)n_new * R * (R + 2);
-        k_begin_new<<<(tot + 255) / 256, 256, 0, st>>>(s.W, s.c, s.D, b.K_old, n_new, R);
-        CKL();
+        LAUNCH(KK_BEGIN_NEW, k_begin_new<<<(tot + 255) / 256, 256, 0, st>>>(s.W, s.c, s.D, b.K_old, n_new, R));
     }
     int n_xn = 0;
     if (N > 0) {
-        k_rowmap<<<(N + 255) / 256, 256, 0, st>>>(b);
-        CKL();
+        LAUNCH(KK_ROWMAP, k_rowmap<<<(N + 255) / 256, 256, 0, st>>>(b));
         n_xn = (int)((N + XV_ROWS - 1) / XV_ROWS);
-        k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, N, J, R, (const T *)m->VT, (T *)m->P, m->xn_part);
-        CKL();
+        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, N, J, R, (const T *)m->VT, (T *)m->P, m->xn_part));
     }
     // per-slice work
     const int nw = sl_warps(R);
@@ -611,8 +686,7 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     int nsb = (int)std::min<int64_t>((b.K_all + nw - 1) / nw, kSliceBlocksMax);
     if (nsb < 1) nsb = 1;
     CK(cudaFuncSetAttribute(k_slices<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_slices<T><<<nsb, 32 * nw, smem, st>>>(b, s, (const T *)m->P, (T *)m->U, m->Gpart);
-    CKL();
+    LAUNCH(KK_SLICES, k_slices<T><<<nsb, 32 * nw, smem, st>>>(b, s, (const T *)m->P, (T *)m->U, m->Gpart));
     // F partials
     int nfb = 0;
     if (N > 0) {
@@ -623,27 +697,19 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
         rpc = (rpc + F_RC - 1) / F_RC * F_RC;
         nfb = (int)((N + rpc - 1) / rpc);
         dim3 grid(nfb, nby);
-        k_f<TI, T><<<grid, 256, 0, st>>>(X, b, J, R, (const T *)m->U, s.W, rpc, (T *)m->Fpart);
-        CKL();
+        LAUNCH(KK_F, k_f<TI, T><<<grid, 256, 0, st>>>(X, b, J, R, (const T *)m->U, s.W, rpc, (T *)m->Fpart));
     }
-    k_f_reduce<T><<<((int64_t)J * R + 255) / 256, 256, 0, st>>>((const T *)m->Fpart, nfb, J, R, lam,
-                                                                s.F, m->Finc);
-    CKL();
-    k_g_reduce<<<(R * R + 7) / 8, 256, 0, st>>>(m->Gpart, nsb, R, lam, s.G, m->Ginc);
-    CKL();
+    LAUNCH(KK_F_REDUCE, k_f_reduce<T><<<((int64_t)J * R + 255) / 256, 256, 0, st>>>((const T *)m->Fpart, nfb, J, R, lam,
+                                                                s.F, m->Finc));
+    LAUNCH(KK_G_REDUCE, k_g_reduce<<<(R * R + 7) / 8, 256, 0, st>>>(m->Gpart, nsb, R, lam, s.G, m->Ginc));
     const size_t psm = (size_t)(3 * R * (R + 1) + (R + 1)) * 8;
-    k_pinv_small<<<1, 32, psm, st>>>(s.G, R, m->rtol, m->GP, nullptr);
-    CKL();
-    k_vupdate<T><<<(J + 7) / 8, 256, 0, st>>>(s.F, m->GP, m->Finc, J, R, s.V, (T *)m->VT,
-                                               m->cross_part);
-    CKL();
-    k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(s.V, J, R, s.Gam);
-    CKL();
-    k_pinv_small<<<1, 32, psm, st>>>(s.Gam, R, m->rtol, s.GamP, s.gam_ok);
-    CKL();
-    k_fitness<<<1, 32, 0, st>>>(m->xn_part, n_xn, m->cross_part, (J + 7) / 8, s.Gam, m->Ginc, R,
-                                m->fit);
-    CKL();
+    LAUNCH(KK_PINV, k_pinv_small<<<1, 32, psm, st>>>(s.G, R, m->rtol, m->GP, nullptr));
+    LAUNCH(KK_VUPDATE, k_vupdate<T><<<(J + 7) / 8, 256, 0, st>>>(s.F, m->GP, m->Finc, J, R, s.V, (T *)m->VT,
+                                               m->cross_part));
+    LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(s.V, J, R, s.Gam));
+    LAUNCH(KK_PINV, k_pinv_small<<<1, 32, psm, st>>>(s.Gam, R, m->rtol, s.GamP, s.gam_ok));
+    LAUNCH(KK_FITNESS, k_fitness<<<1, 32, 0, st>>>(m->xn_part, n_xn, m->cross_part, (J + 7) / 8, s.Gam, m->Ginc, R,
+                                m->fit));
     CK(cudaMemcpyAsync(m->h_fit, m->fit, 3 * 8, cudaMemcpyDeviceToHost, st));
     return DASH_OK;
 }
@@ -653,14 +719,12 @@ static dash_status launch_recompute_c(dash_model *m, const BatchDev &b, const vo
     const int J = m->cfg.J, R = m->cfg.R;
     if (b.N > 0) {
         const int n_xn = (int)((b.N + XV_ROWS - 1) / XV_ROWS);
-        k_xv<TI, T><<<n_xn, 256, 0, m->stream>>>((const TI *)Xv, b.N, J, R, (const T *)m->VT,
-                                                  (T *)m->P, m->xn_part);
-        CKL();
+        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, m->stream>>>((const TI *)Xv, b.N, J, R, (const T *)m->VT,
+                                                  (T *)m->P, m->xn_part));
     }
     const int nb = (b.K_all + 7) / 8;
-    k_c_recompute<T><<<nb > 0 ? nb : 1, 256, 0, m->stream>>>(b, (const T *)m->P, (const T *)m->U, R,
-                                                            m->st.c);
-    CKL();
+    LAUNCH(KK_C_RECOMPUTE, k_c_recompute<T><<<nb > 0 ? nb : 1, 256, 0, m->stream>>>(b, (const T *)m->P, (const T *)m->U, R,
+                                                            m->st.c));
     return DASH_OK;
 }
 
@@ -687,6 +751,7 @@ static dash_status update_common(dash_model *m, int64_t n_seg, const int64_t *id
                                  const int64_t *rp, const void *X, int64_t n_new) {
     if (!m->v_set) return fail(m, DASH_ESTATE, "V is not set (dash_set_factors)");
     if (m->broken) return fail(m, DASH_ESTATE, "model is unusable after a CUDA error");
+    if (m->prof.pending.size() > 8192) prof_collect(m);
     BatchDev b;
     dash_status s = plan_batch(m, n_seg, ids, rp, m->K, n_new, &b);
     if (s) return s;
@@ -730,18 +795,17 @@ extern "C" dash_status dash_update_device(dash_model *m, int64_t n_seg, const in
     return update_common(m, n_seg, slice_ids, row_ptr, X, n_new);
 }
 
-extern "C" dash_status dash_fit_initial(dash_model *m, int32_t n_iter) {
-    if (!m) return DASH_EINVAL;
+static dash_status fit_common(dash_model *m, int64_t n_seg, const int64_t *ids,
+                              const int64_t *rp, const void *X, int64_t n_new, int32_t n_iter) {
     if (n_iter < 1) return fail(m, DASH_EINVAL, "n_iter must be >= 1");
     if (m->K != 0) return fail(m, DASH_ESTATE, "fit_initial needs an empty model");
     if (!m->v_set) return fail(m, DASH_ESTATE, "V is not set (dash_set_factors)");
-    const int64_t n_seg = m->st_segs();
-    const int64_t n_new = m->st_new;
+    if (m->broken) return fail(m, DASH_ESTATE, "model is unusable after a CUDA error");
     for (int64_t s = 0; s < n_seg; ++s)
-        if (m->st_slice[s] < 0 || m->st_slice[s] >= n_new)
+        if (ids[s] < 0 || ids[s] >= n_new)
             return fail(m, DASH_EINVAL, "fit_initial takes new slices only");
     BatchDev b;
-    dash_status s = plan_batch(m, n_seg, m->st_slice.data(), m->st_row.data(), 0, n_new, &b);
+    dash_status s = plan_batch(m, n_seg, ids, rp, 0, n_new, &b);
     if (s) return s;
     CK(cudaEventRecord(m->ev0, m->stream));
     // iteration 1: the slices are new (S_k = I); later iterations: the same
@@ -750,16 +814,39 @@ extern "C" dash_status dash_fit_initial(dash_model *m, int32_t n_iter) {
     for (int it = 0; it < n_iter; ++it) {
         BatchDev bi = b;
         if (it > 0) bi.K_old = bi.K_all;     // no new slices any more
-        s = run_update(m, bi, m->Xs, 0.0, it == 0);
+        s = run_update(m, bi, X, 0.0, it == 0);
         if (s) return s;
     }
     // c_k = vec(X_k)ᵀ(V ⊙ U_k) with the final V (Eq. 6)
-    s = recompute_c(m, b, m->Xs);
+    s = recompute_c(m, b, X);
     if (s) return s;
     CK(cudaEventRecord(m->ev1, m->stream));
     m->K = n_new;
     m->last_N = b.N;
     m->has_last = true;
-    clear_staging(m);
     return DASH_OK;
+}
+
+extern "C" dash_status dash_fit_initial(dash_model *m, int32_t n_iter) {
+    if (!m) return DASH_EINVAL;
+    dash_status s = fit_common(m, m->st_segs(), m->st_slice.data(), m->st_row.data(), m->Xs,
+                               m->st_new, n_iter);
+    if (s == DASH_OK) clear_staging(m);
+    return s;
+}
+
+extern "C" dash_status dash_fit_initial_device(dash_model *m, int64_t n_seg,
+                                               const int64_t *slice_ids, const int64_t *row_ptr,
+                                               const void *X, int32_t n_iter) {
+    if (!m) return DASH_EINVAL;
+    if (m->st_segs() > 0) return fail(m, DASH_ESTATE, "rows are staged");
+    int64_t n_new = 0;
+    dash_status s = check_csr(m, n_seg, slice_ids, row_ptr, 0, &n_new);
+    if (s) return s;
+    const int64_t N = n_seg ? row_ptr[n_seg] : 0;
+    if (N > m->cfg.max_rows) return fail(m, DASH_ENOMEM, "batch rows exceed max_rows");
+    if (n_seg > m->cfg.max_segments) return fail(m, DASH_ENOMEM, "batch segments exceed max_segments");
+    if (n_new > m->cfg.max_slices) return fail(m, DASH_ENOMEM, "slices would exceed max_slices");
+    if (N > 0 && !X) return fail(m, DASH_EINVAL, "X is null");
+    return fit_common(m, n_seg, slice_ids, row_ptr, X, n_new, n_iter);
 }

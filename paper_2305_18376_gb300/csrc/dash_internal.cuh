@@ -9,6 +9,25 @@
 #include "dash_kernels_p.cuh"
 
 namespace dash {
+// kernel kinds for the per-kernel profiler
+enum KernelKind {
+    KK_BEGIN_NEW, KK_ROWMAP, KK_XV, KK_SLICES, KK_F, KK_F_REDUCE, KK_G_REDUCE, KK_PINV,
+    KK_VUPDATE, KK_GAMMA, KK_FITNESS, KK_CAST, KK_C_RECOMPUTE, KK_COUNT
+};
+static const char *const kKernelNames[KK_COUNT] = {
+    "k_begin_new", "k_rowmap", "k_xv", "k_slices", "k_f", "k_f_reduce", "k_g_reduce",
+    "k_pinv_small", "k_vupdate", "k_gamma", "k_fitness", "k_cast", "k_c_recompute"};
+
+struct Profiler {
+    bool on = false;
+    int64_t launches_total = 0;
+    int64_t launches[KK_COUNT] = {};
+    double ms[KK_COUNT] = {};
+    struct Mark { int kind; cudaEvent_t a, b; };
+    std::vector<Mark> pending;
+    std::vector<cudaEvent_t> pool;
+};
+
 constexpr int kFBlocksMax = 1024;       // max row chunks of the F-partial kernel
 constexpr int kSliceBlocksMax = 1216;   // max CTAs of the per-slice kernel (8 per SM)
 }  // namespace dash
@@ -33,6 +52,7 @@ struct dash_model {
 
     // staging: rows copied in by the append calls
     void *Xs = nullptr;
+    int64_t stage_cap = 0;            // rows the staging buffer holds
     int64_t st_rows = 0, st_new = 0;
     std::vector<int64_t> st_slice;    // slice id per staged segment
     std::vector<int64_t> st_row{0};   // row offsets, size = segments + 1
@@ -59,6 +79,8 @@ struct dash_model {
     // last update
     int64_t last_N = 0;
     bool has_last = false;
+
+    dash::Profiler prof;
 
     std::vector<void *> allocs, host_allocs;
 };

@@ -167,35 +167,52 @@ class PlantedStream:
         self.Q = self._planted_q(final, dg)
         self._next = 0
 
-    # -- planted orthonormal Q_k, bucketed by length for batched QR ----------
+    # -- planted orthonormal Q_k, bucketed by length ---------------------------
     def _planted_q(self, final: torch.Tensor, dg: torch.Generator) -> torch.Tensor:
+        """Q_k = the Q factor, with positive diag(R̃), of a Gaussian matrix of
+        the slice's final length.  Computed as a Cholesky QR (R̃ = chol(GᵀG)ᵀ,
+        Q = G R̃⁻¹), which is that same unique factor.  A slice shorter than R
+        gets orthonormal rows instead (first rows of an orthogonal matrix)."""
         R = self.w.R
+        dev = self.device
         total = int(final.sum())
-        Q = torch.zeros(total, R, device=self.device, dtype=self.dtype)
-        G = torch.randn(total, R, generator=dg, device=self.device, dtype=self.dtype)
-        lens = final.tolist()
-        offs = self.q_off.tolist()
-        order = sorted(range(len(lens)), key=lambda k: lens[k])
-        i = 0
-        while i < len(order):
-            lmax_lo = max(lens[order[i]], 1)
-            cap = max(int(lmax_lo * 1.25) + 1, lmax_lo + 8)
-            j = i
-            while j < len(order) and lens[order[j]] <= cap and j - i < 4096:
-                j += 1
-            ids = order[i:j]
-            lmax = max(lens[k] for k in ids)
-            if lmax > 0:
-                pad = torch.zeros(len(ids), lmax, R, device=self.device, dtype=self.dtype)
-                for b, k in enumerate(ids):
-                    pad[b, : lens[k]] = G[offs[k]: offs[k] + lens[k]]
-                q, r = torch.linalg.qr(pad, mode="reduced")
-                sgn = torch.sign(torch.diagonal(r, dim1=-2, dim2=-1))
-                sgn[sgn == 0] = 1
-                q = q * sgn.unsqueeze(-2)
-                for b, k in enumerate(ids):
-                    Q[offs[k]: offs[k] + lens[k]] = q[b, : lens[k]]
-            i = j
+        G = torch.randn(total, R, generator=dg, device=dev, dtype=self.dtype)
+        Q = torch.zeros_like(G)
+        lens = final.clone()
+        offs = self.q_off[:-1]
+        short = torch.nonzero((lens > 0) & (lens < R)).flatten().tolist()
+        for k in short:                      # rare: fewer rows than the rank
+            o, L = int(offs[k]), int(lens[k])
+            q, r = torch.linalg.qr(G[o:o + L].T.contiguous())       # R×L, orthonormal cols
+            sgn = torch.sign(torch.diagonal(r))
+            sgn[sgn == 0] = 1
+            Q[o:o + L] = (q * sgn).T
+        tall = torch.nonzero(lens >= R).flatten()
+        if tall.numel():
+            tl = lens[tall]
+            order = torch.argsort(tl)
+            tall, tl = tall[order], tl[order]
+            i, n = 0, tall.numel()
+            cap_rows = 1 << 23
+            while i < n:
+                l0 = int(tl[i])
+                lim = max(int(l0 * 1.25) + 1, l0 + 8)
+                j = int(torch.searchsorted(tl, torch.tensor(lim), right=True))
+                j = max(j, i + 1)
+                j = min(j, i + max(1, cap_rows // max(int(tl[j - 1]), 1)))
+                ids = tall[i:j]
+                ln = tl[i:j]
+                Lmax = int(ln.max())
+                ar = torch.arange(Lmax)
+                mask = ar[None, :] < ln[:, None]
+                idx = (offs[ids][:, None] + ar[None, :]).masked_fill(~mask, 0)
+                idx_d, mask_d = idx.to(dev), mask.to(dev)
+                pad = G[idx_d] * mask_d[..., None]
+                gram = pad.transpose(1, 2) @ pad
+                Lc = torch.linalg.cholesky(gram)
+                q = torch.linalg.solve_triangular(Lc.transpose(1, 2), pad, upper=True, left=False)
+                Q[idx_d[mask_d]] = q[mask_d]
+                i = j
         return Q
 
     def batch(self, t: int) -> Batch:
@@ -213,19 +230,23 @@ class PlantedStream:
         row_ptr = torch.zeros(k_count + 1, dtype=torch.int64)
         row_ptr[1:] = torch.cumsum(rows, 0)
         N = int(row_ptr[-1])
-        # gather the planted Q rows revealed at this update
+        # gather the planted Q rows revealed at this update, chunk by chunk
         start = self.q_off[:k_count] + self._revealed[:k_count]
         seg_of_row = torch.repeat_interleave(ids, rows)
         within = torch.arange(N, dtype=torch.int64) - row_ptr[:-1].repeat_interleave(rows)
-        src = (start.repeat_interleave(rows) + within).to(self.device)
+        src = start.repeat_interleave(rows) + within
         self._revealed[:k_count] += rows
-        q = self.Q.index_select(0, src)
-        wk = self.W.index_select(0, seg_of_row.to(self.device))
-        X = ((q @ self.H) * wk) @ self.V.T
-        if w.sigma:
-            X = X + w.sigma * torch.randn(N, w.J, generator=self._dgen,
-                                          device=self.device, dtype=self.dtype)
-        return Batch(slice_ids=ids, row_ptr=row_ptr, X=X.contiguous(),
+        X = torch.empty(N, w.J, device=self.device, dtype=self.dtype)
+        chunk = 1 << 21
+        for c0 in range(0, N, chunk):
+            c1 = min(N, c0 + chunk)
+            q = self.Q.index_select(0, src[c0:c1].to(self.device))
+            wk = self.W.index_select(0, seg_of_row[c0:c1].to(self.device))
+            torch.matmul((q @ self.H) * wk, self.V.T, out=X[c0:c1])
+            if w.sigma:
+                X[c0:c1].add_(torch.randn(c1 - c0, w.J, generator=self._dgen,
+                                          device=self.device, dtype=self.dtype), alpha=w.sigma)
+        return Batch(slice_ids=ids, row_ptr=row_ptr, X=X,
                      K_before=K_before, n_new=n_new)
 
 
