@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--cpu-slices", type=int, default=200,
                     help="slices in the oracle's bounded CPU sample")
     ap.add_argument("--profile-out", default="", help="write the per-kernel profile here")
+    ap.add_argument("--k0", type=int, default=0, help="override the initial slice count "
+                    "(reduced cases for profiling only; the bench line uses the workload's)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     return ap.parse_args()
 
 
@@ -250,6 +253,8 @@ def run_ours(a):
             dist.barrier()
 
     w = workload(a.workload)
+    if a.k0:
+        w = type(w)(**{**w.__dict__, "K0": a.k0})
     n_batches = a.warmup + a.steps
     if n_batches > w.steps:
         w = type(w)(**{**w.__dict__, "steps": n_batches})
@@ -416,7 +421,7 @@ def run_ours(a):
                         "peak_source": f"{pk_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     sb = step_bytes(Nm, K_all, w.J, w.R, 4)
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not a.no_cpu:
         r = oracle_sample(a.workload, a.cpu_slices, 2)
         cpu = {"value": sum(r["rows"]) / sum(r["times"]), "unit": "rows/s", "cores": r["cores"],
                "kind": "oracle", "sample": r["sample"], "nproc": r["nproc"]}
