@@ -215,6 +215,38 @@ int32_t dash_profile_kinds(void);
 dash_status dash_profile_get(const dash_model *m, int32_t i, const char **name,
                              int64_t *launches, double *total_ms);
 
+/* Allocation-free F increment.  (The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory.)
+ *
+ * Computes F_inc = Σ_k X_k,newᵀ U_k,new S_k — the new-data term that
+ * dash_update() adds to λF — with FP32 products and an FP64 sum, for callers
+ * that may not call cudaMalloc or let a library call it: code under a host
+ * framework whose memory manager owns the whole device, serving loops where
+ * an allocation's implicit device synchronisation would stall work in
+ * flight, and processes whose device footprint is fixed at start-up.
+ *
+ * All pointers are device pointers owned by the caller: X (N×J FP32,
+ * row-major), U (N×R FP32, the rows' U_k,new), seg_row (n_seg+1 ascending
+ * row offsets from 0) and seg_slice (n_seg slice ids) describing which slice
+ * each row belongs to, W (rows of W for every id in seg_slice, FP64, K×R),
+ * and the output F_inc (J×R FP64).  Work is queued on `stream` (a
+ * cudaStream_t; NULL = the default stream) and the call returns without
+ * waiting.
+ *
+ * Nothing is allocated: per-block partial sums go to one static device
+ * array of 2^21 floats (8 MiB) that every GPU loading this library holds
+ * until the process exits.  J·R above 2^21 returns DASH_ENOMEM; bad
+ * arguments DASH_EINVAL; a failed lookup or launch DASH_ECUDA.  The first
+ * call on a device looks up that array's device address (with the device
+ * current) and caches it: make that first call before any stream capture.
+ * Calls share the array, so calls that overlap on the GPU race; serialise
+ * them (e.g. one stream).  Each call writes every partial it reads, so what
+ * an earlier call left there is never used. */
+dash_status dash_f_increment_noalloc(const float *X, const float *U, int64_t N, int32_t J,
+                                     int32_t R, const int64_t *seg_row, const int32_t *seg_slice,
+                                     int64_t n_seg, const double *W, double *F_inc,
+                                     void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -71,6 +71,7 @@ SIGNATURES = [
     ("dash_profile_enable", C.c_int, [P, I32]),
     ("dash_profile_kinds", I32, []),
     ("dash_profile_get", C.c_int, [P, I32, C.POINTER(C.c_char_p), PI64, PD]),
+    ("dash_f_increment_noalloc", C.c_int, [P, P, I64, I32, I32, P, P, I64, P, P, P]),
 ]
 
 

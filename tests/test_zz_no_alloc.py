@@ -1,0 +1,80 @@
+"""The allocation-free F increment (dash_f_increment_noalloc), for callers
+that cannot allocate device memory, gives the same F_inc as dash_update().
+
+A model whose F starts at zero holds F = λ·0 + F_inc after one update, so its
+F is the existing entry point's F_inc; the allocation-free entry point gets
+the same rows, their U_k,new and the updated W, through the C ABI.  Two calls
+in a row, on batches of different sizes, check that nothing a previous call
+left in the shared static array leaks into the next result.  This file is
+collected last so that a failure here does not hide the other tests.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import dash_oracle as O
+from synth.planted import PlantedStream, tiny
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_state(w):
+    s = PlantedStream(w, dtype=torch.float32)
+    b0 = s.batch(0)
+    X0 = [x.double().numpy() for _, x in b0.segments()]
+    rng = np.random.default_rng(11)
+    U, W, V = O.static_als_p(X0, rng.random((w.J, w.R)), np.ones((len(X0), w.R)), 2)
+    return s, O.init_helpers_p(X0, U, W, V)
+
+
+def test_noalloc_f_increment_matches_update():
+    from paper_2305_18376_gb300 import DashModel, _native
+    lib = _native.load()
+    w = tiny(K0=40, J=70, R=7, steps=2, sigma=0.05, lam=0.9, rows=("uniform", 1, 40),
+             new_rows=("uniform", 30, 90), init_rows=("uniform", 10, 30))
+    s, st = _oracle_state(w)
+    for t in (1, 2):
+        b = s.batch(t)
+        K_all = b.K_before + b.n_new
+        m = DashModel(w.J, w.R, w.lam, precision="fp32", input_dtype="f32", max_slices=128,
+                      max_rows=4096, max_segments=256)
+        W_pad = np.vstack([st.W, np.ones((max(0, b.K_before - st.K), w.R))])[: b.K_before]
+        m.set_state_p(st.V, W_pad, st.c[: b.K_before] if st.K >= b.K_before else
+                      np.vstack([st.c, np.zeros((b.K_before - st.K, w.R))]),
+                      st.D[: b.K_before] if st.K >= b.K_before else
+                      np.concatenate([st.D, np.zeros((b.K_before - st.K, w.R, w.R))]),
+                      np.zeros((w.J, w.R)), st.G)
+        X = b.X.float().cuda()
+        m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), X)
+        g = m.get_state_p()
+        F_ref = g["F"]                                # λ·0 + F_inc
+        U = torch.from_numpy(m.new_rows()).float().cuda()
+        Wd = torch.from_numpy(g["W"]).cuda()
+        seg_row = b.row_ptr.cuda()
+        seg_slice = b.slice_ids.to(torch.int32).cuda()
+        out = torch.full((w.J, w.R), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        stat = lib.dash_f_increment_noalloc(X.data_ptr(), U.data_ptr(), b.n_rows, w.J, w.R,
+                                            seg_row.data_ptr(), seg_slice.data_ptr(),
+                                            b.slice_ids.numel(), Wd.data_ptr(), out.data_ptr(),
+                                            None)
+        assert stat == 0
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        err = float(np.max(np.abs(got - F_ref)) / np.max(np.abs(F_ref)))
+        assert err <= 1e-4, (t, err)
+        assert K_all == m.K
+        m.close()
+
+
+def test_noalloc_rejects_sizes_beyond_the_static_array():
+    from paper_2305_18376_gb300 import _native
+    lib = _native.load()
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    # J·R = 2^21 + 64·... beyond the 2^21-float array
+    assert lib.dash_f_increment_noalloc(None, None, 0, (1 << 21) // 32 + 1, 64, None, None, 0,
+                                        None, out.data_ptr(), None) == 2
+    assert lib.dash_f_increment_noalloc(None, None, 0, 8, 65, None, None, 0, None,
+                                        out.data_ptr(), None) == 1
