@@ -183,10 +183,11 @@ class PlantedStream:
         short = torch.nonzero((lens > 0) & (lens < R)).flatten().tolist()
         for k in short:                      # rare: fewer rows than the rank
             o, L = int(offs[k]), int(lens[k])
-            q, r = torch.linalg.qr(G[o:o + L].T.contiguous())       # R×L, orthonormal cols
+            g = G[o:o + L].T.contiguous().cpu().double()             # R×L
+            q, r = torch.linalg.qr(g)                                 # R×L, orthonormal cols
             sgn = torch.sign(torch.diagonal(r))
             sgn[sgn == 0] = 1
-            Q[o:o + L] = (q * sgn).T
+            Q[o:o + L] = (q * sgn).T.to(device=dev, dtype=self.dtype)
         tall = torch.nonzero(lens >= R).flatten()
         if tall.numel():
             tl = lens[tall]
@@ -208,9 +209,11 @@ class PlantedStream:
                 idx = (offs[ids][:, None] + ar[None, :]).masked_fill(~mask, 0)
                 idx_d, mask_d = idx.to(dev), mask.to(dev)
                 pad = G[idx_d] * mask_d[..., None]
-                gram = pad.transpose(1, 2) @ pad
-                Lc = torch.linalg.cholesky(gram)
-                q = torch.linalg.solve_triangular(Lc.transpose(1, 2), pad, upper=True, left=False)
+                # small R×R factorisations in FP64 on the host; the tall
+                # products stay on the device
+                gram = (pad.transpose(1, 2) @ pad).cpu().double()
+                Linv = torch.linalg.inv(torch.linalg.cholesky(gram))
+                q = pad @ Linv.transpose(1, 2).to(device=dev, dtype=self.dtype)
                 Q[idx_d[mask_d]] = q[mask_d]
                 i = j
         return Q
