@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "dash.h"
@@ -240,13 +241,23 @@ static dash_status init_alloc(dash_model *m) {
     // scratch
     DALLOC(m->P, Nm * R * te, "P = X V");
     DALLOC(m->U, Nm * R * te, "U_new");
-    m->n_xn_max = (Nm + XV_ROWS - 1) / XV_ROWS;
+    m->n_xn_max = m->n_sm + (Nm + XV_ROWS - 1) / XV_ROWS;
     DALLOC(m->xn_part, m->n_xn_max * 8, "||X|| partials");
-    m->n_fb_max = kFBlocksMax;
+    m->n_fb_max = m->n_sm + kFBlocksMax;
     DALLOC(m->Fpart, (size_t)m->n_fb_max * J * R * te, "F partials");
-    m->n_gb_max = kSliceBlocksMax;
+    m->n_gb_max = m->n_sm + kSliceBlocksMax;
     DALLOC(m->Gpart, (size_t)m->n_gb_max * R * R * 8, "G partials");
     DALLOC(m->cross_part, ((J + 7) / 8) * 8, "cross partials");
+    // fused row kernel and general runs
+    DALLOC(m->d_tile_s0, (Sm + 1) * 4, "tiles");
+    DALLOC(m->d_tile_s1, (Sm + 1) * 4, "tiles");
+    DALLOC(m->Vt, J * R * 4, "V Gamma+");
+    DALLOC(m->Gdf, R * R * 8, "Gamma (double-float)");
+    DALLOC(m->wsp, (size_t)m->n_sm * FU_WARPS * fu_wsp_doubles((int)R) * 8, "fallback workspace");
+    DALLOC(m->d_err, 4 * sizeof(int), "error counters");
+    DALLOC(m->d_run_g0, (Sm + 2) * 8, "general runs");
+    DALLOC(m->d_run_row0, (Sm + 2) * 8, "general runs");
+
     // pinned host metadata (upload source)
     dash_status s;
     if ((s = halloc(m, (void **)&m->h_seg_slice, Sm * 4))) return s;
@@ -255,6 +266,13 @@ static dash_status init_alloc(dash_model *m) {
     if ((s = halloc(m, (void **)&m->h_tseg_ptr, (Sm + 1) * 4))) return s;
     if ((s = halloc(m, (void **)&m->h_tseg_idx, Sm * 4))) return s;
     if ((s = halloc(m, (void **)&m->h_fit, 4 * 8))) return s;
+    if ((s = halloc(m, (void **)&m->h_tile_s0, (Sm + 1) * 4))) return s;
+    if ((s = halloc(m, (void **)&m->h_tile_s1, (Sm + 1) * 4))) return s;
+    if ((s = halloc(m, (void **)&m->h_run_g0, (Sm + 2) * 8))) return s;
+    if ((s = halloc(m, (void **)&m->h_run_row0, (Sm + 2) * 8))) return s;
+    if ((s = halloc(m, (void **)&m->h_err, 4 * sizeof(int)))) return s;
+    memset(m->h_err, 0, 4 * sizeof(int));
+    cudaMemsetAsync(m->d_err, 0, 4 * sizeof(int), m->stream);
     return DASH_OK;
 }
 
@@ -288,6 +306,16 @@ extern "C" dash_status dash_init(const dash_config *cfg, dash_model **out) {
     }
     m->rtol = c.pinv_rtol > 0.0 ? c.pinv_rtol : (double)c.R * DBL_EPSILON;
     m->tsize = (c.precision == DASH_PREC_FP64) ? 8 : 4;
+    m->df_state = c.precision != DASH_PREC_FP64;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            m->n_sm = nsm;
+        cudaGetLastError();
+    }
+    m->fused_ok = m->df_state && c.input_dtype == DASH_F32 && c.R <= FU_RP &&
+                  c.J <= FU_WARPS * FU_JG && (c.J % 4) == 0 && c.mode == DASH_MODE_P;
     m->st.J = c.J;
     m->st.R = c.R;
     m->st.lam = c.lambda;
@@ -353,6 +381,38 @@ static dash_status refresh_gamma(dash_model *m) {
     LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, m->stream>>>(m->st.V, J, R, m->st.Gam));
     const size_t sm = (size_t)(3 * R * (R + 1) + (R + 1)) * 8;
     LAUNCH(KK_PINV, k_pinv_small<<<1, 32, sm, m->stream>>>(m->st.Gam, R, m->rtol, m->st.GamP, m->st.gam_ok));
+    int ok = 0;
+    CK(cudaMemcpyAsync(&ok, m->st.gam_ok, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    m->gam_ok_host = ok != 0;
+    m->h_fit[3] = ok;
+    return DASH_OK;
+}
+
+// FP64 host array → device summaries (FP64, or double-float pairs).
+static dash_status put_summ(dash_model *m, double *dst, const double *src, size_t n) {
+    if (!m->df_state) {
+        CK(cudaMemcpy(dst, src, n * 8, cudaMemcpyHostToDevice));
+        return DASH_OK;
+    }
+    std::vector<float> tmp(2 * n);
+    for (size_t i = 0; i < n; ++i) {
+        const float hi = (float)src[i];
+        tmp[2 * i] = hi;
+        tmp[2 * i + 1] = (float)(src[i] - (double)hi);
+    }
+    CK(cudaMemcpy(dst, tmp.data(), n * 8, cudaMemcpyHostToDevice));
+    return DASH_OK;
+}
+
+static dash_status get_summ(dash_model *m, double *dst, const double *src, size_t n) {
+    if (!m->df_state) {
+        CK(cudaMemcpy(dst, src, n * 8, cudaMemcpyDeviceToHost));
+        return DASH_OK;
+    }
+    std::vector<float> tmp(2 * n);
+    CK(cudaMemcpy(tmp.data(), src, n * 8, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) dst[i] = (double)tmp[2 * i] + (double)tmp[2 * i + 1];
     return DASH_OK;
 }
 
@@ -389,8 +449,11 @@ extern "C" dash_status dash_set_state_p(dash_model *m, int64_t K, const double *
     CK(cudaMemcpyAsync(m->st.V, V, J * R * 8, cudaMemcpyHostToDevice, m->stream));
     if (K > 0) {
         CK(cudaMemcpyAsync(m->st.W, W, K * R * 8, cudaMemcpyHostToDevice, m->stream));
-        CK(cudaMemcpyAsync(m->st.c, c, K * R * 8, cudaMemcpyHostToDevice, m->stream));
-        CK(cudaMemcpyAsync(m->st.D, D, K * R * R * 8, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+        dash_status s1 = put_summ(m, m->st.c, c, (size_t)K * R);
+        if (s1) return s1;
+        s1 = put_summ(m, m->st.D, D, (size_t)K * R * R);
+        if (s1) return s1;
     }
     CK(cudaMemcpyAsync(m->st.F, F, J * R * 8, cudaMemcpyHostToDevice, m->stream));
     CK(cudaMemcpyAsync(m->st.G, G, R * R * 8, cudaMemcpyHostToDevice, m->stream));
@@ -412,8 +475,8 @@ extern "C" dash_status dash_get_state_p(const dash_model *mc, double *V, double 
     CK(cudaStreamSynchronize(m->stream));
     if (V) CK(cudaMemcpy(V, m->st.V, J * R * 8, cudaMemcpyDeviceToHost));
     if (W && K) CK(cudaMemcpy(W, m->st.W, K * R * 8, cudaMemcpyDeviceToHost));
-    if (c && K) CK(cudaMemcpy(c, m->st.c, K * R * 8, cudaMemcpyDeviceToHost));
-    if (D && K) CK(cudaMemcpy(D, m->st.D, K * R * R * 8, cudaMemcpyDeviceToHost));
+    if (c && K) { dash_status s1 = get_summ(m, c, m->st.c, (size_t)K * R); if (s1) return s1; }
+    if (D && K) { dash_status s1 = get_summ(m, D, m->st.D, (size_t)K * R * R); if (s1) return s1; }
     if (F) CK(cudaMemcpy(F, m->st.F, J * R * 8, cudaMemcpyDeviceToHost));
     if (G) CK(cudaMemcpy(G, m->st.G, R * R * 8, cudaMemcpyDeviceToHost));
     return DASH_OK;
@@ -599,18 +662,21 @@ extern "C" dash_status dash_append_batch(dash_model *m, int64_t n_seg, const int
 // ---------------------------------------------------------------------------
 
 // Build and upload the device view of a batch: segments, touched slices and
-// their segment lists.  K_old is the slice count before the update.
+// their segment lists, tiles for the fused row kernel (slices with one segment
+// of at most FU_TILE_MAX rows) and the runs of rows left to the general
+// kernels.  K_old is the slice count before the update.
 static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
                               const int64_t *rp /* n_seg+1 absolute */, int64_t K_old,
-                              int64_t n_new, BatchDev *b) {
+                              int64_t n_new, const void *X, bool allow_fused, BatchDev *b) {
     const int64_t K_all = K_old + n_new;
     CK(cudaStreamSynchronize(m->stream));   // pinned metadata buffers are reused
+    m->gam_ok_host = m->h_fit[3] != 0.0;
+    if (m->h_err[0] > 0) return fail(m, DASH_ETIMEOUT, "a bounded device wait timed out");
     int *tslot = m->h_tslot;
     for (int64_t k = 0; k < K_all; ++k) tslot[k] = -1;
-    int n_touch = 0;
-    // count segments per slice, in first-appearance order of ascending id
     std::vector<int> cnt;
     cnt.reserve(1024);
+    int n_touch = 0;
     for (int64_t s = 0; s < n_seg; ++s) {
         const int64_t k = ids[s];
         if (tslot[k] < 0) {
@@ -619,15 +685,36 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
         }
         cnt[tslot[k]] += 1;
     }
-    // renumber touched slots in ascending slice order (fixed reduction order)
+    // which segments the fused kernel finishes
+    const bool fused = allow_fused && m->fused_ok && m->gam_ok_host &&
+                       ((uintptr_t)X % 16) == 0;
+    std::vector<char> fz(n_seg, 0);
+    if (fused) {
+        for (int64_t s = 0; s < n_seg; ++s)
+            fz[s] = cnt[tslot[ids[s]]] == 1 && rp[s + 1] - rp[s] <= FU_TILE_MAX;
+    }
+    // renumber touched slots in ascending slice order (fixed reduction order);
+    // slices finished by the fused kernel get -2
     {
         int t = 0;
-        std::vector<int> remap(n_touch);
-        for (int64_t k = 0; k < K_all; ++k)
-            if (tslot[k] >= 0) { remap[tslot[k]] = t; tslot[k] = t; ++t; }
-        std::vector<int> c2(n_touch);
-        for (int i = 0; i < n_touch; ++i) c2[remap[i]] = cnt[i];
+        std::vector<int> remap(n_touch, -1), fused_slot(n_touch, 0);
+        for (int64_t s = 0; s < n_seg; ++s)
+            if (fz[s]) fused_slot[tslot[ids[s]]] = 1;
+        std::vector<int> c2;
+        c2.reserve(n_touch);
+        for (int64_t k = 0; k < K_all; ++k) {
+            if (tslot[k] < 0) continue;
+            const int old = tslot[k];
+            if (fused_slot[old]) {
+                tslot[k] = -2;
+            } else {
+                remap[old] = t;
+                tslot[k] = t++;
+                c2.push_back(cnt[old]);
+            }
+        }
         cnt.swap(c2);
+        n_touch = t;
     }
     int *tp = m->h_tseg_ptr;
     tp[0] = 0;
@@ -635,10 +722,47 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
     std::vector<int> fillp(tp, tp + n_touch);
     for (int64_t s = 0; s < n_seg; ++s) {
         const int t = tslot[ids[s]];
-        m->h_tseg_idx[fillp[t]++] = (int)s;
+        if (t >= 0) m->h_tseg_idx[fillp[t]++] = (int)s;
         m->h_seg_slice[s] = (int)ids[s];
     }
     for (int64_t s = 0; s <= n_seg; ++s) m->h_seg_row[s] = rp[s];
+    // tiles: runs of consecutive fused segments with <= FU_TILE_MAX rows
+    int nt = 0;
+    {
+        int64_t s = 0;
+        while (s < n_seg) {
+            if (!fz[s]) { ++s; continue; }
+            const int64_t s0 = s;
+            int64_t rows = 0;
+            while (s < n_seg && fz[s] && rows + (rp[s + 1] - rp[s]) <= FU_TILE_MAX) {
+                rows += rp[s + 1] - rp[s];
+                ++s;
+            }
+            m->h_tile_s0[nt] = (int)s0;
+            m->h_tile_s1[nt] = (int)s;
+            ++nt;
+        }
+    }
+    m->n_tiles = nt;
+    // general runs: maximal runs of consecutive non-fused segments
+    int nr = 0;
+    int64_t ng = 0;
+    {
+        int64_t s = 0;
+        while (s < n_seg) {
+            if (fz[s]) { ++s; continue; }
+            const int64_t s0 = s;
+            while (s < n_seg && !fz[s]) ++s;
+            const int64_t rows = rp[s] - rp[s0];
+            if (rows > 0) {
+                m->h_run_row0[nr] = rp[s0];
+                m->h_run_g0[nr] = ng;
+                ++nr;
+                ng += rows;
+            }
+        }
+        m->h_run_g0[nr] = ng;
+    }
     if (n_seg > 0) {
         CK(cudaMemcpyAsync(m->d_seg_slice, m->h_seg_slice, n_seg * 4, cudaMemcpyHostToDevice, m->stream));
         CK(cudaMemcpyAsync(m->d_tseg_idx, m->h_tseg_idx, n_seg * 4, cudaMemcpyHostToDevice, m->stream));
@@ -646,17 +770,28 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
     CK(cudaMemcpyAsync(m->d_seg_row, m->h_seg_row, (n_seg + 1) * 8, cudaMemcpyHostToDevice, m->stream));
     CK(cudaMemcpyAsync(m->d_tseg_ptr, m->h_tseg_ptr, (n_touch + 1) * 4, cudaMemcpyHostToDevice, m->stream));
     if (K_all > 0) CK(cudaMemcpyAsync(m->d_tslot, m->h_tslot, K_all * 4, cudaMemcpyHostToDevice, m->stream));
+    if (nt > 0) {
+        CK(cudaMemcpyAsync(m->d_tile_s0, m->h_tile_s0, nt * 4, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->d_tile_s1, m->h_tile_s1, nt * 4, cudaMemcpyHostToDevice, m->stream));
+    }
+    CK(cudaMemcpyAsync(m->d_run_g0, m->h_run_g0, (nr + 1) * 8, cudaMemcpyHostToDevice, m->stream));
+    if (nr > 0) CK(cudaMemcpyAsync(m->d_run_row0, m->h_run_row0, nr * 8, cudaMemcpyHostToDevice, m->stream));
+    const int64_t N = n_seg ? rp[n_seg] : 0;
     b->n_seg = (int)n_seg;
     b->n_touch = n_touch;
     b->K_all = (int)K_all;
     b->K_old = (int)K_old;
-    b->N = n_seg ? rp[n_seg] : 0;
+    b->N = N;
     b->seg_slice = m->d_seg_slice;
     b->seg_row = m->d_seg_row;
     b->tslot = m->d_tslot;
     b->tseg_ptr = m->d_tseg_ptr;
     b->tseg_idx = m->d_tseg_idx;
     b->row_slice = m->d_row_slice;
+    b->n_runs = nr;
+    b->N_gen = ng;
+    b->run_g0 = m->d_run_g0;
+    b->run_row0 = m->d_run_row0;
     return DASH_OK;
 }
 
@@ -669,61 +804,104 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     StateDev s = m->st;
     s.lam = lam;
     const int64_t N = b.N;
+    const int64_t Ng = b.N_gen;
     const int n_new = b.K_all - b.K_old;
+    constexpr bool DF = std::is_same<T, float>::value;
     if (begin_new && n_new > 0) {
         const int64_t tot = (int64_t)n_new * R * (R + 2);
         LAUNCH(KK_BEGIN_NEW, k_begin_new<<<(tot + 255) / 256, 256, 0, st>>>(s.W, s.c, s.D, b.K_old, n_new, R));
     }
-    int n_xn = 0;
-    if (N > 0) {
-        LAUNCH(KK_ROWMAP, k_rowmap<<<(N + 255) / 256, 256, 0, st>>>(b));
-        n_xn = (int)((N + XV_ROWS - 1) / XV_ROWS);
-        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, N, J, R, (const T *)m->VT, (T *)m->P, m->xn_part));
+    // fused row kernel over the tiles of single-segment slices
+    int g_f = 0;
+    if constexpr (std::is_same<T, float>::value && std::is_same<TI, float>::value) {
+        if (m->n_tiles > 0) {
+            LAUNCH(KK_VTILDE, k_vtilde<<<(J + 7) / 8, 256, 0, st>>>(s.V, s.GamP, s.Gam, J, R, m->Vt, m->Gdf));
+            g_f = std::min(m->n_sm, m->n_tiles);
+            FusedArgs fa;
+            fa.X = X;
+            fa.J = J;
+            fa.R = R;
+            fa.lam = lam;
+            fa.rtol = m->rtol;
+            fa.Vt = m->Vt;
+            fa.Gdf = m->Gdf;
+            fa.Gam = s.Gam;
+            fa.gam_ok = s.gam_ok;
+            fa.n_tiles = m->n_tiles;
+            fa.tile_s0 = m->d_tile_s0;
+            fa.tile_s1 = m->d_tile_s1;
+            fa.seg_row = b.seg_row;
+            fa.seg_slice = b.seg_slice;
+            fa.W = s.W;
+            fa.c = reinterpret_cast<df *>(s.c);
+            fa.D = reinterpret_cast<df *>(s.D);
+            fa.U = (float *)m->U;
+            fa.Fslot = (float *)m->Fpart;
+            fa.Gpart = m->Gpart;
+            fa.xn_part = m->xn_part;
+            fa.wsp = m->wsp;
+            fa.err = m->d_err;
+            const size_t smem = fu_smem_bytes(J);
+            CK(cudaFuncSetAttribute(k_rows_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            LAUNCH(KK_ROWS_FUSED, k_rows_fused<<<g_f, FU_THREADS, smem, st>>>(fa));
+        }
     }
-    // per-slice work
+    int n_xn = 0;
+    if (Ng > 0) {
+        LAUNCH(KK_ROWMAP, k_rowmap<<<(N + 255) / 256, 256, 0, st>>>(b));
+        n_xn = (int)((Ng + XV_ROWS - 1) / XV_ROWS);
+        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, b, J, R, (const T *)m->VT, (T *)m->P,
+                                                        m->xn_part + g_f));
+    }
+    // per-slice work for slices the fused kernel did not finish
     const int nw = sl_warps(R);
     const size_t smem = (size_t)nw * sl_warp_doubles(R) * 8;
     int nsb = (int)std::min<int64_t>((b.K_all + nw - 1) / nw, kSliceBlocksMax);
     if (nsb < 1) nsb = 1;
-    CK(cudaFuncSetAttribute(k_slices<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    LAUNCH(KK_SLICES, k_slices<T><<<nsb, 32 * nw, smem, st>>>(b, s, (const T *)m->P, (T *)m->U, m->Gpart));
-    // F partials
+    CK(cudaFuncSetAttribute(k_slices<T, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LAUNCH(KK_SLICES, k_slices<T, DF><<<nsb, 32 * nw, smem, st>>>(b, s, (const T *)m->P, (T *)m->U,
+                                                                  m->Gpart + (size_t)g_f * R * R));
+    // F partials of the general rows
     int nfb = 0;
-    if (N > 0) {
+    if (Ng > 0) {
         const int nby = (J + F_JB - 1) / F_JB;
-        nfb = (int)std::min<int64_t>(std::max<int64_t>(1, (2 * 152 * 4) / nby), (N + F_RC - 1) / F_RC);
-        nfb = std::min(nfb, m->n_fb_max);
-        int64_t rpc = (N + nfb - 1) / nfb;
+        nfb = (int)std::min<int64_t>(std::max<int64_t>(1, (2 * 152 * 4) / nby), (Ng + F_RC - 1) / F_RC);
+        nfb = std::min(nfb, kFBlocksMax);
+        int64_t rpc = (Ng + nfb - 1) / nfb;
         rpc = (rpc + F_RC - 1) / F_RC * F_RC;
-        nfb = (int)((N + rpc - 1) / rpc);
+        nfb = (int)((Ng + rpc - 1) / rpc);
         dim3 grid(nfb, nby);
-        LAUNCH(KK_F, k_f<TI, T><<<grid, 256, 0, st>>>(X, b, J, R, (const T *)m->U, s.W, rpc, (T *)m->Fpart));
+        LAUNCH(KK_F, k_f<TI, T><<<grid, 256, 0, st>>>(X, b, J, R, (const T *)m->U, s.W, rpc,
+                                                     (T *)m->Fpart + (size_t)g_f * J * R));
     }
-    LAUNCH(KK_F_REDUCE, k_f_reduce<T><<<((int64_t)J * R + 255) / 256, 256, 0, st>>>((const T *)m->Fpart, nfb, J, R, lam,
+    LAUNCH(KK_F_REDUCE, k_f_reduce<T><<<((int64_t)J * R + 255) / 256, 256, 0, st>>>((const T *)m->Fpart, g_f + nfb, J, R, lam,
                                                                 s.F, m->Finc));
-    LAUNCH(KK_G_REDUCE, k_g_reduce<<<(R * R + 7) / 8, 256, 0, st>>>(m->Gpart, nsb, R, lam, s.G, m->Ginc));
+    LAUNCH(KK_G_REDUCE, k_g_reduce<<<(R * R + 7) / 8, 256, 0, st>>>(m->Gpart, g_f + nsb, R, lam, s.G, m->Ginc));
     const size_t psm = (size_t)(3 * R * (R + 1) + (R + 1)) * 8;
     LAUNCH(KK_PINV, k_pinv_small<<<1, 32, psm, st>>>(s.G, R, m->rtol, m->GP, nullptr));
     LAUNCH(KK_VUPDATE, k_vupdate<T><<<(J + 7) / 8, 256, 0, st>>>(s.F, m->GP, m->Finc, J, R, s.V, (T *)m->VT,
                                                m->cross_part));
     LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(s.V, J, R, s.Gam));
     LAUNCH(KK_PINV, k_pinv_small<<<1, 32, psm, st>>>(s.Gam, R, m->rtol, s.GamP, s.gam_ok));
-    LAUNCH(KK_FITNESS, k_fitness<<<1, 32, 0, st>>>(m->xn_part, n_xn, m->cross_part, (J + 7) / 8, s.Gam, m->Ginc, R,
-                                m->fit));
-    CK(cudaMemcpyAsync(m->h_fit, m->fit, 3 * 8, cudaMemcpyDeviceToHost, st));
+    LAUNCH(KK_FITNESS, k_fitness<<<1, 32, 0, st>>>(m->xn_part, g_f + n_xn, m->cross_part, (J + 7) / 8, s.Gam, m->Ginc, R,
+                                s.gam_ok, m->fit));
+    CK(cudaMemcpyAsync(m->h_fit, m->fit, 4 * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(m->h_err, m->d_err, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     return DASH_OK;
 }
 
 template <typename TI, typename T>
-static dash_status launch_recompute_c(dash_model *m, const BatchDev &b, const void *Xv) {
+static dash_status launch_recompute_c(dash_model *m, const BatchDev &b0, const void *Xv) {
     const int J = m->cfg.J, R = m->cfg.R;
+    constexpr bool DF = std::is_same<T, float>::value;
+    const BatchDev &b = b0;     // planned without fused tiles: every row is general
     if (b.N > 0) {
         const int n_xn = (int)((b.N + XV_ROWS - 1) / XV_ROWS);
-        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, m->stream>>>((const TI *)Xv, b.N, J, R, (const T *)m->VT,
+        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, m->stream>>>((const TI *)Xv, b, J, R, (const T *)m->VT,
                                                   (T *)m->P, m->xn_part));
     }
     const int nb = (b.K_all + 7) / 8;
-    LAUNCH(KK_C_RECOMPUTE, k_c_recompute<T><<<nb > 0 ? nb : 1, 256, 0, m->stream>>>(b, (const T *)m->P, (const T *)m->U, R,
+    LAUNCH(KK_C_RECOMPUTE, k_c_recompute<T, DF><<<nb > 0 ? nb : 1, 256, 0, m->stream>>>(b, (const T *)m->P, (const T *)m->U, R,
                                                             m->st.c));
     return DASH_OK;
 }
@@ -753,7 +931,7 @@ static dash_status update_common(dash_model *m, int64_t n_seg, const int64_t *id
     if (m->broken) return fail(m, DASH_ESTATE, "model is unusable after a CUDA error");
     if (m->prof.pending.size() > 8192) prof_collect(m);
     BatchDev b;
-    dash_status s = plan_batch(m, n_seg, ids, rp, m->K, n_new, &b);
+    dash_status s = plan_batch(m, n_seg, ids, rp, m->K, n_new, X, true, &b);
     if (s) return s;
     CK(cudaEventRecord(m->ev0, m->stream));
     s = run_update(m, b, X, m->cfg.lambda, true);
@@ -805,7 +983,7 @@ static dash_status fit_common(dash_model *m, int64_t n_seg, const int64_t *ids,
         if (ids[s] < 0 || ids[s] >= n_new)
             return fail(m, DASH_EINVAL, "fit_initial takes new slices only");
     BatchDev b;
-    dash_status s = plan_batch(m, n_seg, ids, rp, 0, n_new, &b);
+    dash_status s = plan_batch(m, n_seg, ids, rp, 0, n_new, X, true, &b);
     if (s) return s;
     CK(cudaEventRecord(m->ev0, m->stream));
     // iteration 1: the slices are new (S_k = I); later iterations: the same
@@ -817,8 +995,11 @@ static dash_status fit_common(dash_model *m, int64_t n_seg, const int64_t *ids,
         s = run_update(m, bi, X, 0.0, it == 0);
         if (s) return s;
     }
-    // c_k = vec(X_k)ᵀ(V ⊙ U_k) with the final V (Eq. 6)
-    s = recompute_c(m, b, X);
+    // c_k = vec(X_k)ᵀ(V ⊙ U_k) with the final V (Eq. 6), over every row
+    BatchDev ball;
+    s = plan_batch(m, n_seg, ids, rp, 0, n_new, X, false, &ball);
+    if (s) return s;
+    s = recompute_c(m, ball, X);
     if (s) return s;
     CK(cudaEventRecord(m->ev1, m->stream));
     m->K = n_new;

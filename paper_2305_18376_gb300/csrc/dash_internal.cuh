@@ -6,17 +6,20 @@
 #include <vector>
 
 #include "dash.h"
+#include "dash_kernels_fused.cuh"
 #include "dash_kernels_p.cuh"
 
 namespace dash {
 // kernel kinds for the per-kernel profiler
 enum KernelKind {
     KK_BEGIN_NEW, KK_ROWMAP, KK_XV, KK_SLICES, KK_F, KK_F_REDUCE, KK_G_REDUCE, KK_PINV,
-    KK_VUPDATE, KK_GAMMA, KK_FITNESS, KK_CAST, KK_C_RECOMPUTE, KK_COUNT
+    KK_VUPDATE, KK_GAMMA, KK_FITNESS, KK_CAST, KK_C_RECOMPUTE, KK_VTILDE, KK_ROWS_FUSED,
+    KK_COUNT
 };
 static const char *const kKernelNames[KK_COUNT] = {
     "k_begin_new", "k_rowmap", "k_xv", "k_slices", "k_f", "k_f_reduce", "k_g_reduce",
-    "k_pinv_small", "k_vupdate", "k_gamma", "k_fitness", "k_cast", "k_c_recompute"};
+    "k_pinv_small", "k_vupdate", "k_gamma", "k_fitness", "k_cast", "k_c_recompute",
+    "k_vtilde", "k_rows_fused"};
 
 struct Profiler {
     bool on = false;
@@ -41,6 +44,10 @@ struct dash_model {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double rtol = 0.0;
     size_t tsize = 4;                 // bytes of the product arithmetic type
+    bool df_state = false;            // c, D stored as double-float pairs
+    bool fused_ok = false;            // shapes the fused row kernel supports
+    int n_sm = 1;
+    bool gam_ok_host = false;         // mirror of the device flag (Γ nonsingular)
     int64_t K = 0;                    // slices in the model
     bool v_set = false;
 
@@ -65,6 +72,18 @@ struct dash_model {
     int *h_seg_slice = nullptr, *h_tslot = nullptr, *h_tseg_ptr = nullptr, *h_tseg_idx = nullptr;
     int64_t *h_seg_row = nullptr;
     double *h_fit = nullptr;
+
+    // fused row kernel: tiles of single-segment slices, Ṽ, Γ (double-float)
+    int *d_tile_s0 = nullptr, *d_tile_s1 = nullptr;
+    int *h_tile_s0 = nullptr, *h_tile_s1 = nullptr;
+    int n_tiles = 0;
+    float *Vt = nullptr;
+    dash::df *Gdf = nullptr;
+    double *wsp = nullptr;
+    int *d_err = nullptr, *h_err = nullptr;
+    // general rows: runs of consecutive rows left to the general kernels
+    int64_t *d_run_g0 = nullptr, *d_run_row0 = nullptr;
+    int64_t *h_run_g0 = nullptr, *h_run_row0 = nullptr;
 
     // scratch
     void *P = nullptr, *U = nullptr;

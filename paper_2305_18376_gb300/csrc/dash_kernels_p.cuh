@@ -18,9 +18,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df.cuh"
 #include "small_linalg.cuh"
 
 namespace dash {
+
+// Per-slice summaries c_k, D_k are stored as FP64 (FP64 path) or as
+// double-float pairs (mixed path); both are 8 bytes per entry.
+template <bool DF> struct Summ;
+template <> struct Summ<false> {
+    static __device__ __forceinline__ double ld(const double *p, int64_t i) { return p[i]; }
+    static __device__ __forceinline__ void st(double *p, int64_t i, double v) { p[i] = v; }
+};
+template <> struct Summ<true> {
+    static __device__ __forceinline__ double ld(const double *p, int64_t i) {
+        return df_to_double(reinterpret_cast<const df *>(p)[i]);
+    }
+    static __device__ __forceinline__ void st(double *p, int64_t i, double v) {
+        reinterpret_cast<df *>(p)[i] = df_from_double(v);
+    }
+};
 
 // Device view of one update's batch (built on the host from the staged
 // segments).  Segment s covers rows seg_row[s]..seg_row[s+1]-1 of X.
@@ -36,7 +53,23 @@ struct BatchDev {
     const int *tseg_ptr;    // [n_touch + 1]
     const int *tseg_idx;    // segments of each touched slice, in batch order
     int *row_slice;         // [N] filled by k_rowmap
+    // rows handled by the general kernels: n_runs runs of consecutive rows;
+    // general row g lives at run_row0[r] + (g - run_g0[r]) for the run r
+    // with run_g0[r] <= g < run_g0[r+1]
+    int n_runs;
+    int64_t N_gen;
+    const int64_t *run_g0;  // [n_runs + 1]
+    const int64_t *run_row0;// [n_runs]
 };
+
+__device__ __forceinline__ int64_t gen_row(const BatchDev &b, int64_t g) {
+    int lo = 0, hi = b.n_runs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.run_g0[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return b.run_row0[lo] + (g - b.run_g0[lo]);
+}
 
 // Model state on the device (FP64 master copies).
 struct StateDev {
@@ -93,14 +126,18 @@ constexpr int XV_ROWS = 64;
 constexpr int XV_KC = 32;
 
 template <typename TI, typename T>
-__global__ void __launch_bounds__(256) k_xv(const TI *__restrict__ X, int64_t N, int J, int R,
+__global__ void __launch_bounds__(256) k_xv(const TI *__restrict__ X, BatchDev b, int J, int R,
                                             const T *__restrict__ VT, T *__restrict__ P,
                                             double *__restrict__ xn_part) {
     __shared__ T Xs[XV_ROWS][XV_KC + 1];
     __shared__ T Vs[XV_KC][kMaxR];
     __shared__ double red[8];
+    __shared__ int64_t rows_s[XV_ROWS];
     const int tid = threadIdx.x;
-    const int64_t row0 = (int64_t)blockIdx.x * XV_ROWS;
+    const int64_t N = b.N_gen;
+    const int64_t row0 = (int64_t)blockIdx.x * XV_ROWS;   // general row index
+    if (tid < XV_ROWS) rows_s[tid] = (row0 + tid < N) ? gen_row(b, row0 + tid) : -1;
+    __syncthreads();
     const int ri = tid >> 2;
     const int cg = tid & 3;
     T acc[16];
@@ -111,9 +148,9 @@ __global__ void __launch_bounds__(256) k_xv(const TI *__restrict__ X, int64_t N,
         __syncthreads();
         for (int e = tid; e < XV_ROWS * XV_KC; e += 256) {
             const int r = e / XV_KC, jj = e % XV_KC;
-            const int64_t row = row0 + r;
+            const int64_t row = rows_s[r];
             T v = T(0);
-            if (row < N && j0 + jj < J) {
+            if (row >= 0 && j0 + jj < J) {
                 const TI x = X[row * J + j0 + jj];
                 v = (T)x;
                 xn += (double)x * (double)x;
@@ -135,8 +172,8 @@ __global__ void __launch_bounds__(256) k_xv(const TI *__restrict__ X, int64_t N,
             }
         }
     }
-    const int64_t row = row0 + ri;
-    if (row < N) {
+    const int64_t row = rows_s[ri];
+    if (row >= 0) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int r = cg + 4 * q;
@@ -175,7 +212,7 @@ __host__ inline int sl_warps(int R) {
     return nw < 1 ? 1 : (nw > 4 ? 4 : nw);
 }
 
-template <typename T>
+template <typename T, bool DF>
 __global__ void __launch_bounds__(128) k_slices(BatchDev b, StateDev s,
                                                const T *__restrict__ P,
                                                T *__restrict__ U,
@@ -202,6 +239,7 @@ __global__ void __launch_bounds__(128) k_slices(BatchDev b, StateDev s,
     for (int k = blockIdx.x * nw + wid; k < b.K_all; k += total_warps) {
         __syncwarp();
         const int t = b.tslot[k];
+        if (t == -2) continue;                 // finished by the fused row kernel
         const double *Wk = s.W + (int64_t)k * R;
         double *ck = s.c + (int64_t)k * R;
         double *Dk = s.D + (int64_t)k * R * R;
@@ -284,14 +322,14 @@ __global__ void __launch_bounds__(128) k_slices(BatchDev b, StateDev s,
         }
         // ---- c_k, D_k with λ (Eqs. 15, 16), written back -------------------
         for (int i = lane; i < R; i += 32) {
-            const double v = lam_scale(s.lam, ck[i]) + dc[i];
+            const double v = lam_scale(s.lam, Summ<DF>::ld(ck, i)) + dc[i];
             cv[i] = v;
-            ck[i] = v;
+            Summ<DF>::st(ck, i, v);
         }
         for (int i = lane; i < R * R; i += 32) {
             const int r = i / R, q = i % R;
-            const double v = lam_scale(s.lam, Dk[i]) + DD[r * ld + q];
-            Dk[i] = v;
+            const double v = lam_scale(s.lam, Summ<DF>::ld(Dk, i)) + DD[r * ld + q];
+            Summ<DF>::st(Dk, i, v);
             A[r * ld + q] = s.Gam[i] * v;               // Γ ∗ D_k
         }
         __syncwarp();
@@ -334,27 +372,31 @@ __global__ void __launch_bounds__(256) k_f(const TI *__restrict__ X, BatchDev b,
                                            int64_t rows_per_chunk, T *__restrict__ Fpart) {
     __shared__ T Xs[F_RC][F_JB + 1];
     __shared__ T Us[F_RC][kMaxR];
+    __shared__ int64_t rows_s[F_RC];
     const int tid = threadIdx.x;
     const int jj = tid % F_JB, rg = tid / F_JB;
     const int j0 = blockIdx.y * F_JB;
-    const int64_t rbeg = (int64_t)blockIdx.x * rows_per_chunk;
-    const int64_t rend = (b.N < rbeg + rows_per_chunk) ? b.N : rbeg + rows_per_chunk;
+    const int64_t rbeg = (int64_t)blockIdx.x * rows_per_chunk;     // general row indices
+    const int64_t rend = (b.N_gen < rbeg + rows_per_chunk) ? b.N_gen : rbeg + rows_per_chunk;
     T acc[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = T(0);
     for (int64_t c0 = rbeg; c0 < rend; c0 += F_RC) {
         const int nr = (int)(rend - c0 < F_RC ? rend - c0 : F_RC);
         __syncthreads();
+        if (tid < F_RC) rows_s[tid] = tid < nr ? gen_row(b, c0 + tid) : 0;
+        __syncthreads();
         for (int e = tid; e < F_RC * F_JB; e += 256) {
             const int i = e / F_JB, j = e % F_JB;
-            Xs[i][j] = (i < nr && j0 + j < J) ? (T)X[(c0 + i) * J + j0 + j] : T(0);
+            Xs[i][j] = (i < nr && j0 + j < J) ? (T)X[rows_s[i] * J + j0 + j] : T(0);
         }
         for (int e = tid; e < F_RC * R; e += 256) {
             const int i = e / R, r = e % R;
             T v = T(0);
             if (i < nr) {
-                const int k = b.row_slice[c0 + i];
-                v = U[(c0 + i) * R + r] * (T)W[(int64_t)k * R + r];
+                const int64_t row = rows_s[i];
+                const int k = b.row_slice[row];
+                v = U[row * R + r] * (T)W[(int64_t)k * R + r];
             }
             Us[i][r] = v;
         }
@@ -480,7 +522,8 @@ __global__ void k_cast(const double *__restrict__ in, T *__restrict__ out, int64
 __global__ void k_fitness(const double *__restrict__ xn_part, int n_xn,
                           const double *__restrict__ cross_part, int n_cross,
                           const double *__restrict__ Gam, const double *__restrict__ Ginc,
-                          int R, double *__restrict__ out /* [fit, xnorm2, resid2] */) {
+                          int R, const int *__restrict__ gam_ok,
+                          double *__restrict__ out /* [fit, xnorm2, resid2, gam_ok] */) {
     const int lane = threadIdx.x & 31;
     double xn = 0.0, cr = 0.0, qd = 0.0;
     for (int i = lane; i < n_xn; i += 32) xn += xn_part[i];
@@ -494,12 +537,13 @@ __global__ void k_fitness(const double *__restrict__ xn_part, int n_xn,
         out[0] = xn > 0.0 ? 1.0 - sqrt(res / xn) : 1.0;
         out[1] = xn;
         out[2] = res;
+        out[3] = (double)*gam_ok;
     }
 }
 
 // Eq. 6 after the static fit: c_k = vec(X_k)ᵀ(V ⊙ U_k) = Σ_i U(i,:) ∘ P(i,:)
 // with P = X V for the final V; one warp per touched slice, lanes over r.
-template <typename T>
+template <typename T, bool DF>
 __global__ void k_c_recompute(BatchDev b, const T *__restrict__ P, const T *__restrict__ U, int R,
                               double *__restrict__ c) {
     const int lane = threadIdx.x & 31;
@@ -516,7 +560,7 @@ __global__ void k_c_recompute(BatchDev b, const T *__restrict__ P, const T *__re
                         a += (double)U[i * R + r] * (double)P[i * R + r];
                 }
             }
-            c[(int64_t)k * R + r] = a;
+            Summ<DF>::st(c, (int64_t)k * R + r, a);
         }
     }
 }
