@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c4")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--precision", default="f16x3", choices=["fp32", "f16x3"])
     ap.add_argument("--init-iters", type=int, default=3)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -306,6 +306,7 @@ def run_ours(a):
     barrier()
     clocks = sampler.stop()
     launches = m.launch_count() - l0
+    timeouts, fallbacks = m.counters()
     prof = m.profile_report()
     m.profile(False)
     elapsed = e_start.elapsed_time(e_end) / 1e3
@@ -430,7 +431,7 @@ def run_ours(a):
             "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_max / len(timed),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if a.precision == "fp32" else "bf16x3",
+            "dtype": "f32" if a.precision == "fp32" else "f16x3",
             "data": "synthetic", "config": workload_config(w, a),
             "latency": {"p50_ms": statistics.median(lat), "p99_ms": lat[-1]},
             "rows_per_step": Nm, "slices": K_all,
@@ -442,6 +443,7 @@ def run_ours(a):
                               "unit": "GB/s", "frac": sb / (t_max / len(timed)) / 1e9 / pk["hbm_gbs"]},
             "kernels": kernels, "cpu_baseline": cpu, "clocks": clocks,
             "init_seconds": init_s, "src_sha": src_hash(),
+            "diagnostics": {"wait_timeouts": timeouts, "fp64_fallback_solves": fallbacks},
         }
         print(json.dumps(line), flush=True)
         if a.profile_out:

@@ -57,7 +57,7 @@ enum { DASH_MODE_P = 0, DASH_MODE_Q = 1 };
 enum {
     DASH_PREC_FP64 = 0,  /* FP64 products                                      */
     DASH_PREC_FP32 = 1,  /* FP32 products, FP32 accumulation                   */
-    DASH_PREC_BF16X3 = 2 /* tensor cores: BF16 hi/lo split, 3 products, FP32 acc */
+    DASH_PREC_F16X3 = 2  /* tensor cores: FP16 hi/lo split, 3 products, FP32 acc  */
 };
 
 enum { DASH_F64 = 0, DASH_F32 = 1 };        /* element type of staged X   */
@@ -210,6 +210,12 @@ dash_status dash_last_update_ms(const dash_model *m, float *ms);
  * launches and the total milliseconds since profiling was enabled; it
  * synchronises the stream.  *name points to static storage. */
 int64_t dash_launch_count(const dash_model *m);
+
+/* Numerical diagnostics since dash_init: bounded device waits that timed out,
+ * and per-slice solves that left the mixed-precision fast path (a singular
+ * map in Lemma 1 or an FP32 factor that was not trustworthy) for the FP64
+ * pseudo-inverse.  Synchronises the stream. */
+dash_status dash_counters(const dash_model *m, int64_t *timeouts, int64_t *fallbacks);
 dash_status dash_profile_enable(dash_model *m, int32_t on);
 int32_t dash_profile_kinds(void);
 dash_status dash_profile_get(const dash_model *m, int32_t i, const char **name,

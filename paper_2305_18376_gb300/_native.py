@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdash_gb300.so")
 
 DASH_MODE_P, DASH_MODE_Q = 0, 1
-PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2}
+PREC = {"fp64": 0, "fp32": 1, "f16x3": 2}
 DTYPE = {"f64": 0, "f32": 1}
 HOST, DEVICE = 0, 1
 
@@ -72,6 +72,7 @@ SIGNATURES = [
     ("dash_profile_kinds", I32, []),
     ("dash_profile_get", C.c_int, [P, I32, C.POINTER(C.c_char_p), PI64, PD]),
     ("dash_f_increment_noalloc", C.c_int, [P, P, I64, I32, I32, P, P, I64, P, P, P]),
+    ("dash_counters", C.c_int, [P, PI64, PI64]),
 ]
 
 
@@ -197,6 +198,12 @@ class DashModel:
         ms = C.c_float()
         self._ck(self._lib.dash_last_update_ms(self._h, C.byref(ms)))
         return ms.value
+
+    def counters(self):
+        """(wait timeouts, FP64 fallback solves) since the model was created."""
+        a, b = C.c_int64(), C.c_int64()
+        self._ck(self._lib.dash_counters(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def launch_count(self) -> int:
         return int(self._lib.dash_launch_count(self._h))

@@ -80,6 +80,17 @@ static void prof_collect(dash_model *m) {
         m->prof.pool.push_back(mk.b);
     }
     m->prof.pending.clear();
+    if (m->prof.d_phase) {
+        unsigned long long c[3] = {0, 0, 0};
+        if (cudaMemcpy(c, m->prof.d_phase, sizeof c, cudaMemcpyDeviceToHost) == cudaSuccess) {
+            // average per SM, in milliseconds at the device clock
+            for (int i = 0; i < 3; ++i) {
+                m->prof.ms[KK_PH_A + i] += (double)c[i] / m->prof.n_sm / m->prof.clock_khz;
+                if (c[i]) m->prof.launches[KK_PH_A + i] += 1;
+            }
+            cudaMemset(m->prof.d_phase, 0, sizeof c);
+        }
+    }
     cudaGetLastError();
 }
 
@@ -108,6 +119,20 @@ extern "C" int64_t dash_launch_count(const dash_model *m) {
 
 extern "C" dash_status dash_profile_enable(dash_model *m, int32_t on) {
     if (!m) return DASH_EINVAL;
+    if (!m->prof.d_phase) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, 3 * sizeof(unsigned long long)) == cudaSuccess) {
+            m->prof.d_phase = (unsigned long long *)p;
+            m->allocs.push_back(p);
+            cudaMemset(p, 0, 3 * sizeof(unsigned long long));
+            int dev = 0, khz = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+            m->prof.clock_khz = khz > 0 ? khz : 1.0;
+            m->prof.n_sm = m->n_sm;
+        }
+        cudaGetLastError();
+    }
     prof_collect(m);
     m->prof.on = on != 0;
     for (int i = 0; i < KK_COUNT; ++i) {
@@ -118,6 +143,17 @@ extern "C" dash_status dash_profile_enable(dash_model *m, int32_t on) {
 }
 
 extern "C" int32_t dash_profile_kinds(void) { return KK_COUNT; }
+
+extern "C" dash_status dash_counters(const dash_model *mc, int64_t *timeouts, int64_t *fallbacks) {
+    dash_model *m = const_cast<dash_model *>(mc);
+    if (!m) return DASH_EINVAL;
+    int h[4] = {0, 0, 0, 0};
+    CK(cudaStreamSynchronize(m->stream));
+    CK(cudaMemcpy(h, m->d_err, sizeof h, cudaMemcpyDeviceToHost));
+    if (timeouts) *timeouts = h[0];
+    if (fallbacks) *fallbacks = h[1];
+    return DASH_OK;
+}
 
 extern "C" dash_status dash_profile_get(const dash_model *mc, int32_t i, const char **name,
                                         int64_t *launches, double *total_ms) {
@@ -251,10 +287,21 @@ static dash_status init_alloc(dash_model *m) {
     // fused row kernel and general runs
     DALLOC(m->d_tile_s0, (Sm + 1) * 4, "tiles");
     DALLOC(m->d_tile_s1, (Sm + 1) * 4, "tiles");
-    DALLOC(m->Vt, J * R * 4, "V Gamma+");
+    DALLOC(m->GPf, R * R * 4, "R_V^-T (FP32)");
+    DALLOC(m->RV, R * R * 8, "R_V");
+    DALLOC(m->Linv, R * R * 8, "R_V^-T");
+    DALLOC(m->QV, J * R * 4, "Q_V");
     DALLOC(m->Gdf, R * R * 8, "Gamma (double-float)");
-    DALLOC(m->wsp, (size_t)m->n_sm * FU_WARPS * fu_wsp_doubles((int)R) * 8, "fallback workspace");
+    // FP64 fallback workspace: one slot per warp of a grid of at most 2 CTAs per SM
+    DALLOC(m->wsp, (size_t)2 * m->n_sm * FU_WARPS * fu_wsp_doubles((int)R) * 8, "fallback workspace");
     DALLOC(m->d_err, 4 * sizeof(int), "error counters");
+    m->max_chunks = Nm / FU_TILE_MAX + Sm + 1;
+    DALLOC(m->d_ch_row0, m->max_chunks * 8, "chunks");
+    DALLOC(m->d_ch_n, m->max_chunks * 4, "chunks");
+    DALLOC(m->d_ch_k, m->max_chunks * 4, "chunks");
+    DALLOC(m->d_fin_k, Km * 4, "finish list");
+    DALLOC(m->d_fin_c0, (Km + 1) * 4, "finish list");
+    DALLOC(m->dpart, (size_t)m->max_chunks * (R * R + R) * 4, "chunk partials");
     DALLOC(m->d_run_g0, (Sm + 2) * 8, "general runs");
     DALLOC(m->d_run_row0, (Sm + 2) * 8, "general runs");
 
@@ -271,6 +318,11 @@ static dash_status init_alloc(dash_model *m) {
     if ((s = halloc(m, (void **)&m->h_run_g0, (Sm + 2) * 8))) return s;
     if ((s = halloc(m, (void **)&m->h_run_row0, (Sm + 2) * 8))) return s;
     if ((s = halloc(m, (void **)&m->h_err, 4 * sizeof(int)))) return s;
+    if ((s = halloc(m, (void **)&m->h_ch_row0, m->max_chunks * 8))) return s;
+    if ((s = halloc(m, (void **)&m->h_ch_n, m->max_chunks * 4))) return s;
+    if ((s = halloc(m, (void **)&m->h_ch_k, m->max_chunks * 4))) return s;
+    if ((s = halloc(m, (void **)&m->h_fin_k, Km * 4))) return s;
+    if ((s = halloc(m, (void **)&m->h_fin_c0, (Km + 1) * 4))) return s;
     memset(m->h_err, 0, 4 * sizeof(int));
     cudaMemsetAsync(m->d_err, 0, 4 * sizeof(int), m->stream);
     return DASH_OK;
@@ -292,7 +344,7 @@ extern "C" dash_status dash_init(const dash_config *cfg, dash_model **out) {
     else if (!(c.lambda > 0.0 && c.lambda <= 1.0)) st = bad("lambda must be in (0, 1]");
     else if (c.mode != DASH_MODE_P && c.mode != DASH_MODE_Q) st = bad("unknown mode");
     else if (c.precision != DASH_PREC_FP64 && c.precision != DASH_PREC_FP32 &&
-             c.precision != DASH_PREC_BF16X3) st = bad("unknown precision");
+             c.precision != DASH_PREC_F16X3) st = bad("unknown precision");
     else if (c.input_dtype != DASH_F64 && c.input_dtype != DASH_F32) st = bad("unknown input dtype");
     else if (c.n_sweeps != 1) st = bad("only n_sweeps = 1 is supported");
     else if (c.max_slices < 1 || c.max_rows < 1 || c.max_segments < 1) st = bad("capacities must be positive");
@@ -693,6 +745,7 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
         for (int64_t s = 0; s < n_seg; ++s)
             fz[s] = cnt[tslot[ids[s]]] == 1 && rp[s + 1] - rp[s] <= FU_TILE_MAX;
     }
+    m->fused_active = fused;
     // renumber touched slots in ascending slice order (fixed reduction order);
     // slices finished by the fused kernel get -2
     {
@@ -724,6 +777,45 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
         const int t = tslot[ids[s]];
         if (t >= 0) m->h_tseg_idx[fillp[t]++] = (int)s;
         m->h_seg_slice[s] = (int)ids[s];
+    }
+    // fused path: the remaining touched slices are split into chunks, and
+    // every slice not finished by a tile (chunked or untouched) gets a finish entry
+    m->n_chunks = 0;
+    m->n_fin = 0;
+    if (fused) {
+        int nc = 0, nf = 0;
+        for (int64_t k = 0; k < K_all; ++k) {
+            const int t = tslot[k];
+            if (t < 0) continue;
+            m->h_fin_k[nf] = (int)k;
+            m->h_fin_c0[nf] = nc;
+            ++nf;
+            for (int q = tp[t]; q < tp[t + 1]; ++q) {
+                const int sg = m->h_tseg_idx[q];
+                for (int64_t r = rp[sg]; r < rp[sg + 1]; r += FU_TILE_MAX) {
+                    m->h_ch_row0[nc] = r;
+                    m->h_ch_n[nc] = (int)std::min<int64_t>(FU_TILE_MAX, rp[sg + 1] - r);
+                    m->h_ch_k[nc] = (int)k;
+                    ++nc;
+                }
+            }
+        }
+        for (int64_t k = 0; k < K_all; ++k) {
+            if (tslot[k] != -1) continue;
+            m->h_fin_k[nf] = (int)k;
+            m->h_fin_c0[nf] = nc;
+            ++nf;
+        }
+        m->h_fin_c0[nf] = nc;
+        m->n_chunks = nc;
+        m->n_fin = nf;
+        if (nc > 0) {
+            CK(cudaMemcpyAsync(m->d_ch_row0, m->h_ch_row0, nc * 8, cudaMemcpyHostToDevice, m->stream));
+            CK(cudaMemcpyAsync(m->d_ch_n, m->h_ch_n, nc * 4, cudaMemcpyHostToDevice, m->stream));
+            CK(cudaMemcpyAsync(m->d_ch_k, m->h_ch_k, nc * 4, cudaMemcpyHostToDevice, m->stream));
+        }
+        if (nf > 0) CK(cudaMemcpyAsync(m->d_fin_k, m->h_fin_k, nf * 4, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->d_fin_c0, m->h_fin_c0, (nf + 1) * 4, cudaMemcpyHostToDevice, m->stream));
     }
     for (int64_t s = 0; s <= n_seg; ++s) m->h_seg_row[s] = rp[s];
     // tiles: runs of consecutive fused segments with <= FU_TILE_MAX rows
@@ -814,8 +906,13 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     // fused row kernel over the tiles of single-segment slices
     int g_f = 0;
     if constexpr (std::is_same<T, float>::value && std::is_same<TI, float>::value) {
-        if (m->n_tiles > 0) {
-            LAUNCH(KK_VTILDE, k_vtilde<<<(J + 7) / 8, 256, 0, st>>>(s.V, s.GamP, s.Gam, J, R, m->Vt, m->Gdf));
+        if (m->fused_active) {
+            const size_t qsm = (size_t)(2 * R * (R + 1) + R + 1) * 8;
+            LAUNCH(KK_VTILDE, k_vqr<<<1, 32, qsm, st>>>(s.Gam, R, m->rtol, m->RV, m->Linv, m->GPf,
+                                                        m->Gdf, s.gam_ok));
+            LAUNCH(KK_QV, k_qv<<<(J + 7) / 8, 256, 0, st>>>(s.V, m->Linv, J, R, m->QV));
+        }
+        if (m->fused_active && m->n_tiles > 0) {
             g_f = std::min(m->n_sm, m->n_tiles);
             FusedArgs fa;
             fa.X = X;
@@ -823,7 +920,9 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
             fa.R = R;
             fa.lam = lam;
             fa.rtol = m->rtol;
-            fa.Vt = m->Vt;
+            fa.V32 = m->QV;
+            fa.GPf = m->GPf;
+            fa.RV = m->RV;
             fa.Gdf = m->Gdf;
             fa.Gam = s.Gam;
             fa.gam_ok = s.gam_ok;
@@ -841,26 +940,82 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
             fa.xn_part = m->xn_part;
             fa.wsp = m->wsp;
             fa.err = m->d_err;
+            fa.phase_cycles = m->prof.on ? m->prof.d_phase : nullptr;
             const size_t smem = fu_smem_bytes(J);
-            CK(cudaFuncSetAttribute(k_rows_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            LAUNCH(KK_ROWS_FUSED, k_rows_fused<<<g_f, FU_THREADS, smem, st>>>(fa));
+            if (m->cfg.precision == DASH_PREC_F16X3) {
+                CK(cudaFuncSetAttribute(k_rows_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                LAUNCH(KK_ROWS_FUSED, k_rows_fused<true><<<g_f, FU_THREADS, smem, st>>>(fa));
+            } else {
+                CK(cudaFuncSetAttribute(k_rows_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                LAUNCH(KK_ROWS_FUSED, k_rows_fused<false><<<g_f, FU_THREADS, smem, st>>>(fa));
+            }
         }
     }
     int n_xn = 0;
+    // P = X V for the general kernels; P' = X Q_V for the chunked path
+    const T *Vmul = (const T *)m->VT;
+    if constexpr (std::is_same<T, float>::value) {
+        if (m->fused_active) Vmul = (const T *)m->QV;
+    }
     if (Ng > 0) {
         LAUNCH(KK_ROWMAP, k_rowmap<<<(N + 255) / 256, 256, 0, st>>>(b));
         n_xn = (int)((Ng + XV_ROWS - 1) / XV_ROWS);
-        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, b, J, R, (const T *)m->VT, (T *)m->P,
+        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, b, J, R, Vmul, (T *)m->P,
                                                         m->xn_part + g_f));
     }
-    // per-slice work for slices the fused kernel did not finish
-    const int nw = sl_warps(R);
-    const size_t smem = (size_t)nw * sl_warp_doubles(R) * 8;
-    int nsb = (int)std::min<int64_t>((b.K_all + nw - 1) / nw, kSliceBlocksMax);
-    if (nsb < 1) nsb = 1;
-    CK(cudaFuncSetAttribute(k_slices<T, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    LAUNCH(KK_SLICES, k_slices<T, DF><<<nsb, 32 * nw, smem, st>>>(b, s, (const T *)m->P, (T *)m->U,
-                                                                  m->Gpart + (size_t)g_f * R * R));
+    int nsb = 0;
+    bool finished = false;
+    if constexpr (std::is_same<T, float>::value && std::is_same<TI, float>::value) {
+        if (m->fused_active) {
+            // chunks of big / split slices, then every remaining slice's finish
+            FusedArgs fa{};
+            fa.J = J;
+            fa.R = R;
+            fa.lam = lam;
+            fa.rtol = m->rtol;
+            fa.Gdf = m->Gdf;
+            fa.GPf = m->GPf;
+            fa.RV = m->RV;
+            fa.Gam = s.Gam;
+            fa.gam_ok = s.gam_ok;
+            fa.W = s.W;
+            fa.c = reinterpret_cast<df *>(s.c);
+            fa.D = reinterpret_cast<df *>(s.D);
+            fa.U = (float *)m->U;
+            fa.wsp = m->wsp;
+            fa.err = m->d_err;
+            BigArgs bg{};
+            bg.Y = (const float *)m->P;
+            bg.ch_row0 = m->d_ch_row0;
+            bg.ch_n = m->d_ch_n;
+            bg.ch_k = m->d_ch_k;
+            bg.n_chunks = m->n_chunks;
+            bg.fin_k = m->d_fin_k;
+            bg.fin_c0 = m->d_fin_c0;
+            bg.n_fin = m->n_fin;
+            bg.dpart = m->dpart;
+            // both grids stay within the 2-CTAs-per-SM workspace (persistent warps)
+            if (m->n_chunks > 0) {
+                const int gb = std::min(2 * m->n_sm, (m->n_chunks + FU_WARPS - 1) / FU_WARPS);
+                LAUNCH(KK_BIG_B, k_big_b<<<gb, 256, 0, st>>>(fa, bg));
+            }
+            if (m->n_fin > 0) {
+                nsb = std::min(2 * m->n_sm, (m->n_fin + FU_WARPS - 1) / FU_WARPS);
+                LAUNCH(KK_BIG_C, k_big_c<<<nsb, 256, 0, st>>>(fa, bg, m->Gpart + (size_t)g_f * R * R));
+            }
+            finished = true;
+        }
+    }
+    if (!finished) {
+        // per-slice work for slices the fused kernel did not finish
+        const int nw = sl_warps(R);
+        const size_t smem = (size_t)nw * sl_warp_doubles(R) * 8;
+        nsb = (int)std::min<int64_t>((b.K_all + nw - 1) / nw, kSliceBlocksMax);
+        if (nsb < 1) nsb = 1;
+        CK(cudaFuncSetAttribute(k_slices<T, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LAUNCH(KK_SLICES, k_slices<T, DF><<<nsb, 32 * nw, smem, st>>>(b, s, (const T *)m->P, (T *)m->U,
+                                                                      m->Gpart + (size_t)g_f * R * R));
+    }
     // F partials of the general rows
     int nfb = 0;
     if (Ng > 0) {

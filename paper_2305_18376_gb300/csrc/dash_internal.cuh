@@ -14,12 +14,13 @@ namespace dash {
 enum KernelKind {
     KK_BEGIN_NEW, KK_ROWMAP, KK_XV, KK_SLICES, KK_F, KK_F_REDUCE, KK_G_REDUCE, KK_PINV,
     KK_VUPDATE, KK_GAMMA, KK_FITNESS, KK_CAST, KK_C_RECOMPUTE, KK_VTILDE, KK_ROWS_FUSED,
-    KK_COUNT
+    KK_BIG_B, KK_BIG_C, KK_QV, KK_PH_A, KK_PH_EPI, KK_PH_B, KK_COUNT
 };
 static const char *const kKernelNames[KK_COUNT] = {
     "k_begin_new", "k_rowmap", "k_xv", "k_slices", "k_f", "k_f_reduce", "k_g_reduce",
     "k_pinv_small", "k_vupdate", "k_gamma", "k_fitness", "k_cast", "k_c_recompute",
-    "k_vtilde", "k_rows_fused"};
+    "k_vqr", "k_rows_fused", "k_big_b", "k_big_c", "k_qv",
+    "k_rows_fused.phase_a", "k_rows_fused.epilogue", "k_rows_fused.phase_b"};
 
 struct Profiler {
     bool on = false;
@@ -29,6 +30,9 @@ struct Profiler {
     struct Mark { int kind; cudaEvent_t a, b; };
     std::vector<Mark> pending;
     std::vector<cudaEvent_t> pool;
+    unsigned long long *d_phase = nullptr;   // SM cycles per fused-kernel phase
+    double clock_khz = 1.0;
+    int n_sm = 1;
 };
 
 constexpr int kFBlocksMax = 1024;       // max row chunks of the F-partial kernel
@@ -77,10 +81,20 @@ struct dash_model {
     int *d_tile_s0 = nullptr, *d_tile_s1 = nullptr;
     int *h_tile_s0 = nullptr, *h_tile_s1 = nullptr;
     int n_tiles = 0;
-    float *Vt = nullptr;
+    float *GPf = nullptr;             // R_V⁻ᵀ in FP32 (V = Q_V R_V)
+    double *RV = nullptr, *Linv = nullptr;
+    float *QV = nullptr;
     dash::df *Gdf = nullptr;
     double *wsp = nullptr;
     int *d_err = nullptr, *h_err = nullptr;
+    // chunked path for slices the tiles cannot hold, and the finish list
+    int64_t *d_ch_row0 = nullptr, *h_ch_row0 = nullptr;
+    int *d_ch_n = nullptr, *d_ch_k = nullptr, *h_ch_n = nullptr, *h_ch_k = nullptr;
+    int *d_fin_k = nullptr, *d_fin_c0 = nullptr, *h_fin_k = nullptr, *h_fin_c0 = nullptr;
+    int n_chunks = 0, n_fin = 0;
+    int64_t max_chunks = 0;
+    float *dpart = nullptr;
+    bool fused_active = false;        // this update runs the fused + chunked path
     // general rows: runs of consecutive rows left to the general kernels
     int64_t *d_run_g0 = nullptr, *d_run_row0 = nullptr;
     int64_t *h_run_g0 = nullptr, *h_run_row0 = nullptr;

@@ -6,11 +6,14 @@
 // with at most FU_TILE_MAX rows in total, so the CTA owns every new row of
 // its slices and can finish them before moving on:
 //
-//   phase A   Y = X_tile Ṽ with Ṽ = V Γ⁺ (Γ = VᵀV), so that for slices whose
-//             S_k is nonsingular U_k,new = Y S_k⁻¹ (Lemma 1, Eq. 11, with
-//             S(SΓS)⁺ = Γ⁺S⁻¹);  ||X||² for the fitness.
-//   epilogue  per slice (one warp): U_k,new written out; ΔD = UᵀU;
-//             Δc = diag(Uᵀ X V) = diag(ΔD S Γ); c_k ← λc_k + Δc,
+//   phase A   P' = X_tile Q_V with V = Q_V R_V (Q_V orthonormal): Theorem 1's
+//             dominant product on a well-scaled operand; ||X||².
+//   epilogue  per slice (one warp): U_k,new = X V S_k (S_k Γ S_k)⁻¹
+//             = P' R_V⁻ᵀ S_k⁻¹ (Lemma 1, Eq. 11; Γ = VᵀV = R_VᵀR_V), which
+//             loses digits to cond(V) only, not cond(V)²; the general map
+//             S(SΓS)⁺ when S_k has zero entries; written out; ΔD = UᵀU;
+//             Δc = diag(Uᵀ X V) = diag(ΔD S_k Γ) (X V = U S_k Γ);
+//             c_k ← λc_k + Δc,
 //             D_k ← λD_k + ΔD (Eqs. 15-16, double-float);
 //             W(k,:) = c_kᵀ(Γ ∗ D_k)⁺ (Eq. 12) by an FP32 Cholesky factor
 //             refined twice with double-float residuals (FP64 Jacobi
@@ -23,6 +26,8 @@
 // bulk async copies (cp.async.bulk) that complete on mbarriers; every wait
 // is bounded and reports a timeout instead of hanging.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -40,12 +45,19 @@ constexpr int FU_JG = 64;            // max columns per warp group: J <= 8·64
 constexpr int FU_SUB = 16;           // rows per phase-A reduction step
 constexpr int FU_RP = 32;            // lanes = rank slots (R <= 32)
 constexpr int FU_LD = 33;            // leading dimension of the per-warp R×R FP32 factor
+constexpr int FU_YP = 36;            // pitch of the tile's Y / Ũ rows (conflict-free fragments)
+
+// Ring rows are copied one by one into rows of pitch J + 8 floats, which keeps
+// the 64-bit fragment loads of X conflict-free.
+__host__ __device__ inline int fu_pitch(int J) { return J + 8; }
 
 struct FusedArgs {
     const float *X;
     int J, R;
     double lam, rtol;
-    const float *Vt;          // Ṽ = V Γ⁺ (J×R)
+    const float *V32;         // Q_V (J×R, FP32): V = Q_V R_V with orthonormal Q_V
+    const float *GPf;         // R_V⁻ᵀ (R×R, FP32, lower triangular)
+    const double *RV;         // R_V (R×R, FP64, upper triangular)
     const df *Gdf;            // Γ (R×R) double-float
     const double *Gam;        // Γ (R×R) FP64
     const int *gam_ok;
@@ -62,13 +74,12 @@ struct FusedArgs {
     double *xn_part;          // gridDim partials of ||X||²
     double *wsp;              // per-warp FP64 workspace for the fallback paths
     int *err;                 // [0] wait timeouts, [1] fallback solves (count)
+    unsigned long long *phase_cycles;  // optional: SM cycles in phase A, epilogue, phase B
 };
 
 __host__ __device__ inline int fu_chunk_rows(int J) {
-    int ch = FU_SLOT_BYTES / (J * 4);
-    if (ch > 64) ch = 64;
-    if (ch < 1) ch = 1;
-    return ch;
+    (void)J;
+    return 16;                       // one 16-row MMA tile per chunk
 }
 
 __host__ __device__ inline size_t fu_wsp_doubles(int R) {
@@ -78,9 +89,9 @@ __host__ __device__ inline size_t fu_wsp_doubles(int R) {
 // shared memory layout (bytes)
 __host__ __device__ inline size_t fu_smem_bytes(int J) {
     const int ch = fu_chunk_rows(J);
-    size_t b = (size_t)FU_NBUF * ch * J * 4;               // ring
+    size_t b = (size_t)FU_NBUF * ch * fu_pitch(J) * 4;      // ring
     b += (size_t)FU_WARPS * FU_SUB * FU_RP * 4;             // Ypart
-    b += (size_t)FU_TILE_MAX * FU_RP * 4;                   // Ytile
+    b += (size_t)FU_TILE_MAX * FU_YP * 4;                   // Ytile
     b += (size_t)FU_RP * FU_RP * 8;                         // Γ double-float
     b += (size_t)FU_WARPS * FU_RP * FU_LD * 4;              // per-warp FP32 factor
     b += (size_t)FU_WARPS * FU_RP * 8 * 2;                  // per-warp x (df), misc
@@ -150,37 +161,42 @@ __device__ inline bool warp_cholesky_f(float *A, int n, int ld, float tol) {
         for (int i = j + 1 + lane; i < n; i += 32) A[i * ld + j] *= inv;
         __syncwarp();
         if (lane == 0) A[j * ld + j] = l;
-        for (int i = j + 1 + lane; i < n; i += 32) {
-            const float lij = A[i * ld + j];
-            for (int k = j + 1; k <= i; ++k) A[i * ld + k] -= lij * A[k * ld + j];
+        // trailing update of the lower triangle, one (i, k) pair per lane at a
+        // time: m = n-j-1 remaining rows, pairs (a, b) with 0 <= b <= a < m
+        const int m = n - j - 1;
+        const int np = m * (m + 1) / 2;
+        for (int p = lane; p < np; p += 32) {
+            // row a of the pair index p: a(a+1)/2 <= p < (a+1)(a+2)/2
+            int aa = (int)((sqrtf(8.f * p + 1.f) - 1.f) * 0.5f);
+            while ((aa + 1) * (aa + 2) / 2 <= p) ++aa;
+            while (aa * (aa + 1) / 2 > p) --aa;
+            const int bb = p - aa * (aa + 1) / 2;
+            const int i = j + 1 + aa, k = j + 1 + bb;
+            A[i * ld + k] -= A[i * ld + j] * A[k * ld + j];
         }
     }
     __syncwarp();
     return true;
 }
 
-// solve L Lᵀ x = b for one right-hand side held one entry per lane (lane < n)
+// solve L Lᵀ x = b for one right-hand side held one entry per lane (lane < n);
+// rinv holds 1/diag(L) (one entry per lane).  Lane i keeps its own entry in a
+// register; the pivot of step j is broadcast with a shuffle.
 __device__ inline float warp_cholesky_solve_f(const float *L, int n, int ld, float b,
-                                              float *tmp) {
+                                              float rinv) {
     const int lane = threadIdx.x & 31;
-    __syncwarp();
-    if (lane < n) tmp[lane] = b;
+    float y = lane < n ? b : 0.f;
     for (int j = 0; j < n; ++j) {
-        __syncwarp();
-        const float yj = tmp[j] / L[j * ld + j];
-        __syncwarp();
-        if (lane == j) tmp[j] = yj;
-        if (lane > j && lane < n) tmp[lane] -= L[lane * ld + j] * yj;
+        const float yj = __shfl_sync(0xffffffffu, y * rinv, j);
+        if (lane == j) y = yj;
+        else if (lane > j && lane < n) y = fmaf(-L[lane * ld + j], yj, y);
     }
     for (int j = n - 1; j >= 0; --j) {
-        __syncwarp();
-        const float xj = tmp[j] / L[j * ld + j];
-        __syncwarp();
-        if (lane == j) tmp[j] = xj;
-        if (lane < j) tmp[lane] -= L[j * ld + lane] * xj;
+        const float xj = __shfl_sync(0xffffffffu, y * rinv, j);
+        if (lane == j) y = xj;
+        else if (lane < j) y = fmaf(-L[j * ld + lane], xj, y);
     }
-    __syncwarp();
-    return lane < n ? tmp[lane] : 0.f;
+    return lane < n ? y : 0.f;
 }
 
 __device__ __forceinline__ float warp_max_f(float v) {
@@ -189,41 +205,213 @@ __device__ __forceinline__ float warp_max_f(float v) {
     return v;
 }
 
+// Finish slice k from its new-data Gram ΔD (lane r holds row r in dd) and
+// Δc (lane r holds Δc[r]): c_k ← λc_k + Δc, D_k ← λD_k + ΔD (Eqs. 15-16,
+// double-float), W(k,:) = c_kᵀ(Γ ∗ D_k)⁺ (Eq. 12) by an FP32 Cholesky factor
+// with one double-float refinement step (FP64 pseudo-inverse fallback), the
+// slice's share S_k ΔD S_k of G_inc (Eq. 21) added to gacc (lane r: row r).
+// Returns w_k,new[lane].  Called by all 32 lanes of a warp.
+__device__ __forceinline__ float slice_finish(const FusedArgs &a, int k, const float (&dd)[FU_RP],
+                                              float dc, float (&gacc)[FU_RP], const df *Gs,
+                                              float *Lw, df *xw, double *wsp) {
+    const int lane = threadIdx.x & 31;
+    const int R = a.R;
+    df cnew = {0.f, 0.f};
+    float amax = 0.f;
+    const df lamdf = df_from_double(a.lam);
+    const bool keep_old = a.lam != 0.0;
+    df *Dk = a.D + (int64_t)k * R * R;
+    if (lane < R) {
+        const df cold = a.c[(int64_t)k * R + lane];
+        cnew = df_add(keep_old ? df_mul(lamdf, cold) : df{0.f, 0.f}, df_make(dc));
+        a.c[(int64_t)k * R + lane] = cnew;
+    }
+#pragma unroll
+    for (int q = 0; q < FU_RP; ++q) {
+        if (q < R && lane < R) {
+            const df dold = Dk[lane * R + q];
+            const df dn = df_add(keep_old ? df_mul(lamdf, dold) : df{0.f, 0.f}, df_make(dd[q]));
+            Dk[lane * R + q] = dn;
+            const df av = df_mul(Gs[lane * FU_RP + q], dn);
+            Lw[lane * FU_LD + q] = av.hi;
+            if (q == lane) amax = fabsf(av.hi);
+        }
+    }
+    amax = warp_max_f(amax);
+    __syncwarp();
+    bool ok = amax > 0.f && warp_cholesky_f(Lw, R, FU_LD, 1e-6f * amax);
+    df x = {0.f, 0.f};
+    if (ok) {
+        const float rinv = lane < R ? 1.0f / Lw[lane * FU_LD + lane] : 0.f;
+        const float x0 = warp_cholesky_solve_f(Lw, R, FU_LD, lane < R ? cnew.hi : 0.f, rinv);
+        x = df_make(x0);
+        for (int it = 0; it < 1; ++it) {
+            __syncwarp();
+            if (lane < R) xw[lane] = x;
+            __syncwarp();
+            df res = cnew;
+            if (lane < R) {
+                for (int q = 0; q < R; ++q) {
+                    const df av = df_mul(Gs[lane * FU_RP + q], Dk[lane * R + q]);
+                    res = df_add(res, df_neg(df_mul(av, xw[q])));
+                }
+            }
+            const float dx = warp_cholesky_solve_f(Lw, R, FU_LD, lane < R ? res.hi : 0.f, rinv);
+            x = df_add(x, df_make(dx));
+        }
+        ok = __all_sync(0xffffffffu, isfinite(x.hi));
+    }
+    double wnew_d;
+    if (ok) {
+        wnew_d = lane < R ? df_to_double(x) : 0.0;
+    } else {
+        // FP64 pseudo-inverse solve (rare): A = Γ ∗ D_k, b = c_k
+        double *Aw = wsp, *Lf = Aw + R * (R + 1), *Ew = Lf + R * (R + 1);
+        double *bw = Ew + R * (R + 1), *fw = bw + (R + 1);
+        const int ld = R + 1;
+        __syncwarp();
+        for (int e = lane; e < R * R; e += 32) {
+            const int r = e / R, q = e % R;
+            Aw[r * ld + q] = a.Gam[e] * df_to_double(Dk[e]);
+        }
+        if (lane < R) bw[lane] = df_to_double(cnew);
+        __syncwarp();
+        warp_psd_solve(Aw, Lf, Ew, bw, fw, R, ld, a.rtol);
+        __syncwarp();
+        wnew_d = lane < R ? bw[lane] : 0.0;
+        atomicAdd(&a.err[1], 1);
+    }
+    if (lane < R) a.W[(int64_t)k * R + lane] = wnew_d;
+    const float wnew = (float)wnew_d;
+#pragma unroll
+    for (int q = 0; q < FU_RP; ++q) {
+        const float wq = __shfl_sync(0xffffffffu, wnew, q);
+        if (lane < R && q < R) gacc[q] = fmaf(wnew * dd[q], wq, gacc[q]);
+    }
+    return wnew;
+}
+
+// ---- split products on the warp-level tensor-core MMA ------------------------
+// x = hi + lo with hi = round(x), lo = round(x − hi) in FP16; a product a·b
+// is taken as a_hi·b_hi + a_hi·b_lo + a_lo·b_hi (the error-corrected tensor
+// core product of Ootomo and Yokota, 2022), accumulated in FP32.  FP16 halves carry ~22 significant bits per operand once it is scaled
+// by a power of two so that its largest entries lie in [512, 1024) (per row
+// and warp for X in P' = X Q_V, per tile for X and Ũ in the F sums, a fixed
+// 2^9 for the orthonormal Q_V): the lo halves then stay in FP16's normal range
+// and the MMA accumulates the exact products in FP32.
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);   // x0 in the low half
+    const float2 hf = __bfloat1622float2(h);
+    hi = bf16x2_bits(h);
+    lo = bf16x2_bits(__floats2bfloat162_rn(x0 - hf.x, x1 - hf.y));
+}
+// FP16 split: 11-bit mantissas, so hi + lo carries ~22 bits when both halves
+// are normal numbers; callers scale operands by powers of two first.
+__device__ __forceinline__ uint32_t half2_bits(__half2 v) { return *reinterpret_cast<uint32_t *>(&v); }
+// lo is stored scaled by 2^11 so that it stays a normal FP16 number; the
+// correction products are scaled back by 2^-11 after the MMA.
+__device__ __forceinline__ void split_pair_h(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+    const __half2 h = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h);
+    hi = half2_bits(h);
+    lo = half2_bits(__floats2half2_rn((x0 - hf.x) * 2048.f, (x1 - hf.y) * 2048.f));
+}
+__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                        uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// acc += a_hi·b_hi + 2^-11 (a_hi·b_lo' + a_lo'·b_hi) for one 16×8×16 tile, with
+// the main and correction products accumulated separately from zero inside
+// the tensor core and added to acc with IEEE FP32 adds (the tensor core's
+// own FP32 accumulation truncates when aligning a small term to a large one).
+__device__ __forceinline__ void mma_split3(float (&acc)[4], const uint32_t (&ah)[4],
+                                           const uint32_t (&al)[4], uint32_t bh0, uint32_t bh1,
+                                           uint32_t bl0, uint32_t bl1) {
+    float dm[4] = {0.f, 0.f, 0.f, 0.f}, dc[4] = {0.f, 0.f, 0.f, 0.f};
+    mma_f16(dm, ah, bh0, bh1);
+    mma_f16(dc, ah, bl0, bl1);
+    mma_f16(dc, al, bh0, bh1);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[e] += fmaf(dc[e], 4.8828125e-4f, dm[e]);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 // ---------------------------------------------------------------------------
+// TC = true: phases A and B on tensor cores (BF16 split, 3 products);
+// TC = false: FP32 CUDA-core FMAs.
+template <bool TC>
 __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
     extern __shared__ __align__(128) unsigned char fsm[];
     const int J = a.J, R = a.R;
     const int CH = fu_chunk_rows(J);
+    const int P = fu_pitch(J);
     float *ring = reinterpret_cast<float *>(fsm);
-    float *Ypart = ring + (size_t)FU_NBUF * CH * J;
+    float *Ypart = ring + (size_t)FU_NBUF * CH * P;
     float *Ytile = Ypart + FU_WARPS * FU_SUB * FU_RP;
-    df *Gs = reinterpret_cast<df *>(Ytile + FU_TILE_MAX * FU_RP);
+    df *Gs = reinterpret_cast<df *>(Ytile + FU_TILE_MAX * FU_YP);
     float *Lw_all = reinterpret_cast<float *>(Gs + FU_RP * FU_RP);
     df *xw_all = reinterpret_cast<df *>(Lw_all + FU_WARPS * FU_RP * FU_LD);
     float *vw_all = reinterpret_cast<float *>(xw_all + FU_WARPS * FU_RP * 2);
     uint64_t *bars = reinterpret_cast<uint64_t *>(vw_all + FU_WARPS * FU_RP * 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, tg = lane & 3;        // MMA fragment coordinates
+    float *red = vw_all;                           // per-warp maxima for the tile scales
     float *Lw = Lw_all + warp * FU_RP * FU_LD;
     df *xw = xw_all + warp * FU_RP * 2;
-    float *vw = vw_all + warp * FU_RP * 2;
     double *wsp = a.wsp + (size_t)(blockIdx.x * FU_WARPS + warp) * fu_wsp_doubles(R);
 
-    // columns of this warp's group (multiple of 4 so the float4 loads align)
+    // columns of this warp's group: multiples of 16 (TC) or 4 (float4 loads)
     int JGs = (J + FU_WARPS - 1) / FU_WARPS;
-    JGs = (JGs + 3) & ~3;
+    JGs = TC ? ((JGs + 15) & ~15) : ((JGs + 3) & ~3);
     const int jb = warp * JGs;
     const int jn = max(0, min(JGs, J - jb));
 
-    // Ṽ slice in registers: v[q] = Ṽ[jb + q][lane]
-    float v[FU_JG];
+    // V slice in registers.  SIMT: v[q] = V[jb + q][lane].  TC: B fragments
+    // of V (k = j, n = r) for 4 k-steps × 4 n-tiles, hi and lo halves.
+    float v[TC ? 1 : FU_JG];
+    uint32_t vbh[TC ? 4 : 1][4][2], vbl[TC ? 4 : 1][4][2];
+    if constexpr (!TC) {
 #pragma unroll
-    for (int q = 0; q < FU_JG; ++q)
-        v[q] = (q < jn && lane < R) ? a.Vt[(int64_t)(jb + q) * R + lane] : 0.f;
+        for (int q = 0; q < FU_JG; ++q)
+            v[q] = (q < jn && lane < R) ? a.V32[(int64_t)(jb + q) * R + lane] : 0.f;
+    } else {
+#pragma unroll
+        for (int st = 0; st < 4; ++st)
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = jb + 16 * st + 8 * h + 2 * tg;
+                    const int n = 8 * nt + g;
+                    const bool ok0 = (16 * st + 8 * h + 2 * tg) < jn && n < R;
+                    // |Q_V| <= 1: scaled by 2^9 so that the lo halves stay normal
+                    const float v0 = ok0 ? a.V32[(int64_t)j * R + n] * 512.f : 0.f;
+                    const float v1 = ok0 ? a.V32[(int64_t)(j + 1) * R + n] * 512.f : 0.f;
+                    split_pair_h(v0, v1, vbh[st][nt][h], vbl[st][nt][h]);
+                }
+    }
     for (int i = tid; i < R * R; i += FU_THREADS) Gs[(i / R) * FU_RP + (i % R)] = a.Gdf[i];
-    // this CTA's F partial starts at zero
+    // this CTA's F partial starts at zero; so does the ring (its row padding is read)
     float *Fs = a.Fslot + (size_t)blockIdx.x * J * R;
     for (int i = tid; i < J * R; i += FU_THREADS) Fs[i] = 0.f;
+    for (int i = tid; i < FU_NBUF * CH * P; i += FU_THREADS) ring[i] = 0.f;
+    for (int i = tid; i < FU_TILE_MAX * FU_YP; i += FU_THREADS) Ytile[i] = 0.f;
     if (tid == 0) {
         for (int b = 0; b < FU_NBUF; ++b) mbar_init(&bars[b], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -232,14 +420,13 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
     const bool gam_ok = *a.gam_ok != 0;
 
     // ---- chunk stream: for each of my tiles, phase A chunks then phase B ----
-    // producer cursor (thread 0 only)
-    int p_tile = blockIdx.x, p_phase = 0, p_chunk = 0;
+    int p_tile = blockIdx.x, p_phase = 0, p_chunk = 0;   // producer cursor (thread 0)
     auto tile_rows = [&](int t, int64_t &r0, int64_t &r1) {
         r0 = a.seg_row[a.tile_s0[t]];
         r1 = a.seg_row[a.tile_s1[t]];
     };
-    uint32_t issued = 0;       // chunks issued so far (thread 0)
-    auto issue_next = [&]() {  // thread 0: issue the next chunk of the stream
+    uint32_t issued = 0;
+    auto issue_next = [&]() {  // thread 0: copy the next chunk, row by row, into its slot
         while (p_tile < a.n_tiles) {
             int64_t r0, r1;
             tile_rows(p_tile, r0, r1);
@@ -248,10 +435,11 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
                 const int64_t cr0 = r0 + (int64_t)p_chunk * CH;
                 const int cn = (int)((r1 - cr0) < CH ? (r1 - cr0) : CH);
                 const int slot = issued % FU_NBUF;
-                const uint32_t bytes = (uint32_t)cn * J * 4;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&bars[slot], bytes);
-                bulk_g2s(ring + (size_t)slot * CH * J, a.X + cr0 * J, bytes, &bars[slot]);
+                mbar_expect_tx(&bars[slot], (uint32_t)cn * J * 4);
+                float *dst = ring + (size_t)slot * CH * P;
+                for (int r = 0; r < cn; ++r)
+                    bulk_g2s(dst + (size_t)r * P, a.X + (cr0 + r) * J, (uint32_t)J * 4, &bars[slot]);
                 ++issued;
                 ++p_chunk;
                 return;
@@ -269,15 +457,18 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
     double xn_d = 0.0;
     float gacc[FU_RP];                 // lane's row of this warp's G partial
 #pragma unroll
-    for (int s = 0; s < FU_RP; ++s) gacc[s] = 0.f;
+    for (int q = 0; q < FU_RP; ++q) gacc[q] = 0.f;
     bool aborted = false;
+    unsigned long long cyc[3] = {0ull, 0ull, 0ull};
+    long long tmark = clock64();
+    float xmax_t = 0.f;                // max |x| of the current tile (this thread's share)
 
     for (int t = blockIdx.x; t < a.n_tiles && !aborted; t += gridDim.x) {
         int64_t r0, r1;
         tile_rows(t, r0, r1);
         const int nr = (int)(r1 - r0);
         const int nch = (nr + CH - 1) / CH;
-        // ================= phase A: Y = X Ṽ ================================
+        // ================= phase A: P = X V =================================
         for (int cI = 0; cI < nch; ++cI) {
             const int slot = consumed % FU_NBUF;
             const bool got = mbar_wait_bounded(&bars[slot], (consumed / FU_NBUF) & 1, &a.err[0]);
@@ -285,39 +476,121 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
                 aborted = true;
                 break;
             }
-            const float *xs = ring + (size_t)slot * CH * J;
+            const float *xs = ring + (size_t)slot * CH * P;
             const int cn = min(CH, nr - cI * CH);
-            for (int sub = 0; sub < cn; sub += FU_SUB) {
-                const int sn = min(FU_SUB, cn - sub);
-                for (int i = 0; i < sn; ++i) {
-                    const float *xr = xs + (size_t)(sub + i) * J + jb;
-                    float acc = 0.f, sq = 0.f;
+            if constexpr (TC) {
+                float yacc[4][4];
 #pragma unroll
-                    for (int q = 0; q < FU_JG; q += 4) {
-                        if (q < jn) {
-                            const float4 x4 = *reinterpret_cast<const float4 *>(xr + q);
-                            acc = fmaf(x4.x, v[q], acc);
-                            acc = fmaf(x4.y, v[q + 1], acc);
-                            acc = fmaf(x4.z, v[q + 2], acc);
-                            acc = fmaf(x4.w, v[q + 3], acc);
-                            sq = fmaf(x4.x, x4.x, sq);
-                            sq = fmaf(x4.y, x4.y, sq);
-                            sq = fmaf(x4.z, x4.z, sq);
-                            sq = fmaf(x4.w, x4.w, sq);
-                        }
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) yacc[nt][e] = 0.f;
+                float2 xa_[4][4];
+                float m0 = 0.f, m1 = 0.f;   // row maxima over this warp's columns
+#pragma unroll
+                for (int st = 0; st < 4; ++st) {
+                    if (16 * st < jn) {
+                        const int j0 = jb + 16 * st + 2 * tg;
+                        const bool c0 = (16 * st + 2 * tg) < jn, c1 = (16 * st + 8 + 2 * tg) < jn;
+                        const bool rg0 = g < cn, rg1 = g + 8 < cn;
+                        const float2 z = make_float2(0.f, 0.f);
+                        const float2 x00 = (rg0 && c0) ? *reinterpret_cast<const float2 *>(xs + g * P + j0) : z;
+                        const float2 x10 = (rg1 && c0) ? *reinterpret_cast<const float2 *>(xs + (g + 8) * P + j0) : z;
+                        const float2 x01 = (rg0 && c1) ? *reinterpret_cast<const float2 *>(xs + g * P + j0 + 8) : z;
+                        const float2 x11 = (rg1 && c1) ? *reinterpret_cast<const float2 *>(xs + (g + 8) * P + j0 + 8) : z;
+                        xn_f += x00.x * x00.x + x00.y * x00.y + x10.x * x10.x + x10.y * x10.y +
+                                x01.x * x01.x + x01.y * x01.y + x11.x * x11.x + x11.y * x11.y;
+                        xa_[st][0] = x00; xa_[st][1] = x10; xa_[st][2] = x01; xa_[st][3] = x11;
+                        m0 = fmaxf(m0, fmaxf(fmaxf(fabsf(x00.x), fabsf(x00.y)), fmaxf(fabsf(x01.x), fabsf(x01.y))));
+                        m1 = fmaxf(m1, fmaxf(fmaxf(fabsf(x10.x), fabsf(x10.y)), fmaxf(fabsf(x11.x), fabsf(x11.y))));
+                    } else {
+                        const float2 z = make_float2(0.f, 0.f);
+                        xa_[st][0] = z; xa_[st][1] = z; xa_[st][2] = z; xa_[st][3] = z;
                     }
-                    Ypart[(warp * FU_SUB + i) * FU_RP + lane] = acc;
-                    if (lane == 0) xn_f += sq;
                 }
-                __syncthreads();
-                for (int o = tid; o < sn * FU_RP; o += FU_THREADS) {
-                    const int i = o / FU_RP, l = o % FU_RP;
-                    float s = 0.f;
+                // power-of-two scale of rows g and g+8 over this warp's columns:
+                // the four lanes of a row group share the row
+                xmax_t = fmaxf(xmax_t, fmaxf(m0, m1));
+                m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 1));
+                m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 2));
+                m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 1));
+                m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 2));
+                // rows scaled into [512, 1024): FP16 lo halves stay normal
+                int e0 = 0, e1 = 0;
+                if (m0 > 0.f) frexpf(m0, &e0);
+                if (m1 > 0.f) frexpf(m1, &e1);
+                const float s0 = ldexpf(1.f, 10 - e0), s1 = ldexpf(1.f, 10 - e1);
 #pragma unroll
-                    for (int w = 0; w < FU_WARPS; ++w) s += Ypart[(w * FU_SUB + i) * FU_RP + l];
-                    Ytile[(cI * CH + sub + i) * FU_RP + l] = s;
+                for (int st = 0; st < 4; ++st) {
+                    if (16 * st < jn) {
+                        uint32_t ah[4], al[4];
+                        split_pair_h(xa_[st][0].x * s0, xa_[st][0].y * s0, ah[0], al[0]);
+                        split_pair_h(xa_[st][1].x * s1, xa_[st][1].y * s1, ah[1], al[1]);
+                        split_pair_h(xa_[st][2].x * s0, xa_[st][2].y * s0, ah[2], al[2]);
+                        split_pair_h(xa_[st][3].x * s1, xa_[st][3].y * s1, ah[3], al[3]);
+#pragma unroll
+                        for (int nt = 0; nt < 4; ++nt)
+                            mma_split3(yacc[nt], ah, al, vbh[st][nt][0], vbh[st][nt][1],
+                                       vbl[st][nt][0], vbl[st][nt][1]);
+                    }
+                }
+                const float u0 = ldexpf(1.f, e0 - 19), u1 = ldexpf(1.f, e1 - 19);   // 2^(e-10)·2^-9
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    yacc[nt][0] *= u0;
+                    yacc[nt][1] *= u0;
+                    yacc[nt][2] *= u1;
+                    yacc[nt][3] *= u1;
+                }
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    const int c = 8 * nt + 2 * tg;
+                    *reinterpret_cast<float2 *>(&Ypart[(warp * FU_SUB + g) * FU_RP + c]) =
+                        make_float2(yacc[nt][0], yacc[nt][1]);
+                    *reinterpret_cast<float2 *>(&Ypart[(warp * FU_SUB + g + 8) * FU_RP + c]) =
+                        make_float2(yacc[nt][2], yacc[nt][3]);
                 }
                 __syncthreads();
+                for (int o = tid; o < cn * FU_RP; o += FU_THREADS) {
+                    const int i = o / FU_RP, l = o % FU_RP;
+                    float sacc = 0.f;
+#pragma unroll
+                    for (int w = 0; w < FU_WARPS; ++w) sacc += Ypart[(w * FU_SUB + i) * FU_RP + l];
+                    Ytile[(cI * CH + i) * FU_YP + l] = sacc;
+                }
+                __syncthreads();
+            } else {
+                for (int sub = 0; sub < cn; sub += FU_SUB) {
+                    const int sn = min(FU_SUB, cn - sub);
+                    for (int i = 0; i < sn; ++i) {
+                        const float *xr = xs + (size_t)(sub + i) * P + jb;
+                        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, sq0 = 0.f, sq1 = 0.f;
+#pragma unroll
+                        for (int q = 0; q < FU_JG; q += 4) {
+                            if (q < jn) {
+                                const float4 x4 = *reinterpret_cast<const float4 *>(xr + q);
+                                a0 = fmaf(x4.x, v[q], a0);
+                                a1 = fmaf(x4.y, v[q + 1], a1);
+                                a2 = fmaf(x4.z, v[q + 2], a2);
+                                a3 = fmaf(x4.w, v[q + 3], a3);
+                                sq0 = fmaf(x4.x, x4.x, sq0);
+                                sq1 = fmaf(x4.y, x4.y, sq1);
+                                sq0 = fmaf(x4.z, x4.z, sq0);
+                                sq1 = fmaf(x4.w, x4.w, sq1);
+                            }
+                        }
+                        Ypart[(warp * FU_SUB + i) * FU_RP + lane] = (a0 + a1) + (a2 + a3);
+                        if (lane == 0) xn_f += sq0 + sq1;
+                    }
+                    __syncthreads();
+                    for (int o = tid; o < sn * FU_RP; o += FU_THREADS) {
+                        const int i = o / FU_RP, l = o % FU_RP;
+                        float sacc = 0.f;
+#pragma unroll
+                        for (int w = 0; w < FU_WARPS; ++w) sacc += Ypart[(w * FU_SUB + i) * FU_RP + l];
+                        Ytile[(cI * CH + sub + i) * FU_YP + l] = sacc;
+                    }
+                    __syncthreads();
+                }
             }
             ++consumed;
             if (tid == 0) issue_next();
@@ -325,6 +598,11 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
         if (aborted) break;
         xn_d += (double)xn_f;
         xn_f = 0.f;
+        {
+            const long long now = clock64();
+            cyc[0] += (unsigned long long)(now - tmark);
+            tmark = now;
+        }
         // ================= epilogue: one warp per slice ======================
         const int s0 = a.tile_s0[t], s1 = a.tile_s1[t];
         for (int sg = s0 + warp; sg < s1; sg += FU_WARPS) {
@@ -335,17 +613,17 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
             const float wold = (float)wold_d;
             const bool fast = gam_ok && __all_sync(0xffffffffu, wold_d != 0.0);
             float dc = 0.f;                       // Δc[lane]
+            // U = P' mcol: fast path mcol = column `lane` of R_V⁻ᵀ S⁻¹; general
+            // path (zero weights) mcol = column of R_V S (S Γ S)⁺ (FP64, rare)
+            float mcol[FU_RP], rvcol[FU_RP];
             if (fast) {
                 const float winv = lane < R ? 1.0f / wold : 0.f;
-                for (int i = 0; i < n; ++i) {
-                    float *y = Ytile + (ia + i) * FU_RP;
-                    const float u = y[lane] * winv;
-                    __syncwarp();
-                    y[lane] = u;
-                    if (lane < R) a.U[(r0 + ia + i) * R + lane] = u;
+#pragma unroll
+                for (int t = 0; t < FU_RP; ++t) {
+                    mcol[t] = (t < R && lane < R) ? a.GPf[t * R + lane] * winv : 0.f;
+                    rvcol[t] = 0.f;
                 }
             } else {
-                // general Lemma 1 map M = S (S Γ S)⁺ (FP64, rare): P = Y Γ, U = P M
                 double *Aw = wsp, *Ew = Aw + R * (R + 1), *Mw = Ew + R * (R + 1);
                 double *fw = Mw + R * (R + 1);
                 const int ld = R + 1;
@@ -355,27 +633,44 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
                 }
                 __syncwarp();
                 warp_psd_pinv(Aw, Ew, fw, Mw, R, ld, a.rtol, 1, false);
-                for (int e = lane; e < R * R; e += 32) {
-                    const int r = e / R, q = e % R;
-                    Mw[r * ld + q] *= a.W[(int64_t)k * R + r];
-                }
                 __syncwarp();
-                for (int i = 0; i < n; ++i) {
-                    float *y = Ytile + (ia + i) * FU_RP;
-                    float p = 0.f;                            // P[i][lane] = Σ_t Y[i][t] Γ[t][lane]
-                    for (int q = 0; q < R; ++q)
-                        p = fmaf(y[q], lane < R ? Gs[q * FU_RP + lane].hi : 0.f, p);
-                    float u = 0.f;                            // U[i][lane] = Σ_s P[i][s] M[s][lane]
-                    for (int q = 0; q < R; ++q) {
-                        const float ps = __shfl_sync(0xffffffffu, p, q);
-                        if (lane < R) u = fmaf(ps, (float)Mw[q * ld + lane], u);
-                    }
-                    dc = fmaf(u, p, dc);
-                    __syncwarp();
-                    y[lane] = lane < R ? u : 0.f;
-                    if (lane < R) a.U[(r0 + ia + i) * R + lane] = u;
+#pragma unroll
+                for (int t = 0; t < FU_RP; ++t) {
+                    double m = 0.0;
+                    if (t < R && lane < R)
+                        for (int q = t; q < R; ++q)
+                            m += a.RV[t * R + q] * a.W[(int64_t)k * R + q] * Mw[q * ld + lane];
+                    mcol[t] = (float)m;
+                    rvcol[t] = (t < R && lane < R) ? (float)a.RV[t * R + lane] : 0.f;
                 }
                 atomicAdd(&a.err[1], 1);
+            }
+            for (int i = 0; i < n; ++i) {
+                float *y = Ytile + (ia + i) * FU_YP;
+                float u0 = 0.f, u1 = 0.f, pl = 0.f;
+#pragma unroll
+                for (int t = 0; t < FU_RP; t += 4) {
+                    const float4 p4 = *reinterpret_cast<const float4 *>(y + t);
+                    u0 = fmaf(p4.x, mcol[t], u0);
+                    u1 = fmaf(p4.y, mcol[t + 1], u1);
+                    u0 = fmaf(p4.z, mcol[t + 2], u0);
+                    u1 = fmaf(p4.w, mcol[t + 3], u1);
+                }
+                if (!fast) {                      // general path: Σ_i U(i,r) (X V)(i,r)
+#pragma unroll
+                    for (int t = 0; t < FU_RP; t += 4) {
+                        const float4 p4 = *reinterpret_cast<const float4 *>(y + t);
+                        pl = fmaf(p4.x, rvcol[t], pl);
+                        pl = fmaf(p4.y, rvcol[t + 1], pl);
+                        pl = fmaf(p4.z, rvcol[t + 2], pl);
+                        pl = fmaf(p4.w, rvcol[t + 3], pl);
+                    }
+                }
+                const float u = u0 + u1;
+                dc = fmaf(u, pl, dc);
+                __syncwarp();
+                y[lane] = u;
+                if (lane < R) a.U[(r0 + ia + i) * R + lane] = u;
             }
             __syncwarp();
             // ΔD row `lane`: dd[q] = Σ_i U[i][lane] U[i][q]
@@ -383,7 +678,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
 #pragma unroll
             for (int q = 0; q < FU_RP; ++q) dd[q] = 0.f;
             for (int i = 0; i < n; ++i) {
-                const float *y = Ytile + (ia + i) * FU_RP;
+                const float *y = Ytile + (ia + i) * FU_YP;
                 const float ul = y[lane];
 #pragma unroll
                 for (int q = 0; q < FU_RP; q += 4) {
@@ -395,97 +690,73 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
                 }
             }
             if (fast) {            // Δc = diag(ΔD S Γ): Δc[r] = Σ_q ΔD[r][q] w_q Γ[q][r]
-                float s = 0.f;
+                float sacc = 0.f;
 #pragma unroll
                 for (int q = 0; q < FU_RP; ++q) {
                     const float wq = __shfl_sync(0xffffffffu, wold, q);
-                    if (q < R && lane < R) s = fmaf(dd[q] * wq, Gs[q * FU_RP + lane].hi, s);
+                    if (q < R && lane < R) sacc = fmaf(dd[q] * wq, Gs[q * FU_RP + lane].hi, sacc);
                 }
-                dc = s;
+                dc = sacc;
             }
-            // c_k, D_k with λ (double-float), A = Γ ∗ D_k into the FP32 factor
-            df cnew = {0.f, 0.f};
-            float amax = 0.f;
-            const float lamf_hi = (float)a.lam;
-            const df lamdf = df_from_double(a.lam);
-            df *Dk = a.D + (int64_t)k * R * R;
-            if (lane < R) {
-                const df cold = a.c[(int64_t)k * R + lane];
-                cnew = df_add(a.lam == 0.0 ? df{0.f, 0.f} : df_mul(lamdf, cold), df_make(dc));
-                a.c[(int64_t)k * R + lane] = cnew;
-                for (int q = 0; q < R; ++q) {
-                    const df dold = Dk[lane * R + q];
-                    const df dn = df_add(a.lam == 0.0 ? df{0.f, 0.f} : df_mul(lamdf, dold),
-                                         df_make(dd[q]));
-                    Dk[lane * R + q] = dn;
-                    const df av = df_mul(Gs[lane * FU_RP + q], dn);
-                    Lw[lane * FU_LD + q] = av.hi;
-                    if (q == lane) amax = fabsf(av.hi);
-                }
-            }
-            (void)lamf_hi;
-            amax = warp_max_f(amax);
-            __syncwarp();
-            // FP32 Cholesky, then two double-float refinement steps
-            bool ok = amax > 0.f && warp_cholesky_f(Lw, R, FU_LD, 1e-6f * amax);
-            df x = {0.f, 0.f};
-            if (ok) {
-                float x0 = warp_cholesky_solve_f(Lw, R, FU_LD, lane < R ? cnew.hi : 0.f, vw);
-                x = df_make(x0);
-                for (int it = 0; it < 2; ++it) {
-                    __syncwarp();
-                    if (lane < R) xw[lane] = x;
-                    __syncwarp();
-                    df res = cnew;
-                    if (lane < R) {
-                        for (int q = 0; q < R; ++q) {
-                            const df av = df_mul(Gs[lane * FU_RP + q], Dk[lane * R + q]);
-                            res = df_add(res, df_neg(df_mul(av, xw[q])));
-                        }
-                    }
-                    const float dx = warp_cholesky_solve_f(Lw, R, FU_LD, lane < R ? res.hi : 0.f, vw);
-                    x = df_add(x, df_make(dx));
-                }
-                // accept only if finite
-                ok = __all_sync(0xffffffffu, isfinite(x.hi));
-            }
-            double wnew_d;
-            if (ok) {
-                wnew_d = lane < R ? df_to_double(x) : 0.0;
-            } else {
-                // FP64 pseudo-inverse solve (rare): A = Γ ∗ D_k, b = c_k
-                double *Aw = wsp, *Lf = Aw + R * (R + 1), *Ew = Lf + R * (R + 1);
-                double *bw = Ew + R * (R + 1), *fw = bw + (R + 1);
-                const int ld = R + 1;
-                __syncwarp();
-                for (int e = lane; e < R * R; e += 32) {
-                    const int r = e / R, q = e % R;
-                    Aw[r * ld + q] = a.Gam[e] * df_to_double(Dk[e]);
-                }
-                if (lane < R) bw[lane] = df_to_double(cnew);
-                __syncwarp();
-                warp_psd_solve(Aw, Lf, Ew, bw, fw, R, ld, a.rtol);
-                __syncwarp();
-                wnew_d = lane < R ? bw[lane] : 0.0;
-                atomicAdd(&a.err[1], 1);
-            }
-            if (lane < R) a.W[(int64_t)k * R + lane] = wnew_d;
-            const float wnew = (float)wnew_d;
-            // G share with the new S_k (Eq. 21): G[lane][q] += w_lane ΔD[lane][q] w_q
-#pragma unroll
-            for (int q = 0; q < FU_RP; ++q) {
-                const float wq = __shfl_sync(0xffffffffu, wnew, q);
-                if (lane < R && q < R) gacc[q] = fmaf(wnew * dd[q], wq, gacc[q]);
-            }
+            const float wnew = slice_finish(a, k, dd, dc, gacc, Gs, Lw, xw, wsp);
             // Ũ = U S_k,new for phase B
-            for (int i = 0; i < n; ++i) Ytile[(ia + i) * FU_RP + lane] *= (lane < R ? wnew : 0.f);
+            for (int i = 0; i < n; ++i) Ytile[(ia + i) * FU_YP + lane] *= (lane < R ? wnew : 0.f);
             __syncwarp();
         }
         __syncthreads();
+        {
+            const long long now = clock64();
+            cyc[1] += (unsigned long long)(now - tmark);
+            tmark = now;
+        }
         // ================= phase B: F partial += Xᵀ Ũ ========================
-        float facc[FU_JG];
+        float facc[TC ? 4 : 1][4][4];        // TC: m-tile (j) × n-tile (r) × fragment
+        float fs[TC ? 1 : FU_JG];            // SIMT: one column r = lane, j = jb + q
+        float sx = 1.f, su = 1.f;            // TC: power-of-two tile scales of X and Ũ
+        int ex = 0, eu = 0;
+        if constexpr (TC) {
+            // tile maxima of |X| (from phase A) and |Ũ|, reduced over the CTA
+            float um = 0.f;
+            for (int o = tid; o < nr * FU_RP; o += FU_THREADS)
+                um = fmaxf(um, fabsf(Ytile[(o / FU_RP) * FU_YP + (o % FU_RP)]));
+            float xm = xmax_t;
 #pragma unroll
-        for (int q = 0; q < FU_JG; ++q) facc[q] = 0.f;
+            for (int off = 16; off > 0; off >>= 1) {
+                xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, off));
+                um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, off));
+            }
+            if (lane == 0) {
+                red[warp] = xm;
+                red[FU_WARPS + warp] = um;
+            }
+            __syncthreads();
+            xm = 0.f;
+            um = 0.f;
+#pragma unroll
+            for (int w = 0; w < FU_WARPS; ++w) {
+                xm = fmaxf(xm, red[w]);
+                um = fmaxf(um, red[FU_WARPS + w]);
+            }
+            if (xm > 0.f) frexpf(xm, &ex);
+            if (um > 0.f) frexpf(um, &eu);
+            ex -= 10;                        // scaled maxima in [512, 1024)
+            eu -= 10;
+            sx = ldexpf(1.f, -ex);
+            su = ldexpf(1.f, -eu);
+            xmax_t = 0.f;
+            __syncthreads();
+        }
+        if constexpr (TC) {
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) facc[mt][nt][e] = 0.f;
+        } else {
+#pragma unroll
+            for (int q = 0; q < FU_JG; ++q) fs[q] = 0.f;
+        }
         for (int cI = 0; cI < nch; ++cI) {
             const int slot = consumed % FU_NBUF;
             const bool got = mbar_wait_bounded(&bars[slot], (consumed / FU_NBUF) & 1, &a.err[0]);
@@ -493,19 +764,60 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
                 aborted = true;
                 break;
             }
-            const float *xs = ring + (size_t)slot * CH * J;
+            const float *xs = ring + (size_t)slot * CH * P;
             const int cn = min(CH, nr - cI * CH);
-            for (int i = 0; i < cn; ++i) {
-                const float ut = Ytile[(cI * CH + i) * FU_RP + lane];
-                const float *xr = xs + (size_t)i * J + jb;
+            if constexpr (TC) {
+                // B fragments of Ũ (k = row, n = r): rows 2tg, 2tg+1 and +8
+                const float *ut = Ytile + (size_t)(cI * CH) * FU_YP;
+                const bool k0 = 2 * tg < cn, k1 = 2 * tg + 1 < cn, k2 = 2 * tg + 8 < cn, k3 = 2 * tg + 9 < cn;
+                uint32_t bh[4][2], bl[4][2];
 #pragma unroll
-                for (int q = 0; q < FU_JG; q += 4) {
-                    if (q < jn) {
-                        const float4 x4 = *reinterpret_cast<const float4 *>(xr + q);
-                        facc[q] = fmaf(x4.x, ut, facc[q]);
-                        facc[q + 1] = fmaf(x4.y, ut, facc[q + 1]);
-                        facc[q + 2] = fmaf(x4.z, ut, facc[q + 2]);
-                        facc[q + 3] = fmaf(x4.w, ut, facc[q + 3]);
+                for (int nt = 0; nt < 4; ++nt) {
+                    const int c = 8 * nt + g;
+                    split_pair_h(k0 ? ut[(2 * tg) * FU_YP + c] * su : 0.f,
+                                 k1 ? ut[(2 * tg + 1) * FU_YP + c] * su : 0.f, bh[nt][0], bl[nt][0]);
+                    split_pair_h(k2 ? ut[(2 * tg + 8) * FU_YP + c] * su : 0.f,
+                                 k3 ? ut[(2 * tg + 9) * FU_YP + c] * su : 0.f, bh[nt][1], bl[nt][1]);
+                }
+#pragma unroll
+                for (int mt = 0; mt < 4; ++mt) {
+                    if (16 * mt < jn) {
+                        // A fragments of Xᵀ (m = j, k = row)
+                        const int jm = jb + 16 * mt + g;
+                        const bool m0 = (16 * mt + g) < jn, m1 = (16 * mt + g + 8) < jn;
+                        float xa[8];
+                        xa[0] = (m0 && k0) ? xs[(2 * tg) * P + jm] : 0.f;
+                        xa[1] = (m0 && k1) ? xs[(2 * tg + 1) * P + jm] : 0.f;
+                        xa[2] = (m1 && k0) ? xs[(2 * tg) * P + jm + 8] : 0.f;
+                        xa[3] = (m1 && k1) ? xs[(2 * tg + 1) * P + jm + 8] : 0.f;
+                        xa[4] = (m0 && k2) ? xs[(2 * tg + 8) * P + jm] : 0.f;
+                        xa[5] = (m0 && k3) ? xs[(2 * tg + 9) * P + jm] : 0.f;
+                        xa[6] = (m1 && k2) ? xs[(2 * tg + 8) * P + jm + 8] : 0.f;
+                        xa[7] = (m1 && k3) ? xs[(2 * tg + 9) * P + jm + 8] : 0.f;
+                        uint32_t ah[4], al[4];
+                        split_pair_h(xa[0] * sx, xa[1] * sx, ah[0], al[0]);
+                        split_pair_h(xa[2] * sx, xa[3] * sx, ah[1], al[1]);
+                        split_pair_h(xa[4] * sx, xa[5] * sx, ah[2], al[2]);
+                        split_pair_h(xa[6] * sx, xa[7] * sx, ah[3], al[3]);
+#pragma unroll
+                        for (int nt = 0; nt < 4; ++nt)
+                            mma_split3(facc[mt][nt], ah, al, bh[nt][0], bh[nt][1], bl[nt][0],
+                                       bl[nt][1]);
+                    }
+                }
+            } else {
+                for (int i = 0; i < cn; ++i) {
+                    const float ut = Ytile[(cI * CH + i) * FU_YP + lane];
+                    const float *xr = xs + (size_t)i * P + jb;
+#pragma unroll
+                    for (int q = 0; q < FU_JG; q += 4) {
+                        if (q < jn) {
+                            const float4 x4 = *reinterpret_cast<const float4 *>(xr + q);
+                            fs[q] = fmaf(x4.x, ut, fs[q]);
+                            fs[q + 1] = fmaf(x4.y, ut, fs[q + 1]);
+                            fs[q + 2] = fmaf(x4.z, ut, fs[q + 2]);
+                            fs[q + 3] = fmaf(x4.w, ut, fs[q + 3]);
+                        }
                     }
                 }
             }
@@ -514,12 +826,36 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
             if (tid == 0) issue_next();
         }
         if (aborted) break;
-        if (lane < R) {
+        if constexpr (TC) {
 #pragma unroll
-            for (int q = 0; q < FU_JG; ++q)
-                if (q < jn) Fs[(int64_t)(jb + q) * R + lane] += facc[q];
+            for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int jl = 16 * mt + g + 8 * (e >> 1);
+                        const int r = 8 * nt + 2 * tg + (e & 1);
+                        if (jl < jn && r < R)
+                            Fs[(int64_t)(jb + jl) * R + r] += ldexpf(facc[mt][nt][e], ex + eu);
+                    }
+        } else {
+            if (lane < R) {
+#pragma unroll
+                for (int q = 0; q < FU_JG; ++q)
+                    if (q < jn) Fs[(int64_t)(jb + q) * R + lane] += fs[q];
+            }
         }
         __syncthreads();
+        {
+            const long long now = clock64();
+            cyc[2] += (unsigned long long)(now - tmark);
+            tmark = now;
+        }
+    }
+    if (a.phase_cycles && tid == 0) {
+        atomicAdd(&a.phase_cycles[0], cyc[0]);
+        atomicAdd(&a.phase_cycles[1], cyc[1]);
+        atomicAdd(&a.phase_cycles[2], cyc[2]);
     }
     if (aborted) {
         // let copies already issued land (bounded) before the CTA exits
@@ -532,43 +868,263 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
     }
     // ---- CTA partials of G and ||X||² (fixed order) -------------------------
     __syncthreads();
-    float *gsm = Ypart;        // reuse: FU_WARPS × R × R floats (needs R*R*8 <= Ypart size)
-    for (int q = 0; q < FU_RP; ++q)
-        if (lane < R && q < R) gsm[(warp * FU_RP + lane) * FU_RP + q] = gacc[q];
+    float *gsm = Ypart;        // FU_WARPS × FU_RP × FU_RP floats: spans Ypart and Ytile
+#pragma unroll
+    for (int q = 0; q < FU_RP; ++q) gsm[(warp * FU_RP + lane) * FU_RP + q] = gacc[q];
     __syncthreads();
     for (int e = tid; e < R * R; e += FU_THREADS) {
         const int r = e / R, q = e % R;
-        double s = 0.0;
-        for (int w = 0; w < FU_WARPS; ++w) s += (double)gsm[(w * FU_RP + r) * FU_RP + q];
-        a.Gpart[(int64_t)blockIdx.x * R * R + e] = s;
+        double sacc = 0.0;
+        for (int w = 0; w < FU_WARPS; ++w) sacc += (double)gsm[(w * FU_RP + r) * FU_RP + q];
+        a.Gpart[(int64_t)blockIdx.x * R * R + e] = sacc;
     }
-    // ||X||²: lane 0 of each warp holds its warp's share
     __syncthreads();
-    double *xsm = reinterpret_cast<double *>(Ytile);
-    if (lane == 0) xsm[warp] = xn_d;
+    // ||X||²: TC — every lane holds a distinct share; SIMT — lane 0 of each warp
+    double xs_d = TC ? (double)xn_d : (lane == 0 ? xn_d : 0.0);
+    xs_d = warp_sum(xs_d);
+    double *xsm = reinterpret_cast<double *>(Ytile + 2 * FU_WARPS * FU_RP);
+    if (lane == 0) xsm[warp] = xs_d;
     __syncthreads();
     if (tid == 0) {
-        double s = 0.0;
-        for (int w = 0; w < FU_WARPS; ++w) s += xsm[w];
-        a.xn_part[blockIdx.x] = s;
+        double sacc = 0.0;
+        for (int w = 0; w < FU_WARPS; ++w) sacc += xsm[w];
+        a.xn_part[blockIdx.x] = sacc;
     }
 }
 
-// Ṽ = V Γ⁺ (FP32) and Γ in double-float, one warp per row of V.
-__global__ void k_vtilde(const double *__restrict__ V, const double *__restrict__ GamP,
-                         const double *__restrict__ Gam, int J, int R, float *__restrict__ Vt,
-                         df *__restrict__ Gdf) {
-    const int lane = threadIdx.x & 31;
-    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j < J) {
-        for (int q = lane; q < R; q += 32) {
-            double s = 0.0;
-            for (int r = 0; r < R; ++r) s += V[(int64_t)j * R + r] * GamP[r * R + q];
-            Vt[(int64_t)j * R + q] = (float)s;
+// V = Q_V R_V from Γ = VᵀV = R_VᵀR_V (Cholesky, FP64, one warp): R_V (upper),
+// L⁻¹ = R_V⁻ᵀ (lower) in FP64 and FP32, and Γ in double-float.  Clears
+// *gam_ok when Γ is not safely positive definite (the same test as Γ⁺).
+__global__ void k_vqr(const double *__restrict__ Gam, int R, double rtol, double *__restrict__ RV,
+                      double *__restrict__ Linv, float *__restrict__ LinvF, df *__restrict__ Gdf,
+                      int *__restrict__ gam_ok) {
+    extern __shared__ double qsm[];
+    const int ld = R + 1, lane = threadIdx.x & 31;
+    double *L = qsm, *Li = qsm + R * ld, *rinv = Li + R * ld;
+    for (int e = lane; e < R * R; e += 32) {
+        L[(e / R) * ld + (e % R)] = Gam[e];
+        Gdf[e] = df_from_double(Gam[e]);
+    }
+    __syncwarp();
+    double md = 0.0;
+    for (int i = lane; i < R; i += 32) md = fmax(md, fabs(L[i * ld + i]));
+    md = warp_max(md);
+    const bool ok = md > 0.0 && warp_cholesky(L, R, ld, 100.0 * rtol * md);
+    if (!ok) {
+        if (lane == 0) *gam_ok = 0;
+        return;
+    }
+    for (int i = lane; i < R; i += 32) rinv[i] = 1.0 / L[i * ld + i];
+    __syncwarp();
+    // lane c: column c of L⁻¹ by forward substitution (no divisions in the loop)
+    for (int c = lane; c < R; c += 32) {
+        for (int i = 0; i < R; ++i) {
+            double x = 0.0;
+            if (i >= c) {
+                x = (i == c) ? 1.0 : 0.0;
+                for (int q = c; q < i; ++q) x -= L[i * ld + q] * Li[q * ld + c];
+                x *= rinv[i];
+            }
+            Li[i * ld + c] = x;
         }
     }
-    if (blockIdx.x == 0)
-        for (int e = threadIdx.x; e < R * R; e += blockDim.x) Gdf[e] = df_from_double(Gam[e]);
+    __syncwarp();
+    for (int e = lane; e < R * R; e += 32) {
+        const int i = e / R, q = e % R;
+        RV[e] = (q >= i) ? L[q * ld + i] : 0.0;     // R_V = Lᵀ
+        Linv[e] = Li[i * ld + q];
+        LinvF[e] = (float)Li[i * ld + q];
+    }
+}
+
+// Q_V = V R_V⁻¹ = V L⁻ᵀ in FP32, one warp per row of V.
+__global__ void k_qv(const double *__restrict__ V, const double *__restrict__ Linv, int J, int R,
+                     float *__restrict__ QV) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= J) return;
+    for (int c = lane; c < R; c += 32) {
+        double s = 0.0;
+        for (int t = 0; t <= c; ++t) s += V[(int64_t)j * R + t] * Linv[c * R + t];
+        QV[(int64_t)j * R + c] = (float)s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Slices the tiles cannot hold (more than FU_TILE_MAX new rows, or several
+// segments) are split into chunks of at most FU_TILE_MAX rows of one segment.
+//   k_big_b  one warp per chunk: U from P' = X Q_V (computed by k_xv) as in
+//            the tiles, written out; chunk partials of ΔD = UᵀU and Δc.
+//   k_big_c  one warp per slice (big slices, then untouched slices with no
+//            chunks): sums its chunk partials in order, then slice_finish().
+// Slices whose S_k has a zero entry take the FP64 map M = S(SΓS)⁺ in k_big_b.
+struct BigArgs {
+    const float *Y;           // N×R, rows of big slices hold P' = X Q_V
+    const int64_t *ch_row0;   // chunk start row
+    const int *ch_n;          // chunk rows
+    const int *ch_k;          // chunk slice
+    int n_chunks;
+    const int *fin_k;         // slices to finish: big slices then untouched
+    const int *fin_c0;        // [n_fin + 1] chunk range per slice (0 chunks: untouched)
+    int n_fin;
+    float *dpart;             // n_chunks × (R·R + R)
+};
+
+__device__ __forceinline__ void big_chunk(const FusedArgs &a, const BigArgs &bg, int ch,
+                                          float (*Usw)[FU_RP]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int R = a.R;
+    const int k = bg.ch_k[ch];
+    const int64_t row0 = bg.ch_row0[ch];
+    const int n = bg.ch_n[ch];
+    const bool gam_ok = *a.gam_ok != 0;
+    const double wold_d = lane < R ? a.W[(int64_t)k * R + lane] : 1.0;
+    const bool fast = gam_ok && __all_sync(0xffffffffu, wold_d != 0.0);
+    double *wsp = a.wsp + (size_t)(blockIdx.x * FU_WARPS + warp) * fu_wsp_doubles(R);
+    const int ld = R + 1;
+    // U = P' mcol: fast path mcol = column `lane` of R_V⁻ᵀ S⁻¹; general path
+    // (zero weights) mcol = column of R_V S (S Γ S)⁺ in FP64 (rare)
+    float mcol[FU_RP], rvcol[FU_RP];
+    if (fast) {
+        const float winv = lane < R ? 1.0f / (float)wold_d : 0.f;
+#pragma unroll
+        for (int t = 0; t < FU_RP; ++t) {
+            mcol[t] = (t < R && lane < R) ? a.GPf[t * R + lane] * winv : 0.f;
+            rvcol[t] = 0.f;
+        }
+    } else {
+        double *Aw = wsp, *Ew = Aw + R * ld, *Mw = Ew + R * ld, *fw = Mw + R * ld;
+        for (int e = lane; e < R * R; e += 32) {
+            const int r = e / R, q = e % R;
+            Aw[r * ld + q] = a.W[(int64_t)k * R + r] * a.Gam[e] * a.W[(int64_t)k * R + q];
+        }
+        __syncwarp();
+        warp_psd_pinv(Aw, Ew, fw, Mw, R, ld, a.rtol, 1, false);
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < FU_RP; ++t) {
+            double m = 0.0;
+            if (t < R && lane < R)
+                for (int q = t; q < R; ++q)
+                    m += a.RV[t * R + q] * a.W[(int64_t)k * R + q] * Mw[q * ld + lane];
+            mcol[t] = (float)m;
+            rvcol[t] = (t < R && lane < R) ? (float)a.RV[t * R + lane] : 0.f;
+        }
+        atomicAdd(&a.err[1], 1);
+    }
+    float dd[FU_RP];
+#pragma unroll
+    for (int q = 0; q < FU_RP; ++q) dd[q] = 0.f;
+    float dc = 0.f;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int m = min(32, n - i0);
+        // P' rows → shared, then U = P' mcol per row
+        for (int i = 0; i < m; ++i)
+            Usw[i][lane] = lane < R ? bg.Y[(row0 + i0 + i) * R + lane] : 0.f;
+        __syncwarp();
+        for (int i = 0; i < m; ++i) {
+            float u = 0.f, pl = 0.f;
+#pragma unroll
+            for (int t = 0; t < FU_RP; t += 4) {
+                const float4 p4 = *reinterpret_cast<const float4 *>(&Usw[i][t]);
+                u = fmaf(p4.x, mcol[t], u);
+                u = fmaf(p4.y, mcol[t + 1], u);
+                u = fmaf(p4.z, mcol[t + 2], u);
+                u = fmaf(p4.w, mcol[t + 3], u);
+                if (!fast) {
+                    pl = fmaf(p4.x, rvcol[t], pl);
+                    pl = fmaf(p4.y, rvcol[t + 1], pl);
+                    pl = fmaf(p4.z, rvcol[t + 2], pl);
+                    pl = fmaf(p4.w, rvcol[t + 3], pl);
+                }
+            }
+            dc = fmaf(u, pl, dc);
+            __syncwarp();
+            Usw[i][lane] = u;
+            if (lane < R) a.U[(row0 + i0 + i) * R + lane] = u;
+        }
+        __syncwarp();
+        for (int i = 0; i < m; ++i) {
+            const float ul = Usw[i][lane];
+#pragma unroll
+            for (int q = 0; q < FU_RP; q += 4) {
+                const float4 u4 = *reinterpret_cast<const float4 *>(&Usw[i][q]);
+                dd[q] = fmaf(ul, u4.x, dd[q]);
+                dd[q + 1] = fmaf(ul, u4.y, dd[q + 1]);
+                dd[q + 2] = fmaf(ul, u4.z, dd[q + 2]);
+                dd[q + 3] = fmaf(ul, u4.w, dd[q + 3]);
+            }
+        }
+        __syncwarp();
+    }
+    if (fast) {                       // Δc = diag(ΔD S Γ) for this chunk
+        float sacc = 0.f;
+        const float wl = lane < R ? (float)wold_d : 0.f;
+#pragma unroll
+        for (int q = 0; q < FU_RP; ++q) {
+            const float wq = __shfl_sync(0xffffffffu, wl, q);
+            if (q < R && lane < R) sacc = fmaf(dd[q] * wq, (float)a.Gam[q * R + lane], sacc);
+        }
+        dc = sacc;
+    }
+    float *out = bg.dpart + (size_t)ch * (R * R + R);
+    if (lane < R) {
+#pragma unroll
+        for (int q = 0; q < FU_RP; ++q)
+            if (q < R) out[lane * R + q] = dd[q];
+        out[R * R + lane] = dc;
+    }
+}
+
+__global__ void __launch_bounds__(256, 1) k_big_b(FusedArgs a, BigArgs bg) {
+    __shared__ __align__(16) float Us[FU_WARPS][32][FU_RP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int R = a.R;
+    for (int ch = blockIdx.x * FU_WARPS + warp; ch < bg.n_chunks; ch += gridDim.x * FU_WARPS) {
+        big_chunk(a, bg, ch, Us[warp]);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_big_c(FusedArgs a, BigArgs bg, double *Gpart_out) {
+    __shared__ df Gs[FU_RP * FU_RP];
+    __shared__ __align__(16) float Lw_all[FU_WARPS][FU_RP * FU_LD];   // also the G reduction
+    __shared__ df xw_all[FU_WARPS][FU_RP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int R = a.R;
+    for (int i = threadIdx.x; i < R * R; i += blockDim.x) Gs[(i / R) * FU_RP + (i % R)] = a.Gdf[i];
+    __syncthreads();
+    float gacc[FU_RP];
+#pragma unroll
+    for (int q = 0; q < FU_RP; ++q) gacc[q] = 0.f;
+    double *wsp = a.wsp + (size_t)(blockIdx.x * FU_WARPS + warp) * fu_wsp_doubles(R);
+    for (int f = blockIdx.x * FU_WARPS + warp; f < bg.n_fin; f += gridDim.x * FU_WARPS) {
+        const int k = bg.fin_k[f];
+        float dd[FU_RP];
+#pragma unroll
+        for (int q = 0; q < FU_RP; ++q) dd[q] = 0.f;
+        float dc = 0.f;
+        for (int c = bg.fin_c0[f]; c < bg.fin_c0[f + 1]; ++c) {
+            const float *in = bg.dpart + (size_t)c * (R * R + R);
+            if (lane < R) {
+#pragma unroll
+                for (int q = 0; q < FU_RP; ++q)
+                    if (q < R) dd[q] += in[lane * R + q];
+                dc += in[R * R + lane];
+            }
+        }
+        slice_finish(a, k, dd, dc, gacc, Gs, Lw_all[warp], xw_all[warp], wsp);
+    }
+    __syncthreads();
+    float *gsm = &Lw_all[0][0];             // FU_WARPS × FU_RP × FU_RP floats fit in Lw_all
+#pragma unroll
+    for (int q = 0; q < FU_RP; ++q) gsm[(warp * FU_RP + lane) * FU_RP + q] = gacc[q];
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+        const int r = e / R, q = e % R;
+        double s = 0.0;
+        for (int w = 0; w < FU_WARPS; ++w) s += (double)gsm[(w * FU_RP + r) * FU_RP + q];
+        Gpart_out[(int64_t)blockIdx.x * R * R + e] = s;
+    }
 }
 
 }  // namespace dash

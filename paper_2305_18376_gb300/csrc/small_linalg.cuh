@@ -168,6 +168,35 @@ __device__ inline void warp_spectral_apply(const double *E, const double *f, int
     __syncwarp();
 }
 
+// Inverse of an SPD matrix from its Cholesky factor (lower triangle of L,
+// as left by warp_cholesky): lane c solves L Lᵀ x = e_c for column c of the
+// inverse on its own, with the reciprocals of diag(L) computed once, so the
+// inner loops need no divisions and no warp synchronisation (FP64 division
+// is a long software sequence on parts with a slow FP64 pipe).  out must not
+// alias L; rinv is length-n workspace.  n <= 64.
+__device__ inline void warp_cholesky_inverse(const double *L, int n, int ld, double *out,
+                                             double *rinv) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < n; i += 32) rinv[i] = 1.0 / L[i * ld + i];
+    __syncwarp();
+    for (int c = lane; c < n; c += 32) {
+        // forward: L y = e_c (y[i] = 0 for i < c); y kept in column c of out
+        for (int i = 0; i < c; ++i) out[i * ld + c] = 0.0;
+        for (int i = c; i < n; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) s -= L[i * ld + k] * out[k * ld + c];
+            out[i * ld + c] = s * rinv[i];
+        }
+        // backward: Lᵀ x = y
+        for (int i = n - 1; i >= 0; --i) {
+            double s = out[i * ld + c];
+            for (int k = i + 1; k < n; ++k) s -= L[k * ld + i] * out[k * ld + c];
+            out[i * ld + c] = s * rinv[i];
+        }
+    }
+    __syncwarp();
+}
+
 // Pseudo-inverse (power 1) or pseudo-inverse square root (power 2) of the
 // symmetric PSD matrix in A, written to out.  A and E are destroyed (E is
 // workspace), f is length-n workspace.  When `try_cholesky` and power == 1,
@@ -182,14 +211,7 @@ __device__ inline void warp_psd_pinv(double *A, double *E, double *f, double *ou
         for (int i = lane; i < n * n; i += 32) E[(i / n) * ld + (i % n)] = A[(i / n) * ld + (i % n)];
         __syncwarp();
         if (md > 0.0 && warp_cholesky(E, n, ld, 100.0 * rtol * md)) {
-            // columns of the inverse: solve L Lᵀ x = e_c, one column per pass
-            for (int c = 0; c < n; ++c) {
-                for (int i = lane; i < n; i += 32) f[i] = (i == c) ? 1.0 : 0.0;
-                __syncwarp();
-                warp_cholesky_solve(E, n, ld, f);
-                for (int i = lane; i < n; i += 32) out[i * ld + c] = f[i];
-            }
-            __syncwarp();
+            warp_cholesky_inverse(E, n, ld, out, f);
             // symmetrise
             for (int idx = lane; idx < n * n; idx += 32) {
                 const int r = idx / n, c = idx % n;

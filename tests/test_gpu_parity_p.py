@@ -15,7 +15,8 @@ from tests._parity import (FIT_TOL, TOL, compare_state_p, gpu_rows_by_slice, ora
 
 pytestmark = pytest.mark.gpu
 
-PREC_DTYPE = {"fp64": ("f64", torch.float64), "fp32": ("f32", torch.float32)}
+PREC_DTYPE = {"fp64": ("f64", torch.float64), "fp32": ("f32", torch.float32),
+              "f16x3": ("f32", torch.float32)}
 
 
 def _model(J, R, lam, prec, **kw):
@@ -63,6 +64,7 @@ def _run_stream(w, prec, n_steps, init_iters=3, via="batch", seed_v=1):
             assert first == b.K_before
             m.update()
         g = m.get_state_p()
+        print(f"  update {t} errors:", {k: rel(g[k], getattr(st, k)) for k in "VWcDFG"})
         errs = compare_state_p(g, st, TOL[prec], f"update {t}")
         rows = gpu_rows_by_slice(m.new_rows(), b)
         errs["U"] = max(rel(rows[k], Uo[k]) for k in rows)
@@ -76,7 +78,7 @@ def _run_stream(w, prec, n_steps, init_iters=3, via="batch", seed_v=1):
     return worst
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3"])
 def test_small_stream_parity(prec):
     w = tiny(K0=6, J=9, R=3, steps=4, sigma=0.05, lam=0.9)
     _run_stream(w, prec, 4)
@@ -95,12 +97,13 @@ def test_c1_workload_fp64():
     print("c1 fp64 worst relative errors:", worst)
 
 
-def test_c2_shaped_fp32():
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_c2_shaped(prec):
     """c2's shape (J=88, R=10, +1 row per slice, +10 slices) at K0=300."""
     w = workload("c2", K0=300, init_rows=("uniform", 50, 300), new_slice_rows=("uniform", 50, 100),
                  steps=5)
-    worst = _run_stream(w, "fp32", 5, init_iters=3)
-    print("c2-shaped fp32 worst relative errors:", worst)
+    worst = _run_stream(w, prec, 5, init_iters=3)
+    print(f"c2-shaped {prec} worst relative errors:", worst)
 
 
 def _state_from_oracle(w, prec, lam):
@@ -114,7 +117,7 @@ def _state_from_oracle(w, prec, lam):
     return O.init_helpers_p(X0, U, W, V)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3"])
 def test_ragged_edge_batch_from_oracle_state(prec):
     """One update from an oracle state with: a slice split in two segments,
     untouched slices (λ decay only), a 1-row segment, a segment longer than
@@ -160,7 +163,7 @@ def test_rank_deficient_gram_uses_the_pseudo_inverse(prec):
         assert rel(got[k], Uo[k]) <= tol
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3"])
 def test_zero_weight_entries_take_the_general_lemma1_path(prec):
     """A slice whose S_k has zero entries: S (S Γ S)⁺ ≠ Γ⁻¹ S⁻¹ (in the
     fused kernel this is its in-kernel FP64 fallback)."""
@@ -183,14 +186,25 @@ def test_zero_weight_entries_take_the_general_lemma1_path(prec):
         assert rel(got[k], Uo[k]) <= tol
 
 
-def test_fused_tiles_span_many_slices_and_ctas():
-    """FP32 path with a few thousand small slices of 1-64 rows (c4's update
-    shape at small J and R): many tiles per CTA, big and split slices on the
-    general path in the same update."""
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_fused_tiles_span_many_slices_and_ctas(prec):
+    """A few thousand small slices of 1-64 rows (c4's update shape at small J
+    and R): many tiles per CTA, big and split slices on the chunked path in
+    the same update."""
     w = tiny(K0=3000, J=48, R=8, steps=2, sigma=0.1, lam=0.95, rows=("uniform", 1, 64),
              new=5, new_rows=("uniform", 100, 700), init_rows=("uniform", 8, 40))
-    worst = _run_stream(w, "fp32", 2, init_iters=2)
-    print("many-slice fp32 worst relative errors:", worst)
+    worst = _run_stream(w, prec, 2, init_iters=2)
+    print(f"many-slice {prec} worst relative errors:", worst)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3"])
+def test_c4_shape_small_k(prec):
+    """c4's J = 512 and R = 32 (full register tiles of the MMA path) at
+    K0 = 300 slices."""
+    w = workload("c4", K0=300, steps=2, init_rows=("uniform", 40, 300),
+                 new_slices_per_step=3, new_slice_rows=("uniform", 200, 600))
+    worst = _run_stream(w, prec, 2, init_iters=2)
+    print(f"c4-shaped {prec} worst relative errors:", worst)
 
 
 def test_empty_update_is_pure_decay():
