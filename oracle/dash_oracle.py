@@ -26,6 +26,11 @@ mentions and Dash drops):
   T_k = B_k^{-1/2} (pseudo-inverse square root),  Q_k,new = A_new T_k,
   Y_k = T_k Z_k  (= Q_kᵀ Λ_k X_k),  then one CP-ALS sweep H → V → W on {Y_k}.
 With one batch and an empty model this is one classic PARAFAC2-ALS iteration.
+B_k is carried as its triangular square root L_k (B_k = L_kᵀL_k, L_k the R
+factor of the λ^{age/2}-weighted stacked A rows), updated by a QR of
+[√λ L_k; A_new], and T_k comes from the SVD of L_k: forming B_k itself
+squares cond(A_k), and on planted tensors with U(0,1) factors cond(B_k)
+reaches 1e9-1e12, where any B-based T_k loses 7-12 digits.
 
 Parity pins (tests/test_oracle_*.py): Lemma 1–3 optimality against direct
 least squares, the Khatri–Rao identity of Appendix A.2, λ = 1 exactness of
@@ -81,6 +86,42 @@ def inv_sqrt_psd(B: np.ndarray, rtol: Optional[float] = None) -> np.ndarray:
     d = np.zeros_like(mu)
     d[keep] = 1.0 / np.sqrt(mu[keep])
     return (E * d) @ E.T
+
+
+def r_factor(M: np.ndarray) -> np.ndarray:
+    """The R factor of a thin QR of M (rows ≥ 0), as an R×R upper-triangular
+    matrix with a non-negative diagonal (zero rows appended when M has fewer
+    rows than columns).  It is the unique square root of MᵀM of that shape
+    when M has full column rank."""
+    M = np.asarray(M, dtype=np.float64)
+    n = M.shape[1]
+    out = np.zeros((n, n))
+    if M.shape[0] == 0:
+        return out
+    Rf = np.linalg.qr(M, mode="r")
+    sgn = np.where(np.diag(Rf) < 0.0, -1.0, 1.0)
+    Rf = Rf * sgn[:, None]
+    out[:Rf.shape[0]] = Rf
+    return out
+
+
+def inv_sqrt_from_factor(L: np.ndarray, rtol: Optional[float] = None) -> np.ndarray:
+    """T = (LᵀL)^{-1/2} in the pseudo-inverse sense from the SVD
+    L = U diag(σ) Pᵀ: T = P diag(1/σ) Pᵀ, with the directions whose
+    eigenvalue σ² of LᵀL is <= rtol·σ_max² dropped (the cut of
+    inv_sqrt_psd applied to B = LᵀL).  Works on L, whose condition number
+    is the square root of B's."""
+    L = np.asarray(L, dtype=np.float64)
+    n = L.shape[1]
+    if rtol is None:
+        rtol = n * EPS
+    _, sig, Pt = np.linalg.svd(L)
+    if sig.size == 0 or sig[0] == 0.0:
+        return np.zeros((n, n))
+    keep = sig * sig > rtol * sig[0] * sig[0]
+    d = np.zeros_like(sig)
+    d[keep] = 1.0 / sig[keep]
+    return (Pt.T * d) @ Pt
 
 
 def vec(X: np.ndarray) -> np.ndarray:
@@ -263,12 +304,17 @@ class StateQ:
     V: np.ndarray          # J×R
     H: np.ndarray          # R×R
     W: np.ndarray          # K×R
-    B: np.ndarray          # K×R×R   λ-weighted Σ A_kᵀA_k
+    L: np.ndarray          # K×R×R   upper-triangular, L_kᵀL_k = B_k = λ-weighted Σ A_kᵀA_k
     Z: np.ndarray          # K×R×J   λ-weighted Σ A_kᵀX_k
 
     @property
     def K(self) -> int:
         return self.W.shape[0]
+
+    @property
+    def B(self) -> np.ndarray:
+        """B_k = L_kᵀL_k (formed only for inspection)."""
+        return np.einsum("kij,kil->kjl", self.L, self.L)
 
     def copy(self) -> "StateQ":
         return StateQ(*(np.array(getattr(self, f.name)) for f in dataclasses.fields(self)))
@@ -278,7 +324,7 @@ def empty_state_q(V0: np.ndarray, H0: Optional[np.ndarray] = None) -> StateQ:
     J, R = V0.shape
     H = np.eye(R) if H0 is None else np.array(H0, dtype=np.float64)
     return StateQ(V=np.array(V0, dtype=np.float64), H=H, W=np.zeros((0, R)),
-                  B=np.zeros((0, R, R)), Z=np.zeros((0, R, J)))
+                  L=np.zeros((0, R, R)), Z=np.zeros((0, R, J)))
 
 
 def cp_sweep(Y: Sequence[np.ndarray], H: np.ndarray, V: np.ndarray, W: np.ndarray,
@@ -305,28 +351,38 @@ def cp_sweep(Y: Sequence[np.ndarray], H: np.ndarray, V: np.ndarray, W: np.ndarra
 
 
 def dash_update_q(state: StateQ, segments, n_new: int, lam: float,
-                  rtol: Optional[float] = None
+                  rtol: Optional[float] = None, a_noise=None
                   ) -> Tuple[StateQ, Dict[int, np.ndarray], Dict[int, np.ndarray]]:
     """One constrained-mode update.  Returns the new state, the new rows of
-    Q_k (A_new T_k) and the new rows A_new, per touched slice."""
+    Q_k (A_new T_k) and the new rows A_new, per touched slice.
+
+    a_noise (tests only, default None): a function applied to each A_new
+    right after it is formed and to each updated L_k, so that a test can
+    measure how far a rounding of the bulk product and of the QR update
+    moves the result; None leaves the arithmetic as written."""
     J, R = state.V.shape
     K = state.K
     Kn = K + n_new
     X = _group(segments, K, n_new, J)
     V, H = state.V, state.H
     W = np.vstack([state.W, np.ones((n_new, R))])   # S_k := I for new slices
-    B = np.concatenate([lam * state.B, np.zeros((n_new, R, R))], axis=0)
+    # √λ·L_k is the factor of λB_k; new slices start from zero
+    L = np.concatenate([np.sqrt(lam) * state.L, np.zeros((n_new, R, R))], axis=0)
     Z = np.concatenate([lam * state.Z, np.zeros((n_new, R, J))], axis=0)
     A: Dict[int, np.ndarray] = {}
     for k, Xk in X.items():
         A[k] = Xk @ V @ np.diag(W[k]) @ H.T
-        B[k] = B[k] + A[k].T @ A[k]
+        if a_noise is not None:
+            A[k] = a_noise(A[k])
+        L[k] = r_factor(np.vstack([L[k], A[k]]))   # (L')ᵀL' = λB_k + A_newᵀA_new
+        if a_noise is not None:
+            L[k] = np.triu(a_noise(L[k]))
         Z[k] = Z[k] + A[k].T @ Xk
-    T = [inv_sqrt_psd(B[k], rtol) for k in range(Kn)]
+    T = [inv_sqrt_from_factor(L[k], rtol) for k in range(Kn)]
     Y = [T[k] @ Z[k] for k in range(Kn)]
     H2, V2, W2 = cp_sweep(Y, H, V, W, rtol)
     Qnew = {k: A[k] @ T[k] for k in X}
-    return StateQ(V=V2, H=H2, W=W2, B=B, Z=Z), Qnew, A
+    return StateQ(V=V2, H=H2, W=W2, L=L, Z=Z), Qnew, A
 
 
 def parafac2_als(X: Sequence[np.ndarray], H0, V0, W0, n_iter: int):
@@ -354,19 +410,23 @@ def parafac2_als(X: Sequence[np.ndarray], H0, V0, W0, n_iter: int):
     return Q, H, V, W
 
 
-def init_helpers_q(X: Sequence[np.ndarray], H, V, W) -> StateQ:
+def init_helpers_q(X: Sequence[np.ndarray], H, V, W, a_noise=None) -> StateQ:
     """Constrained-mode helpers of the initial tensor from its final factors
-    (the analogue of Eqs. 6-9): B_k = A_kᵀA_k, Z_k = A_kᵀX_k with
-    A_k = X_k V S_k Hᵀ."""
+    (the analogue of Eqs. 6-9): L_k = R factor of A_k (B_k = A_kᵀA_k),
+    Z_k = A_kᵀX_k with A_k = X_k V S_k Hᵀ."""
     K = len(X)
     J, R = V.shape
-    B = np.zeros((K, R, R))
+    L = np.zeros((K, R, R))
     Z = np.zeros((K, R, J))
     for k in range(K):
         A = X[k] @ V @ np.diag(W[k]) @ H.T
-        B[k] = A.T @ A
+        if a_noise is not None:                     # tests only (see dash_update_q)
+            A = a_noise(A)
+        L[k] = r_factor(A)
+        if a_noise is not None:
+            L[k] = np.triu(a_noise(L[k]))
         Z[k] = A.T @ X[k]
-    return StateQ(V=np.array(V), H=np.array(H), W=np.array(W), B=B, Z=Z)
+    return StateQ(V=np.array(V), H=np.array(H), W=np.array(W), L=L, Z=Z)
 
 
 # ---------------------------------------------------------------------------

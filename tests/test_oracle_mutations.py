@@ -39,6 +39,19 @@ def _lambda_dropped_on_old_f_g(state, segments, n_new, lam, **kw):
 
 _ORIG_UPDATE = O.dash_update_p
 
+
+def _r_factor_unsquared(M):
+    L = _ORIG_R_FACTOR(M)
+    return L * L                                               # entrywise square
+
+
+def _polar_via_transpose(L, rtol=None):
+    return _ORIG_INV_SQRT_F(L.T, rtol)                          # factor transposed
+
+
+_ORIG_R_FACTOR = O.r_factor
+_ORIG_INV_SQRT_F = O.inv_sqrt_from_factor
+
 CASES = [
     ("update_u_new", _dropped_s_in_lemma1, [P.test_lemma1_u_new_is_the_least_squares_solution]),
     ("solve_w_row", _sum_not_hadamard,
@@ -46,6 +59,9 @@ CASES = [
     ("c_term", _transposed_c_term, [P.test_c_term_equals_explicit_triple_sum]),
     ("update_u_new", _u_without_pinv_cutoff, [P.test_lemma1_u_new_is_the_least_squares_solution]),
     ("dash_update_p", _lambda_dropped_on_old_f_g, [P.test_worked_example_rank_one_exact_fractions]),
+    ("r_factor", _r_factor_unsquared, [lambda: P.test_mode_q_summaries_exact_and_q_orthonormal(0.8)]),
+    ("inv_sqrt_from_factor", _polar_via_transpose,
+     [P.test_mode_q_single_batch_equals_parafac2_als_iteration]),
 ]
 
 

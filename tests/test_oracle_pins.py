@@ -89,6 +89,48 @@ def test_inv_sqrt_gives_polar_factor():
     assert np.allclose(np.sort(ev), [0, 0, 1, 1], atol=1e-8)
 
 
+def test_r_factor_is_the_triangular_square_root():
+    M = RNG.standard_normal((9, 4))
+    L = O.r_factor(M)
+    assert np.all(np.tril(L, -1) == 0) and np.all(np.diag(L) > 0)
+    assert _rel(L.T @ L, M.T @ M) < 1e-13
+    assert _rel(L, np.linalg.cholesky(M.T @ M).T) < 1e-12
+    # fewer rows than columns: zero rows below, still LᵀL = MᵀM
+    M2 = RNG.standard_normal((2, 4))
+    L2 = O.r_factor(M2)
+    assert L2.shape == (4, 4) and np.all(L2[2:] == 0)
+    assert _rel(L2.T @ L2, M2.T @ M2) < 1e-13
+    assert np.all(O.r_factor(np.zeros((0, 3))) == 0)
+    # updating by stacking equals factoring all rows at once
+    M3 = RNG.standard_normal((5, 4))
+    up = O.r_factor(np.vstack([np.sqrt(0.7) * L, M3]))
+    assert _rel(up.T @ up, 0.7 * M.T @ M + M3.T @ M3) < 1e-13
+
+
+def test_inv_sqrt_from_factor_is_accurate_where_the_gram_is_not():
+    """T = (LᵀL)^{-1/2} from the factor gives the polar factor A·T to about
+    eps·cond(A); through B = AᵀA only to eps·cond(A)²."""
+    A = RNG.standard_normal((9, 4))
+    T = O.inv_sqrt_from_factor(O.r_factor(A))
+    P, _, Zt = np.linalg.svd(A, full_matrices=False)
+    assert _rel(A @ T, P @ Zt) < 1e-13
+    assert _rel(T, O.inv_sqrt_psd(A.T @ A)) < 1e-12
+    # cond(A) = 1e6: the Gram route has cond 1e12
+    U, _ = np.linalg.qr(RNG.standard_normal((40, 4)))
+    Vq, _ = np.linalg.qr(RNG.standard_normal((4, 4)))
+    A = (U * np.array([1.0, 1e-2, 1e-4, 1e-6])) @ Vq.T
+    polar = U @ Vq.T
+    err_f = _rel(A @ O.inv_sqrt_from_factor(O.r_factor(A)), polar)
+    assert err_f < 1e-8
+    # rank-deficient: same cut as inv_sqrt_psd on the Gram matrix
+    A2 = A[:, :2] @ RNG.standard_normal((2, 4))
+    T2 = O.inv_sqrt_from_factor(O.r_factor(A2))
+    Q2 = A2 @ T2
+    ev = np.linalg.eigvalsh(Q2.T @ Q2)
+    assert np.allclose(np.sort(ev), [0, 0, 1, 1], atol=1e-8)
+    assert np.all(O.inv_sqrt_from_factor(np.zeros((3, 3))) == 0)
+
+
 # ---------------------------------------------------------------------------
 # Lemma 1-3 as least-squares minimisers
 # ---------------------------------------------------------------------------
@@ -380,9 +422,10 @@ def test_mode_q_single_batch_equals_parafac2_als_iteration():
 
 @pytest.mark.parametrize("lam", [1.0, 0.8])
 def test_mode_q_summaries_exact_and_q_orthonormal(lam):
-    """B_k, Z_k equal the λ-weighted sums over stored A rows (exact at any λ:
-    A rows are frozen), and Q_k = Ã_k T_k satisfies Q_kᵀΛQ_k = I when B_k has
-    full rank (QᵀQ = I at λ = 1)."""
+    """L_kᵀL_k = B_k and Z_k equal the λ-weighted sums over stored A rows
+    (exact at any λ: A rows are frozen), L_k is the Cholesky factor of that
+    sum, and Q_k = Ã_k T_k satisfies Q_kᵀΛQ_k = I when B_k has full rank
+    (QᵀQ = I at λ = 1)."""
     s = PlantedStream(tiny(K0=4, J=6, R=3, steps=3, sigma=0.05, lam=lam,
                            init_rows=("uniform", 5, 9)))
     ost = O.OracleStream("Q", RNG.random((6, 3)), lam)
@@ -393,10 +436,14 @@ def test_mode_q_summaries_exact_and_q_orthonormal(lam):
         Xk, Ak, wts = ost.slice_rows(k)
         B = (Ak * wts[:, None]).T @ Ak
         Z = (Ak * wts[:, None]).T @ Xk
-        assert _rel(ost.state.B[k], B) < 1e-12
+        L = ost.state.L[k]
+        assert np.all(np.tril(L, -1) == 0) and np.all(np.diag(L) >= 0)
+        assert _rel(L.T @ L, B) < 1e-12
         assert _rel(ost.state.Z[k], Z) < 1e-12
         if Ak.shape[0] >= 3:
-            T = O.inv_sqrt_psd(ost.state.B[k])
+            # the unique triangular square root: Cholesky of the from-scratch B
+            assert _rel(L, np.linalg.cholesky(B).T) < 1e-9
+            T = O.inv_sqrt_from_factor(L)
             Q = Ak @ T
             assert _rel((Q * wts[:, None]).T @ Q, np.eye(3)) < 1e-8
 
@@ -413,12 +460,12 @@ def test_mode_q_planted_truth_is_a_fixed_point():
                                 _segs(b), b.n_new, 1.0)
     # W of new slices starts at 1, so seed them with the planted weights
     st0 = O.StateQ(V=s.V.numpy(), H=s.H.numpy(), W=s.W.numpy()[:8],
-                   B=np.zeros((8, 3, 3)), Z=np.zeros((8, 3, 7)))
+                   L=np.zeros((8, 3, 3)), Z=np.zeros((8, 3, 7)))
     st1, Qn, _ = O.dash_update_q(st0, _segs(b), 0, 1.0)
     fit = O.fitness(X, [O.reconstruct_q(Qn[k], st1.H, st1.W[k], st1.V) for k in range(8)])
-    # the streamed form sees A only through B = AᵀA, so Q is accurate to
-    # about eps·cond(B); the SVD form of PARAFAC2-ALS to round-off
-    kappa = max(np.linalg.cond(st1.B[k]) for k in range(8))
+    # the streamed form sees A only through its R factor L, so Q is accurate
+    # to about eps·cond(L) = eps·cond(A); the SVD form of PARAFAC2-ALS to round-off
+    kappa = max(np.linalg.cond(st1.L[k]) for k in range(8))
     assert 1 - fit < 10 * O.EPS * kappa
     Q, H, V, W = O.parafac2_als(X, s.H.numpy(), s.V.numpy(), s.W.numpy()[:8], 1)
     fit_svd = O.fitness(X, [O.reconstruct_q(Q[k], H, W[k], V) for k in range(8)])
@@ -448,7 +495,7 @@ def test_mode_q_noiseless_recovery_from_seeded_start():
     fit = O.fitness(X, [O.reconstruct_q(Q[k], H, W[k], V) for k in range(K0)])
     assert fit > 1 - 1e-9
     # the streaming form run as repeated single-batch updates agrees
-    st = O.StateQ(V=V0, H=H0, W=W0, B=np.zeros((K0, R, R)), Z=np.zeros((K0, R, J)))
+    st = O.StateQ(V=V0, H=H0, W=W0, L=np.zeros((K0, R, R)), Z=np.zeros((K0, R, J)))
     for _ in range(250):
         st, Qn, _ = O.dash_update_q(st, _segs(b), 0, 0.0)
     fit2 = O.fitness(X, [O.reconstruct_q(Qn[k], st.H, st.W[k], st.V) for k in range(K0)])
