@@ -357,9 +357,9 @@ def dash_update_q(state: StateQ, segments, n_new: int, lam: float,
     Q_k (A_new T_k) and the new rows A_new, per touched slice.
 
     a_noise (tests only, default None): a function applied to each A_new
-    right after it is formed and to each updated L_k, so that a test can
-    measure how far a rounding of the bulk product and of the QR update
-    moves the result; None leaves the arithmetic as written."""
+    right after it is formed, to each updated L_k and to the swept H, V, W,
+    so that a test can measure how far roundings of that size move the
+    result; None leaves the arithmetic as written."""
     J, R = state.V.shape
     K = state.K
     Kn = K + n_new
@@ -381,6 +381,8 @@ def dash_update_q(state: StateQ, segments, n_new: int, lam: float,
     T = [inv_sqrt_from_factor(L[k], rtol) for k in range(Kn)]
     Y = [T[k] @ Z[k] for k in range(Kn)]
     H2, V2, W2 = cp_sweep(Y, H, V, W, rtol)
+    if a_noise is not None:
+        H2, V2, W2 = a_noise(H2), a_noise(V2), a_noise(W2)
     Qnew = {k: A[k] @ T[k] for k in X}
     return StateQ(V=V2, H=H2, W=W2, L=L, Z=Z), Qnew, A
 

@@ -174,13 +174,31 @@ class DashModel:
         self._ck(self._lib.dash_get_state_p(self._h, *(_pd(out[k]) for k in "VWcDFG")))
         return out
 
+    def set_state_q(self, V, H, W, L, Y):
+        """Load a mode-Q state: factors V, H, W, the triangular factors L_k of
+        B_k and the projected data Y_k = T_k Z_k (K×R×J)."""
+        K = int(np.asarray(W).shape[0])
+        R, J = self.R, self.J
+        V, H, W = _f64(V, (J, R)), _f64(H, (R, R)), _f64(W, (K, R))
+        L, Y = _f64(L, (K, R, R)), _f64(Y, (K, R, J))
+        self._ck(self._lib.dash_set_state_q(self._h, K, _pd(V), _pd(H), _pd(W), _pd(L), _pd(Y)))
+
+    def get_state_q(self) -> dict:
+        K, R, J = self.K, self.R, self.J
+        out = dict(V=np.empty((J, R)), H=np.empty((R, R)), W=np.empty((K, R)),
+                   L=np.empty((K, R, R)), Y=np.empty((K, R, J)))
+        self._ck(self._lib.dash_get_state_q(self._h, *(_pd(out[k]) for k in "VHWLY")))
+        return out
+
     def factors(self, k_first: int = 0, k_count: Optional[int] = None):
+        """(V, W rows) in mode P; (V, W rows, H) in mode Q."""
         if k_count is None:
             k_count = self.K - k_first
         V = np.empty((self.J, self.R))
         W = np.empty((k_count, self.R))
-        self._ck(self._lib.dash_factors(self._h, _pd(V), _pd(W), k_first, k_count, None))
-        return V, W
+        H = np.empty((self.R, self.R)) if self.mode == "Q" else None
+        self._ck(self._lib.dash_factors(self._h, _pd(V), _pd(W), k_first, k_count, _pd(H)))
+        return (V, W) if H is None else (V, W, H)
 
     def new_rows(self) -> np.ndarray:
         n = C.c_int64()

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "dash.h"
+#include "dash_host.cuh"
 #include "dash_internal.cuh"
 
 using namespace dash;
@@ -21,7 +22,7 @@ using namespace dash;
 // ---------------------------------------------------------------------------
 // errors
 // ---------------------------------------------------------------------------
-static dash_status fail(dash_model *m, dash_status s, const char *fmt, ...) {
+dash_status dash::fail(dash_model *m, dash_status s, const char *fmt, ...) {
     if (m) {
         char buf[512];
         va_list ap;
@@ -33,30 +34,10 @@ static dash_status fail(dash_model *m, dash_status s, const char *fmt, ...) {
     return s;
 }
 
-#define CK(call)                                                                         \
-    do {                                                                                 \
-        cudaError_t e_ = (call);                                                         \
-        if (e_ != cudaSuccess) {                                                         \
-            m->broken = true;                                                            \
-            return fail(m, DASH_ECUDA, "%s failed: %s (%s:%d)", #call,                   \
-                        cudaGetErrorString(e_), __FILE__, __LINE__);                     \
-        }                                                                                \
-    } while (0)
-
-#define CKL()                                                                            \
-    do {                                                                                 \
-        cudaError_t e_ = cudaGetLastError();                                             \
-        if (e_ != cudaSuccess) {                                                         \
-            m->broken = true;                                                            \
-            return fail(m, DASH_ECUDA, "kernel launch failed: %s (%s:%d)",               \
-                        cudaGetErrorString(e_), __FILE__, __LINE__);                     \
-        }                                                                                \
-    } while (0)
-
 // ---------------------------------------------------------------------------
 // launch accounting and the optional per-kernel profiler
 // ---------------------------------------------------------------------------
-static cudaEvent_t prof_event(dash_model *m) {
+cudaEvent_t dash::prof_event(dash_model *m) {
     if (!m->prof.pool.empty()) {
         cudaEvent_t e = m->prof.pool.back();
         m->prof.pool.pop_back();
@@ -93,25 +74,6 @@ static void prof_collect(dash_model *m) {
     }
     cudaGetLastError();
 }
-
-// Launch a kernel on the model's stream; with profiling on, bracket it with
-// events.  Every launch is counted.
-#define LAUNCH(kind, ...)                                                                \
-    do {                                                                                 \
-        cudaEvent_t a_ = nullptr;                                                        \
-        if (m->prof.on) {                                                                \
-            a_ = prof_event(m);                                                          \
-            cudaEventRecord(a_, m->stream);                                              \
-        }                                                                                \
-        __VA_ARGS__;                                                                     \
-        CKL();                                                                           \
-        m->prof.launches_total += 1;                                                     \
-        if (m->prof.on) {                                                                \
-            cudaEvent_t b_ = prof_event(m);                                              \
-            cudaEventRecord(b_, m->stream);                                              \
-            m->prof.pending.push_back({(int)(kind), a_, b_});                            \
-        }                                                                                \
-    } while (0)
 
 extern "C" int64_t dash_launch_count(const dash_model *m) {
     return m ? m->prof.launches_total : -1;
@@ -263,7 +225,23 @@ static dash_status init_alloc(dash_model *m) {
         DALLOC(m->st.c, Km * R * 8, "c");
         DALLOC(m->st.D, Km * R * R * 8, "D");
     } else {
-        return fail(m, DASH_EINVAL, "mode Q is not available in this build");
+        DALLOC(m->qL, Km * R * R * 8, "L_k");
+        DALLOC(m->qE, Km * R * R * 8, "E_k");
+        DALLOC(m->qBh, Km * R * R * 8, "B_k^1/2");
+        DALLOC(m->qC, Km * R * R * 8, "carry C_k");
+        DALLOC(m->qY, (size_t)Km * R * J * te, "Y_k");
+        DALLOC(m->qA, (size_t)Nm * R * te, "A_new");
+        DALLOC(m->qH, R * R * 8, "H");
+        DALLOC(m->qWW, R * R * 8, "W^T W");
+        DALLOC(m->qPV, R * R * 8, "V-step pinv");
+        DALLOC(m->qPW, R * R * 8, "W-step pinv");
+        m->q_lt_max = 4 * m->n_sm;
+        DALLOC(m->qMH, (size_t)m->q_lt_max * R * R * 8, "H-MTTKRP partials");
+        DALLOC(m->qWWp, (size_t)m->q_lt_max * R * R * 8, "W^T W partials");
+        m->q_vslots = 2 * m->n_sm;
+        DALLOC(m->qslots, (size_t)m->q_vslots * J * R * 8, "V-MTTKRP slots");
+        m->q_out_max = 4 * m->n_sm;
+        DALLOC(m->qfit, (size_t)m->q_out_max * 2 * 8, "residual partials");
     }
     // staging and batch metadata
     m->stage_cap = c.max_staged_rows > 0 ? std::min<int64_t>(c.max_staged_rows, Nm) : Nm;
@@ -479,7 +457,18 @@ extern "C" dash_status dash_set_factors(dash_model *m, const double *V, const do
     if (!V) return fail(m, DASH_EINVAL, "V is null");
     const int J = m->cfg.J, R = m->cfg.R;
     if (!finite_all(V, (size_t)J * R)) return fail(m, DASH_EINVAL, "V has non-finite entries");
-    (void)H;
+    if (m->cfg.mode == DASH_MODE_Q) {
+        std::vector<double> Hh((size_t)R * R, 0.0);
+        if (H) {
+            if (!finite_all(H, (size_t)R * R)) return fail(m, DASH_EINVAL, "H has non-finite entries");
+            std::copy(H, H + (size_t)R * R, Hh.begin());
+        } else {
+            for (int i = 0; i < R; ++i) Hh[(size_t)i * R + i] = 1.0;
+        }
+        CK(cudaMemcpy(m->qH, Hh.data(), (size_t)R * R * 8, cudaMemcpyHostToDevice));
+    } else if (H) {
+        return fail(m, DASH_EINVAL, "H exists only in mode Q");
+    }
     CK(cudaMemcpyAsync(m->st.V, V, (size_t)J * R * 8, cudaMemcpyHostToDevice, m->stream));
     CK(cudaStreamSynchronize(m->stream));
     dash_status s = refresh_gamma(m);
@@ -534,17 +523,70 @@ extern "C" dash_status dash_get_state_p(const dash_model *mc, double *V, double 
     return DASH_OK;
 }
 
-extern "C" dash_status dash_set_state_q(dash_model *m, int64_t, const double *, const double *,
-                                        const double *, const double *, const double *) {
+// Mode-Q state on the host is FP64; on the device L_k, E_k and B_k^{1/2} use
+// the scalar type of the R×R work (FP64, or double-float pairs) and Y_k the
+// product type.  Loading a state derives E_k and B_k^{1/2} from L_k.
+extern "C" dash_status dash_set_state_q(dash_model *m, int64_t K, const double *V, const double *H,
+                                        const double *W, const double *L, const double *Y) {
     if (!m) return DASH_EINVAL;
-    return fail(m, DASH_ESTATE, "model is not in mode Q");
+    if (m->cfg.mode != DASH_MODE_Q) return fail(m, DASH_ESTATE, "model is not in mode Q");
+    if (K < 0 || K > m->cfg.max_slices) return fail(m, DASH_ENOMEM, "K = %lld exceeds capacity", (long long)K);
+    if (!V || !H || (K > 0 && (!W || !L || !Y))) return fail(m, DASH_EINVAL, "null state array");
+    if (m->st_segs() > 0) return fail(m, DASH_ESTATE, "rows are staged; update or discard first");
+    const int64_t J = m->cfg.J, R = m->cfg.R;
+    if (!finite_all(V, J * R) || !finite_all(H, R * R)) return fail(m, DASH_EINVAL, "non-finite factors");
+    for (int64_t k = 0; k < K; ++k)
+        for (int64_t i = 0; i < R; ++i)
+            for (int64_t j = 0; j < i; ++j)
+                if (L[(k * R + i) * R + j] != 0.0)
+                    return fail(m, DASH_EINVAL, "L_%lld is not upper-triangular", (long long)k);
+    CK(cudaStreamSynchronize(m->stream));
+    CK(cudaMemcpy(m->st.V, V, J * R * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->qH, H, R * R * 8, cudaMemcpyHostToDevice));
+    if (K > 0) {
+        CK(cudaMemcpy(m->st.W, W, K * R * 8, cudaMemcpyHostToDevice));
+        dash_status s1 = put_summ(m, m->qL, L, (size_t)K * R * R);
+        if (s1) return s1;
+        if (m->tsize == 8) {
+            CK(cudaMemcpy(m->qY, Y, (size_t)K * R * J * 8, cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> yf((size_t)K * R * J);
+            for (size_t i = 0; i < yf.size(); ++i) yf[i] = (float)Y[i];
+            CK(cudaMemcpy(m->qY, yf.data(), yf.size() * 4, cudaMemcpyHostToDevice));
+        }
+    }
+    m->K = K;
+    dash_status s = refresh_gamma(m);
+    if (s) return s;
+    s = prepare_q(m);
+    if (s) return s;
+    CK(cudaStreamSynchronize(m->stream));
+    m->v_set = true;
+    m->has_last = false;
+    return DASH_OK;
 }
 
-extern "C" dash_status dash_get_state_q(const dash_model *mc, double *, double *, double *,
-                                        double *, double *) {
+extern "C" dash_status dash_get_state_q(const dash_model *mc, double *V, double *H, double *W,
+                                        double *L, double *Y) {
     dash_model *m = const_cast<dash_model *>(mc);
     if (!m) return DASH_EINVAL;
-    return fail(m, DASH_ESTATE, "model is not in mode Q");
+    if (m->cfg.mode != DASH_MODE_Q) return fail(m, DASH_ESTATE, "model is not in mode Q");
+    const int64_t J = m->cfg.J, R = m->cfg.R, K = m->K;
+    CK(cudaStreamSynchronize(m->stream));
+    if (V) CK(cudaMemcpy(V, m->st.V, J * R * 8, cudaMemcpyDeviceToHost));
+    if (H) CK(cudaMemcpy(H, m->qH, R * R * 8, cudaMemcpyDeviceToHost));
+    if (W && K) CK(cudaMemcpy(W, m->st.W, K * R * 8, cudaMemcpyDeviceToHost));
+    if (L && K) { dash_status s1 = get_summ(m, L, m->qL, (size_t)K * R * R); if (s1) return s1; }
+    if (Y && K) {
+        if (m->tsize == 8) {
+            CK(cudaMemcpy(Y, m->qY, (size_t)K * R * J * 8, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> yf((size_t)K * R * J);
+            CK(cudaMemcpy(yf.data(), m->qY, yf.size() * 4, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < yf.size(); ++i) Y[i] = yf[i];
+        }
+    }
+    return DASH_OK;
 }
 
 extern "C" dash_status dash_factors(const dash_model *mc, double *V, double *W, int64_t k_first,
@@ -559,7 +601,10 @@ extern "C" dash_status dash_factors(const dash_model *mc, double *V, double *W, 
     if (V) CK(cudaMemcpy(V, m->st.V, J * R * 8, cudaMemcpyDeviceToHost));
     if (W && k_count)
         CK(cudaMemcpy(W, m->st.W + k_first * R, k_count * R * 8, cudaMemcpyDeviceToHost));
-    if (H) return fail(m, DASH_ESTATE, "H exists only in mode Q");
+    if (H) {
+        if (m->cfg.mode != DASH_MODE_Q) return fail(m, DASH_ESTATE, "H exists only in mode Q");
+        CK(cudaMemcpy(H, m->qH, R * R * 8, cudaMemcpyDeviceToHost));
+    }
     return DASH_OK;
 }
 
@@ -887,197 +932,10 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
     return DASH_OK;
 }
 
-template <typename TI, typename T>
-static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void *Xv, double lam,
-                                   bool begin_new) {
-    const int J = m->cfg.J, R = m->cfg.R;
-    cudaStream_t st = m->stream;
-    const TI *X = (const TI *)Xv;
-    StateDev s = m->st;
-    s.lam = lam;
-    const int64_t N = b.N;
-    const int64_t Ng = b.N_gen;
-    const int n_new = b.K_all - b.K_old;
-    constexpr bool DF = std::is_same<T, float>::value;
-    if (begin_new && n_new > 0) {
-        const int64_t tot = (int64_t)n_new * R * (R + 2);
-        LAUNCH(KK_BEGIN_NEW, k_begin_new<<<(tot + 255) / 256, 256, 0, st>>>(s.W, s.c, s.D, b.K_old, n_new, R));
-    }
-    // fused row kernel over the tiles of single-segment slices
-    int g_f = 0;
-    if constexpr (std::is_same<T, float>::value && std::is_same<TI, float>::value) {
-        if (m->fused_active) {
-            const size_t qsm = (size_t)(2 * R * (R + 1) + R + 1) * 8;
-            LAUNCH(KK_VTILDE, k_vqr<<<1, 32, qsm, st>>>(s.Gam, R, m->rtol, m->RV, m->Linv, m->GPf,
-                                                        m->Gdf, s.gam_ok));
-            LAUNCH(KK_QV, k_qv<<<(J + 7) / 8, 256, 0, st>>>(s.V, m->Linv, J, R, m->QV));
-        }
-        if (m->fused_active && m->n_tiles > 0) {
-            g_f = std::min(m->n_sm, m->n_tiles);
-            FusedArgs fa;
-            fa.X = X;
-            fa.J = J;
-            fa.R = R;
-            fa.lam = lam;
-            fa.rtol = m->rtol;
-            fa.V32 = m->QV;
-            fa.GPf = m->GPf;
-            fa.RV = m->RV;
-            fa.Gdf = m->Gdf;
-            fa.Gam = s.Gam;
-            fa.gam_ok = s.gam_ok;
-            fa.n_tiles = m->n_tiles;
-            fa.tile_s0 = m->d_tile_s0;
-            fa.tile_s1 = m->d_tile_s1;
-            fa.seg_row = b.seg_row;
-            fa.seg_slice = b.seg_slice;
-            fa.W = s.W;
-            fa.c = reinterpret_cast<df *>(s.c);
-            fa.D = reinterpret_cast<df *>(s.D);
-            fa.U = (float *)m->U;
-            fa.Fslot = (float *)m->Fpart;
-            fa.Gpart = m->Gpart;
-            fa.xn_part = m->xn_part;
-            fa.wsp = m->wsp;
-            fa.err = m->d_err;
-            fa.phase_cycles = m->prof.on ? m->prof.d_phase : nullptr;
-            const size_t smem = fu_smem_bytes(J);
-            if (m->cfg.precision == DASH_PREC_F16X3) {
-                CK(cudaFuncSetAttribute(k_rows_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                LAUNCH(KK_ROWS_FUSED, k_rows_fused<true><<<g_f, FU_THREADS, smem, st>>>(fa));
-            } else {
-                CK(cudaFuncSetAttribute(k_rows_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                LAUNCH(KK_ROWS_FUSED, k_rows_fused<false><<<g_f, FU_THREADS, smem, st>>>(fa));
-            }
-        }
-    }
-    int n_xn = 0;
-    // P = X V for the general kernels; P' = X Q_V for the chunked path
-    const T *Vmul = (const T *)m->VT;
-    if constexpr (std::is_same<T, float>::value) {
-        if (m->fused_active) Vmul = (const T *)m->QV;
-    }
-    if (Ng > 0) {
-        LAUNCH(KK_ROWMAP, k_rowmap<<<(N + 255) / 256, 256, 0, st>>>(b));
-        n_xn = (int)((Ng + XV_ROWS - 1) / XV_ROWS);
-        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, b, J, R, Vmul, (T *)m->P,
-                                                        m->xn_part + g_f));
-    }
-    int nsb = 0;
-    bool finished = false;
-    if constexpr (std::is_same<T, float>::value && std::is_same<TI, float>::value) {
-        if (m->fused_active) {
-            // chunks of big / split slices, then every remaining slice's finish
-            FusedArgs fa{};
-            fa.J = J;
-            fa.R = R;
-            fa.lam = lam;
-            fa.rtol = m->rtol;
-            fa.Gdf = m->Gdf;
-            fa.GPf = m->GPf;
-            fa.RV = m->RV;
-            fa.Gam = s.Gam;
-            fa.gam_ok = s.gam_ok;
-            fa.W = s.W;
-            fa.c = reinterpret_cast<df *>(s.c);
-            fa.D = reinterpret_cast<df *>(s.D);
-            fa.U = (float *)m->U;
-            fa.wsp = m->wsp;
-            fa.err = m->d_err;
-            BigArgs bg{};
-            bg.Y = (const float *)m->P;
-            bg.ch_row0 = m->d_ch_row0;
-            bg.ch_n = m->d_ch_n;
-            bg.ch_k = m->d_ch_k;
-            bg.n_chunks = m->n_chunks;
-            bg.fin_k = m->d_fin_k;
-            bg.fin_c0 = m->d_fin_c0;
-            bg.n_fin = m->n_fin;
-            bg.dpart = m->dpart;
-            // both grids stay within the 2-CTAs-per-SM workspace (persistent warps)
-            if (m->n_chunks > 0) {
-                const int gb = std::min(2 * m->n_sm, (m->n_chunks + FU_WARPS - 1) / FU_WARPS);
-                LAUNCH(KK_BIG_B, k_big_b<<<gb, 256, 0, st>>>(fa, bg));
-            }
-            if (m->n_fin > 0) {
-                nsb = std::min(2 * m->n_sm, (m->n_fin + FU_WARPS - 1) / FU_WARPS);
-                LAUNCH(KK_BIG_C, k_big_c<<<nsb, 256, 0, st>>>(fa, bg, m->Gpart + (size_t)g_f * R * R));
-            }
-            finished = true;
-        }
-    }
-    if (!finished) {
-        // per-slice work for slices the fused kernel did not finish
-        const int nw = sl_warps(R);
-        const size_t smem = (size_t)nw * sl_warp_doubles(R) * 8;
-        nsb = (int)std::min<int64_t>((b.K_all + nw - 1) / nw, kSliceBlocksMax);
-        if (nsb < 1) nsb = 1;
-        CK(cudaFuncSetAttribute(k_slices<T, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        LAUNCH(KK_SLICES, k_slices<T, DF><<<nsb, 32 * nw, smem, st>>>(b, s, (const T *)m->P, (T *)m->U,
-                                                                      m->Gpart + (size_t)g_f * R * R));
-    }
-    // F partials of the general rows
-    int nfb = 0;
-    if (Ng > 0) {
-        const int nby = (J + F_JB - 1) / F_JB;
-        nfb = (int)std::min<int64_t>(std::max<int64_t>(1, (2 * 152 * 4) / nby), (Ng + F_RC - 1) / F_RC);
-        nfb = std::min(nfb, kFBlocksMax);
-        int64_t rpc = (Ng + nfb - 1) / nfb;
-        rpc = (rpc + F_RC - 1) / F_RC * F_RC;
-        nfb = (int)((Ng + rpc - 1) / rpc);
-        dim3 grid(nfb, nby);
-        LAUNCH(KK_F, k_f<TI, T><<<grid, 256, 0, st>>>(X, b, J, R, (const T *)m->U, s.W, rpc,
-                                                     (T *)m->Fpart + (size_t)g_f * J * R));
-    }
-    LAUNCH(KK_F_REDUCE, k_f_reduce<T><<<((int64_t)J * R + 255) / 256, 256, 0, st>>>((const T *)m->Fpart, g_f + nfb, J, R, lam,
-                                                                s.F, m->Finc));
-    LAUNCH(KK_G_REDUCE, k_g_reduce<<<(R * R + 7) / 8, 256, 0, st>>>(m->Gpart, g_f + nsb, R, lam, s.G, m->Ginc));
-    const size_t psm = (size_t)(3 * R * (R + 1) + (R + 1)) * 8;
-    LAUNCH(KK_PINV, k_pinv_small<<<1, 32, psm, st>>>(s.G, R, m->rtol, m->GP, nullptr));
-    LAUNCH(KK_VUPDATE, k_vupdate<T><<<(J + 7) / 8, 256, 0, st>>>(s.F, m->GP, m->Finc, J, R, s.V, (T *)m->VT,
-                                               m->cross_part));
-    LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(s.V, J, R, s.Gam));
-    LAUNCH(KK_PINV, k_pinv_small<<<1, 32, psm, st>>>(s.Gam, R, m->rtol, s.GamP, s.gam_ok));
-    LAUNCH(KK_FITNESS, k_fitness<<<1, 32, 0, st>>>(m->xn_part, g_f + n_xn, m->cross_part, (J + 7) / 8, s.Gam, m->Ginc, R,
-                                s.gam_ok, m->fit));
-    CK(cudaMemcpyAsync(m->h_fit, m->fit, 4 * 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(m->h_err, m->d_err, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    return DASH_OK;
-}
-
-template <typename TI, typename T>
-static dash_status launch_recompute_c(dash_model *m, const BatchDev &b0, const void *Xv) {
-    const int J = m->cfg.J, R = m->cfg.R;
-    constexpr bool DF = std::is_same<T, float>::value;
-    const BatchDev &b = b0;     // planned without fused tiles: every row is general
-    if (b.N > 0) {
-        const int n_xn = (int)((b.N + XV_ROWS - 1) / XV_ROWS);
-        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, m->stream>>>((const TI *)Xv, b, J, R, (const T *)m->VT,
-                                                  (T *)m->P, m->xn_part));
-    }
-    const int nb = (b.K_all + 7) / 8;
-    LAUNCH(KK_C_RECOMPUTE, k_c_recompute<T, DF><<<nb > 0 ? nb : 1, 256, 0, m->stream>>>(b, (const T *)m->P, (const T *)m->U, R,
-                                                            m->st.c));
-    return DASH_OK;
-}
-
-static dash_status recompute_c(dash_model *m, const BatchDev &b, const void *X) {
-    const bool f64in = m->cfg.input_dtype == DASH_F64;
-    if (m->tsize == 8)
-        return f64in ? launch_recompute_c<double, double>(m, b, X) : launch_recompute_c<float, double>(m, b, X);
-    return f64in ? launch_recompute_c<double, float>(m, b, X) : launch_recompute_c<float, float>(m, b, X);
-}
-
 static dash_status run_update(dash_model *m, const BatchDev &b, const void *X, double lam,
                               bool begin_new) {
-    const bool f64in = m->cfg.input_dtype == DASH_F64;
-    if (m->cfg.mode != DASH_MODE_P) return fail(m, DASH_ESTATE, "mode Q is not available");
-    if (m->tsize == 8) {
-        return f64in ? launch_update_p<double, double>(m, b, X, lam, begin_new)
-                     : launch_update_p<float, double>(m, b, X, lam, begin_new);
-    }
-    return f64in ? launch_update_p<double, float>(m, b, X, lam, begin_new)
-                 : launch_update_p<float, float>(m, b, X, lam, begin_new);
+    if (m->cfg.mode == DASH_MODE_Q) return run_update_q(m, b, X, lam, begin_new, true);
+    return run_update_p(m, b, X, lam, begin_new);
 }
 
 static dash_status update_common(dash_model *m, int64_t n_seg, const int64_t *ids,
@@ -1150,12 +1008,20 @@ static dash_status fit_common(dash_model *m, int64_t n_seg, const int64_t *ids,
         s = run_update(m, bi, X, 0.0, it == 0);
         if (s) return s;
     }
-    // c_k = vec(X_k)ᵀ(V ⊙ U_k) with the final V (Eq. 6), over every row
-    BatchDev ball;
-    s = plan_batch(m, n_seg, ids, rp, 0, n_new, X, false, &ball);
-    if (s) return s;
-    s = recompute_c(m, ball, X);
-    if (s) return s;
+    if (m->cfg.mode == DASH_MODE_Q) {
+        // helpers of the final factors (L_k, Z_k of A_k = X_k V S_k Hᵀ), no sweep
+        BatchDev bi = b;
+        bi.K_old = bi.K_all;
+        s = run_update_q(m, bi, X, 0.0, false, false);
+        if (s) return s;
+    } else {
+        // c_k = vec(X_k)ᵀ(V ⊙ U_k) with the final V (Eq. 6), over every row
+        BatchDev ball;
+        s = plan_batch(m, n_seg, ids, rp, 0, n_new, X, false, &ball);
+        if (s) return s;
+        s = recompute_c(m, ball, X);
+        if (s) return s;
+    }
     CK(cudaEventRecord(m->ev1, m->stream));
     m->K = n_new;
     m->last_N = b.N;

@@ -8,19 +8,24 @@
 #include "dash.h"
 #include "dash_kernels_fused.cuh"
 #include "dash_kernels_p.cuh"
+#include "dash_kernels_q.cuh"
 
 namespace dash {
 // kernel kinds for the per-kernel profiler
 enum KernelKind {
     KK_BEGIN_NEW, KK_ROWMAP, KK_XV, KK_SLICES, KK_F, KK_F_REDUCE, KK_G_REDUCE, KK_PINV,
     KK_VUPDATE, KK_GAMMA, KK_FITNESS, KK_CAST, KK_C_RECOMPUTE, KK_VTILDE, KK_ROWS_FUSED,
-    KK_BIG_B, KK_BIG_C, KK_QV, KK_PH_A, KK_PH_EPI, KK_PH_B, KK_COUNT
+    KK_BIG_B, KK_BIG_C, KK_QV, KK_PH_A, KK_PH_EPI, KK_PH_B,
+    KK_Q_BEGIN, KK_Q_AROWS, KK_Q_Y, KK_Q_LT, KK_Q_H, KK_Q_VPART, KK_Q_V, KK_Q_PW, KK_Q_W,
+    KK_Q_OUT, KK_Q_FIT, KK_COUNT
 };
 static const char *const kKernelNames[KK_COUNT] = {
     "k_begin_new", "k_rowmap", "k_xv", "k_slices", "k_f", "k_f_reduce", "k_g_reduce",
     "k_pinv_small", "k_vupdate", "k_gamma", "k_fitness", "k_cast", "k_c_recompute",
     "k_vqr", "k_rows_fused", "k_big_b", "k_big_c", "k_qv",
-    "k_rows_fused.phase_a", "k_rows_fused.epilogue", "k_rows_fused.phase_b"};
+    "k_rows_fused.phase_a", "k_rows_fused.epilogue", "k_rows_fused.phase_b",
+    "k_q_begin_new", "k_q_arows", "k_q_y", "k_q_lt", "k_q_h", "k_q_vpart", "k_q_v", "k_q_pw",
+    "k_q_w", "k_q_out", "k_q_fit"};
 
 struct Profiler {
     bool on = false;
@@ -108,6 +113,16 @@ struct dash_model {
     double *Gpart = nullptr;
     int n_gb_max = 0;
     double *cross_part = nullptr;
+
+    // constrained mode (Q): per-slice factor L_k, eigenbasis E_k and B_k^{1/2}
+    // (in the scalar type: double, or double-float pairs), the carry C_k
+    // (FP64), the projected data Y_k and the A rows in the product type; H and
+    // the small solve results
+    double *qL = nullptr, *qE = nullptr, *qBh = nullptr, *qC = nullptr;
+    void *qY = nullptr, *qA = nullptr;
+    double *qH = nullptr, *qWW = nullptr, *qPV = nullptr, *qPW = nullptr;
+    double *qMH = nullptr, *qWWp = nullptr, *qslots = nullptr, *qfit = nullptr;
+    int q_lt_max = 0, q_vslots = 0, q_out_max = 0;
 
     // last update
     int64_t last_N = 0;

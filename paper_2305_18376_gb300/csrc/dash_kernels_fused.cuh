@@ -895,7 +895,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
 // V = Q_V R_V from Γ = VᵀV = R_VᵀR_V (Cholesky, FP64, one warp): R_V (upper),
 // L⁻¹ = R_V⁻ᵀ (lower) in FP64 and FP32, and Γ in double-float.  Clears
 // *gam_ok when Γ is not safely positive definite (the same test as Γ⁺).
-__global__ void k_vqr(const double *__restrict__ Gam, int R, double rtol, double *__restrict__ RV,
+static __global__ void k_vqr(const double *__restrict__ Gam, int R, double rtol, double *__restrict__ RV,
                       double *__restrict__ Linv, float *__restrict__ LinvF, df *__restrict__ Gdf,
                       int *__restrict__ gam_ok) {
     extern __shared__ double qsm[];
@@ -938,7 +938,7 @@ __global__ void k_vqr(const double *__restrict__ Gam, int R, double rtol, double
 }
 
 // Q_V = V R_V⁻¹ = V L⁻ᵀ in FP32, one warp per row of V.
-__global__ void k_qv(const double *__restrict__ V, const double *__restrict__ Linv, int J, int R,
+static __global__ void k_qv(const double *__restrict__ V, const double *__restrict__ Linv, int J, int R,
                      float *__restrict__ QV) {
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -1076,7 +1076,7 @@ __device__ __forceinline__ void big_chunk(const FusedArgs &a, const BigArgs &bg,
     }
 }
 
-__global__ void __launch_bounds__(256, 1) k_big_b(FusedArgs a, BigArgs bg) {
+static __global__ void __launch_bounds__(256, 1) k_big_b(FusedArgs a, BigArgs bg) {
     __shared__ __align__(16) float Us[FU_WARPS][32][FU_RP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = a.R;
@@ -1085,7 +1085,7 @@ __global__ void __launch_bounds__(256, 1) k_big_b(FusedArgs a, BigArgs bg) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_big_c(FusedArgs a, BigArgs bg, double *Gpart_out) {
+static __global__ void __launch_bounds__(256) k_big_c(FusedArgs a, BigArgs bg, double *Gpart_out) {
     __shared__ df Gs[FU_RP * FU_RP];
     __shared__ __align__(16) float Lw_all[FU_WARPS][FU_RP * FU_LD];   // also the G reduction
     __shared__ df xw_all[FU_WARPS][FU_RP];

@@ -94,7 +94,7 @@ __device__ __forceinline__ double lam_scale(double lam, double x) { return lam =
 // ---------------------------------------------------------------------------
 // P0: new slices start with S_k = I (Lemma 1 for a slice without S_k), zero
 // helpers.
-__global__ void k_begin_new(double *W, double *c, double *D, int K_old, int n_new, int R) {
+static __global__ void k_begin_new(double *W, double *c, double *D, int K_old, int n_new, int R) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t tot = (int64_t)n_new * R * (R + 2);
     if (i >= tot) return;
@@ -106,7 +106,7 @@ __global__ void k_begin_new(double *W, double *c, double *D, int K_old, int n_ne
     else D[(int64_t)k * R * R + (e - 2 * R)] = 0.0;
 }
 
-__global__ void k_rowmap(BatchDev b) {
+static __global__ void k_rowmap(BatchDev b) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.N) return;
     int lo = 0, hi = b.n_seg - 1;         // last segment with seg_row[s] <= i
@@ -432,7 +432,7 @@ __global__ void k_f_reduce(const T *__restrict__ Fpart, int nb, int J, int R, do
 }
 
 // P8: G ← λG + Σ partials (Eq. 21), one warp per entry, fixed lane order.
-__global__ void k_g_reduce(const double *__restrict__ Gpart, int nb, int R, double lam,
+static __global__ void k_g_reduce(const double *__restrict__ Gpart, int nb, int R, double lam,
                            double *__restrict__ G, double *__restrict__ Ginc) {
     const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -448,7 +448,7 @@ __global__ void k_g_reduce(const double *__restrict__ Gpart, int nb, int R, doub
 
 // G⁺ (or Γ⁺) of a symmetric PSD R×R matrix by one warp; ok (optional)
 // receives 1 when the Cholesky path was taken.
-__global__ void k_pinv_small(const double *__restrict__ Min, int R, double rtol,
+static __global__ void k_pinv_small(const double *__restrict__ Min, int R, double rtol,
                              double *__restrict__ Mout, int *ok) {
     extern __shared__ double sm[];
     const int ld = R + 1, lane = threadIdx.x & 31;
@@ -499,7 +499,7 @@ __global__ void k_vupdate(const double *__restrict__ F, const double *__restrict
 }
 
 // P1: Γ = VᵀV, one warp per entry (r, q), lanes over j.
-__global__ void k_gamma(const double *__restrict__ V, int J, int R, double *__restrict__ Gam) {
+static __global__ void k_gamma(const double *__restrict__ V, int J, int R, double *__restrict__ Gam) {
     const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (e >= R * R) return;
@@ -519,7 +519,7 @@ __global__ void k_cast(const double *__restrict__ in, T *__restrict__ out, int64
 
 // P10: batch fitness from FP64 Gram terms, one warp:
 //   ||X − X̂||² = ||X||² − 2 Σ V ∗ F_inc + Σ Γ ∗ G_inc.
-__global__ void k_fitness(const double *__restrict__ xn_part, int n_xn,
+static __global__ void k_fitness(const double *__restrict__ xn_part, int n_xn,
                           const double *__restrict__ cross_part, int n_cross,
                           const double *__restrict__ Gam, const double *__restrict__ Ginc,
                           int R, const int *__restrict__ gam_ok,

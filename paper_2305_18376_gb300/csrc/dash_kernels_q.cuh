@@ -1,0 +1,572 @@
+// Constrained-mode (U_k = Q_k H S_k) streaming update: the old/new split of
+// Dash applied to PARAFAC2 with column-orthonormal Q_k.  Per update, in
+// stream order:
+//
+//   k_xv          P = X_new V                                   (shared with mode P)
+//   k_q_arows     A_new = P S_k Hᵀ, row by row
+//   k_q_lt        per slice: L_k ← R factor of [√λ L_k; A_new]  (L_kᵀL_k = B_k),
+//                 the eigenbasis of B_k, T_k = B_k^{-1/2} and B_k^{1/2},
+//                 the carry matrix C_k = T_k,new·B_k,old^{1/2}, and the new
+//                 rows of Q_k = A_new T_k
+//   k_q_y         Y_k ← λ·C_k·Y_k + Q_k,newᵀX_new for every slice, with the
+//                 per-CTA partials of the H-MTTKRP Σ_k Y_k V S_k and of WᵀW
+//   k_q_h         H = (Σ_k Y_k V S_k)(VᵀV ∗ WᵀW)⁺ and (HᵀH ∗ WᵀW)⁺
+//   k_q_vpart     V-MTTKRP shares Y_kᵀ H S_k
+//   k_q_v         V = (Σ_k Y_kᵀ H S_k)(HᵀH ∗ WᵀW)⁺
+//   k_gamma       VᵀV of the new V
+//   k_q_pw        (HᵀH ∗ VᵀV)⁺
+//   k_q_w         W(k,:) = diag(Hᵀ Y_k V)ᵀ (HᵀH ∗ VᵀV)⁺
+//   k_q_out       the batch residual ‖X_new − Q_new H S_k Vᵀ‖² with the
+//                 updated factors
+// One CP-ALS sweep H → V → W on {Y_k}; with one batch on an empty model the
+// whole update is one PARAFAC2-ALS iteration (Procrustes step + sweep).
+//
+// State per slice: L_k (B_k's triangular factor), the projected data
+// Y_k = T_k Z_k = Q_kᵀΛ_kX_k (R×J) with Z_k = Σ λ^age A_kᵀX_k, and, as
+// derived data, the eigenbasis E_k and B_k^{1/2}.  Y_k is carried instead
+// of Z_k: its rows have the size of the data, while T_k's entries reach
+// cond(A_k) (up to 1e6 on planted U(0,1) factors), so any product T_k·Z_k
+// formed in FP32 would lose that many digits to cancellation.  The carry
+// follows from Z_new = λZ_old + A_newᵀX_new:
+//   Y_new = T_new Z_new = λ (T_new B_old^{1/2}) Y_old + Q_newᵀX_new,
+// and since B_new ⪰ λB_old, ‖T_new B_old^{1/2}‖ <= λ^{-1/2}: the carry is a
+// bounded R×R map, safe to apply in the product type.
+//
+// Precision: the bulk products (P, A, Y, the MTTKRPs, the residual) run in
+// the product type T; everything that touches L_k or T_k runs in the scalar
+// type S (double, or double-float in the mixed path).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dash_kernels_p.cuh"
+#include "rr_linalg.cuh"
+#include "small_linalg.cuh"
+
+namespace dash {
+
+struct QDev {
+    int J, R;
+    double lam, rtol;
+    double *V;      // J×R
+    double *H;      // R×R
+    double *W;      // Kmax×R
+    double *L;      // Kmax×R×R, upper-triangular factor of B_k (S storage: double or df)
+    double *E;      // Kmax×R×R, eigenbasis of B_k (S storage)
+    double *Bh;     // Kmax×R×R, B_k^{1/2} (S storage)
+    double *C;      // Kmax×R×R, carry T_k,new B_k,old^{1/2} of this update (FP64)
+    double *Gam;    // R×R  VᵀV (current V)
+};
+
+__host__ __device__ inline int q_ld(int R) { return R + 1; }
+
+// P0 for mode Q: new slices start with w = 1, empty summaries and the
+// identity as eigenbasis estimate.
+template <class S, typename T>
+__global__ void k_q_begin_new(double *W, double *Lraw, double *Eraw, double *Bhraw, T *Y, int K_old,
+                              int n_new, int R, int J) {
+    const int64_t per = (int64_t)R * (1 + 3 * R + J);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_new * per) return;
+    const int k = K_old + (int)(i / per);
+    int64_t e = i % per;
+    S *L = reinterpret_cast<S *>(Lraw);
+    S *E = reinterpret_cast<S *>(Eraw);
+    S *Bh = reinterpret_cast<S *>(Bhraw);
+    const int64_t RR = (int64_t)R * R;
+    if (e < R) { W[(int64_t)k * R + e] = 1.0; return; }
+    e -= R;
+    if (e < RR) { L[k * RR + e] = RT<S>::zero(); return; }
+    e -= RR;
+    if (e < RR) { E[k * RR + e] = (e / R == e % R) ? RT<S>::one() : RT<S>::zero(); return; }
+    e -= RR;
+    if (e < RR) { Bh[k * RR + e] = RT<S>::zero(); return; }
+    e -= RR;
+    Y[(int64_t)k * R * J + e] = T(0);
+}
+
+// Q1: A_new = P S_k Hᵀ, one thread per entry.
+template <typename T>
+__global__ void k_q_arows(int64_t N, int R, const int *__restrict__ row_slice,
+                          const T *__restrict__ P, const double *__restrict__ W,
+                          const double *__restrict__ H, T *__restrict__ A) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * R) return;
+    const int64_t i = e / R;
+    const int r = (int)(e % R);
+    const int k = row_slice[i];
+    T a = T(0);
+    for (int s = 0; s < R; ++s) a += P[i * R + s] * (T)(W[(int64_t)k * R + s] * H[r * R + s]);
+    A[e] = a;
+}
+
+// Q3: per slice, one warp.
+//   mode 0 (update): L_k ← √λ L_k, then the A rows of slice k folded in (QR);
+//     eigen-decomposition of B_k = L_kᵀL_k warm-started from E_k; T_k and
+//     B_k^{1/2}; the carry C_k = T_k B_k,old^{1/2} (FP64, λ > 0 only); the new
+//     Q rows A_new T_k (product type).
+//   mode 1 (prepare): E_k and B_k^{1/2} from a loaded L_k (cold start).
+template <class S>
+__host__ __device__ inline size_t q_lt_warp_bytes(int R) {
+    const int ld = q_ld(R);
+    return (size_t)5 * R * ld * sizeof(S) + (size_t)2 * R * sizeof(S);
+}
+
+template <class S, typename T>
+__global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restrict__ Qrows, int mode,
+                       int passes, float jac_tol) {
+    using O = RT<S>;
+    extern __shared__ unsigned char qlt_raw[];
+    const int R = q.R, ld = q_ld(R);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned char *base = qlt_raw + (size_t)wid * q_lt_warp_bytes<S>(R);
+    S *Lw = reinterpret_cast<S *>(base);
+    S *Ew = Lw + R * ld;
+    S *Gw = Ew + R * ld;
+    S *Mw = Gw + R * ld;
+    S *E2 = Mw + R * ld;
+    S *finv = E2 + R * ld;
+    S *fsq = finv + R;
+    const int chunk = R < 32 ? R : 32;      // A rows per QR step (staged in Gw)
+    const S sl = O::from_d(sqrt(q.lam));
+    const int64_t RR = (int64_t)R * R;
+    S *Lg = reinterpret_cast<S *>(q.L);
+    S *Eg = reinterpret_cast<S *>(q.E);
+    S *Bg = reinterpret_cast<S *>(q.Bh);
+    for (int k = blockIdx.x * nw + wid; k < b.K_all; k += gridDim.x * nw) {
+        const int t = mode == 0 ? b.tslot[k] : -1;
+        __syncwarp();
+        for (int i = lane; i < R * R; i += 32) {
+            const S v = Lg[k * RR + i];
+            Lw[(i / R) * ld + (i % R)] = mode == 1 ? v : (q.lam == 0.0 ? O::zero() : O::mul(sl, v));
+            Ew[(i / R) * ld + (i % R)] = mode == 1 ? ((i / R == i % R) ? O::one() : O::zero())
+                                                   : Eg[k * RR + i];
+        }
+        __syncwarp();
+        if (t >= 0) {
+            for (int si = b.tseg_ptr[t]; si < b.tseg_ptr[t + 1]; ++si) {
+                const int sg = b.tseg_idx[si];
+                const int64_t r0 = b.seg_row[sg], r1 = b.seg_row[sg + 1];
+                for (int64_t c0 = r0; c0 < r1; c0 += chunk) {
+                    const int m = (int)(r1 - c0 < chunk ? r1 - c0 : chunk);
+                    for (int e = lane; e < m * R; e += 32)
+                        Gw[(e / R) * ld + (e % R)] = O::from_d((double)A[(c0 + e / R) * R + (e % R)]);
+                    __syncwarp();
+                    warp_qr_append(Lw, ld, Gw, ld, m, R);
+                }
+            }
+        }
+        if (mode == 0)
+            for (int i = lane; i < R * R; i += 32) Lg[k * RR + i] = Lw[(i / R) * ld + (i % R)];
+        warp_eig_factor(Lw, Ew, Gw, Mw, E2, R, ld, passes, jac_tol, 40, 1e-7f);
+        warp_sqrt_weights(Mw, R, ld, q.rtol, finv, fsq);
+        for (int i = lane; i < R * R; i += 32) Eg[k * RR + i] = Ew[(i / R) * ld + (i % R)];
+        // T_k → E2
+        warp_spectral_s(Ew, finv, R, ld, E2);
+        if (mode == 0 && q.lam != 0.0) {
+            // C_k = T_k · B_old^{1/2}  (B_old^{1/2} → Gw, product → Mw)
+            for (int i = lane; i < R * R; i += 32) Gw[(i / R) * ld + (i % R)] = Bg[k * RR + i];
+            __syncwarp();
+            for (int idx = lane; idx < R * R; idx += 32) {
+                const int r = idx / R, c = idx % R;
+                S a = O::zero();
+                for (int p = 0; p < R; ++p) a = O::fma(a, E2[r * ld + p], Gw[p * ld + c]);
+                q.C[k * RR + idx] = O::to_d(a);
+            }
+            __syncwarp();
+        }
+        // B_k^{1/2} → Gw → global
+        warp_spectral_s(Ew, fsq, R, ld, Gw);
+        for (int i = lane; i < R * R; i += 32) Bg[k * RR + i] = Gw[(i / R) * ld + (i % R)];
+        // new Q rows = A_new T_k (A rows staged through Mw)
+        if (t >= 0) {
+            for (int si = b.tseg_ptr[t]; si < b.tseg_ptr[t + 1]; ++si) {
+                const int sg = b.tseg_idx[si];
+                const int64_t r0 = b.seg_row[sg], r1 = b.seg_row[sg + 1];
+                for (int64_t c0 = r0; c0 < r1; c0 += chunk) {
+                    const int m = (int)(r1 - c0 < chunk ? r1 - c0 : chunk);
+                    __syncwarp();
+                    for (int e = lane; e < m * R; e += 32)
+                        Mw[(e / R) * ld + (e % R)] = O::from_d((double)A[(c0 + e / R) * R + (e % R)]);
+                    __syncwarp();
+                    for (int e = lane; e < m * R; e += 32) {
+                        const int i = e / R, c = e % R;
+                        S a = O::zero();
+                        for (int p = 0; p < R; ++p) a = O::fma(a, Mw[i * ld + p], E2[p * ld + c]);
+                        Qrows[(c0 + i) * R + c] = (T)O::to_d(a);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Q2: Y_k ← λ C_k Y_k + Q_k,newᵀ X_new for every slice (λ C_k Y_k alone for
+// untouched ones), then YV_k = Y_k V (old V) folded into the per-CTA
+// H-MTTKRP partial Σ_k YV_k S_k, and Σ_k w_k w_kᵀ.  One CTA per slice
+// (grid-stride), 256 threads; columns in chunks of 64: thread (jj, rg) owns
+// column jc+jj and the rows r ≡ rg (mod 4).
+constexpr int QZ_THREADS = 256;
+constexpr int QZ_JC = 64;
+constexpr int QZ_RC = 32;     // Q rows staged per pass
+
+template <typename T>
+__host__ __device__ inline size_t q_y_smem(int R) {
+    return ((size_t)QZ_JC * R + (size_t)QZ_RC * R + (size_t)R * (QZ_JC + 1) + (size_t)R * R) * sizeof(T);
+}
+
+template <typename TI, typename T>
+__global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI *__restrict__ X,
+                                                    const T *__restrict__ Qrows, T *__restrict__ Y,
+                                                    const T *__restrict__ VT, double *__restrict__ MHpart,
+                                                    double *__restrict__ WWpart) {
+    extern __shared__ unsigned char qy_raw[];
+    const int R = q.R, J = q.J, tid = threadIdx.x;
+    T *Vs = reinterpret_cast<T *>(qy_raw);           // QZ_JC × R
+    T *Qs = Vs + QZ_JC * R;                          // QZ_RC × R
+    T *Ys = Qs + QZ_RC * R;                          // R × (QZ_JC + 1)
+    T *Cs = Ys + R * (QZ_JC + 1);                    // R × R   λ C_k
+    const int jj = tid % QZ_JC, rg = tid / QZ_JC;
+    const int nq = (R + 3) / 4;
+    double mh[16], ww[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) { mh[u] = 0.0; ww[u] = 0.0; }
+    for (int k = blockIdx.x; k < b.K_all; k += gridDim.x) {
+        const int t = b.tslot[k];
+        T *Yk = Y + (int64_t)k * R * J;
+        __syncthreads();
+        for (int e = tid; e < R * R; e += QZ_THREADS)
+            Cs[e] = q.lam == 0.0 ? T(0) : (T)(q.lam * q.C[(int64_t)k * R * R + e]);
+        double yv[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) yv[u] = 0.0;
+        for (int jc = 0; jc < J; jc += QZ_JC) {
+            const int j = jc + jj;
+            __syncthreads();
+            for (int e = tid; e < QZ_JC * R; e += QZ_THREADS) {
+                const int j2 = jc + e / R;
+                Vs[e] = j2 < J ? VT[(int64_t)j2 * R + (e % R)] : T(0);
+            }
+            // old Y chunk → Ys (all R rows, needed by every output row)
+            for (int e = tid; e < R * QZ_JC; e += QZ_THREADS) {
+                const int r = e / QZ_JC, c = e % QZ_JC;
+                Ys[r * (QZ_JC + 1) + c] = (q.lam != 0.0 && jc + c < J) ? Yk[(int64_t)r * J + jc + c] : T(0);
+            }
+            __syncthreads();
+            T acc[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int r = rg + 4 * u;
+                T a = T(0);
+                if (u < nq && r < R)
+                    for (int p = 0; p < R; ++p) a += Cs[r * R + p] * Ys[p * (QZ_JC + 1) + jj];
+                acc[u] = a;
+            }
+            if (t >= 0) {
+                for (int si = b.tseg_ptr[t]; si < b.tseg_ptr[t + 1]; ++si) {
+                    const int sg = b.tseg_idx[si];
+                    const int64_t r0 = b.seg_row[sg], r1 = b.seg_row[sg + 1];
+                    for (int64_t c0 = r0; c0 < r1; c0 += QZ_RC) {
+                        const int nr = (int)(r1 - c0 < QZ_RC ? r1 - c0 : QZ_RC);
+                        __syncthreads();
+                        for (int e = tid; e < nr * R; e += QZ_THREADS) Qs[e] = Qrows[c0 * R + e];
+                        __syncthreads();
+                        if (j < J) {
+                            for (int i = 0; i < nr; ++i) {
+                                const T x = (T)X[(c0 + i) * J + j];
+#pragma unroll
+                                for (int u = 0; u < 16; ++u) {
+                                    const int r = rg + 4 * u;
+                                    if (u < nq && r < R) acc[u] += Qs[i * R + r] * x;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int r = rg + 4 * u;
+                if (u < nq && r < R) {
+                    if (j < J) Yk[(int64_t)r * J + j] = acc[u];
+                    Ys[r * (QZ_JC + 1) + jj] = j < J ? acc[u] : T(0);
+                }
+            }
+            __syncthreads();
+            // YV partial over this column chunk: thread owns pairs (r, s)
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int e = tid + u * QZ_THREADS;
+                if (e < R * R) {
+                    const int r = e / R, s2 = e % R;
+                    T a = T(0);
+                    for (int c = 0; c < QZ_JC; ++c) a += Ys[r * (QZ_JC + 1) + c] * Vs[c * R + s2];
+                    yv[u] += (double)a;
+                }
+            }
+        }
+        const double *wk = q.W + (int64_t)k * R;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = tid + u * QZ_THREADS;
+            if (e < R * R) {
+                const int r = e / R, s2 = e % R;
+                mh[u] += yv[u] * wk[s2];
+                ww[u] += wk[r] * wk[s2];
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int e = tid + u * QZ_THREADS;
+        if (e < R * R) {
+            MHpart[(int64_t)blockIdx.x * R * R + e] = mh[u];
+            WWpart[(int64_t)blockIdx.x * R * R + e] = ww[u];
+        }
+    }
+}
+
+// H = MH (Γ ∗ WᵀW)⁺ and PV = (HᵀH ∗ WᵀW)⁺, one warp; WW (R×R) is kept.
+static __global__ void k_q_h(const double *__restrict__ MHpart, const double *__restrict__ WWpart, int nb,
+                      QDev q, double *__restrict__ WW, double *__restrict__ PV) {
+    extern __shared__ double hs[];
+    const int R = q.R, ld = q_ld(R), lane = threadIdx.x & 31;
+    double *MH = hs, *A = MH + R * ld, *E = A + R * ld, *O = E + R * ld, *f = O + R * ld;
+    for (int e = lane; e < R * R; e += 32) {
+        double m = 0.0, ww = 0.0;
+        for (int p = 0; p < nb; ++p) {
+            m += MHpart[(int64_t)p * R * R + e];
+            ww += WWpart[(int64_t)p * R * R + e];
+        }
+        MH[(e / R) * ld + (e % R)] = m;
+        WW[e] = ww;
+        A[(e / R) * ld + (e % R)] = q.Gam[e] * ww;
+    }
+    __syncwarp();
+    warp_psd_pinv(A, E, f, O, R, ld, q.rtol, 1, true);
+    // H = MH O
+    for (int e = lane; e < R * R; e += 32) {
+        const int r = e / R, s = e % R;
+        double a = 0.0;
+        for (int p = 0; p < R; ++p) a += MH[r * ld + p] * O[p * ld + s];
+        E[r * ld + s] = a;
+    }
+    __syncwarp();
+    for (int e = lane; e < R * R; e += 32) q.H[e] = E[(e / R) * ld + (e % R)];
+    __syncwarp();
+    // PV = (HᵀH ∗ WᵀW)⁺
+    for (int e = lane; e < R * R; e += 32) {
+        const int r = e / R, s = e % R;
+        double a = 0.0;
+        for (int p = 0; p < R; ++p) a += E[p * ld + r] * E[p * ld + s];
+        A[r * ld + s] = a * WW[e];
+    }
+    __syncwarp();
+    warp_psd_pinv(A, MH, f, O, R, ld, q.rtol, 1, true);
+    for (int e = lane; e < R * R; e += 32) PV[e] = O[(e / R) * ld + (e % R)];
+}
+
+// V-MTTKRP: slot_b += Y_kᵀ (H S_k) for the slices of CTA b.  A thread owns
+// one column j (and all s) per pass over j.
+constexpr int QV_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(QV_THREADS) k_q_vpart(int K_all, QDev q, const T *__restrict__ Y,
+                                                        double *__restrict__ slots) {
+    extern __shared__ double vs[];
+    const int R = q.R, J = q.J, tid = threadIdx.x;
+    T *Ms = reinterpret_cast<T *>(vs);        // R × R   H S_k in T
+    double *sl = slots + (size_t)blockIdx.x * J * R;
+    for (int e = tid; e < J * R; e += QV_THREADS) sl[e] = 0.0;
+    for (int k = blockIdx.x; k < K_all; k += gridDim.x) {
+        __syncthreads();
+        for (int e = tid; e < R * R; e += QV_THREADS)
+            Ms[e] = (T)(q.H[e] * q.W[(int64_t)k * R + (e % R)]);
+        __syncthreads();
+        const T *Yk = Y + (int64_t)k * R * J;
+        for (int j = tid; j < J; j += QV_THREADS) {
+            T acc[64];
+#pragma unroll
+            for (int s = 0; s < 64; ++s) acc[s] = T(0);
+            for (int r = 0; r < R; ++r) {
+                const T y = Yk[(int64_t)r * J + j];
+#pragma unroll
+                for (int s = 0; s < 64; ++s)
+                    if (s < R) acc[s] += y * Ms[r * R + s];
+            }
+#pragma unroll
+            for (int s = 0; s < 64; ++s)
+                if (s < R) sl[(int64_t)j * R + s] += (double)acc[s];
+        }
+    }
+}
+
+// V = (Σ slots) PV, one warp per row j; V in the product type refreshed.
+template <typename T>
+__global__ void k_q_v(const double *__restrict__ slots, int nb, const double *__restrict__ PV, int J,
+                      int R, double *__restrict__ V, T *__restrict__ VT) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= J) return;
+    for (int s = lane; s < R; s += 32) {
+        double v = 0.0;
+        for (int r = 0; r < R; ++r) {
+            double m = 0.0;
+            for (int p = 0; p < nb; ++p) m += slots[(size_t)p * J * R + (int64_t)j * R + r];
+            v += m * PV[r * R + s];
+        }
+        V[(int64_t)j * R + s] = v;
+        VT[(int64_t)j * R + s] = (T)v;
+    }
+}
+
+// PW = (HᵀH ∗ VᵀV)⁺ with the new H and V (one warp).
+static __global__ void k_q_pw(QDev q, double *__restrict__ PW) {
+    extern __shared__ double ws[];
+    const int R = q.R, ld = q_ld(R), lane = threadIdx.x & 31;
+    double *A = ws, *E = A + R * ld, *O = E + R * ld, *f = O + R * ld;
+    for (int e = lane; e < R * R; e += 32) {
+        const int r = e / R, s = e % R;
+        double a = 0.0;
+        for (int p = 0; p < R; ++p) a += q.H[p * R + r] * q.H[p * R + s];
+        A[r * ld + s] = a * q.Gam[e];
+    }
+    __syncwarp();
+    warp_psd_pinv(A, E, f, O, R, ld, q.rtol, 1, true);
+    for (int e = lane; e < R * R; e += 32) PW[e] = O[(e / R) * ld + (e % R)];
+}
+
+// W(k,:) = u PW with u_r = (Hᵀ Y_k V)[r][r] = Σ_q H[q][r] (Y_k V)[q][r].
+// One CTA per slice; Y_k V in column chunks.
+template <typename T>
+__host__ __device__ inline size_t q_w_smem(int R) {
+    return ((size_t)QZ_JC * R + (size_t)R * (QZ_JC + 1)) * sizeof(T) + (size_t)(64 + R * R) * 8 + 16;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(QZ_THREADS) k_q_w(int K_all, QDev q, const T *__restrict__ Y,
+                                                    const T *__restrict__ VT,
+                                                    const double *__restrict__ PW) {
+    extern __shared__ unsigned char qw_raw[];
+    const int R = q.R, J = q.J, tid = threadIdx.x;
+    T *Vs = reinterpret_cast<T *>(qw_raw);            // QZ_JC × R
+    T *Ys = Vs + QZ_JC * R;                           // R × (QZ_JC + 1)
+    const size_t off = (((size_t)QZ_JC * R + (size_t)R * (QZ_JC + 1)) * sizeof(T) + 15) / 16 * 16;
+    double *u = reinterpret_cast<double *>(qw_raw + off);   // 64
+    double *red = u + 64;                                   // R × R
+    for (int k = blockIdx.x; k < K_all; k += gridDim.x) {
+        const T *Yk = Y + (int64_t)k * R * J;
+        double yv[16];
+#pragma unroll
+        for (int v = 0; v < 16; ++v) yv[v] = 0.0;
+        for (int jc = 0; jc < J; jc += QZ_JC) {
+            __syncthreads();
+            for (int e = tid; e < QZ_JC * R; e += QZ_THREADS) {
+                const int j2 = jc + e / R;
+                Vs[e] = j2 < J ? VT[(int64_t)j2 * R + (e % R)] : T(0);
+            }
+            for (int e = tid; e < R * QZ_JC; e += QZ_THREADS) {
+                const int r = e / QZ_JC, c = e % QZ_JC;
+                Ys[r * (QZ_JC + 1) + c] = jc + c < J ? Yk[(int64_t)r * J + jc + c] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int v = 0; v < 16; ++v) {
+                const int e = tid + v * QZ_THREADS;
+                if (e < R * R) {
+                    const int r = e / R, s = e % R;
+                    T a = T(0);
+                    for (int c = 0; c < QZ_JC; ++c) a += Ys[r * (QZ_JC + 1) + c] * Vs[c * R + s];
+                    yv[v] += (double)a;
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 16; ++v) {
+            const int e = tid + v * QZ_THREADS;
+            if (e < R * R) red[e] = q.H[e] * yv[v];
+        }
+        __syncthreads();
+        for (int r = tid; r < R; r += QZ_THREADS) {
+            double a = 0.0;
+            for (int p = 0; p < R; ++p) a += red[p * R + r];
+            u[r] = a;
+        }
+        __syncthreads();
+        for (int s = tid; s < R; s += QZ_THREADS) {
+            double a = 0.0;
+            for (int r = 0; r < R; ++r) a += u[r] * PW[r * R + s];
+            q.W[(int64_t)k * R + s] = a;
+        }
+    }
+}
+
+// The squared residual of X_new against Q_new H S_k Vᵀ with the updated
+// factors; one warp per row, per-CTA partials of (Σ residual², Σ ‖x‖²).
+template <typename TI, typename T>
+__global__ void k_q_out(int64_t N, QDev q, const int *__restrict__ row_slice,
+                        const TI *__restrict__ X, const T *__restrict__ Qrows, const T *__restrict__ VT,
+                        double *__restrict__ fitpart) {
+    extern __shared__ double os[];
+    const int R = q.R, J = q.J;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double *z = os + (size_t)wid * 64;      // per warp: z = q H S
+    double res = 0.0, xn = 0.0;
+    for (int64_t row = (int64_t)blockIdx.x * nw + wid; row < N; row += (int64_t)gridDim.x * nw) {
+        const int k = row_slice[row];
+        __syncwarp();
+        for (int s = lane; s < R; s += 32) {
+            double a = 0.0;
+            for (int r = 0; r < R; ++r) a = fma((double)Qrows[row * R + r], q.H[r * R + s], a);
+            z[s] = a * q.W[(int64_t)k * R + s];
+        }
+        __syncwarp();
+        for (int j = lane; j < J; j += 32) {
+            T xh = T(0);
+            for (int s = 0; s < R; ++s) xh += (T)z[s] * VT[(int64_t)j * R + s];
+            const double x = (double)X[row * J + j];
+            const double d = x - (double)xh;
+            res += d * d;
+            xn += x * x;
+        }
+    }
+    res = warp_sum(res);
+    xn = warp_sum(xn);
+    __shared__ double red[2][32];
+    if (lane == 0) {
+        red[0][wid] = res;
+        red[1][wid] = xn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, c = 0.0;
+        for (int w2 = 0; w2 < nw; ++w2) {
+            a += red[0][w2];
+            c += red[1][w2];
+        }
+        fitpart[2 * blockIdx.x] = a;
+        fitpart[2 * blockIdx.x + 1] = c;
+    }
+}
+
+static __global__ void k_q_fit(const double *__restrict__ fitpart, int nb, const int *__restrict__ gam_ok,
+                        double *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    double a = 0.0, c = 0.0;
+    for (int p = lane; p < nb; p += 32) {
+        a += fitpart[2 * p];
+        c += fitpart[2 * p + 1];
+    }
+    a = warp_sum(a);
+    c = warp_sum(c);
+    if (lane == 0) {
+        out[0] = c > 0.0 ? 1.0 - sqrt(a / c) : 1.0;
+        out[1] = c;
+        out[2] = a;
+        out[3] = (double)*gam_ok;
+    }
+}
+
+}  // namespace dash

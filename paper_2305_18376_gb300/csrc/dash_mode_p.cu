@@ -1,0 +1,205 @@
+// Launch sequence of one mode-P update (Algorithm 1) on the model's stream:
+// the fused row kernel over tiles of single-segment slices, the chunked path
+// for large or split slices, the general kernels, and the global reductions
+// and solves (Eqs. 11-21).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "dash_host.cuh"
+
+namespace dash {
+
+template <typename TI, typename T>
+static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void *Xv, double lam,
+                                   bool begin_new) {
+    const int J = m->cfg.J, R = m->cfg.R;
+    cudaStream_t st = m->stream;
+    const TI *X = (const TI *)Xv;
+    StateDev s = m->st;
+    s.lam = lam;
+    const int64_t N = b.N;
+    const int64_t Ng = b.N_gen;
+    const int n_new = b.K_all - b.K_old;
+    constexpr bool DF = std::is_same<T, float>::value;
+    if (begin_new && n_new > 0) {
+        const int64_t tot = (int64_t)n_new * R * (R + 2);
+        LAUNCH(KK_BEGIN_NEW, k_begin_new<<<(tot + 255) / 256, 256, 0, st>>>(s.W, s.c, s.D, b.K_old, n_new, R));
+    }
+    // fused row kernel over the tiles of single-segment slices
+    int g_f = 0;
+    if constexpr (std::is_same<T, float>::value && std::is_same<TI, float>::value) {
+        if (m->fused_active) {
+            const size_t qsm = (size_t)(2 * R * (R + 1) + R + 1) * 8;
+            LAUNCH(KK_VTILDE, k_vqr<<<1, 32, qsm, st>>>(s.Gam, R, m->rtol, m->RV, m->Linv, m->GPf,
+                                                        m->Gdf, s.gam_ok));
+            LAUNCH(KK_QV, k_qv<<<(J + 7) / 8, 256, 0, st>>>(s.V, m->Linv, J, R, m->QV));
+        }
+        if (m->fused_active && m->n_tiles > 0) {
+            g_f = std::min(m->n_sm, m->n_tiles);
+            FusedArgs fa;
+            fa.X = X;
+            fa.J = J;
+            fa.R = R;
+            fa.lam = lam;
+            fa.rtol = m->rtol;
+            fa.V32 = m->QV;
+            fa.GPf = m->GPf;
+            fa.RV = m->RV;
+            fa.Gdf = m->Gdf;
+            fa.Gam = s.Gam;
+            fa.gam_ok = s.gam_ok;
+            fa.n_tiles = m->n_tiles;
+            fa.tile_s0 = m->d_tile_s0;
+            fa.tile_s1 = m->d_tile_s1;
+            fa.seg_row = b.seg_row;
+            fa.seg_slice = b.seg_slice;
+            fa.W = s.W;
+            fa.c = reinterpret_cast<df *>(s.c);
+            fa.D = reinterpret_cast<df *>(s.D);
+            fa.U = (float *)m->U;
+            fa.Fslot = (float *)m->Fpart;
+            fa.Gpart = m->Gpart;
+            fa.xn_part = m->xn_part;
+            fa.wsp = m->wsp;
+            fa.err = m->d_err;
+            fa.phase_cycles = m->prof.on ? m->prof.d_phase : nullptr;
+            const size_t smem = fu_smem_bytes(J);
+            if (m->cfg.precision == DASH_PREC_F16X3) {
+                CK(cudaFuncSetAttribute(k_rows_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                LAUNCH(KK_ROWS_FUSED, k_rows_fused<true><<<g_f, FU_THREADS, smem, st>>>(fa));
+            } else {
+                CK(cudaFuncSetAttribute(k_rows_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                LAUNCH(KK_ROWS_FUSED, k_rows_fused<false><<<g_f, FU_THREADS, smem, st>>>(fa));
+            }
+        }
+    }
+    int n_xn = 0;
+    // P = X V for the general kernels; P' = X Q_V for the chunked path
+    const T *Vmul = (const T *)m->VT;
+    if constexpr (std::is_same<T, float>::value) {
+        if (m->fused_active) Vmul = (const T *)m->QV;
+    }
+    if (Ng > 0) {
+        LAUNCH(KK_ROWMAP, k_rowmap<<<(N + 255) / 256, 256, 0, st>>>(b));
+        n_xn = (int)((Ng + XV_ROWS - 1) / XV_ROWS);
+        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, b, J, R, Vmul, (T *)m->P,
+                                                        m->xn_part + g_f));
+    }
+    int nsb = 0;
+    bool finished = false;
+    if constexpr (std::is_same<T, float>::value && std::is_same<TI, float>::value) {
+        if (m->fused_active) {
+            // chunks of big / split slices, then every remaining slice's finish
+            FusedArgs fa{};
+            fa.J = J;
+            fa.R = R;
+            fa.lam = lam;
+            fa.rtol = m->rtol;
+            fa.Gdf = m->Gdf;
+            fa.GPf = m->GPf;
+            fa.RV = m->RV;
+            fa.Gam = s.Gam;
+            fa.gam_ok = s.gam_ok;
+            fa.W = s.W;
+            fa.c = reinterpret_cast<df *>(s.c);
+            fa.D = reinterpret_cast<df *>(s.D);
+            fa.U = (float *)m->U;
+            fa.wsp = m->wsp;
+            fa.err = m->d_err;
+            BigArgs bg{};
+            bg.Y = (const float *)m->P;
+            bg.ch_row0 = m->d_ch_row0;
+            bg.ch_n = m->d_ch_n;
+            bg.ch_k = m->d_ch_k;
+            bg.n_chunks = m->n_chunks;
+            bg.fin_k = m->d_fin_k;
+            bg.fin_c0 = m->d_fin_c0;
+            bg.n_fin = m->n_fin;
+            bg.dpart = m->dpart;
+            // both grids stay within the 2-CTAs-per-SM workspace (persistent warps)
+            if (m->n_chunks > 0) {
+                const int gb = std::min(2 * m->n_sm, (m->n_chunks + FU_WARPS - 1) / FU_WARPS);
+                LAUNCH(KK_BIG_B, k_big_b<<<gb, 256, 0, st>>>(fa, bg));
+            }
+            if (m->n_fin > 0) {
+                nsb = std::min(2 * m->n_sm, (m->n_fin + FU_WARPS - 1) / FU_WARPS);
+                LAUNCH(KK_BIG_C, k_big_c<<<nsb, 256, 0, st>>>(fa, bg, m->Gpart + (size_t)g_f * R * R));
+            }
+            finished = true;
+        }
+    }
+    if (!finished) {
+        // per-slice work for slices the fused kernel did not finish
+        const int nw = sl_warps(R);
+        const size_t smem = (size_t)nw * sl_warp_doubles(R) * 8;
+        nsb = (int)std::min<int64_t>((b.K_all + nw - 1) / nw, kSliceBlocksMax);
+        if (nsb < 1) nsb = 1;
+        CK(cudaFuncSetAttribute(k_slices<T, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LAUNCH(KK_SLICES, k_slices<T, DF><<<nsb, 32 * nw, smem, st>>>(b, s, (const T *)m->P, (T *)m->U,
+                                                                      m->Gpart + (size_t)g_f * R * R));
+    }
+    // F partials of the general rows
+    int nfb = 0;
+    if (Ng > 0) {
+        const int nby = (J + F_JB - 1) / F_JB;
+        nfb = (int)std::min<int64_t>(std::max<int64_t>(1, (2 * 152 * 4) / nby), (Ng + F_RC - 1) / F_RC);
+        nfb = std::min(nfb, kFBlocksMax);
+        int64_t rpc = (Ng + nfb - 1) / nfb;
+        rpc = (rpc + F_RC - 1) / F_RC * F_RC;
+        nfb = (int)((Ng + rpc - 1) / rpc);
+        dim3 grid(nfb, nby);
+        LAUNCH(KK_F, k_f<TI, T><<<grid, 256, 0, st>>>(X, b, J, R, (const T *)m->U, s.W, rpc,
+                                                     (T *)m->Fpart + (size_t)g_f * J * R));
+    }
+    LAUNCH(KK_F_REDUCE, k_f_reduce<T><<<((int64_t)J * R + 255) / 256, 256, 0, st>>>((const T *)m->Fpart, g_f + nfb, J, R, lam,
+                                                                s.F, m->Finc));
+    LAUNCH(KK_G_REDUCE, k_g_reduce<<<(R * R + 7) / 8, 256, 0, st>>>(m->Gpart, g_f + nsb, R, lam, s.G, m->Ginc));
+    const size_t psm = (size_t)(3 * R * (R + 1) + (R + 1)) * 8;
+    LAUNCH(KK_PINV, k_pinv_small<<<1, 32, psm, st>>>(s.G, R, m->rtol, m->GP, nullptr));
+    LAUNCH(KK_VUPDATE, k_vupdate<T><<<(J + 7) / 8, 256, 0, st>>>(s.F, m->GP, m->Finc, J, R, s.V, (T *)m->VT,
+                                               m->cross_part));
+    LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(s.V, J, R, s.Gam));
+    LAUNCH(KK_PINV, k_pinv_small<<<1, 32, psm, st>>>(s.Gam, R, m->rtol, s.GamP, s.gam_ok));
+    LAUNCH(KK_FITNESS, k_fitness<<<1, 32, 0, st>>>(m->xn_part, g_f + n_xn, m->cross_part, (J + 7) / 8, s.Gam, m->Ginc, R,
+                                s.gam_ok, m->fit));
+    CK(cudaMemcpyAsync(m->h_fit, m->fit, 4 * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(m->h_err, m->d_err, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    return DASH_OK;
+}
+
+template <typename TI, typename T>
+static dash_status launch_recompute_c(dash_model *m, const BatchDev &b0, const void *Xv) {
+    const int J = m->cfg.J, R = m->cfg.R;
+    constexpr bool DF = std::is_same<T, float>::value;
+    const BatchDev &b = b0;     // planned without fused tiles: every row is general
+    if (b.N > 0) {
+        const int n_xn = (int)((b.N + XV_ROWS - 1) / XV_ROWS);
+        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, m->stream>>>((const TI *)Xv, b, J, R, (const T *)m->VT,
+                                                  (T *)m->P, m->xn_part));
+    }
+    const int nb = (b.K_all + 7) / 8;
+    LAUNCH(KK_C_RECOMPUTE, k_c_recompute<T, DF><<<nb > 0 ? nb : 1, 256, 0, m->stream>>>(b, (const T *)m->P, (const T *)m->U, R,
+                                                            m->st.c));
+    return DASH_OK;
+}
+
+dash_status recompute_c(dash_model *m, const BatchDev &b, const void *X) {
+    const bool f64in = m->cfg.input_dtype == DASH_F64;
+    if (m->tsize == 8)
+        return f64in ? launch_recompute_c<double, double>(m, b, X) : launch_recompute_c<float, double>(m, b, X);
+    return f64in ? launch_recompute_c<double, float>(m, b, X) : launch_recompute_c<float, float>(m, b, X);
+}
+
+dash_status run_update_p(dash_model *m, const BatchDev &b, const void *X, double lam, bool begin_new) {
+    const bool f64in = m->cfg.input_dtype == DASH_F64;
+    if (m->tsize == 8) {
+        return f64in ? launch_update_p<double, double>(m, b, X, lam, begin_new)
+                     : launch_update_p<float, double>(m, b, X, lam, begin_new);
+    }
+    return f64in ? launch_update_p<double, float>(m, b, X, lam, begin_new)
+                 : launch_update_p<float, float>(m, b, X, lam, begin_new);
+}
+
+}  // namespace dash

@@ -1,0 +1,143 @@
+// Launch sequence of one constrained-mode (Q) update on the model's stream:
+// the A rows, the λ-weighted summaries Z_k and L_k, T_k = (L_kᵀL_k)^{-1/2},
+// one CP-ALS sweep H → V → W, the new Q rows and the batch residual.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "dash_host.cuh"
+
+namespace dash {
+
+// Mode Q: one update (sweep = true) or, for the end of a static fit, the
+// summaries of the current factors alone (sweep = false: L_k, Y_k, the new
+// Q rows and the residual; factors untouched).
+static QDev make_qdev(dash_model *m, double lam) {
+    QDev q;
+    q.J = m->cfg.J;
+    q.R = m->cfg.R;
+    q.lam = lam;
+    q.rtol = m->rtol;
+    q.V = m->st.V;
+    q.H = m->qH;
+    q.W = m->st.W;
+    q.L = m->qL;
+    q.E = m->qE;
+    q.Bh = m->qBh;
+    q.C = m->qC;
+    q.Gam = m->st.Gam;
+    return q;
+}
+
+// Warps per CTA of k_q_lt: as many per-warp workspaces as fit in 190 KB.
+template <class S>
+static int q_lt_warps(int R) {
+    const size_t wb = q_lt_warp_bytes<S>(R);
+    return (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(190 * 1024) / wb));
+}
+
+template <class S, typename T>
+static dash_status launch_lt(dash_model *m, const BatchDev &b, const QDev &q, const T *A, T *Qrows,
+                             int mode) {
+    const int R = m->cfg.R;
+    const int nw = q_lt_warps<S>(R);
+    const size_t smem = (size_t)nw * q_lt_warp_bytes<S>(R);
+    const int grid = std::max(1, std::min((b.K_all + nw - 1) / nw, 4 * m->n_sm));
+    const float jtol = std::is_same<S, double>::value ? 1e-15f : 1e-13f;
+    CK(cudaFuncSetAttribute(k_q_lt<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LAUNCH(KK_Q_LT, (k_q_lt<S, T><<<grid, 32 * nw, smem, m->stream>>>(b, q, A, Qrows, mode, 6, jtol)));
+    return DASH_OK;
+}
+
+template <typename TI, typename T, class S>
+static dash_status launch_update_q(dash_model *m, const BatchDev &b, const void *Xv, double lam,
+                                   bool begin_new, bool sweep) {
+    const int J = m->cfg.J, R = m->cfg.R;
+    cudaStream_t st = m->stream;
+    const TI *X = (const TI *)Xv;
+    const int64_t N = b.N;
+    const int n_new = b.K_all - b.K_old;
+    const QDev q = make_qdev(m, lam);
+    T *Y = (T *)m->qY;
+    T *A = (T *)m->qA;
+    T *Qrows = (T *)m->U;
+    if (begin_new && n_new > 0) {
+        const int64_t tot = (int64_t)n_new * R * (1 + 3 * R + J);
+        LAUNCH(KK_Q_BEGIN, (k_q_begin_new<S, T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+                               m->st.W, m->qL, m->qE, m->qBh, Y, b.K_old, n_new, R, J)));
+    }
+    if (N > 0) {
+        LAUNCH(KK_ROWMAP, k_rowmap<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(b));
+        const int n_xn = (int)((N + XV_ROWS - 1) / XV_ROWS);
+        LAUNCH(KK_XV, (k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, b, J, R, (const T *)m->VT, (T *)m->P,
+                                                         m->xn_part)));
+        LAUNCH(KK_Q_AROWS, (k_q_arows<T><<<(unsigned)((N * R + 255) / 256), 256, 0, st>>>(
+                               N, R, b.row_slice, (const T *)m->P, m->st.W, m->qH, A)));
+    }
+    dash_status s = launch_lt<S, T>(m, b, q, A, Qrows, 0);
+    if (s) return s;
+    const int gy = std::max(1, std::min(b.K_all, m->q_lt_max));
+    if (b.K_all > 0) {
+        const size_t ysm = q_y_smem<T>(R);
+        CK(cudaFuncSetAttribute(k_q_y<TI, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm));
+        LAUNCH(KK_Q_Y, (k_q_y<TI, T><<<gy, QZ_THREADS, ysm, st>>>(b, q, X, Qrows, Y, (const T *)m->VT,
+                                                                   m->qMH, m->qWWp)));
+    } else {
+        CK(cudaMemsetAsync(m->qMH, 0, (size_t)R * R * 8, st));
+        CK(cudaMemsetAsync(m->qWWp, 0, (size_t)R * R * 8, st));
+    }
+    const int ld = R + 1;
+    if (sweep) {
+        LAUNCH(KK_Q_H, (k_q_h<<<1, 32, (size_t)(4 * R * ld + R) * 8, st>>>(m->qMH, m->qWWp, gy, q,
+                                                                             m->qWW, m->qPV)));
+        const int gv = std::max(1, std::min(b.K_all, m->q_vslots));
+        LAUNCH(KK_Q_VPART, (k_q_vpart<T><<<gv, QV_THREADS, (size_t)R * R * sizeof(T), st>>>(
+                               b.K_all, q, Y, m->qslots)));
+        LAUNCH(KK_Q_V, (k_q_v<T><<<(J + 7) / 8, 256, 0, st>>>(m->qslots, gv, m->qPV, J, R, m->st.V,
+                                                               (T *)m->VT)));
+        LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(m->st.V, J, R, m->st.Gam));
+        LAUNCH(KK_Q_PW, (k_q_pw<<<1, 32, (size_t)(3 * R * ld + R) * 8, st>>>(q, m->qPW)));
+        if (b.K_all > 0) {
+            const int gw = std::min(b.K_all, 4 * m->n_sm);
+            const size_t wsm = q_w_smem<T>(R);
+            CK(cudaFuncSetAttribute(k_q_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
+            LAUNCH(KK_Q_W, (k_q_w<T><<<gw, QZ_THREADS, wsm, st>>>(b.K_all, q, Y, (const T *)m->VT, m->qPW)));
+        }
+    }
+    int go = 1;
+    if (N > 0) {
+        go = (int)std::min<int64_t>((N + 7) / 8, m->q_out_max);
+        LAUNCH(KK_Q_OUT, (k_q_out<TI, T><<<go, 256, 8 * 64 * 8, st>>>(N, q, b.row_slice, X, Qrows,
+                                                                     (const T *)m->VT, m->qfit)));
+    } else {
+        CK(cudaMemsetAsync(m->qfit, 0, 2 * 8, st));
+    }
+    LAUNCH(KK_Q_FIT, (k_q_fit<<<1, 32, 0, st>>>(m->qfit, go, m->st.gam_ok, m->fit)));
+    CK(cudaMemcpyAsync(m->h_fit, m->fit, 4 * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(m->h_err, m->d_err, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    return DASH_OK;
+}
+
+dash_status run_update_q(dash_model *m, const BatchDev &b, const void *X, double lam,
+                         bool begin_new, bool sweep) {
+    const bool f64in = m->cfg.input_dtype == DASH_F64;
+    if (m->tsize == 8) {
+        return f64in ? launch_update_q<double, double, double>(m, b, X, lam, begin_new, sweep)
+                     : launch_update_q<float, double, double>(m, b, X, lam, begin_new, sweep);
+    }
+    return f64in ? launch_update_q<double, float, df>(m, b, X, lam, begin_new, sweep)
+                 : launch_update_q<float, float, df>(m, b, X, lam, begin_new, sweep);
+}
+
+dash_status prepare_q(dash_model *m) {
+    if (m->K == 0) return DASH_OK;
+    BatchDev b{};
+    b.K_all = (int)m->K;
+    b.K_old = (int)m->K;
+    const QDev q = make_qdev(m, m->cfg.lambda);
+    if (m->tsize == 8) return launch_lt<double, double>(m, b, q, nullptr, nullptr, 1);
+    return launch_lt<df, float>(m, b, q, nullptr, nullptr, 1);
+}
+
+}  // namespace dash

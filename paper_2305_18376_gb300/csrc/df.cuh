@@ -64,6 +64,29 @@ __device__ __forceinline__ df df_mul_f(df a, float b) {
 // a + b·c with b, c double-float
 __device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(a, df_mul(b, c)); }
 
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
+// Square root, reciprocal and reciprocal square root: an FP32 approximation
+// refined by one Newton step whose residual is formed exactly with the
+// error-free product (Karp and Markstein's scheme), about 44 bits.
+__device__ __forceinline__ df df_sqrt(df a) {
+    if (!(a.hi > 0.f)) return {0.f, 0.f};
+    const float x = sqrtf(a.hi);
+    const df r = df_sub(a, two_prod(x, x));            // a − x², small
+    return fast_two_sum(x, r.hi * (0.5f / x));
+}
+__device__ __forceinline__ df df_recip(df a) {
+    const float x = 1.0f / a.hi;
+    const df e = df_sub(df_make(1.0f), df_mul_f(a, x));  // 1 − a·x, small
+    return fast_two_sum(x, x * e.hi);
+}
+__device__ __forceinline__ df df_rsqrt(df a) {
+    if (!(a.hi > 0.f)) return {0.f, 0.f};
+    const float x = rsqrtf(a.hi);
+    const df e = df_sub(df_make(1.0f), df_mul(a, two_prod(x, x)));   // 1 − a·x²
+    return fast_two_sum(x, 0.5f * x * e.hi);
+}
+
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
 __device__ __forceinline__ df df_from_double(double x) {

