@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--k0", type=int, default=0, help="override the initial slice count "
                     "(reduced cases for profiling only; the bench line uses the workload's)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--q-steps", type=int, default=4,
+                    help="timed updates of the constrained-mode (Q) measurement; 0 skips it")
+    ap.add_argument("--q-init-iters", type=int, default=2)
     return ap.parse_args()
 
 
@@ -115,24 +118,56 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # algorithmic work ("Roofline")
 # ---------------------------------------------------------------------------
-def algorithmic(kernel: str, N: int, K_all: int, J: int, R: int, tsize: int, isize: int):
-    """(bytes, flops) one launch must move / do, by kernel."""
-    state = K_all * (R + R * (R + 1) // 2 + R) * 8 * 2      # c, D (sym.), W read + write
+def algorithmic(kernel: str, plan: dict, N: int, K_all: int, J: int, R: int, tsize: int,
+                isize: int):
+    """(bytes, flops) one launch must move / do, by kernel.  plan: the
+    library's account of the batch (dash_last_plan), averaged over the timed
+    updates: rows and slices of the fused tiles, chunked-path rows, rows of
+    the general kernels.  Per-slice mode-P state is c_k (R), the symmetric
+    D_k (R(R+1)/2) and W(k,:) (R), FP64-sized, read and written."""
+    per_slice = (R + R * (R + 1) // 2 + R) * 8 * 2
+    tr, ts = plan.get("tile_rows", 0), plan.get("tile_slices", 0)
+    cr, gr = plan.get("chunk_rows", 0), plan.get("general_rows", 0)
+    if kernel == "k_rows_fused":         # one read of every tile row, U written
+        return tr * J * isize + tr * R * 4 + ts * per_slice, 4 * tr * J * R
     if kernel == "k_xv":
-        return N * J * isize + N * R * tsize, 2 * N * J * R
+        n = cr + gr
+        return n * J * isize + n * R * tsize, 2 * n * J * R
     if kernel == "k_f":
-        return N * J * isize + N * R * tsize, 2 * N * J * R
+        n = cr + gr
+        return n * J * isize + n * R * tsize, 2 * n * J * R
+    if kernel == "k_big_b":              # P' read, U written
+        return 2 * cr * R * 4, 2 * cr * R * R
+    if kernel == "k_big_c":              # state of every slice not finished in a tile
+        return (K_all - ts) * per_slice, 0
     if kernel == "k_slices":
-        return 2 * N * R * tsize + state, N * (2 * R * R + R * R) + K_all * (R ** 3 // 3)
-    if kernel == "k_rows":      # fused single-read pass
-        return N * J * isize + N * R * tsize + state, 4 * N * J * R
+        return 2 * N * R * tsize + K_all * per_slice, N * (3 * R * R) + K_all * (R ** 3 // 3)
+    # mode Q (all rows general); Y_k is K×R×J in the product type
+    Yb = K_all * R * J * tsize
+    if kernel == "k_q_y":                # Y read + written, X read, new Q rows read
+        return 2 * Yb + N * J * isize + N * R * tsize, 2 * K_all * R * J * R + 2 * N * R * J
+    if kernel in ("k_q_vpart", "k_q_w"):  # one pass over Y
+        return Yb, 2 * K_all * R * J * R
+    if kernel == "k_q_out":              # X read, Q rows read
+        return N * J * isize + N * R * tsize, 2 * N * J * R
+    if kernel == "k_q_lt":               # L, E, B^1/2 read + written, carry written, A read, Q written
+        return K_all * R * R * 8 * 7 + 2 * N * R * tsize, 0
     return None, None
 
 
 def step_bytes(N, K_all, J, R, isize):
-    """§8(d) algorithmic bytes of one update: X read once, U written, the
-    per-slice helpers read and written."""
+    """§8(d) algorithmic bytes of one mode-P update: X read once, U written,
+    the per-slice helpers read and written."""
     return N * J * isize + N * R * 4 + K_all * (R + R * (R + 1) // 2 + R) * 8 * 2
+
+
+def step_bytes_q(N, K_all, J, R, isize, tsize=4):
+    """Algorithmic bytes of one mode-Q update: X read once, the new Q rows
+    written, Y_k read and written once (its update, fused with the H-MTTKRP)
+    and read twice more (the V-MTTKRP needs the new H, the W step the new V),
+    the per-slice factors L_k, E_k, B_k^{1/2} read and written."""
+    return (N * J * isize + N * R * tsize + 4 * K_all * R * J * tsize
+            + K_all * R * R * 8 * 6)
 
 
 def src_hash():
@@ -278,6 +313,17 @@ def run_ours(a):
     m.sync()
     init_s = time.perf_counter() - t0
     fit_init = m.fitness()[0]
+    # the constrained mode is fitted on the same initial tensor now, measured later
+    mq = None
+    if a.q_steps > 0 and world == 1:
+        mq = DashModel(w.J, w.R, w.lam, mode="Q", precision=a.precision, input_dtype="f32",
+                       max_slices=K_total + 8, max_rows=max_rows, max_segments=max_seg + 8,
+                       stream=stream.cuda_stream, max_staged_rows=1)
+        mq.set_factors(V0)
+        t1 = time.perf_counter()
+        mq.fit_initial_device(b0.slice_ids.numpy(), b0.row_ptr.numpy(), b0.X, a.q_init_iters)
+        mq.sync()
+        q_init_s = time.perf_counter() - t1
     del b0
     torch.cuda.empty_cache()
     for b in batches[: a.warmup]:
@@ -297,10 +343,12 @@ def run_ours(a):
     sampler.start()
     e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_start.record(stream)
+    plans = []
     for (ea, eb), b in zip(evs, timed):
         ea.record(stream)
         m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X)
         eb.record(stream)
+        plans.append(m.last_plan())
     e_end.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -397,8 +445,9 @@ def run_ours(a):
     top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     roof = None
     kernels = {}
+    plan = {k: statistics.mean(p[k] for p in plans) for k in plans[0]}
     for name, (n, ms) in prof.items():
-        by, fl = algorithmic(name, Nm, K_all, w.J, w.R, 4, 4)
+        by, fl = algorithmic(name, plan, Nm, K_all, w.J, w.R, 4, 4)
         d = {"launches": n, "ms_total": ms, "ms_per_launch": ms / n}
         if by:
             d["gbs"] = by / (ms / n / 1e3) / 1e9
@@ -406,7 +455,7 @@ def run_ours(a):
         kernels[name] = d
     if top:
         name, (n, ms) = top
-        by, fl = algorithmic(name, Nm, K_all, w.J, w.R, 4, 4)
+        by, fl = algorithmic(name, plan, Nm, K_all, w.J, w.R, 4, 4)
         if by:
             per = ms / n / 1e3
             ach = by / per / 1e9
@@ -421,6 +470,10 @@ def run_ours(a):
                         "frac": ach / hbm, "traffic": ncu_traffic(name), "kernel": name,
                         "peak_source": f"{pk_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     sb = step_bytes(Nm, K_all, w.J, w.R, 4)
+    mode_q = None
+    if mq is not None:
+        mode_q = measure_mode_q(a, w, mq, batches, stream, K_total, step_rows, max_seg, pk, q_init_s)
+        mq.close()
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         r = oracle_sample(a.workload, a.cpu_slices, 2)
@@ -434,14 +487,14 @@ def run_ours(a):
             "dtype": "f32" if a.precision == "fp32" else "f16x3",
             "data": "synthetic", "config": workload_config(w, a),
             "latency": {"p50_ms": statistics.median(lat), "p99_ms": lat[-1]},
-            "rows_per_step": Nm, "slices": K_all,
+            "rows_per_step": Nm, "slices": K_all, "plan": plan,
             "fitness": {"init": fit_init, "last_step": fit_last},
             "fp64": fp64, "e2e": e2e, "gpu_launches": launches,
             "roofline": roof,
             "step_roofline": {"bound": "hbm", "algorithmic_bytes": sb,
                               "achieved": sb / (t_max / len(timed)) / 1e9, "peak": pk["hbm_gbs"],
                               "unit": "GB/s", "frac": sb / (t_max / len(timed)) / 1e9 / pk["hbm_gbs"]},
-            "kernels": kernels, "cpu_baseline": cpu, "clocks": clocks,
+            "kernels": kernels, "mode_q": mode_q, "cpu_baseline": cpu, "clocks": clocks,
             "init_seconds": init_s, "src_sha": src_hash(),
             "diagnostics": {"wait_timeouts": timeouts, "fp64_fallback_solves": fallbacks},
         }
@@ -452,6 +505,83 @@ def run_ours(a):
     m.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def measure_mode_q(a, w, mq, batches, stream, K_total, step_rows, max_seg, pk, init_s):
+    """The constrained mode (U_k = Q_k H S_k) on the same stream: one untimed
+    update, then q_steps timed ones (CUDA events on the model's stream), the
+    FP64 path replayed from a snapshot for two of them."""
+    import numpy as np
+    import torch
+    from paper_2305_18376_gb300 import DashModel
+    n_t = min(a.q_steps, len(batches) - 1)
+    mq.update_device(batches[0].slice_ids.numpy(), batches[0].row_ptr.numpy(), batches[0].X)
+    mq.sync()
+    snap = None if a.no_fp64 else mq.get_state_q()
+    timed = batches[1:1 + n_t]
+    mq.profile(True)
+    evs = []
+    for b in timed:
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        mq.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X)
+        eb.record(stream)
+        evs.append((ea, eb))
+    torch.cuda.synchronize()
+    prof = mq.profile_report()
+    mq.profile(False)
+    lat = sorted(ea.elapsed_time(eb) for ea, eb in evs)
+    rows = sum(b.n_rows for b in timed)
+    Nm = int(statistics.mean(b.n_rows for b in timed))
+    K_all = w.K0 + w.new_slices_per_step * (1 + n_t)
+    kernels = {}
+    for name, (n, ms) in prof.items():
+        by, fl = algorithmic(name, {"general_rows": Nm}, Nm, K_all, w.J, w.R, 4, 4)
+        d = {"launches": n, "ms_total": ms, "ms_per_launch": ms / n}
+        if by:
+            d["gbs"] = by / (ms / n / 1e3) / 1e9
+        kernels[name] = d
+    sbq = step_bytes_q(Nm, K_all, w.J, w.R, 4)
+    t_step = sum(lat) / len(lat) / 1e3
+    out = {"value": rows / (sum(lat) / 1e3), "unit": "rows/s", "steps": n_t, "warmup": 1,
+           "ms_per_step": 1e3 * t_step, "p50_ms": statistics.median(lat), "p99_ms": lat[-1],
+           "init_seconds": init_s, "init_iters": a.q_init_iters, "fitness": mq.fitness()[0],
+           "step_roofline": {"bound": "hbm", "algorithmic_bytes": sbq, "achieved": sbq / t_step / 1e9,
+                             "peak": pk["hbm_gbs"], "unit": "GB/s",
+                             "frac": sbq / t_step / 1e9 / pk["hbm_gbs"]},
+           "kernels": kernels}
+    if snap is not None:
+        n64 = min(2, n_t)
+        m64 = DashModel(w.J, w.R, w.lam, mode="Q", precision="fp64", input_dtype="f32",
+                        max_slices=K_total + 8, max_rows=step_rows, max_segments=max_seg + 8,
+                        stream=stream.cuda_stream, max_staged_rows=1)
+        m64.set_state_q(**snap)
+        mm = DashModel(w.J, w.R, w.lam, mode="Q", precision=a.precision, input_dtype="f32",
+                       max_slices=K_total + 8, max_rows=step_rows, max_segments=max_seg + 8,
+                       stream=stream.cuda_stream, max_staged_rows=1)
+        mm.set_state_q(**snap)
+        del snap
+        l64, dfit = [], []
+        for b in timed[:n64]:
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            m64.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X)
+            eb.record(stream)
+            f64v = m64.fitness()[0]
+            mm.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X)
+            dfit.append(abs(mm.fitness()[0] - f64v))
+            torch.cuda.synchronize()
+            l64.append(ea.elapsed_time(eb))
+        s64, smx = m64.get_state_q(), mm.get_state_q()
+        err = {k: float(np.max(np.abs(smx[k] - s64[k])) / max(np.max(np.abs(s64[k])), 1e-300))
+               for k in ("V", "H", "W", "L", "Y")}
+        out["fp64"] = {"value": sum(b.n_rows for b in timed[:n64]) / (sum(l64) / 1e3),
+                       "unit": "rows/s", "ms_per_step": sum(l64) / len(l64), "steps": n64,
+                       "max_abs_fitness_diff_mixed_vs_fp64": float(max(dfit)),
+                       "max_rel_err_mixed_vs_fp64": err}
+        m64.close()
+        mm.close()
+    return out
 
 
 def main():

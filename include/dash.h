@@ -46,7 +46,8 @@ typedef enum dash_status {
     DASH_ENOMEM = 2,     /* device allocation failed or a capacity exceeded */
     DASH_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed      */
     DASH_ESTATE = 4,     /* call not valid now (e.g. V never set)            */
-    DASH_ENUMERIC = 5,   /* a non-finite value reached the factors           */
+    DASH_ENUMERIC = 5,   /* a non-finite value reached the factors (reported
+                            by the next fitness/state read or update)        */
     DASH_ETIMEOUT = 6    /* a bounded device wait gave up                    */
 } dash_status;
 
@@ -237,6 +238,16 @@ dash_status dash_profile_enable(dash_model *m, int32_t on);
 int32_t dash_profile_kinds(void);
 dash_status dash_profile_get(const dash_model *m, int32_t i, const char **name,
                              int64_t *launches, double *total_ms);
+
+/* How the last update's batch was planned (diagnostics and roofline
+ * accounting; the paper has no counterpart).  Mode P: rows and slices
+ * finished by the fused row kernel's tiles (single-segment slices of at most
+ * 256 rows), its tile count, rows of larger or split slices taken by the
+ * chunked path, and rows of the general kernels (batches the fused path does
+ * not take).  Mode Q: every row is a general row.  Any pointer may be NULL.
+ * DASH_ESTATE before the first update. */
+dash_status dash_last_plan(const dash_model *m, int64_t *tile_rows, int64_t *tile_slices,
+                           int64_t *tiles, int64_t *chunk_rows, int64_t *general_rows);
 
 /* Allocation-free F increment.  (The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory.)

@@ -71,6 +71,7 @@ SIGNATURES = [
     ("dash_profile_enable", C.c_int, [P, I32]),
     ("dash_profile_kinds", I32, []),
     ("dash_profile_get", C.c_int, [P, I32, C.POINTER(C.c_char_p), PI64, PD]),
+    ("dash_last_plan", C.c_int, [P, PI64, PI64, PI64, PI64, PI64]),
     ("dash_f_increment_noalloc", C.c_int, [P, P, I64, I32, I32, P, P, I64, P, P, P]),
     ("dash_counters", C.c_int, [P, PI64, PI64]),
 ]
@@ -211,6 +212,14 @@ class DashModel:
         f, x = C.c_double(), C.c_double()
         self._ck(self._lib.dash_fitness(self._h, C.byref(f), C.byref(x)))
         return f.value, x.value
+
+    def last_plan(self) -> dict:
+        """How the last batch was planned: tile rows/slices of the fused row
+        kernel, tiles, chunked-path rows, general-kernel rows."""
+        v = [C.c_int64() for _ in range(5)]
+        self._ck(self._lib.dash_last_plan(self._h, *(C.byref(x) for x in v)))
+        return dict(zip(("tile_rows", "tile_slices", "tiles", "chunk_rows", "general_rows"),
+                        (x.value for x in v)))
 
     def last_update_ms(self) -> float:
         ms = C.c_float()

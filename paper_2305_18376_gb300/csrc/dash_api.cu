@@ -566,6 +566,14 @@ extern "C" dash_status dash_set_state_q(dash_model *m, int64_t K, const double *
     return DASH_OK;
 }
 
+// After a synchronisation: the device counter of non-finite per-slice
+// results (copied back at the end of every update) must be zero.
+static dash_status check_numeric(dash_model *m) {
+    if (m->h_err[2] > 0)
+        return fail(m, DASH_ENUMERIC, "%d slice factors came out non-finite", m->h_err[2]);
+    return DASH_OK;
+}
+
 extern "C" dash_status dash_get_state_q(const dash_model *mc, double *V, double *H, double *W,
                                         double *L, double *Y) {
     dash_model *m = const_cast<dash_model *>(mc);
@@ -573,6 +581,7 @@ extern "C" dash_status dash_get_state_q(const dash_model *mc, double *V, double 
     if (m->cfg.mode != DASH_MODE_Q) return fail(m, DASH_ESTATE, "model is not in mode Q");
     const int64_t J = m->cfg.J, R = m->cfg.R, K = m->K;
     CK(cudaStreamSynchronize(m->stream));
+    if (dash_status sn = check_numeric(m)) return sn;
     if (V) CK(cudaMemcpy(V, m->st.V, J * R * 8, cudaMemcpyDeviceToHost));
     if (H) CK(cudaMemcpy(H, m->qH, R * R * 8, cudaMemcpyDeviceToHost));
     if (W && K) CK(cudaMemcpy(W, m->st.W, K * R * 8, cudaMemcpyDeviceToHost));
@@ -630,8 +639,23 @@ extern "C" dash_status dash_fitness(const dash_model *mc, double *fit_batch, dou
     if (!m) return DASH_EINVAL;
     if (!m->has_last) return fail(m, DASH_ESTATE, "no update has run");
     CK(cudaStreamSynchronize(m->stream));
+    if (dash_status sn = check_numeric(m)) return sn;
     if (fit_batch) *fit_batch = m->h_fit[0];
     if (x_norm2) *x_norm2 = m->h_fit[1];
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_last_plan(const dash_model *mc, int64_t *tile_rows,
+                                      int64_t *tile_slices, int64_t *tiles, int64_t *chunk_rows,
+                                      int64_t *general_rows) {
+    dash_model *m = const_cast<dash_model *>(mc);
+    if (!m) return DASH_EINVAL;
+    if (!m->has_last) return fail(m, DASH_ESTATE, "no update has run");
+    if (tile_rows) *tile_rows = m->plan_tile_rows;
+    if (tile_slices) *tile_slices = m->plan_tile_slices;
+    if (tiles) *tiles = m->plan_tiles;
+    if (chunk_rows) *chunk_rows = m->plan_chunk_rows;
+    if (general_rows) *general_rows = m->plan_general_rows;
     return DASH_OK;
 }
 
@@ -769,6 +793,8 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
     CK(cudaStreamSynchronize(m->stream));   // pinned metadata buffers are reused
     m->gam_ok_host = m->h_fit[3] != 0.0;
     if (m->h_err[0] > 0) return fail(m, DASH_ETIMEOUT, "a bounded device wait timed out");
+    if (m->h_err[2] > 0)
+        return fail(m, DASH_ENUMERIC, "%d slice factors came out non-finite", m->h_err[2]);
     int *tslot = m->h_tslot;
     for (int64_t k = 0; k < K_all; ++k) tslot[k] = -1;
     std::vector<int> cnt;
@@ -881,6 +907,17 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
         }
     }
     m->n_tiles = nt;
+    {
+        int64_t tr = 0, ts = 0;
+        for (int64_t q = 0; q < n_seg; ++q)
+            if (fz[q]) {
+                tr += rp[q + 1] - rp[q];
+                ++ts;
+            }
+        m->plan_tile_rows = tr;
+        m->plan_tile_slices = ts;
+        m->plan_tiles = nt;
+    }
     // general runs: maximal runs of consecutive non-fused segments
     int nr = 0;
     int64_t ng = 0;
@@ -900,6 +937,9 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
         }
         m->h_run_g0[nr] = ng;
     }
+    // with the fused path on, the rows outside tiles go through the chunked path
+    m->plan_chunk_rows = fused ? ng : 0;
+    m->plan_general_rows = fused ? 0 : ng;
     if (n_seg > 0) {
         CK(cudaMemcpyAsync(m->d_seg_slice, m->h_seg_slice, n_seg * 4, cudaMemcpyHostToDevice, m->stream));
         CK(cudaMemcpyAsync(m->d_tseg_idx, m->h_tseg_idx, n_seg * 4, cudaMemcpyHostToDevice, m->stream));

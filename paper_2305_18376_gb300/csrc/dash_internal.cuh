@@ -124,6 +124,10 @@ struct dash_model {
     double *qMH = nullptr, *qWWp = nullptr, *qslots = nullptr, *qfit = nullptr;
     int q_lt_max = 0, q_vslots = 0, q_out_max = 0;
 
+    // plan of the last batch (dash_last_plan)
+    int64_t plan_tile_rows = 0, plan_tile_slices = 0, plan_tiles = 0, plan_chunk_rows = 0,
+            plan_general_rows = 0;
+
     // last update
     int64_t last_N = 0;
     bool has_last = false;

@@ -56,6 +56,7 @@ struct QDev {
     double *Bh;     // Kmax×R×R, B_k^{1/2} (S storage)
     double *C;      // Kmax×R×R, carry T_k,new B_k,old^{1/2} of this update (FP64)
     double *Gam;    // R×R  VᵀV (current V)
+    int *err;       // [2]: slices whose factor or eigenvalues came out non-finite
 };
 
 __host__ __device__ inline int q_ld(int R) { return R + 1; }
@@ -159,6 +160,13 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
         if (mode == 0)
             for (int i = lane; i < R * R; i += 32) Lg[k * RR + i] = Lw[(i / R) * ld + (i % R)];
         warp_eig_factor(Lw, Ew, Gw, Mw, E2, R, ld, passes, jac_tol, 40, 1e-7f);
+        {
+            // a non-finite factor or eigenvalue must not pass silently
+            bool ok = true;
+            for (int i = lane; i < R; i += 32) ok = ok && isfinite(O::to_d(Mw[i * ld + i]));
+            for (int i = lane; i < R * R; i += 32) ok = ok && isfinite(O::to_d(Lw[(i / R) * ld + (i % R)]));
+            if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicAdd(q.err + 2, 1);
+        }
         warp_sqrt_weights(Mw, R, ld, q.rtol, finv, fsq);
         for (int i = lane; i < R * R; i += 32) Eg[k * RR + i] = Ew[(i / R) * ld + (i % R)];
         // T_k → E2

@@ -27,6 +27,7 @@ static QDev make_qdev(dash_model *m, double lam) {
     q.Bh = m->qBh;
     q.C = m->qC;
     q.Gam = m->st.Gam;
+    q.err = m->d_err;
     return q;
 }
 

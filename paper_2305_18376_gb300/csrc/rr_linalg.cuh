@@ -36,6 +36,7 @@ namespace dash {
 template <class S> struct RT;
 
 template <> struct RT<double> {
+    static __device__ __forceinline__ bool invertible(double a) { return fabs(a) > 1e-290; }
     static __device__ __forceinline__ double zero() { return 0.0; }
     static __device__ __forceinline__ double one() { return 1.0; }
     static __device__ __forceinline__ double from_d(double x) { return x; }
@@ -54,6 +55,8 @@ template <> struct RT<double> {
 };
 
 template <> struct RT<df> {
+    // FP32 exponent range: keep the reciprocal (and its Newton step) normal
+    static __device__ __forceinline__ bool invertible(df a) { return fabsf(a.hi) > 1e-30f; }
     static __device__ __forceinline__ df zero() { return {0.f, 0.f}; }
     static __device__ __forceinline__ df one() { return {1.f, 0.f}; }
     static __device__ __forceinline__ df from_d(double x) { return df_from_double(x); }
@@ -94,10 +97,14 @@ __device__ void warp_qr_append(S *L, int ld, S *A, int lda, int m, int R) {
         const S sq = warp_sum_s(O::mul(aij, aij));
         const S ljj = L[j * ld + j];
         __syncwarp();
-        if (O::hi(sq) != 0.f) {
-            const S alpha = O::sqrt_(O::fma(sq, ljj, ljj));
-            const S v0 = O::add(ljj, alpha);                 // ljj >= 0: no cancellation
-            const S tau = O::recip(O::mul(alpha, v0));        // 2 / vᵀv
+        const S alpha = O::sqrt_(O::fma(sq, ljj, ljj));
+        const S v0 = O::add(ljj, alpha);                     // ljj >= 0: no cancellation
+        const S av = O::mul(alpha, v0);
+        // nothing below the diagonal (sq = 0), or only residues so small that
+        // vᵀv/2 is not invertible in the working type (the column of a
+        // rank-deficient slice after its rank is reached): no reflection
+        if (O::hi(sq) != 0.f && O::invertible(av)) {
+            const S tau = O::recip(av);                        // 2 / vᵀv
             for (int c = j + 1 + lane; c < R; c += 32) {
                 S d = O::mul(v0, L[j * ld + c]);
                 for (int i = 0; i < m; ++i) d = O::fma(d, A[i * lda + j], A[i * lda + c]);

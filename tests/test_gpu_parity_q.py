@@ -186,6 +186,41 @@ def test_ragged_edges_q(prec):
     m.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "f16x3"])
+def test_short_slices_at_rank_32_q(prec):
+    """R = 32 with slices of 1-15 rows (rank-deficient L_k, whose QR leaves
+    only rounding residues in the columns past the rank): every result stays
+    finite and matches the oracle."""
+    _, tdt = PREC_DTYPE[prec]
+    J, R, lam = 40, 32, 0.9
+    rng = np.random.default_rng(21)
+    sizes = [60, 9, 15, 3, 1, 45, 12, 33]
+    X0 = [torch.from_numpy(rng.random((n, J)) + 0.1 * rng.standard_normal((n, J))).to(tdt)
+          .to(torch.float64).numpy() for n in sizes]
+    V0 = rng.random((J, R))
+    st = _oracle_fit(X0, V0, R, 2)
+    m = _model(J, R, lam, prec, max_slices=32, max_rows=1024, max_segments=64)
+    m.set_factors(V0)
+    rp = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    m.append_batch(np.arange(len(sizes), dtype=np.int64), rp,
+                   np.concatenate(X0).astype(np.float64 if prec == "fp64" else np.float32))
+    m.fit_initial(2)
+    b = ragged_batch(len(sizes), 1, J, rows=[2, 0, 4, 1, 7, 3], seed=8, dtype=tdt,
+                     slice_ids=[1, 2, 3, 4, 8, 0])
+    segs = segs_np(b, tdt)
+    X = O._group(segs, st.K, b.n_new, J)
+    st, Qo, _ = O.dash_update_q(st, list(X.items()), b.n_new, lam)
+    m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.to(tdt).numpy())
+    m.update()
+    g = m.get_state_q()                    # DASH_ENUMERIC would raise here
+    for k, v in g.items():
+        assert np.all(np.isfinite(v)), k
+    errs = {k: rel(g[k], v) for k, v in (("V", st.V), ("H", st.H), ("W", st.W))}
+    print(f"short slices R=32 {prec}:", errs)
+    assert max(errs.values()) <= (1e-8 if prec == "fp64" else 1e-4), errs
+    m.close()
+
+
 def test_q_orthonormal_and_deterministic():
     """The first update on an empty model sees every row of a slice at once,
     so its Q rows are the polar factor: QᵀQ = I when the slice has at least
