@@ -344,12 +344,14 @@ def run_ours(a):
     e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_start.record(stream)
     plans = []
+    torch.cuda.nvtx.range_push("dash_p_timed")    # ncu --nvtx-include dash_p_timed/
     for (ea, eb), b in zip(evs, timed):
         ea.record(stream)
         m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X)
         eb.record(stream)
         plans.append(m.last_plan())
     e_end.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
@@ -521,12 +523,14 @@ def measure_mode_q(a, w, mq, batches, stream, K_total, step_rows, max_seg, pk, i
     timed = batches[1:1 + n_t]
     mq.profile(True)
     evs = []
+    torch.cuda.nvtx.range_push("dash_q_timed")    # ncu --nvtx-include dash_q_timed/
     for b in timed:
         ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ea.record(stream)
         mq.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X)
         eb.record(stream)
         evs.append((ea, eb))
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     prof = mq.profile_report()
     mq.profile(False)

@@ -15,7 +15,8 @@ namespace dash {
 enum KernelKind {
     KK_BEGIN_NEW, KK_ROWMAP, KK_XV, KK_SLICES, KK_F, KK_F_REDUCE, KK_G_REDUCE, KK_PINV,
     KK_VUPDATE, KK_GAMMA, KK_FITNESS, KK_CAST, KK_C_RECOMPUTE, KK_VTILDE, KK_ROWS_FUSED,
-    KK_BIG_B, KK_BIG_C, KK_QV, KK_PH_A, KK_PH_EPI, KK_PH_B,
+    KK_BIG_B, KK_BIG_C, KK_QV, KK_PH_A, KK_PH_EPI, KK_PH_B, KK_EPI_U, KK_EPI_DD, KK_EPI_FIN,
+    KK_EPI_SCALE,
     KK_Q_BEGIN, KK_Q_AROWS, KK_Q_Y, KK_Q_LT, KK_Q_H, KK_Q_VPART, KK_Q_V, KK_Q_PW, KK_Q_W,
     KK_Q_OUT, KK_Q_FIT, KK_COUNT
 };
@@ -24,6 +25,8 @@ static const char *const kKernelNames[KK_COUNT] = {
     "k_pinv_small", "k_vupdate", "k_gamma", "k_fitness", "k_cast", "k_c_recompute",
     "k_vqr", "k_rows_fused", "k_big_b", "k_big_c", "k_qv",
     "k_rows_fused.phase_a", "k_rows_fused.epilogue", "k_rows_fused.phase_b",
+    "k_rows_fused.epilogue.u_rows", "k_rows_fused.epilogue.gram", "k_rows_fused.epilogue.finish",
+    "k_rows_fused.epilogue.scale",
     "k_q_begin_new", "k_q_arows", "k_q_y", "k_q_lt", "k_q_h", "k_q_vpart", "k_q_v", "k_q_pw",
     "k_q_w", "k_q_out", "k_q_fit"};
 

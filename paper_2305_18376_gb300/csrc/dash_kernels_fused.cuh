@@ -205,65 +205,120 @@ __device__ __forceinline__ float warp_max_f(float v) {
     return v;
 }
 
+// L Lᵀ x = b with lane i holding row i of L in `row` (registers) and L also
+// in Lw (row i at Lw[i·FU_LD]); myinv = 1/L[i][i] on lane i.  Forward
+// substitution broadcasts y_j from lane j; backward reads column entries
+// L[j][i] from Lw.  Returns x[lane] (0 for lanes >= R).
+__device__ __forceinline__ float chol_solve_reg(const float (&row)[FU_RP], const float *Lw,
+                                                float myinv, bool act, float b) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float y = act ? b : 0.f;
+#pragma unroll 32
+    for (int j = 0; j < FU_RP; ++j) {
+        const float yj = __shfl_sync(full, y * myinv, j);
+        if (lane == j) y = yj;
+        else if (lane > j) y = fmaf(-row[j], yj, y);
+    }
+#pragma unroll 32
+    for (int j = FU_RP - 1; j >= 0; --j) {
+        const float xj = __shfl_sync(full, y * myinv, j);
+        if (lane == j) y = xj;
+        else if (lane < j) y = fmaf(-Lw[j * FU_LD + lane], xj, y);
+    }
+    return act ? y : 0.f;
+}
+
 // Finish slice k from its new-data Gram ΔD (lane r holds row r in dd) and
 // Δc (lane r holds Δc[r]): c_k ← λc_k + Δc, D_k ← λD_k + ΔD (Eqs. 15-16,
 // double-float), W(k,:) = c_kᵀ(Γ ∗ D_k)⁺ (Eq. 12) by an FP32 Cholesky factor
 // with one double-float refinement step (FP64 pseudo-inverse fallback), the
 // slice's share S_k ΔD S_k of G_inc (Eq. 21) added to gacc (lane r: row r).
 // Returns w_k,new[lane].  Called by all 32 lanes of a warp.
+//
+// Everything lives in registers, lane l owning row l: D_k is read and written
+// column by column (coalesced; D_k is symmetric, so lane l's column is its
+// row), A = Γ ∗ D_k is kept as double-float pairs, and the Cholesky factor is
+// formed right-looking with the pivot column broadcast by shuffles.  Lw (a
+// per-warp R×FU_LD float block) only carries L for the backward solve.
 __device__ __forceinline__ float slice_finish(const FusedArgs &a, int k, const float (&dd)[FU_RP],
                                               float dc, float (&gacc)[FU_RP], const df *Gs,
                                               float *Lw, df *xw, double *wsp) {
+    (void)xw;
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int R = a.R;
+    const bool act = lane < R;
     df cnew = {0.f, 0.f};
-    float amax = 0.f;
     const df lamdf = df_from_double(a.lam);
     const bool keep_old = a.lam != 0.0;
     df *Dk = a.D + (int64_t)k * R * R;
-    if (lane < R) {
+    if (act) {
         const df cold = a.c[(int64_t)k * R + lane];
         cnew = df_add(keep_old ? df_mul(lamdf, cold) : df{0.f, 0.f}, df_make(dc));
         a.c[(int64_t)k * R + lane] = cnew;
     }
+    // D_k ← λD_k + ΔD and A = Γ ∗ D_k (row `lane`), coalesced over columns.
+    // Rows and columns >= R stay zero: the factorisation below then runs over
+    // all 32 (unrolled, no per-step guards) and leaves them zero.
+    float row[FU_RP];
+    float mydiag = 0.f;
 #pragma unroll
-    for (int q = 0; q < FU_RP; ++q) {
-        if (q < R && lane < R) {
-            const df dold = Dk[lane * R + q];
-            const df dn = df_add(keep_old ? df_mul(lamdf, dold) : df{0.f, 0.f}, df_make(dd[q]));
-            Dk[lane * R + q] = dn;
-            const df av = df_mul(Gs[lane * FU_RP + q], dn);
-            Lw[lane * FU_LD + q] = av.hi;
-            if (q == lane) amax = fabsf(av.hi);
+    for (int r = 0; r < FU_RP; ++r) {
+        row[r] = 0.f;
+        if (r < R && act) {
+            const df dold = Dk[r * R + lane];
+            const df dn = df_add(keep_old ? df_mul(lamdf, dold) : df{0.f, 0.f}, df_make(dd[r]));
+            Dk[r * R + lane] = dn;
+            row[r] = df_mul(Gs[r * FU_RP + lane], dn).hi;      // Γ symmetric: conflict-free
+            if (r == lane) mydiag = row[r];
         }
     }
-    amax = warp_max_f(amax);
-    __syncwarp();
-    bool ok = amax > 0.f && warp_cholesky_f(Lw, R, FU_LD, 1e-6f * amax);
+    const float amax = warp_max_f(fabsf(mydiag));
+    // right-looking Cholesky of A (hi parts), lane l = row l
+    const float tol = 1e-6f * amax;
+    bool ok = amax > 0.f;
+    float myinv = 0.f;
+#pragma unroll 32
+    for (int j = 0; j < FU_RP; ++j) {
+        const float piv = __shfl_sync(full, row[j], j);
+        if (j < R) ok = ok && (piv > tol);
+        const float inv = rsqrtf(fmaxf(piv, 1e-30f));
+        const float lij = (lane == j) ? piv * inv : row[j] * inv;
+        row[j] = lij;
+        if (lane == j) myinv = inv;
+#pragma unroll 31
+        for (int q = j + 1; q < FU_RP; ++q) {
+            const float lqj = __shfl_sync(full, lij, q);
+            row[q] = fmaf(-lij, lqj, row[q]);
+        }
+    }
     df x = {0.f, 0.f};
     if (ok) {
-        const float rinv = lane < R ? 1.0f / Lw[lane * FU_LD + lane] : 0.f;
-        const float x0 = warp_cholesky_solve_f(Lw, R, FU_LD, lane < R ? cnew.hi : 0.f, rinv);
-        x = df_make(x0);
-        for (int it = 0; it < 1; ++it) {
-            __syncwarp();
-            if (lane < R) xw[lane] = x;
-            __syncwarp();
-            df res = cnew;
-            if (lane < R) {
-                for (int q = 0; q < R; ++q) {
-                    const df av = df_mul(Gs[lane * FU_RP + q], Dk[lane * R + q]);
-                    res = df_add(res, df_neg(df_mul(av, xw[q])));
-                }
+        // L (lower) to shared for the backward solve: Lw[i][j], row i by lane i
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < FU_RP; ++j) Lw[lane * FU_LD + j] = row[j];
+        __syncwarp();
+        const float x0 = chol_solve_reg(row, Lw, myinv, act, cnew.hi);
+        // one refinement step: res = c − A x0 in double-float, A re-formed
+        // from the D_k just written (an L1 hit)
+        df res = cnew;
+#pragma unroll
+        for (int r = 0; r < FU_RP; ++r) {
+            const float xr = __shfl_sync(full, x0, r);
+            if (r < R && act) {
+                const df av = df_mul(Gs[r * FU_RP + lane], Dk[r * R + lane]);
+                res = df_sub(res, df_mul_f(av, xr));
             }
-            const float dx = warp_cholesky_solve_f(Lw, R, FU_LD, lane < R ? res.hi : 0.f, rinv);
-            x = df_add(x, df_make(dx));
         }
-        ok = __all_sync(0xffffffffu, isfinite(x.hi));
+        const float dx = chol_solve_reg(row, Lw, myinv, act, res.hi);
+        x = df_add(df_make(x0), df_make(dx));
+        ok = __all_sync(full, isfinite(x.hi));
     }
     double wnew_d;
     if (ok) {
-        wnew_d = lane < R ? df_to_double(x) : 0.0;
+        wnew_d = act ? df_to_double(x) : 0.0;
     } else {
         // FP64 pseudo-inverse solve (rare): A = Γ ∗ D_k, b = c_k
         double *Aw = wsp, *Lf = Aw + R * (R + 1), *Ew = Lf + R * (R + 1);
@@ -274,20 +329,21 @@ __device__ __forceinline__ float slice_finish(const FusedArgs &a, int k, const f
             const int r = e / R, q = e % R;
             Aw[r * ld + q] = a.Gam[e] * df_to_double(Dk[e]);
         }
-        if (lane < R) bw[lane] = df_to_double(cnew);
+        if (act) bw[lane] = df_to_double(cnew);
         __syncwarp();
         warp_psd_solve(Aw, Lf, Ew, bw, fw, R, ld, a.rtol);
         __syncwarp();
-        wnew_d = lane < R ? bw[lane] : 0.0;
-        atomicAdd(&a.err[1], 1);
+        wnew_d = act ? bw[lane] : 0.0;
+        if (lane == 0) atomicAdd(&a.err[1], 1);
     }
-    if (lane < R) a.W[(int64_t)k * R + lane] = wnew_d;
+    if (act) a.W[(int64_t)k * R + lane] = wnew_d;
     const float wnew = (float)wnew_d;
 #pragma unroll
     for (int q = 0; q < FU_RP; ++q) {
-        const float wq = __shfl_sync(0xffffffffu, wnew, q);
-        if (lane < R && q < R) gacc[q] = fmaf(wnew * dd[q], wq, gacc[q]);
+        const float wq = __shfl_sync(full, wnew, q);
+        if (act && q < R) gacc[q] = fmaf(wnew * dd[q], wq, gacc[q]);
     }
+    __syncwarp();
     return wnew;
 }
 
@@ -460,6 +516,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
     for (int q = 0; q < FU_RP; ++q) gacc[q] = 0.f;
     bool aborted = false;
     unsigned long long cyc[3] = {0ull, 0ull, 0ull};
+    long long wcyc[4] = {0, 0, 0, 0};      // per warp: U rows, ΔD, slice finish, Ũ scaling
     long long tmark = clock64();
     float xmax_t = 0.f;                // max |x| of the current tile (this thread's share)
 
@@ -468,6 +525,21 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
         tile_rows(t, r0, r1);
         const int nr = (int)(r1 - r0);
         const int nch = (nr + CH - 1) / CH;
+        {
+            // bring this tile's per-slice state (D_k, c_k, W(k,:)) into L2 while
+            // phase A streams X, so the epilogue does not wait on HBM for it
+            const int ts0 = a.tile_s0[t], ts1 = a.tile_s1[t];
+            const int ld_ = (R * R * 8 + 127) / 128, lc = (R * 8 + 127) / 128;
+            const int per = ld_ + 2 * lc;
+            for (int e = tid; e < (ts1 - ts0) * per; e += FU_THREADS) {
+                const int k = a.seg_slice[ts0 + e / per], l = e % per;
+                const char *pp;
+                if (l < ld_) pp = reinterpret_cast<const char *>(a.D + (int64_t)k * R * R) + l * 128;
+                else if (l < ld_ + lc) pp = reinterpret_cast<const char *>(a.c + (int64_t)k * R) + (l - ld_) * 128;
+                else pp = reinterpret_cast<const char *>(a.W + (int64_t)k * R) + (l - ld_ - lc) * 128;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pp));
+            }
+        }
         // ================= phase A: P = X V =================================
         for (int cI = 0; cI < nch; ++cI) {
             const int slot = consumed % FU_NBUF;
@@ -606,6 +678,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
         // ================= epilogue: one warp per slice ======================
         const int s0 = a.tile_s0[t], s1 = a.tile_s1[t];
         for (int sg = s0 + warp; sg < s1; sg += FU_WARPS) {
+            long long w0 = a.phase_cycles ? clock64() : 0;
             const int k = a.seg_slice[sg];
             const int ia = (int)(a.seg_row[sg] - r0);
             const int n = (int)(a.seg_row[sg + 1] - a.seg_row[sg]);
@@ -643,7 +716,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
                     mcol[t] = (float)m;
                     rvcol[t] = (t < R && lane < R) ? (float)a.RV[t * R + lane] : 0.f;
                 }
-                atomicAdd(&a.err[1], 1);
+                if (lane == 0) atomicAdd(&a.err[1], 1);
             }
             for (int i = 0; i < n; ++i) {
                 float *y = Ytile + (ia + i) * FU_YP;
@@ -673,6 +746,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
                 if (lane < R) a.U[(r0 + ia + i) * R + lane] = u;
             }
             __syncwarp();
+            if (a.phase_cycles) { const long long w1 = clock64(); wcyc[0] += w1 - w0; w0 = w1; }
             // ΔD row `lane`: dd[q] = Σ_i U[i][lane] U[i][q]
             float dd[FU_RP];
 #pragma unroll
@@ -698,10 +772,13 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
                 }
                 dc = sacc;
             }
+            if (a.phase_cycles) { const long long w1 = clock64(); wcyc[1] += w1 - w0; w0 = w1; }
             const float wnew = slice_finish(a, k, dd, dc, gacc, Gs, Lw, xw, wsp);
+            if (a.phase_cycles) { const long long w1 = clock64(); wcyc[2] += w1 - w0; w0 = w1; }
             // Ũ = U S_k,new for phase B
             for (int i = 0; i < n; ++i) Ytile[(ia + i) * FU_YP + lane] *= (lane < R ? wnew : 0.f);
             __syncwarp();
+            if (a.phase_cycles) { const long long w1 = clock64(); wcyc[3] += w1 - w0; }
         }
         __syncthreads();
         {
@@ -857,6 +934,10 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
         atomicAdd(&a.phase_cycles[1], cyc[1]);
         atomicAdd(&a.phase_cycles[2], cyc[2]);
     }
+    if (a.phase_cycles && lane == 0) {     // epilogue sub-phases, summed over warps
+#pragma unroll
+        for (int i = 0; i < 4; ++i) atomicAdd(&a.phase_cycles[3 + i], (unsigned long long)wcyc[i]);
+    }
     if (aborted) {
         // let copies already issued land (bounded) before the CTA exits
         if (tid == 0) {
@@ -1010,7 +1091,7 @@ __device__ __forceinline__ void big_chunk(const FusedArgs &a, const BigArgs &bg,
             mcol[t] = (float)m;
             rvcol[t] = (t < R && lane < R) ? (float)a.RV[t * R + lane] : 0.f;
         }
-        atomicAdd(&a.err[1], 1);
+        if (lane == 0) atomicAdd(&a.err[1], 1);
     }
     float dd[FU_RP];
 #pragma unroll
