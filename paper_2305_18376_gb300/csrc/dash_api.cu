@@ -240,7 +240,7 @@ static dash_status init_alloc(dash_model *m) {
         m->q_lt_max = 4 * m->n_sm;
         DALLOC(m->qMH, (size_t)m->q_lt_max * R * R * 8, "H-MTTKRP partials");
         DALLOC(m->qWWp, (size_t)m->q_lt_max * R * R * 8, "W^T W partials");
-        m->q_vslots = 2 * m->n_sm;
+        m->q_vslots = 4 * m->n_sm;
         DALLOC(m->qslots, (size_t)m->q_vslots * J * R * 8, "V-MTTKRP slots");
         m->q_out_max = 4 * m->n_sm;
         DALLOC(m->qfit, (size_t)m->q_out_max * 2 * 8, "residual partials");

@@ -39,6 +39,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "dash_kernels_p.cuh"
 #include "rr_linalg.cuh"
 #include "small_linalg.cuh"
@@ -110,7 +112,7 @@ __global__ void k_q_arows(int64_t N, int R, const int *__restrict__ row_slice,
 template <class S>
 __host__ __device__ inline size_t q_lt_warp_bytes(int R) {
     const int ld = q_ld(R);
-    return (size_t)5 * R * ld * sizeof(S) + (size_t)2 * R * sizeof(S);
+    return (size_t)4 * R * ld * sizeof(S) + (size_t)3 * R * sizeof(S);
 }
 
 template <class S, typename T>
@@ -123,10 +125,10 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
     unsigned char *base = qlt_raw + (size_t)wid * q_lt_warp_bytes<S>(R);
     S *Lw = reinterpret_cast<S *>(base);
     S *Ew = Lw + R * ld;
-    S *Gw = Ew + R * ld;
-    S *Mw = Gw + R * ld;
-    S *E2 = Mw + R * ld;
-    S *finv = E2 + R * ld;
+    S *Gw = Ew + R * ld;      // G, the rotations, then T_k
+    S *Mw = Gw + R * ld;      // M, then B_old^{1/2}, B_new^{1/2}, staged A rows
+    S *mu = Mw + R * ld;
+    S *finv = mu + R;
     S *fsq = finv + R;
     const int chunk = R < 32 ? R : 32;      // A rows per QR step (staged in Gw)
     const S sl = O::from_d(sqrt(q.lam));
@@ -159,33 +161,41 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
         }
         if (mode == 0)
             for (int i = lane; i < R * R; i += 32) Lg[k * RR + i] = Lw[(i / R) * ld + (i % R)];
-        warp_eig_factor(Lw, Ew, Gw, Mw, E2, R, ld, passes, jac_tol, 40, 1e-7f);
+        {
+            // FP32 pre-pass (float scratch in G and M), then the working-type passes
+            float *f0 = reinterpret_cast<float *>(Gw);
+            const int fs = R * ld;
+            if (!std::is_same<S, float>::value)
+                warp_eig_prepass_f32<S>(Lw, Ew, f0, f0 + fs, f0 + 2 * fs, f0 + 3 * fs,
+                                        reinterpret_cast<float *>(mu), Gw, Mw, R, ld, 12);
+        }
+        warp_eig_factor(Lw, Ew, Gw, Mw, mu, R, ld, passes, jac_tol, 40, 1e-7f);
         {
             // a non-finite factor or eigenvalue must not pass silently
             bool ok = true;
-            for (int i = lane; i < R; i += 32) ok = ok && isfinite(O::to_d(Mw[i * ld + i]));
+            for (int i = lane; i < R; i += 32) ok = ok && isfinite(O::to_d(mu[i]));
             for (int i = lane; i < R * R; i += 32) ok = ok && isfinite(O::to_d(Lw[(i / R) * ld + (i % R)]));
             if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicAdd(q.err + 2, 1);
         }
-        warp_sqrt_weights(Mw, R, ld, q.rtol, finv, fsq);
+        warp_sqrt_weights(mu, R, q.rtol, finv, fsq);
         for (int i = lane; i < R * R; i += 32) Eg[k * RR + i] = Ew[(i / R) * ld + (i % R)];
-        // T_k → E2
-        warp_spectral_s(Ew, finv, R, ld, E2);
+        // T_k → Gw
+        warp_spectral_s(Ew, finv, R, ld, Gw);
         if (mode == 0 && q.lam != 0.0) {
-            // C_k = T_k · B_old^{1/2}  (B_old^{1/2} → Gw, product → Mw)
-            for (int i = lane; i < R * R; i += 32) Gw[(i / R) * ld + (i % R)] = Bg[k * RR + i];
+            // C_k = T_k · B_old^{1/2}  (B_old^{1/2} → Mw)
+            for (int i = lane; i < R * R; i += 32) Mw[(i / R) * ld + (i % R)] = Bg[k * RR + i];
             __syncwarp();
             for (int idx = lane; idx < R * R; idx += 32) {
                 const int r = idx / R, c = idx % R;
                 S a = O::zero();
-                for (int p = 0; p < R; ++p) a = O::fma(a, E2[r * ld + p], Gw[p * ld + c]);
+                for (int p = 0; p < R; ++p) a = O::fma(a, Gw[r * ld + p], Mw[p * ld + c]);
                 q.C[k * RR + idx] = O::to_d(a);
             }
             __syncwarp();
         }
-        // B_k^{1/2} → Gw → global
-        warp_spectral_s(Ew, fsq, R, ld, Gw);
-        for (int i = lane; i < R * R; i += 32) Bg[k * RR + i] = Gw[(i / R) * ld + (i % R)];
+        // B_k^{1/2} → Mw → global
+        warp_spectral_s(Ew, fsq, R, ld, Mw);
+        for (int i = lane; i < R * R; i += 32) Bg[k * RR + i] = Mw[(i / R) * ld + (i % R)];
         // new Q rows = A_new T_k (A rows staged through Mw)
         if (t >= 0) {
             for (int si = b.tseg_ptr[t]; si < b.tseg_ptr[t + 1]; ++si) {
@@ -200,7 +210,7 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
                     for (int e = lane; e < m * R; e += 32) {
                         const int i = e / R, c = e % R;
                         S a = O::zero();
-                        for (int p = 0; p < R; ++p) a = O::fma(a, Mw[i * ld + p], E2[p * ld + c]);
+                        for (int p = 0; p < R; ++p) a = O::fma(a, Mw[i * ld + p], Gw[p * ld + c]);
                         Qrows[(c0 + i) * R + c] = (T)O::to_d(a);
                     }
                 }
@@ -224,7 +234,7 @@ __host__ __device__ inline size_t q_y_smem(int R) {
     return ((size_t)QZ_JC * R + (size_t)QZ_RC * R + (size_t)R * (QZ_JC + 1) + (size_t)R * R) * sizeof(T);
 }
 
-template <typename TI, typename T>
+template <typename TI, typename T, int RM>
 __global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI *__restrict__ X,
                                                     const T *__restrict__ Qrows, T *__restrict__ Y,
                                                     const T *__restrict__ VT, double *__restrict__ MHpart,
@@ -237,18 +247,20 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI
     T *Cs = Ys + R * (QZ_JC + 1);                    // R × R   λ C_k
     const int jj = tid % QZ_JC, rg = tid / QZ_JC;
     const int nq = (R + 3) / 4;
-    double mh[16], ww[16];
+    constexpr int NQ = RM / 4;                        // rows of Y per thread
+    constexpr int NP = (RM * RM + QZ_THREADS - 1) / QZ_THREADS;   // (r, s) pairs per thread
+    double mh[NP], ww[NP];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) { mh[u] = 0.0; ww[u] = 0.0; }
+    for (int u = 0; u < NP; ++u) { mh[u] = 0.0; ww[u] = 0.0; }
     for (int k = blockIdx.x; k < b.K_all; k += gridDim.x) {
         const int t = b.tslot[k];
         T *Yk = Y + (int64_t)k * R * J;
         __syncthreads();
         for (int e = tid; e < R * R; e += QZ_THREADS)
             Cs[e] = q.lam == 0.0 ? T(0) : (T)(q.lam * q.C[(int64_t)k * R * R + e]);
-        double yv[16];
+        double yv[NP];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) yv[u] = 0.0;
+        for (int u = 0; u < NP; ++u) yv[u] = 0.0;
         for (int jc = 0; jc < J; jc += QZ_JC) {
             const int j = jc + jj;
             __syncthreads();
@@ -262,9 +274,9 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI
                 Ys[r * (QZ_JC + 1) + c] = (q.lam != 0.0 && jc + c < J) ? Yk[(int64_t)r * J + jc + c] : T(0);
             }
             __syncthreads();
-            T acc[16];
+            T acc[NQ];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
+            for (int u = 0; u < NQ; ++u) {
                 const int r = rg + 4 * u;
                 T a = T(0);
                 if (u < nq && r < R)
@@ -284,7 +296,7 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI
                             for (int i = 0; i < nr; ++i) {
                                 const T x = (T)X[(c0 + i) * J + j];
 #pragma unroll
-                                for (int u = 0; u < 16; ++u) {
+                                for (int u = 0; u < NQ; ++u) {
                                     const int r = rg + 4 * u;
                                     if (u < nq && r < R) acc[u] += Qs[i * R + r] * x;
                                 }
@@ -295,7 +307,7 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI
             }
             __syncthreads();
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
+            for (int u = 0; u < NQ; ++u) {
                 const int r = rg + 4 * u;
                 if (u < nq && r < R) {
                     if (j < J) Yk[(int64_t)r * J + j] = acc[u];
@@ -305,7 +317,7 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI
             __syncthreads();
             // YV partial over this column chunk: thread owns pairs (r, s)
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
+            for (int u = 0; u < NP; ++u) {
                 const int e = tid + u * QZ_THREADS;
                 if (e < R * R) {
                     const int r = e / R, s2 = e % R;
@@ -317,7 +329,7 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI
         }
         const double *wk = q.W + (int64_t)k * R;
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
+        for (int u = 0; u < NP; ++u) {
             const int e = tid + u * QZ_THREADS;
             if (e < R * R) {
                 const int r = e / R, s2 = e % R;
@@ -327,7 +339,7 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI
         }
     }
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
+    for (int u = 0; u < NP; ++u) {
         const int e = tid + u * QZ_THREADS;
         if (e < R * R) {
             MHpart[(int64_t)blockIdx.x * R * R + e] = mh[u];
@@ -376,38 +388,42 @@ static __global__ void k_q_h(const double *__restrict__ MHpart, const double *__
     for (int e = lane; e < R * R; e += 32) PV[e] = O[(e / R) * ld + (e % R)];
 }
 
-// V-MTTKRP: slot_b += Y_kᵀ (H S_k) for the slices of CTA b.  A thread owns
-// one column j (and all s) per pass over j.
-constexpr int QV_THREADS = 256;
+// V-MTTKRP: slot_b[j][s] = Σ_{k in CTA b} w_k[s] Σ_r Y_k[r][j] H[r][s]
+// (= Σ_k Y_kᵀ H S_k).  A thread owns column j of every slice of its CTA and
+// keeps its R accumulators in registers across those slices; H sits in
+// shared memory, and Y_k's column j is read coalesced across the threads.
+constexpr int QV_THREADS = 128;
 
-template <typename T>
+template <typename T, int RM>
 __global__ void __launch_bounds__(QV_THREADS) k_q_vpart(int K_all, QDev q, const T *__restrict__ Y,
                                                         double *__restrict__ slots) {
-    extern __shared__ double vs[];
+    __shared__ T Hs[RM * RM];
     const int R = q.R, J = q.J, tid = threadIdx.x;
-    T *Ms = reinterpret_cast<T *>(vs);        // R × R   H S_k in T
+    for (int e = tid; e < R * R; e += QV_THREADS) Hs[e] = (T)q.H[e];
+    __syncthreads();
     double *sl = slots + (size_t)blockIdx.x * J * R;
-    for (int e = tid; e < J * R; e += QV_THREADS) sl[e] = 0.0;
-    for (int k = blockIdx.x; k < K_all; k += gridDim.x) {
-        __syncthreads();
-        for (int e = tid; e < R * R; e += QV_THREADS)
-            Ms[e] = (T)(q.H[e] * q.W[(int64_t)k * R + (e % R)]);
-        __syncthreads();
-        const T *Yk = Y + (int64_t)k * R * J;
-        for (int j = tid; j < J; j += QV_THREADS) {
-            T acc[64];
+    for (int j = tid; j < J; j += QV_THREADS) {
+        T acc[RM];
 #pragma unroll
-            for (int s = 0; s < 64; ++s) acc[s] = T(0);
+        for (int s2 = 0; s2 < RM; ++s2) acc[s2] = T(0);
+        for (int k = blockIdx.x; k < K_all; k += gridDim.x) {
+            const T *Yk = Y + (int64_t)k * R * J + j;
+            const double *wk = q.W + (int64_t)k * R;
+            T t[RM];
+#pragma unroll
+            for (int s2 = 0; s2 < RM; ++s2) t[s2] = T(0);
             for (int r = 0; r < R; ++r) {
-                const T y = Yk[(int64_t)r * J + j];
+                const T y = Yk[(int64_t)r * J];
 #pragma unroll
-                for (int s = 0; s < 64; ++s)
-                    if (s < R) acc[s] += y * Ms[r * R + s];
+                for (int s2 = 0; s2 < RM; ++s2) t[s2] += y * Hs[r * R + s2];
             }
 #pragma unroll
-            for (int s = 0; s < 64; ++s)
-                if (s < R) sl[(int64_t)j * R + s] += (double)acc[s];
+            for (int s2 = 0; s2 < RM; ++s2)
+                if (s2 < R) acc[s2] += (T)wk[s2] * t[s2];
         }
+#pragma unroll
+        for (int s2 = 0; s2 < RM; ++s2)
+            if (s2 < R) sl[(int64_t)j * R + s2] = (double)acc[s2];
     }
 }
 
@@ -512,32 +528,72 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_w(int K_all, QDev q, const T *
 }
 
 // The squared residual of X_new against Q_new H S_k Vᵀ with the updated
-// factors; one warp per row, per-CTA partials of (Σ residual², Σ ‖x‖²).
+// factors.  Vᵀ (R×Jc, product type) is staged in shared memory one column
+// chunk of Jc (a multiple of 128) at a time; one warp per row forms
+// z = q H S_k and x̂ = z Vᵀ four columns at a time (lane l owns columns
+// 4l + 128m of the chunk), then Σ (x − x̂)² and Σ x².  Per-CTA partials of
+// (Σ residual², Σ ‖x‖²).
+template <typename T>
+__host__ __device__ inline int q_out_chunk(int R, int J) {
+    const int Jp = ((J + 127) / 128) * 128;
+    int cap = (int)((190 * 1024) / ((size_t)R * sizeof(T)) / 128) * 128;
+    if (cap < 128) cap = 128;
+    return Jp < cap ? Jp : cap;
+}
+template <typename T>
+__host__ __device__ inline size_t q_out_smem(int R, int J) {
+    return ((size_t)R * q_out_chunk<T>(R, J) + 8 * 64) * sizeof(T);
+}
+
 template <typename TI, typename T>
-__global__ void k_q_out(int64_t N, QDev q, const int *__restrict__ row_slice,
-                        const TI *__restrict__ X, const T *__restrict__ Qrows, const T *__restrict__ VT,
-                        double *__restrict__ fitpart) {
-    extern __shared__ double os[];
+__global__ void __launch_bounds__(256) k_q_out(int64_t N, QDev q, const int *__restrict__ row_slice,
+                                               const TI *__restrict__ X, const T *__restrict__ Qrows,
+                                               const T *__restrict__ VT, double *__restrict__ fitpart) {
+    extern __shared__ unsigned char qo_raw[];
     const int R = q.R, J = q.J;
+    const int Jc = q_out_chunk<T>(R, J);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double *z = os + (size_t)wid * 64;      // per warp: z = q H S
+    T *Vt = reinterpret_cast<T *>(qo_raw);                     // R × Jc, Vt[s][j] = V[j0 + j][s]
+    T *zs = Vt + (size_t)R * Jc + (size_t)wid * 64;            // per warp z
     double res = 0.0, xn = 0.0;
-    for (int64_t row = (int64_t)blockIdx.x * nw + wid; row < N; row += (int64_t)gridDim.x * nw) {
-        const int k = row_slice[row];
-        __syncwarp();
-        for (int s = lane; s < R; s += 32) {
-            double a = 0.0;
-            for (int r = 0; r < R; ++r) a = fma((double)Qrows[row * R + r], q.H[r * R + s], a);
-            z[s] = a * q.W[(int64_t)k * R + s];
+    for (int jb = 0; jb < J; jb += Jc) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < R * Jc; e += blockDim.x) {
+            const int s2 = e / Jc, j = jb + e % Jc;
+            Vt[e] = j < J ? VT[(int64_t)j * R + s2] : T(0);
         }
-        __syncwarp();
-        for (int j = lane; j < J; j += 32) {
-            T xh = T(0);
-            for (int s = 0; s < R; ++s) xh += (T)z[s] * VT[(int64_t)j * R + s];
-            const double x = (double)X[row * J + j];
-            const double d = x - (double)xh;
-            res += d * d;
-            xn += x * x;
+        __syncthreads();
+        for (int64_t row = (int64_t)blockIdx.x * nw + wid; row < N; row += (int64_t)gridDim.x * nw) {
+            const int k = row_slice[row];
+            __syncwarp();
+            for (int s2 = lane; s2 < R; s2 += 32) {
+                T a = T(0);
+                for (int r = 0; r < R; ++r) a += Qrows[row * R + r] * (T)q.H[r * R + s2];
+                zs[s2] = a * (T)q.W[(int64_t)k * R + s2];
+            }
+            __syncwarp();
+            const TI *xr = X + row * J + jb;
+            for (int j0 = 4 * lane; j0 < Jc && jb + j0 < J; j0 += 128) {
+                T h0 = T(0), h1 = T(0), h2 = T(0), h3 = T(0);
+                for (int s2 = 0; s2 < R; ++s2) {
+                    const T z = zs[s2];
+                    const T *v = Vt + (size_t)s2 * Jc + j0;
+                    h0 += z * v[0];
+                    h1 += z * v[1];
+                    h2 += z * v[2];
+                    h3 += z * v[3];
+                }
+                const T hh[4] = {h0, h1, h2, h3};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (jb + j0 + u < J) {
+                        const double x = (double)xr[j0 + u];
+                        const double d = x - (double)hh[u];
+                        res += d * d;
+                        xn += x * x;
+                    }
+                }
+            }
         }
     }
     res = warp_sum(res);

@@ -31,11 +31,11 @@ static QDev make_qdev(dash_model *m, double lam) {
     return q;
 }
 
-// Warps per CTA of k_q_lt: as many per-warp workspaces as fit in 190 KB.
+// Warps per CTA of k_q_lt: as many per-warp workspaces as fit in 212 KB.
 template <class S>
 static int q_lt_warps(int R) {
     const size_t wb = q_lt_warp_bytes<S>(R);
-    return (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(190 * 1024) / wb));
+    return (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(212 * 1024) / wb));
 }
 
 template <class S, typename T>
@@ -81,9 +81,15 @@ static dash_status launch_update_q(dash_model *m, const BatchDev &b, const void 
     const int gy = std::max(1, std::min(b.K_all, m->q_lt_max));
     if (b.K_all > 0) {
         const size_t ysm = q_y_smem<T>(R);
-        CK(cudaFuncSetAttribute(k_q_y<TI, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm));
-        LAUNCH(KK_Q_Y, (k_q_y<TI, T><<<gy, QZ_THREADS, ysm, st>>>(b, q, X, Qrows, Y, (const T *)m->VT,
-                                                                   m->qMH, m->qWWp)));
+        if (R <= 32) {
+            CK(cudaFuncSetAttribute(k_q_y<TI, T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm));
+            LAUNCH(KK_Q_Y, (k_q_y<TI, T, 32><<<gy, QZ_THREADS, ysm, st>>>(b, q, X, Qrows, Y, (const T *)m->VT,
+                                                                           m->qMH, m->qWWp)));
+        } else {
+            CK(cudaFuncSetAttribute(k_q_y<TI, T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm));
+            LAUNCH(KK_Q_Y, (k_q_y<TI, T, 64><<<gy, QZ_THREADS, ysm, st>>>(b, q, X, Qrows, Y, (const T *)m->VT,
+                                                                           m->qMH, m->qWWp)));
+        }
     } else {
         CK(cudaMemsetAsync(m->qMH, 0, (size_t)R * R * 8, st));
         CK(cudaMemsetAsync(m->qWWp, 0, (size_t)R * R * 8, st));
@@ -93,8 +99,10 @@ static dash_status launch_update_q(dash_model *m, const BatchDev &b, const void 
         LAUNCH(KK_Q_H, (k_q_h<<<1, 32, (size_t)(4 * R * ld + R) * 8, st>>>(m->qMH, m->qWWp, gy, q,
                                                                              m->qWW, m->qPV)));
         const int gv = std::max(1, std::min(b.K_all, m->q_vslots));
-        LAUNCH(KK_Q_VPART, (k_q_vpart<T><<<gv, QV_THREADS, (size_t)R * R * sizeof(T), st>>>(
-                               b.K_all, q, Y, m->qslots)));
+        if (R <= 32)
+            LAUNCH(KK_Q_VPART, (k_q_vpart<T, 32><<<gv, QV_THREADS, 0, st>>>(b.K_all, q, Y, m->qslots)));
+        else
+            LAUNCH(KK_Q_VPART, (k_q_vpart<T, 64><<<gv, QV_THREADS, 0, st>>>(b.K_all, q, Y, m->qslots)));
         LAUNCH(KK_Q_V, (k_q_v<T><<<(J + 7) / 8, 256, 0, st>>>(m->qslots, gv, m->qPV, J, R, m->st.V,
                                                                (T *)m->VT)));
         LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(m->st.V, J, R, m->st.Gam));
@@ -109,8 +117,10 @@ static dash_status launch_update_q(dash_model *m, const BatchDev &b, const void 
     int go = 1;
     if (N > 0) {
         go = (int)std::min<int64_t>((N + 7) / 8, m->q_out_max);
-        LAUNCH(KK_Q_OUT, (k_q_out<TI, T><<<go, 256, 8 * 64 * 8, st>>>(N, q, b.row_slice, X, Qrows,
-                                                                     (const T *)m->VT, m->qfit)));
+        const size_t osm = q_out_smem<T>(R, J);
+        CK(cudaFuncSetAttribute(k_q_out<TI, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osm));
+        LAUNCH(KK_Q_OUT, (k_q_out<TI, T><<<go, 256, osm, st>>>(N, q, b.row_slice, X, Qrows,
+                                                              (const T *)m->VT, m->qfit)));
     } else {
         CK(cudaMemsetAsync(m->qfit, 0, 2 * 8, st));
     }

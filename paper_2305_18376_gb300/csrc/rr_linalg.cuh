@@ -54,6 +54,26 @@ template <> struct RT<double> {
     static __device__ __forceinline__ double shfl_xor(double a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
 };
 
+template <> struct RT<float> {
+    static __device__ __forceinline__ bool invertible(float a) { return fabsf(a) > 1e-30f; }
+    static __device__ __forceinline__ float zero() { return 0.f; }
+    static __device__ __forceinline__ float one() { return 1.f; }
+    static __device__ __forceinline__ float from_d(double x) { return (float)x; }
+    static __device__ __forceinline__ float from_f(float x) { return x; }
+    static __device__ __forceinline__ double to_d(float a) { return (double)a; }
+    static __device__ __forceinline__ float hi(float a) { return a; }
+    static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+    static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+    static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+    static __device__ __forceinline__ float mulf(float a, float b) { return a * b; }
+    static __device__ __forceinline__ float fma(float acc, float a, float b) { return fmaf(a, b, acc); }
+    static __device__ __forceinline__ float sqrt_(float a) { return a > 0.f ? sqrtf(a) : 0.f; }
+    // correctly rounded: rotations built from it stay orthogonal to FP32 round-off
+    static __device__ __forceinline__ float rsqrt_(float a) { return a > 0.f ? 1.f / sqrtf(a) : 0.f; }
+    static __device__ __forceinline__ float recip(float a) { return 1.f / a; }
+    static __device__ __forceinline__ float shfl_xor(float a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+};
+
 template <> struct RT<df> {
     // FP32 exponent range: keep the reciprocal (and its Newton step) normal
     static __device__ __forceinline__ bool invertible(df a) { return fabsf(a.hi) > 1e-30f; }
@@ -178,16 +198,17 @@ __device__ int warp_jacobi_rel(S *M, S *E2, int R, int ld, float tol, int max_sw
 
 // Eigen-decomposition of B = LᵀL from its factor: L is R×R upper-triangular
 // (shared).  E: on entry an orthogonal basis estimate (I for a cold start),
-// on exit the eigenbasis; on exit the diagonal of M holds the eigenvalues.
-// G, M, E2: R×ld shared workspaces.  Each pass forms G = L·E, M = GᵀG and
-// runs Jacobi on M, then E ← E·E2.  Passes repeat until the freshly formed M
-// starts within omega_stop of diagonal (max |M_pq|/sqrt(M_pp M_qq)): Jacobi
-// with FP32 angles and zeroed off-diagonals leaves residuals of about
-// 6e-8 times the scaled off-diagonal it started from, so the last pass must
-// start nearly diagonal; a cold start with cond(B) ~ 1e10 needs 3-4 passes,
-// a warm start 1-2.  Returns the passes run.
+// on exit the eigenbasis; mu (length R) receives the eigenvalues.  G and M:
+// R×ld shared workspaces (G also holds the pass's rotations).  Each pass
+// forms G = L·E and M = GᵀG, runs Jacobi on M, then E ← E·(rotations).
+// Passes repeat until the freshly formed M starts within omega_stop of
+// diagonal (max |M_pq|/sqrt(M_pp M_qq)): Jacobi with FP32 angles and zeroed
+// off-diagonals leaves residuals of about 6e-8 times the scaled off-diagonal
+// it started from, so the last pass must start nearly diagonal; a cold start
+// with cond(B) ~ 1e10 needs 3-4 passes, a warm start 1-2.  Returns the
+// passes run.
 template <class S>
-__device__ int warp_eig_factor(const S *L, S *E, S *G, S *M, S *E2, int R, int ld, int max_passes,
+__device__ int warp_eig_factor(const S *L, S *E, S *G, S *M, S *mu, int R, int ld, int max_passes,
                                float tol, int max_sweeps, float omega_stop) {
     using O = RT<S>;
     const int lane = threadIdx.x & 31;
@@ -223,37 +244,91 @@ __device__ int warp_eig_factor(const S *L, S *E, S *G, S *M, S *E2, int R, int l
         }
 #pragma unroll
         for (int m = 16; m > 0; m >>= 1) om = fmaxf(om, __shfl_xor_sync(0xffffffffu, om, m));
-        warp_jacobi_rel(M, E2, R, ld, tol, max_sweeps);
-        // E ← E·E2 (through G)
+        warp_jacobi_rel(M, G, R, ld, tol, max_sweeps);          // rotations → G
+        for (int i = lane; i < R; i += 32) mu[i] = M[i * ld + i];
+        __syncwarp();
+        // E ← E·G (through M)
         for (int c = lane; c < R; c += 32)
             for (int r = 0; r < R; ++r) {
                 S a = O::zero();
-                for (int k = 0; k < R; ++k) a = O::fma(a, E[r * ld + k], E2[k * ld + c]);
-                G[r * ld + c] = a;
+                for (int k = 0; k < R; ++k) a = O::fma(a, E[r * ld + k], G[k * ld + c]);
+                M[r * ld + c] = a;
             }
         __syncwarp();
-        for (int i = lane; i < R * R; i += 32) E[(i / R) * ld + (i % R)] = G[(i / R) * ld + (i % R)];
+        for (int i = lane; i < R * R; i += 32) E[(i / R) * ld + (i % R)] = M[(i / R) * ld + (i % R)];
         __syncwarp();
         if (om <= omega_stop) break;
     }
     return pass;
 }
 
-// Spectral weights of B^{-1/2} and B^{1/2} from the eigenvalues μ_i (the
-// diagonal of M after warp_eig_factor): finv_i = μ_i^{-1/2} and
-// fsq_i = μ_i^{1/2} for μ_i > rtol·max μ, both 0 otherwise (the
-// pseudo-inverse cut; B^{1/2}·B^{-1/2} is then the projector on the kept
-// eigenvectors).
+template <class A, class B> __device__ __forceinline__ B rt_cast(A a) {
+    return RT<B>::from_d(RT<A>::to_d(a));
+}
+template <> __device__ __forceinline__ float rt_cast<df, float>(df a) { return a.hi + a.lo; }
+template <> __device__ __forceinline__ df rt_cast<float, df>(float a) { return {a, 0.f}; }
+
+// A cheap first pass for warp_eig_factor: the same Gram-Jacobi pass in FP32
+// on FP32 copies of L and E (scratch Lf, Ef, Gf, Mf: R×ld floats; muf: R),
+// then the refined basis back in S, re-orthogonalised to S precision by two
+// Newton–Schulz steps E ← E (3I − EᵀE)/2 (the thousands of FP32 rotations
+// leave EᵀE − I near 1e-5; each step squares that).  Gs, Ms: R×ld S
+// scratch.  The S passes that follow then start close to diagonal.
 template <class S>
-__device__ void warp_sqrt_weights(const S *M, int R, int ld, double rtol, S *finv, S *fsq) {
+__device__ void warp_eig_prepass_f32(const S *L, S *E, float *Lf, float *Ef, float *Gf, float *Mf,
+                                     float *muf, S *Gs, S *Ms, int R, int ld, int max_sweeps) {
+    using O = RT<S>;
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < R * R; i += 32) {
+        const int r = i / R, c = i % R;
+        Lf[r * ld + c] = rt_cast<S, float>(L[r * ld + c]);
+        Ef[r * ld + c] = rt_cast<S, float>(E[r * ld + c]);
+    }
+    __syncwarp();
+    warp_eig_factor<float>(Lf, Ef, Gf, Mf, muf, R, ld, 1, 1e-6f, max_sweeps, 0.f);
+    for (int i = lane; i < R * R; i += 32) {
+        const int r = i / R, c = i % R;
+        E[r * ld + c] = rt_cast<float, S>(Ef[r * ld + c]);
+    }
+    __syncwarp();
+    // twice: P = EᵀE (→ Gs), then E·(3I − P)/2 (→ Ms), copied back to E
+    for (int step = 0; step < 2; ++step) {
+    for (int b = lane; b < R; b += 32)
+        for (int a = 0; a < R; ++a) {
+            S acc = O::zero();
+            for (int i = 0; i < R; ++i) acc = O::fma(acc, E[i * ld + a], E[i * ld + b]);
+            Gs[a * ld + b] = acc;
+        }
+    __syncwarp();
+    for (int c = lane; c < R; c += 32)
+        for (int r = 0; r < R; ++r) {
+            S acc = O::zero();
+            for (int k = 0; k < R; ++k) {
+                const S pk = (k == c) ? O::sub(O::from_f(3.f), Gs[k * ld + c]) : O::sub(O::zero(), Gs[k * ld + c]);
+                acc = O::fma(acc, E[r * ld + k], pk);
+            }
+            Ms[r * ld + c] = O::mulf(acc, 0.5f);
+        }
+    __syncwarp();
+    for (int i = lane; i < R * R; i += 32) E[(i / R) * ld + (i % R)] = Ms[(i / R) * ld + (i % R)];
+    __syncwarp();
+    }
+}
+
+// Spectral weights of B^{-1/2} and B^{1/2} from the eigenvalues mu:
+// finv_i = μ_i^{-1/2} and fsq_i = μ_i^{1/2} for μ_i > rtol·max μ, both 0
+// otherwise (the pseudo-inverse cut; B^{1/2}·B^{-1/2} is then the projector
+// on the kept eigenvectors).
+template <class S>
+__device__ void warp_sqrt_weights(const S *mu, int R, double rtol, S *finv, S *fsq) {
     using O = RT<S>;
     const int lane = threadIdx.x & 31;
     double mx = 0.0;
-    for (int i = lane; i < R; i += 32) mx = fmax(mx, O::to_d(M[i * ld + i]));
+    for (int i = lane; i < R; i += 32) mx = fmax(mx, O::to_d(mu[i]));
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, m));
     for (int i = lane; i < R; i += 32) {
-        const S v = M[i * ld + i];
+        const S v = mu[i];
         const bool keep = mx > 0.0 && O::to_d(v) > rtol * mx;
         finv[i] = keep ? O::rsqrt_(v) : O::zero();
         fsq[i] = keep ? O::sqrt_(v) : O::zero();
