@@ -62,7 +62,7 @@ static void prof_collect(dash_model *m) {
     }
     m->prof.pending.clear();
     if (m->prof.d_phase) {
-        unsigned long long c[7] = {0, 0, 0, 0, 0, 0, 0};
+        unsigned long long c[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         if (cudaMemcpy(c, m->prof.d_phase, sizeof c, cudaMemcpyDeviceToHost) == cudaSuccess) {
             // phases: average per SM; epilogue sub-phases: average per warp;
             // milliseconds at the device clock
@@ -70,6 +70,12 @@ static void prof_collect(dash_model *m) {
                 const double per = i < 3 ? m->prof.n_sm : (double)m->prof.n_sm * FU_WARPS;
                 m->prof.ms[KK_PH_A + i] += (double)c[i] / per / m->prof.clock_khz;
                 if (c[i]) m->prof.launches[KK_PH_A + i] += 1;
+            }
+            // k_q_lt sub-phases: summed over its warps, reported per warp
+            for (int i = 0; i < 4; ++i) {
+                const double per = m->prof.q_lt_warps > 0 ? m->prof.q_lt_warps : 1.0;
+                m->prof.ms[KK_QLT_QR + i] += (double)c[7 + i] / per / m->prof.clock_khz;
+                if (c[7 + i]) m->prof.launches[KK_QLT_QR + i] += 1;
             }
             cudaMemset(m->prof.d_phase, 0, sizeof c);
         }
@@ -85,10 +91,10 @@ extern "C" dash_status dash_profile_enable(dash_model *m, int32_t on) {
     if (!m) return DASH_EINVAL;
     if (!m->prof.d_phase) {
         void *p = nullptr;
-        if (cudaMalloc(&p, 7 * sizeof(unsigned long long)) == cudaSuccess) {
+        if (cudaMalloc(&p, 11 * sizeof(unsigned long long)) == cudaSuccess) {
             m->prof.d_phase = (unsigned long long *)p;
             m->allocs.push_back(p);
-            cudaMemset(p, 0, 7 * sizeof(unsigned long long));
+            cudaMemset(p, 0, 11 * sizeof(unsigned long long));
             int dev = 0, khz = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);

@@ -18,7 +18,7 @@ enum KernelKind {
     KK_BIG_B, KK_BIG_C, KK_QV, KK_PH_A, KK_PH_EPI, KK_PH_B, KK_EPI_U, KK_EPI_DD, KK_EPI_FIN,
     KK_EPI_SCALE,
     KK_Q_BEGIN, KK_Q_AROWS, KK_Q_Y, KK_Q_LT, KK_Q_H, KK_Q_VPART, KK_Q_V, KK_Q_PW, KK_Q_W,
-    KK_Q_OUT, KK_Q_FIT, KK_COUNT
+    KK_Q_OUT, KK_Q_FIT, KK_QLT_QR, KK_QLT_PRE, KK_QLT_PASS, KK_QLT_TAIL, KK_COUNT
 };
 static const char *const kKernelNames[KK_COUNT] = {
     "k_begin_new", "k_rowmap", "k_xv", "k_slices", "k_f", "k_f_reduce", "k_g_reduce",
@@ -28,7 +28,8 @@ static const char *const kKernelNames[KK_COUNT] = {
     "k_rows_fused.epilogue.u_rows", "k_rows_fused.epilogue.gram", "k_rows_fused.epilogue.finish",
     "k_rows_fused.epilogue.scale",
     "k_q_begin_new", "k_q_arows", "k_q_y", "k_q_lt", "k_q_h", "k_q_vpart", "k_q_v", "k_q_pw",
-    "k_q_w", "k_q_out", "k_q_fit"};
+    "k_q_w", "k_q_out", "k_q_fit", "k_q_lt.qr", "k_q_lt.fp32_pass", "k_q_lt.passes",
+    "k_q_lt.tail"};
 
 struct Profiler {
     bool on = false;
@@ -41,6 +42,7 @@ struct Profiler {
     unsigned long long *d_phase = nullptr;   // SM cycles per fused-kernel phase
     double clock_khz = 1.0;
     int n_sm = 1;
+    double q_lt_warps = 0.0;    // warps of the last profiled k_q_lt launch
 };
 
 constexpr int kFBlocksMax = 1024;       // max row chunks of the F-partial kernel

@@ -59,6 +59,7 @@ struct QDev {
     double *C;      // Kmax×R×R, carry T_k,new B_k,old^{1/2} of this update (FP64)
     double *Gam;    // R×R  VᵀV (current V)
     int *err;       // [2]: slices whose factor or eigenvalues came out non-finite
+    unsigned long long *phase;   // optional [4]: k_q_lt cycles in QR, FP32 pass, passes, tail
 };
 
 __host__ __device__ inline int q_ld(int R) { return R + 1; }
@@ -136,7 +137,9 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
     S *Lg = reinterpret_cast<S *>(q.L);
     S *Eg = reinterpret_cast<S *>(q.E);
     S *Bg = reinterpret_cast<S *>(q.Bh);
+    long long pc[4] = {0, 0, 0, 0};
     for (int k = blockIdx.x * nw + wid; k < b.K_all; k += gridDim.x * nw) {
+        long long c0k = q.phase ? clock64() : 0;
         const int t = mode == 0 ? b.tslot[k] : -1;
         __syncwarp();
         for (int i = lane; i < R * R; i += 32) {
@@ -161,15 +164,18 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
         }
         if (mode == 0)
             for (int i = lane; i < R * R; i += 32) Lg[k * RR + i] = Lw[(i / R) * ld + (i % R)];
+        if (q.phase) { const long long c1 = clock64(); pc[0] += c1 - c0k; c0k = c1; }
         {
             // FP32 pre-pass (float scratch in G and M), then the working-type passes
             float *f0 = reinterpret_cast<float *>(Gw);
             const int fs = R * ld;
             if (!std::is_same<S, float>::value)
                 warp_eig_prepass_f32<S>(Lw, Ew, f0, f0 + fs, f0 + 2 * fs, f0 + 3 * fs,
-                                        reinterpret_cast<float *>(mu), Gw, Mw, R, ld, 12);
+                                        reinterpret_cast<float *>(mu), Gw, Mw, R, ld, 6);
         }
+        if (q.phase) { const long long c1 = clock64(); pc[1] += c1 - c0k; c0k = c1; }
         warp_eig_factor(Lw, Ew, Gw, Mw, mu, R, ld, passes, jac_tol, 40, 1e-7f);
+        if (q.phase) { const long long c1 = clock64(); pc[2] += c1 - c0k; c0k = c1; }
         {
             // a non-finite factor or eigenvalue must not pass silently
             bool ok = true;
@@ -217,7 +223,10 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
             }
         }
         __syncwarp();
+        if (q.phase) pc[3] += clock64() - c0k;
     }
+    if (q.phase && lane == 0)
+        for (int i = 0; i < 4; ++i) atomicAdd(q.phase + i, (unsigned long long)pc[i]);
 }
 
 // Q2: Y_k ← λ C_k Y_k + Q_k,newᵀ X_new for every slice (λ C_k Y_k alone for

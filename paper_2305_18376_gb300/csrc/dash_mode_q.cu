@@ -28,6 +28,7 @@ static QDev make_qdev(dash_model *m, double lam) {
     q.C = m->qC;
     q.Gam = m->st.Gam;
     q.err = m->d_err;
+    q.phase = m->prof.on && m->prof.d_phase ? m->prof.d_phase + 7 : nullptr;
     return q;
 }
 
@@ -47,6 +48,7 @@ static dash_status launch_lt(dash_model *m, const BatchDev &b, const QDev &q, co
     const int grid = std::max(1, std::min((b.K_all + nw - 1) / nw, 4 * m->n_sm));
     const float jtol = std::is_same<S, double>::value ? 1e-15f : 1e-13f;
     CK(cudaFuncSetAttribute(k_q_lt<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    m->prof.q_lt_warps = (double)grid * nw;
     LAUNCH(KK_Q_LT, (k_q_lt<S, T><<<grid, 32 * nw, smem, m->stream>>>(b, q, A, Qrows, mode, 6, jtol)));
     return DASH_OK;
 }

@@ -68,8 +68,13 @@ template <> struct RT<float> {
     static __device__ __forceinline__ float mulf(float a, float b) { return a * b; }
     static __device__ __forceinline__ float fma(float acc, float a, float b) { return fmaf(a, b, acc); }
     static __device__ __forceinline__ float sqrt_(float a) { return a > 0.f ? sqrtf(a) : 0.f; }
-    // correctly rounded: rotations built from it stay orthogonal to FP32 round-off
-    static __device__ __forceinline__ float rsqrt_(float a) { return a > 0.f ? 1.f / sqrtf(a) : 0.f; }
+    // rsqrtf refined by one Newton step (about 1 ulp): rotations built from
+    // it stay orthogonal to FP32 round-off
+    static __device__ __forceinline__ float rsqrt_(float a) {
+        if (!(a > 0.f)) return 0.f;
+        const float y = rsqrtf(a);
+        return y * fmaf(-0.5f * a * y, y, 1.5f);
+    }
     static __device__ __forceinline__ float recip(float a) { return 1.f / a; }
     static __device__ __forceinline__ float shfl_xor(float a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
 };
@@ -160,10 +165,15 @@ __device__ int warp_jacobi_rel(S *M, S *E2, int R, int ld, float tol, int max_sw
                 const float fpq = O::hi(mpq), fpp = O::hi(mpp), fqq = O::hi(mqq);
                 __syncwarp();
                 if (!(fabsf(fpq) > tol * sqrtf(fabsf(fpp)) * sqrtf(fabsf(fqq)))) continue;
-                const float th = (fqq - fpp) / (2.0f * fpq);
+                // the angle only has to be close: approximate reciprocal and
+                // square root (the pair (c, s) below is exactly orthogonal)
+                const float th = (fqq - fpp) * __frcp_rn(2.0f * fpq);
                 float t;
-                if (fabsf(th) > 1e18f) t = 0.5f / th;
-                else t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+                if (fabsf(th) > 1e18f) t = 0.5f * __frcp_rn(th);
+                else {
+                    const float h = fmaf(th, th, 1.0f);
+                    t = copysignf(__frcp_rn(fabsf(th) + h * rsqrtf(h)), th);
+                }
                 const S tt = O::from_f(t);
                 const S c = O::rsqrt_(O::fma(O::one(), tt, tt));
                 const S s = O::mulf(c, t);
