@@ -179,14 +179,20 @@ def src_hash():
 
 
 def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken from the current kernel sources (else None)."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel's sources are unchanged since the capture (else None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     e = d.get(kernel)
-    if not e or e.get("src_sha") != src_hash():
+    if not e:
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2305_18376_gb300", "csrc")
+    for fn in e.get("src_files", []):
+        h.update(open(os.path.join(csrc, fn), "rb").read())
+    if h.hexdigest()[:16] != e.get("src_sha"):
         return None
     return e.get("dram_bytes_per_launch_full")
 
