@@ -214,6 +214,22 @@ dash_status dash_new_rows(const dash_model *m, double *out, int64_t *n_rows);
  * ||X_new||²_F. */
 dash_status dash_fitness(const dash_model *m, double *fit_batch, double *x_norm2);
 
+/* Reconstruction errors of the last update's new data with the updated
+ * factors, from a second read of its rows (the paper's slice-level and
+ * tensor-level reconstruction errors, Definitions 1-2, also its local error
+ * of §4.1):
+ *   se_k = Σ |X_k,new − X̂_k,new| / (I_k,new·J),  te = mean of se_k over the
+ *   slices that received rows (ascending slice order),
+ * with X̂_k,new = U_k,new S_k Vᵀ (mode P) or Q_k,new H S_k Vᵀ (mode Q), plus the
+ * batch fitness of dash_fitness() computed from the direct residual.  Any
+ * output may be NULL; se, if given, has se_len >= dash_num_slices() entries
+ * and receives NaN for slices without new rows.  The rows are read where the
+ * update read them: call it before staging anything new (DASH_ESTATE after
+ * an append) and, for dash_update_device(), while the caller's X is still
+ * valid.  Synchronises the stream. */
+dash_status dash_local_errors(dash_model *m, double *te, double *fit_direct, double *se,
+                              int64_t se_len);
+
 /* Wait for all work issued on the model's stream. */
 dash_status dash_sync(dash_model *m);
 

@@ -72,6 +72,7 @@ SIGNATURES = [
     ("dash_profile_kinds", I32, []),
     ("dash_profile_get", C.c_int, [P, I32, C.POINTER(C.c_char_p), PI64, PD]),
     ("dash_last_plan", C.c_int, [P, PI64, PI64, PI64, PI64, PI64]),
+    ("dash_local_errors", C.c_int, [P, PD, PD, PD, I64]),
     ("dash_f_increment_noalloc", C.c_int, [P, P, I64, I32, I32, P, P, I64, P, P, P]),
     ("dash_counters", C.c_int, [P, PI64, PI64]),
 ]
@@ -220,6 +221,14 @@ class DashModel:
         self._ck(self._lib.dash_last_plan(self._h, *(C.byref(x) for x in v)))
         return dict(zip(("tile_rows", "tile_slices", "tiles", "chunk_rows", "general_rows"),
                         (x.value for x in v)))
+
+    def local_errors(self):
+        """(te, direct batch fitness, se per slice (NaN without new rows)) of
+        the last update: Definitions 1-2 from a second read of its rows."""
+        te, fd = C.c_double(), C.c_double()
+        se = np.empty(self.K)
+        self._ck(self._lib.dash_local_errors(self._h, C.byref(te), C.byref(fd), _pd(se), se.size))
+        return te.value, fd.value, se
 
     def last_update_ms(self) -> float:
         ms = C.c_float()

@@ -390,6 +390,8 @@ extern "C" void dash_destroy(dash_model *m) {
     if (!m) return;
     cudaStreamSynchronize(m->stream);
     prof_collect(m);
+    if (m->err_rows) cudaFree(m->err_rows);
+    if (m->err_segs) cudaFree(m->err_segs);
     for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
     free_all(m);
     cudaEventDestroy(m->ev0);
@@ -667,6 +669,83 @@ extern "C" dash_status dash_last_plan(const dash_model *mc, int64_t *tile_rows,
     return DASH_OK;
 }
 
+// ---------------------------------------------------------------------------
+// reconstruction errors of the last update (Definitions 1-2)
+// ---------------------------------------------------------------------------
+template <typename TI, typename T>
+static dash_status launch_resid(dash_model *m, int64_t N, int n_seg) {
+    const int J = m->cfg.J, R = m->cfg.R;
+    const size_t smem = err_smem<T>(R, J);
+    CK(cudaFuncSetAttribute(k_resid_rows<TI, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (int)std::min<int64_t>((N + 7) / 8, 4 * (int64_t)m->n_sm);
+    LAUNCH(KK_Q_OUT, (k_resid_rows<TI, T><<<grid, 256, smem, m->stream>>>(
+                         N, J, R, n_seg, m->d_seg_row, m->d_seg_slice, (const TI *)m->last_X,
+                         (const T *)m->U, m->cfg.mode == DASH_MODE_Q ? m->qH : nullptr, m->st.W,
+                         (const T *)m->VT, m->err_rows)));
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_local_errors(dash_model *m, double *te, double *fit_direct, double *se,
+                                         int64_t se_len) {
+    if (!m) return DASH_EINVAL;
+    if (!m->has_last) return fail(m, DASH_ESTATE, "no update has run");
+    if (!m->last_X && m->last_N > 0)
+        return fail(m, DASH_ESTATE, "the last batch's rows are gone (rows were staged since)");
+    if (se && se_len < m->K) return fail(m, DASH_EINVAL, "se needs %lld entries", (long long)m->K);
+    const int64_t N = m->last_N;
+    const int n_seg = (int)m->last_ids.size();
+    const int J = m->cfg.J;
+    if (N > 0) {
+        if (m->err_rows_cap < N) {
+            if (m->err_rows) cudaFree(m->err_rows);
+            m->err_rows = nullptr;
+            CK(cudaMalloc(&m->err_rows, (size_t)N * 3 * 8));
+            m->err_rows_cap = N;
+        }
+        if (m->err_segs_cap < n_seg) {
+            if (m->err_segs) cudaFree(m->err_segs);
+            m->err_segs = nullptr;
+            CK(cudaMalloc(&m->err_segs, (size_t)n_seg * 3 * 8));
+            m->err_segs_cap = n_seg;
+        }
+        const bool f64in = m->cfg.input_dtype == DASH_F64;
+        dash_status s;
+        if (m->tsize == 8) s = f64in ? launch_resid<double, double>(m, N, n_seg) : launch_resid<float, double>(m, N, n_seg);
+        else s = f64in ? launch_resid<double, float>(m, N, n_seg) : launch_resid<float, float>(m, N, n_seg);
+        if (s) return s;
+        LAUNCH(KK_Q_FIT, (k_resid_segs<<<(n_seg + 127) / 128, 128, 0, m->stream>>>(n_seg, m->d_seg_row,
+                                                                                 m->err_rows, m->err_segs)));
+    }
+    std::vector<double> seg((size_t)n_seg * 3, 0.0);
+    if (N > 0) CK(cudaMemcpyAsync(seg.data(), m->err_segs, seg.size() * 8, cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    // group segments by slice, in segment order; te averages over the slices
+    // with new rows, in ascending slice order
+    std::vector<double> abs_k(m->K, 0.0);
+    std::vector<int64_t> n_k(m->K, 0);
+    double sq = 0.0, xn = 0.0;
+    for (int s = 0; s < n_seg; ++s) {
+        const int64_t k = m->last_ids[s];
+        abs_k[k] += seg[(size_t)s * 3];
+        n_k[k] += m->last_rp[s + 1] - m->last_rp[s];
+        sq += seg[(size_t)s * 3 + 1];
+        xn += seg[(size_t)s * 3 + 2];
+    }
+    double tsum = 0.0;
+    int64_t tcount = 0;
+    for (int64_t k = 0; k < m->K; ++k) {
+        const double v = n_k[k] > 0 ? abs_k[k] / ((double)n_k[k] * J) : NAN;
+        if (n_k[k] > 0) {
+            tsum += v;
+            ++tcount;
+        }
+        if (se) se[k] = v;
+    }
+    if (te) *te = tcount ? tsum / (double)tcount : 0.0;
+    if (fit_direct) *fit_direct = xn > 0.0 ? 1.0 - std::sqrt(sq / xn) : 1.0;
+    return DASH_OK;
+}
+
 extern "C" dash_status dash_last_update_ms(const dash_model *mc, float *ms) {
     dash_model *m = const_cast<dash_model *>(mc);
     if (!m || !ms) return DASH_EINVAL;
@@ -681,6 +760,7 @@ extern "C" dash_status dash_last_update_ms(const dash_model *mc, float *ms) {
 // ---------------------------------------------------------------------------
 static dash_status stage_rows(dash_model *m, int64_t k, const void *X, int64_t I, int64_t ld,
                               int32_t where) {
+    m->last_X = nullptr;                  // the staging buffer is about to be reused
     const int64_t J = m->cfg.J;
     const size_t ie = (m->cfg.input_dtype == DASH_F64) ? 8 : 4;
     if (I < 0) return fail(m, DASH_EINVAL, "negative row count");
@@ -761,6 +841,7 @@ static dash_status check_csr(dash_model *m, int64_t n_seg, const int64_t *ids, c
 extern "C" dash_status dash_append_batch(dash_model *m, int64_t n_seg, const int64_t *slice_ids,
                                          const int64_t *row_ptr, const void *X, int32_t where) {
     if (!m) return DASH_EINVAL;
+    m->last_X = nullptr;                  // the staging buffer is about to be reused
     int64_t n_new = 0;
     dash_status s = check_csr(m, n_seg, slice_ids, row_ptr, m->K + m->st_new, &n_new);
     if (s) return s;
@@ -1001,6 +1082,9 @@ static dash_status update_common(dash_model *m, int64_t n_seg, const int64_t *id
     m->K += n_new;
     m->last_N = b.N;
     m->has_last = true;
+    m->last_X = X;
+    m->last_ids.assign(ids, ids + n_seg);
+    m->last_rp.assign(rp, rp + n_seg + 1);
     return DASH_OK;
 }
 
@@ -1074,6 +1158,9 @@ static dash_status fit_common(dash_model *m, int64_t n_seg, const int64_t *ids,
     m->K = n_new;
     m->last_N = b.N;
     m->has_last = true;
+    m->last_X = X;
+    m->last_ids.assign(ids, ids + n_seg);
+    m->last_rp.assign(rp, rp + n_seg + 1);
     return DASH_OK;
 }
 

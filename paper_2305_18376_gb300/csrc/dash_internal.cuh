@@ -9,6 +9,7 @@
 #include "dash_kernels_fused.cuh"
 #include "dash_kernels_p.cuh"
 #include "dash_kernels_q.cuh"
+#include "dash_kernels_err.cuh"
 
 namespace dash {
 // kernel kinds for the per-kernel profiler
@@ -128,6 +129,13 @@ struct dash_model {
     double *qH = nullptr, *qWW = nullptr, *qPV = nullptr, *qPW = nullptr;
     double *qMH = nullptr, *qWWp = nullptr, *qslots = nullptr, *qfit = nullptr;
     int q_lt_max = 0, q_vslots = 0, q_out_max = 0;
+
+    // the last update's batch, for dash_local_errors (valid until the next
+    // append or update): X, its segments on the host, and error scratch
+    const void *last_X = nullptr;
+    std::vector<int64_t> last_ids, last_rp;
+    double *err_rows = nullptr, *err_segs = nullptr;
+    int64_t err_rows_cap = 0, err_segs_cap = 0;
 
     // plan of the last batch (dash_last_plan)
     int64_t plan_tile_rows = 0, plan_tile_slices = 0, plan_tiles = 0, plan_chunk_rows = 0,

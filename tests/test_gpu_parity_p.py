@@ -249,3 +249,41 @@ def test_capacity_and_argument_errors_leave_state_unchanged():
     m.append_slices([np.ones((3, 6), np.float32)])
     m.update()
     assert m.K == 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f16x3"])
+def test_local_errors_match_definitions(prec):
+    """Definitions 1-2 on the last update's rows: se per slice, te, and the
+    direct batch fitness, against the oracle's slice_error / tensor_error /
+    fitness with the same updated factors."""
+    _, tdt = PREC_DTYPE[prec]
+    w = tiny(K0=7, J=10, R=3, steps=2, sigma=0.05, lam=0.9, new=2)
+    s = PlantedStream(w)
+    rng = np.random.default_rng(4)
+    b0 = s.batch(0)
+    X0 = [x for _, x in segs_np(b0, tdt)]
+    U, W, V = O.static_als_p(X0, rng.random((w.J, w.R)), np.ones((len(X0), w.R)), 2)
+    st = O.init_helpers_p(X0, U, W, V)
+    m = _model(w.J, w.R, w.lam, prec, max_slices=64, max_rows=1024, max_segments=256)
+    m.set_state_p(st.V, st.W, st.c, st.D, st.F, st.G)
+    for t in (1, 2):
+        b = s.batch(t)
+        X = O._group(segs_np(b, tdt), st.K, b.n_new, w.J)
+        st, Uo = O.dash_update_p(st, list(X.items()), b.n_new, w.lam)
+        m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.to(tdt).cuda())
+        te, fd, se = m.local_errors()
+        ks = sorted(X)
+        Xh = {k: O.reconstruct_p(Uo[k], st.W[k], st.V) for k in ks}
+        se_o = {k: O.slice_error(X[k], Xh[k]) for k in ks if X[k].shape[0] > 0}
+        te_o = O.tensor_error([X[k] for k in se_o], [Xh[k] for k in se_o])
+        fit_o = O.fitness([X[k] for k in ks], [Xh[k] for k in ks])
+        tol = TOL[prec] * 10
+        assert abs(te - te_o) <= tol * max(te_o, 1e-30), (te, te_o)
+        assert abs(fd - fit_o) <= FIT_TOL[prec], (fd, fit_o)
+        for k, v in se_o.items():
+            assert abs(se[k] - v) <= tol * max(v, 1e-30), (k, se[k], v)
+        untouched = [k for k in range(st.K) if k not in se_o]
+        assert all(np.isnan(se[k]) for k in untouched)
+        # the direct fitness agrees with the Gram-form fitness of the update
+        assert abs(m.fitness()[0] - fd) <= (1e-9 if prec == "fp64" else 1e-3)
+    m.close()

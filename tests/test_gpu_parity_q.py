@@ -259,3 +259,34 @@ def test_set_state_q_rejects_lower_entries():
     with pytest.raises(DashError):
         m.set_state_q(np.ones((5, 2)), np.eye(2), np.ones((1, 2)), L, np.zeros((1, 2, 5)))
     m.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_local_errors_q(prec):
+    """Definitions 1-2 in mode Q (X̂ = Q_new H S_k Vᵀ with the updated
+    factors), and the direct fitness equals dash_fitness()."""
+    _, tdt = PREC_DTYPE[prec]
+    w = tiny(K0=6, J=9, R=3, steps=1, sigma=0.05, lam=0.9)
+    s = PlantedStream(w)
+    rng = np.random.default_rng(1)
+    V0 = rng.random((w.J, w.R))
+    b0 = s.batch(0)
+    X0 = [x for _, x in segs_np(b0, tdt)]
+    st = _oracle_fit(X0, V0, w.R, 2)
+    m = _model(w.J, w.R, w.lam, prec, max_slices=64, max_rows=1024, max_segments=256)
+    m.set_state_q(st.V, st.H, st.W, st.L, oracle_y(st))
+    b = s.batch(1)
+    X = O._group(segs_np(b, tdt), st.K, b.n_new, w.J)
+    st, Qo, _ = O.dash_update_q(st, list(X.items()), b.n_new, w.lam)
+    m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.to(tdt).cuda())
+    te, fd, se = m.local_errors()
+    ks = sorted(X)
+    Xh = {k: O.reconstruct_q(Qo[k], st.H, st.W[k], st.V) for k in ks}
+    se_o = {k: O.slice_error(X[k], Xh[k]) for k in ks if X[k].shape[0] > 0}
+    te_o = O.tensor_error([X[k] for k in se_o], [Xh[k] for k in se_o])
+    tol = 1e-8 if prec == "fp64" else 1e-4
+    assert abs(te - te_o) <= tol * te_o, (te, te_o)
+    for k, v in se_o.items():
+        assert abs(se[k] - v) <= tol * v, (k, se[k], v)
+    assert abs(m.fitness()[0] - fd) <= 1e-12
+    m.close()
