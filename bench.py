@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c4")
     ap.add_argument("--precision", default="f16x3", choices=["fp32", "f16x3"])
+    ap.add_argument("--row-path", default="auto", choices=["auto", "fused", "split"],
+                    help="mode-P row pipeline (f16x3 only)")
     ap.add_argument("--init-iters", type=int, default=3)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -130,6 +132,12 @@ def algorithmic(kernel: str, plan: dict, N: int, K_all: int, J: int, R: int, tsi
     cr, gr = plan.get("chunk_rows", 0), plan.get("general_rows", 0)
     if kernel == "k_rows_fused":         # one read of every tile row, U written
         return tr * J * isize + tr * R * 4 + ts * per_slice, 4 * tr * J * R
+    if kernel == "k_xq_tc":              # X read, P' written (chunked-path rows)
+        return cr * J * isize + cr * R * 4, 2 * cr * J * R
+    if kernel == "k_f_tc":               # X and U read, the row's slice id
+        return cr * J * isize + cr * R * 4 + cr * 4, 2 * cr * J * R
+    if kernel == "k_utilde":             # U read, U ∘ w written (rank padded to 8)
+        return cr * R * 4 + cr * (-(-R // 8) * 8) * 4, cr * R
     if kernel == "k_xv":
         n = cr + gr
         return n * J * isize + n * R * tsize, 2 * n * J * R
@@ -266,7 +274,8 @@ def workload_config(w, a):
                         f"init rows {w.init_rows}, +{w.rows_per_step} rows per slice and "
                         f"+{w.new_slices_per_step} slices {w.new_slice_rows} per update, "
                         f"sigma={w.sigma}, lambda={w.lam}",
-            "mode": "P (Algorithm 1)", "precision": a.precision, "input": "f32",
+            "mode": "P (Algorithm 1)", "precision": a.precision, "row_path": a.row_path,
+            "input": "f32",
             "init": f"{a.init_iters} static ALS iterations on the GPU",
             "l2": "inputs larger than L2 (each step's X_new is GBs)"}
 
@@ -312,6 +321,7 @@ def run_ours(a):
     m = DashModel(w.J, w.R, w.lam, precision=a.precision, input_dtype="f32",
                   max_slices=K_total + 8, max_rows=max_rows, max_segments=max_seg + 8,
                   stream=stream.cuda_stream, max_staged_rows=step_rows)
+    m.set_row_path(a.row_path)
     V0 = np.random.default_rng(7).random((w.J, w.R))
     m.set_factors(V0)
     t0 = time.perf_counter()
@@ -393,6 +403,7 @@ def run_ours(a):
                        max_slices=K_total + 8, max_rows=step_rows, max_segments=max_seg + 8,
                        stream=stream.cuda_stream, max_staged_rows=1)
         mm.set_state_p(**snap)
+        mm.set_row_path(a.row_path)
         ev64 = []
         for b in timed:
             ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

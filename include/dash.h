@@ -265,6 +265,20 @@ dash_status dash_profile_get(const dash_model *m, int32_t i, const char **name,
 dash_status dash_last_plan(const dash_model *m, int64_t *tile_rows, int64_t *tile_slices,
                            int64_t *tiles, int64_t *chunk_rows, int64_t *general_rows);
 
+/* Row pipeline of a mode-P update with FP32 input and DASH_PREC_F16X3
+ * products (the paper has no counterpart: both compute Algorithm 1's P2-P7
+ * on the same rows, in different kernels).
+ *   DASH_ROWS_FUSED  tiles of single-segment slices (at most 256 new rows)
+ *                    in one fused row kernel; other slices in row chunks.
+ *   DASH_ROWS_SPLIT  every slice in row chunks: X·Q_V and the F increment
+ *                    (Eq. 20) as two streaming tensor-core passes over X,
+ *                    the per-slice work (P4, P6, P7) in between.
+ *   DASH_ROWS_AUTO   the library's choice (currently DASH_ROWS_SPLIT).
+ * Takes effect at the next update; other paths ignore it.  DASH_EINVAL for
+ * an unknown value. */
+enum { DASH_ROWS_AUTO = 0, DASH_ROWS_FUSED = 1, DASH_ROWS_SPLIT = 2 };
+dash_status dash_set_row_path(dash_model *m, int32_t path);
+
 /* Allocation-free F increment.  (The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory.)
  *

@@ -72,6 +72,7 @@ SIGNATURES = [
     ("dash_profile_kinds", I32, []),
     ("dash_profile_get", C.c_int, [P, I32, C.POINTER(C.c_char_p), PI64, PD]),
     ("dash_last_plan", C.c_int, [P, PI64, PI64, PI64, PI64, PI64]),
+    ("dash_set_row_path", C.c_int, [P, I32]),
     ("dash_local_errors", C.c_int, [P, PD, PD, PD, I64]),
     ("dash_f_increment_noalloc", C.c_int, [P, P, I64, I32, I32, P, P, I64, P, P, P]),
     ("dash_counters", C.c_int, [P, PI64, PI64]),
@@ -221,6 +222,13 @@ class DashModel:
         self._ck(self._lib.dash_last_plan(self._h, *(C.byref(x) for x in v)))
         return dict(zip(("tile_rows", "tile_slices", "tiles", "chunk_rows", "general_rows"),
                         (x.value for x in v)))
+
+    ROW_PATHS = {"auto": 0, "fused": 1, "split": 2}
+
+    def set_row_path(self, path: str) -> None:
+        """Mode-P row pipeline for the next updates: "fused", "split" or
+        "auto" (the library's choice)."""
+        self._ck(self._lib.dash_set_row_path(self._h, self.ROW_PATHS[path]))
 
     def local_errors(self):
         """(te, direct batch fitness, se per slice (NaN without new rows)) of

@@ -278,6 +278,13 @@ static dash_status init_alloc(dash_model *m) {
     DALLOC(m->Linv, R * R * 8, "R_V^-T");
     DALLOC(m->QV, J * R * 4, "Q_V");
     DALLOC(m->Gdf, R * R * 8, "Gamma (double-float)");
+    DALLOC(m->xq_frag, (size_t)((J + 15) / 16) * ((R + 7) / 8) * 32 * 16, "Q_V fragments");
+    DALLOC(m->xq_bexp, 4, "Q_V fragment scale");
+    if (m->fused_ok) {
+        DALLOC(m->Ut, (size_t)Nm * 8 * ((R + 7) / 8) * 4, "U o w rows");
+        DALLOC(m->xe, (size_t)(Nm + 16) * 4, "row exponents");
+        DALLOC(m->gex, (size_t)(Nm / 16 + 2) * 8, "group exponents");
+    }
     // FP64 fallback workspace: one slot per warp of a grid of at most 2 CTAs per SM
     DALLOC(m->wsp, (size_t)2 * m->n_sm * FU_WARPS * fu_wsp_doubles((int)R) * 8, "fallback workspace");
     DALLOC(m->d_err, 4 * sizeof(int), "error counters");
@@ -669,6 +676,14 @@ extern "C" dash_status dash_last_plan(const dash_model *mc, int64_t *tile_rows,
     return DASH_OK;
 }
 
+extern "C" dash_status dash_set_row_path(dash_model *m, int32_t path) {
+    if (!m) return DASH_EINVAL;
+    if (path != DASH_ROWS_AUTO && path != DASH_ROWS_FUSED && path != DASH_ROWS_SPLIT)
+        return fail(m, DASH_EINVAL, "unknown row path %d", path);
+    m->row_path = path;
+    return DASH_OK;
+}
+
 // ---------------------------------------------------------------------------
 // reconstruction errors of the last update (Definitions 1-2)
 // ---------------------------------------------------------------------------
@@ -900,8 +915,12 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
     // which segments the fused kernel finishes
     const bool fused = allow_fused && m->fused_ok && m->gam_ok_host &&
                        ((uintptr_t)X % 16) == 0;
+    // split: no tiles, every touched slice through the chunked path
+    const bool split = fused && m->cfg.precision == DASH_PREC_F16X3 &&
+                       (m->row_path == DASH_ROWS_SPLIT || (m->row_path == DASH_ROWS_AUTO && kAutoSplit));
+    m->split_active = split;
     std::vector<char> fz(n_seg, 0);
-    if (fused) {
+    if (fused && !split) {
         for (int64_t s = 0; s < n_seg; ++s)
             fz[s] = cnt[tslot[ids[s]]] == 1 && rp[s + 1] - rp[s] <= FU_TILE_MAX;
     }

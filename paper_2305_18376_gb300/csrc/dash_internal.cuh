@@ -10,6 +10,7 @@
 #include "dash_kernels_p.cuh"
 #include "dash_kernels_q.cuh"
 #include "dash_kernels_err.cuh"
+#include "dash_kernels_stream.cuh"
 
 namespace dash {
 // kernel kinds for the per-kernel profiler
@@ -19,7 +20,8 @@ enum KernelKind {
     KK_BIG_B, KK_BIG_C, KK_QV, KK_PH_A, KK_PH_EPI, KK_PH_B, KK_EPI_U, KK_EPI_DD, KK_EPI_FIN,
     KK_EPI_SCALE,
     KK_Q_BEGIN, KK_Q_AROWS, KK_Q_Y, KK_Q_LT, KK_Q_H, KK_Q_VPART, KK_Q_V, KK_Q_PW, KK_Q_W,
-    KK_Q_OUT, KK_Q_FIT, KK_QLT_QR, KK_QLT_PRE, KK_QLT_PASS, KK_QLT_TAIL, KK_COUNT
+    KK_Q_OUT, KK_Q_FIT, KK_QLT_QR, KK_QLT_PRE, KK_QLT_PASS, KK_QLT_TAIL,
+    KK_XQ_PREP, KK_XQ_TC, KK_F_TC, KK_UTILDE, KK_COUNT
 };
 static const char *const kKernelNames[KK_COUNT] = {
     "k_begin_new", "k_rowmap", "k_xv", "k_slices", "k_f", "k_f_reduce", "k_g_reduce",
@@ -30,7 +32,7 @@ static const char *const kKernelNames[KK_COUNT] = {
     "k_rows_fused.epilogue.scale",
     "k_q_begin_new", "k_q_arows", "k_q_y", "k_q_lt", "k_q_h", "k_q_vpart", "k_q_v", "k_q_pw",
     "k_q_w", "k_q_out", "k_q_fit", "k_q_lt.qr", "k_q_lt.fp32_pass", "k_q_lt.passes",
-    "k_q_lt.tail"};
+    "k_q_lt.tail", "k_xq_bfrag", "k_xq_tc", "k_f_tc", "k_utilde"};
 
 struct Profiler {
     bool on = false;
@@ -48,6 +50,7 @@ struct Profiler {
 
 constexpr int kFBlocksMax = 1024;       // max row chunks of the F-partial kernel
 constexpr int kSliceBlocksMax = 1216;   // max CTAs of the per-slice kernel (8 per SM)
+constexpr bool kAutoSplit = true;       // DASH_ROWS_AUTO takes the split row pipeline
 }  // namespace dash
 
 struct dash_model {
@@ -106,6 +109,16 @@ struct dash_model {
     int64_t max_chunks = 0;
     float *dpart = nullptr;
     bool fused_active = false;        // this update runs the fused + chunked path
+    // row pipeline of mode P (DASH_ROWS_*) and whether this update splits:
+    // every slice through the chunked path, with the streaming tensor-core
+    // kernels for P' = X Q_V and the F partials
+    int row_path = 0;
+    bool split_active = false;
+    uint4 *xq_frag = nullptr;         // Q_V split into MMA fragments
+    int *xq_bexp = nullptr;           // power-of-two scale of those fragments
+    float *Ut = nullptr;              // Ũ = U ∘ w_new rows, group-scaled (pitch 8·⌈R/8⌉)
+    int *xe = nullptr;                // exponent of each general row's max |x|
+    int2 *gex = nullptr;              // per 16-row group: {X exponent, Ũ exponent}
     // general rows: runs of consecutive rows left to the general kernels
     int64_t *d_run_g0 = nullptr, *d_run_row0 = nullptr;
     int64_t *h_run_g0 = nullptr, *h_run_row0 = nullptr;

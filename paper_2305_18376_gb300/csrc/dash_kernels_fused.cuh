@@ -261,17 +261,26 @@ __device__ __forceinline__ float slice_finish(const FusedArgs &a, int k, const f
     // D_k ← λD_k + ΔD and A = Γ ∗ D_k (row `lane`), coalesced over columns.
     // Rows and columns >= R stay zero: the factorisation below then runs over
     // all 32 (unrolled, no per-step guards) and leaves them zero.
+    // (loads in batches of 4 ahead of the stores, so a batch costs one memory
+    // round trip)
     float row[FU_RP];
     float mydiag = 0.f;
 #pragma unroll
-    for (int r = 0; r < FU_RP; ++r) {
-        row[r] = 0.f;
-        if (r < R && act) {
-            const df dold = Dk[r * R + lane];
-            const df dn = df_add(keep_old ? df_mul(lamdf, dold) : df{0.f, 0.f}, df_make(dd[r]));
-            Dk[r * R + lane] = dn;
-            row[r] = df_mul(Gs[r * FU_RP + lane], dn).hi;      // Γ symmetric: conflict-free
-            if (r == lane) mydiag = row[r];
+    for (int r0 = 0; r0 < FU_RP; r0 += 4) {
+        df dold[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            dold[u] = (r0 + u < R && act && keep_old) ? Dk[(r0 + u) * R + lane] : df{0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u;
+            row[r] = 0.f;
+            if (r < R && act) {
+                const df dn = df_add(keep_old ? df_mul(lamdf, dold[u]) : df{0.f, 0.f}, df_make(dd[r]));
+                Dk[r * R + lane] = dn;
+                row[r] = df_mul(Gs[r * FU_RP + lane], dn).hi;      // Γ symmetric: conflict-free
+                if (r == lane) mydiag = row[r];
+            }
         }
     }
     const float amax = warp_max_f(fabsf(mydiag));
@@ -1051,47 +1060,55 @@ struct BigArgs {
     float *dpart;             // n_chunks × (R·R + R)
 };
 
+// General Lemma 1 map of slice k (rare: a zero weight or a singular Γ):
+// column `lane` of R_V S (S Γ S)⁺ in FP64, rounded into Mo[t][lane].
+static __device__ __noinline__ void big_general_map(const FusedArgs &a, int k, float (*Mo)[FU_RP]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int R = a.R;
+    double *wsp = a.wsp + (size_t)(blockIdx.x * FU_WARPS + warp) * fu_wsp_doubles(R);
+    const int ld = R + 1;
+    double *Aw = wsp, *Ew = Aw + R * ld, *Mw = Ew + R * ld, *fw = Mw + R * ld;
+    for (int e = lane; e < R * R; e += 32) {
+        const int r = e / R, q = e % R;
+        Aw[r * ld + q] = a.W[(int64_t)k * R + r] * a.Gam[e] * a.W[(int64_t)k * R + q];
+    }
+    __syncwarp();
+    warp_psd_pinv(Aw, Ew, fw, Mw, R, ld, a.rtol, 1, false);
+    __syncwarp();
+    for (int t = 0; t < FU_RP; ++t) {
+        double m = 0.0;
+        if (t < R && lane < R)
+            for (int q = t; q < R; ++q) m += a.RV[t * R + q] * a.W[(int64_t)k * R + q] * Mw[q * ld + lane];
+        Mo[t][lane] = (float)m;
+    }
+    __syncwarp();
+    if (lane == 0) atomicAdd(&a.err[1], 1);
+}
+
 __device__ __forceinline__ void big_chunk(const FusedArgs &a, const BigArgs &bg, int ch,
                                           float (*Usw)[FU_RP]) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     const int R = a.R;
+    const bool act = lane < R;
     const int k = bg.ch_k[ch];
     const int64_t row0 = bg.ch_row0[ch];
     const int n = bg.ch_n[ch];
     const bool gam_ok = *a.gam_ok != 0;
-    const double wold_d = lane < R ? a.W[(int64_t)k * R + lane] : 1.0;
+    const double wold_d = act ? a.W[(int64_t)k * R + lane] : 1.0;
     const bool fast = gam_ok && __all_sync(0xffffffffu, wold_d != 0.0);
-    double *wsp = a.wsp + (size_t)(blockIdx.x * FU_WARPS + warp) * fu_wsp_doubles(R);
-    const int ld = R + 1;
     // U = P' mcol: fast path mcol = column `lane` of R_V⁻ᵀ S⁻¹; general path
-    // (zero weights) mcol = column of R_V S (S Γ S)⁺ in FP64 (rare)
-    float mcol[FU_RP], rvcol[FU_RP];
+    // (zero weights) mcol = column of R_V S (S Γ S)⁺ in FP64 (rare), and Δc
+    // then needs P' R_V, read from global memory row by row
+    float mcol[FU_RP];
     if (fast) {
-        const float winv = lane < R ? 1.0f / (float)wold_d : 0.f;
+        const float winv = act ? 1.0f / (float)wold_d : 0.f;
 #pragma unroll
-        for (int t = 0; t < FU_RP; ++t) {
-            mcol[t] = (t < R && lane < R) ? a.GPf[t * R + lane] * winv : 0.f;
-            rvcol[t] = 0.f;
-        }
+        for (int t = 0; t < FU_RP; ++t) mcol[t] = (t < R && act) ? a.GPf[t * R + lane] * winv : 0.f;
     } else {
-        double *Aw = wsp, *Ew = Aw + R * ld, *Mw = Ew + R * ld, *fw = Mw + R * ld;
-        for (int e = lane; e < R * R; e += 32) {
-            const int r = e / R, q = e % R;
-            Aw[r * ld + q] = a.W[(int64_t)k * R + r] * a.Gam[e] * a.W[(int64_t)k * R + q];
-        }
-        __syncwarp();
-        warp_psd_pinv(Aw, Ew, fw, Mw, R, ld, a.rtol, 1, false);
-        __syncwarp();
+        big_general_map(a, k, Usw);
 #pragma unroll
-        for (int t = 0; t < FU_RP; ++t) {
-            double m = 0.0;
-            if (t < R && lane < R)
-                for (int q = t; q < R; ++q)
-                    m += a.RV[t * R + q] * a.W[(int64_t)k * R + q] * Mw[q * ld + lane];
-            mcol[t] = (float)m;
-            rvcol[t] = (t < R && lane < R) ? (float)a.RV[t * R + lane] : 0.f;
-        }
-        if (lane == 0) atomicAdd(&a.err[1], 1);
+        for (int t = 0; t < FU_RP; ++t) mcol[t] = Usw[t][lane];
+        __syncwarp();
     }
     float dd[FU_RP];
 #pragma unroll
@@ -1099,32 +1116,40 @@ __device__ __forceinline__ void big_chunk(const FusedArgs &a, const BigArgs &bg,
     float dc = 0.f;
     for (int i0 = 0; i0 < n; i0 += 32) {
         const int m = min(32, n - i0);
-        // P' rows → shared, then U = P' mcol per row
-        for (int i = 0; i < m; ++i)
-            Usw[i][lane] = lane < R ? bg.Y[(row0 + i0 + i) * R + lane] : 0.f;
+        // P' rows → shared (lane = column), loads issued 8 rows at a time
+        const float *yb = bg.Y + (row0 + i0) * R + lane;
+        for (int i = 0; i < m; i += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (act && i + u < m) ? yb[(int64_t)(i + u) * R] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i + u < m) Usw[i + u][lane] = v[u];
+        }
         __syncwarp();
+#pragma unroll 1
         for (int i = 0; i < m; ++i) {
-            float u = 0.f, pl = 0.f;
+            float u0 = 0.f, u1 = 0.f, u2 = 0.f, u3 = 0.f;
 #pragma unroll
             for (int t = 0; t < FU_RP; t += 4) {
                 const float4 p4 = *reinterpret_cast<const float4 *>(&Usw[i][t]);
-                u = fmaf(p4.x, mcol[t], u);
-                u = fmaf(p4.y, mcol[t + 1], u);
-                u = fmaf(p4.z, mcol[t + 2], u);
-                u = fmaf(p4.w, mcol[t + 3], u);
-                if (!fast) {
-                    pl = fmaf(p4.x, rvcol[t], pl);
-                    pl = fmaf(p4.y, rvcol[t + 1], pl);
-                    pl = fmaf(p4.z, rvcol[t + 2], pl);
-                    pl = fmaf(p4.w, rvcol[t + 3], pl);
-                }
+                u0 = fmaf(p4.x, mcol[t], u0);
+                u1 = fmaf(p4.y, mcol[t + 1], u1);
+                u2 = fmaf(p4.z, mcol[t + 2], u2);
+                u3 = fmaf(p4.w, mcol[t + 3], u3);
             }
-            dc = fmaf(u, pl, dc);
+            const float u = (u0 + u1) + (u2 + u3);
+            if (!fast) {
+                float pl = 0.f;
+                for (int t = 0; t < R; ++t) pl = fmaf(Usw[i][t], act ? (float)a.RV[t * R + lane] : 0.f, pl);
+                dc = fmaf(u, pl, dc);
+            }
             __syncwarp();
             Usw[i][lane] = u;
-            if (lane < R) a.U[(row0 + i0 + i) * R + lane] = u;
+            if (act) a.U[(row0 + i0 + i) * R + lane] = u;
         }
         __syncwarp();
+#pragma unroll 1
         for (int i = 0; i < m; ++i) {
             const float ul = Usw[i][lane];
 #pragma unroll
@@ -1139,25 +1164,33 @@ __device__ __forceinline__ void big_chunk(const FusedArgs &a, const BigArgs &bg,
         __syncwarp();
     }
     if (fast) {                       // Δc = diag(ΔD S Γ) for this chunk
-        float sacc = 0.f;
-        const float wl = lane < R ? (float)wold_d : 0.f;
+        // ΔD through shared memory (Usw[q][l] = ΔD[q][l], symmetric), so the
+        // loop over q needs no register-indexed dd
 #pragma unroll
-        for (int q = 0; q < FU_RP; ++q) {
+        for (int q = 0; q < FU_RP; ++q) Usw[q][lane] = dd[q];
+        __syncwarp();
+        const float wl = act ? (float)wold_d : 0.f;
+        float sacc = 0.f;
+#pragma unroll 4
+        for (int q = 0; q < R; ++q) {
             const float wq = __shfl_sync(0xffffffffu, wl, q);
-            if (q < R && lane < R) sacc = fmaf(dd[q] * wq, (float)a.Gam[q * R + lane], sacc);
+            if (act) sacc = fmaf(Usw[q][lane] * wq, a.Gdf[q * R + lane].hi, sacc);   // (float)Γ
         }
+        __syncwarp();
         dc = sacc;
     }
+    // ΔD is symmetric (entry (l, q) and (q, l) are the same FMA sequence), so
+    // lane l stores column l: coalesced
     float *out = bg.dpart + (size_t)ch * (R * R + R);
-    if (lane < R) {
+    if (act) {
 #pragma unroll
         for (int q = 0; q < FU_RP; ++q)
-            if (q < R) out[lane * R + q] = dd[q];
+            if (q < R) out[q * R + lane] = dd[q];
         out[R * R + lane] = dc;
     }
 }
 
-static __global__ void __launch_bounds__(256, 1) k_big_b(FusedArgs a, BigArgs bg) {
+static __global__ void __launch_bounds__(256, 2) k_big_b(FusedArgs a, BigArgs bg) {
     __shared__ __align__(16) float Us[FU_WARPS][32][FU_RP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = a.R;
@@ -1186,10 +1219,10 @@ static __global__ void __launch_bounds__(256) k_big_c(FusedArgs a, BigArgs bg, d
         float dc = 0.f;
         for (int c = bg.fin_c0[f]; c < bg.fin_c0[f + 1]; ++c) {
             const float *in = bg.dpart + (size_t)c * (R * R + R);
-            if (lane < R) {
+            if (lane < R) {                 // symmetric: column `lane`, coalesced
 #pragma unroll
                 for (int q = 0; q < FU_RP; ++q)
-                    if (q < R) dd[q] += in[lane * R + q];
+                    if (q < R) dd[q] += in[q * R + lane];
                 dc += in[R * R + lane];
             }
         }

@@ -81,11 +81,28 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     if constexpr (std::is_same<T, float>::value) {
         if (m->fused_active) Vmul = (const T *)m->QV;
     }
+    bool split = false;
+    if constexpr (std::is_same<T, float>::value && std::is_same<TI, float>::value) split = m->split_active;
     if (Ng > 0) {
         LAUNCH(KK_ROWMAP, k_rowmap<<<(N + 255) / 256, 256, 0, st>>>(b));
-        n_xn = (int)((Ng + XV_ROWS - 1) / XV_ROWS);
-        LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, b, J, R, Vmul, (T *)m->P,
-                                                        m->xn_part + g_f));
+        if (split) {
+            // P' = X Q_V on the tensor cores, Q_V pre-split into fragments
+            const int nfr = ((J + 15) / 16) * ((R + 7) / 8) * 32;
+            LAUNCH(KK_XQ_PREP, k_xq_bscale<<<1, 32, 0, st>>>(m->QV, J * R, m->xq_bexp));
+            LAUNCH(KK_XQ_PREP, k_xq_bfrag<<<(nfr + 255) / 256, 256, 0, st>>>(m->QV, J, R, m->xq_bexp,
+                                                                            m->xq_frag));
+            const int64_t ntile = (Ng + 15) / 16;
+            n_xn = (int)std::min<int64_t>(m->n_sm, (ntile + XQ_WARPS - 1) / XQ_WARPS);
+            const size_t smem = xq_smem(J, R);
+            CK(cudaFuncSetAttribute(k_xq_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            LAUNCH(KK_XQ_TC, k_xq_tc<<<n_xn, XQ_THREADS, smem, st>>>((const float *)X, b, J, R, m->xq_frag,
+                                                                     m->xq_bexp, (float *)m->P,
+                                                                     m->xn_part + g_f, m->xe));
+        } else {
+            n_xn = (int)((Ng + XV_ROWS - 1) / XV_ROWS);
+            LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, b, J, R, Vmul, (T *)m->P,
+                                                            m->xn_part + g_f));
+        }
     }
     int nsb = 0;
     bool finished = false;
@@ -142,7 +159,32 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     }
     // F partials of the general rows
     int nfb = 0;
-    if (Ng > 0) {
+    if (Ng > 0 && split) {
+        // Ũ = U ∘ w_new, then the F partials on the tensor cores: one CTA per
+        // SM, rows in equal shares
+        const int NT = (R + 7) / 8;
+        LAUNCH(KK_UTILDE, k_utilde<<<(unsigned)((Ng + 15) / 16), 128, 0, st>>>(b, R, 8 * NT, (const float *)m->U,
+                                                                              s.W, m->xe, m->Ut, m->gex));
+        nfb = (int)std::min<int64_t>(m->n_sm, (Ng + 127) / 128);
+        const int64_t rpc = ((Ng + nfb - 1) / nfb + 15) / 16 * 16;
+        nfb = (int)((Ng + rpc - 1) / rpc);
+        dim3 grid(nfb, (J + FT_JCTA - 1) / FT_JCTA);
+        float *Fo = (float *)m->Fpart + (size_t)g_f * J * R;
+        const float *Xf = (const float *)X;
+        const size_t fsm = ft_smem();
+        switch (NT) {
+#define FTC(n)                                                                                       \
+    case n:                                                                                          \
+        CK(cudaFuncSetAttribute(k_f_tc<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));  \
+        LAUNCH(KK_F_TC, k_f_tc<n><<<grid, FT_THREADS, fsm, st>>>(Xf, b, J, R, m->Ut, m->gex, rpc, Fo));       \
+        break;
+            FTC(1)
+            FTC(2)
+            FTC(3)
+            FTC(4)
+#undef FTC
+        }
+    } else if (Ng > 0) {
         const int nby = (J + F_JB - 1) / F_JB;
         nfb = (int)std::min<int64_t>(std::max<int64_t>(1, (2 * 152 * 4) / nby), (Ng + F_RC - 1) / F_RC);
         nfb = std::min(nfb, kFBlocksMax);

@@ -16,13 +16,20 @@ from tests._parity import (FIT_TOL, TOL, compare_state_p, gpu_rows_by_slice, ora
 pytestmark = pytest.mark.gpu
 
 PREC_DTYPE = {"fp64": ("f64", torch.float64), "fp32": ("f32", torch.float32),
-              "f16x3": ("f32", torch.float32)}
+              "f16x3": ("f32", torch.float32), "f16x3-fused": ("f32", torch.float32),
+              "f16x3-split": ("f32", torch.float32)}
 
 
 def _model(J, R, lam, prec, **kw):
+    """prec: a precision, or "f16x3-fused" / "f16x3-split" for the tensor-core
+    products with that row pipeline."""
     from paper_2305_18376_gb300 import DashModel
     idt, _ = PREC_DTYPE[prec]
-    return DashModel(J, R, lam, precision=prec, input_dtype=idt, **kw)
+    base, _, path = prec.partition("-")
+    m = DashModel(J, R, lam, precision=base, input_dtype=idt, **kw)
+    if path:
+        m.set_row_path(path)
+    return m
 
 
 def _run_stream(w, prec, n_steps, init_iters=3, via="batch", seed_v=1):
@@ -78,7 +85,7 @@ def _run_stream(w, prec, n_steps, init_iters=3, via="batch", seed_v=1):
     return worst
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3-fused", "f16x3-split"])
 def test_small_stream_parity(prec):
     w = tiny(K0=6, J=9, R=3, steps=4, sigma=0.05, lam=0.9)
     _run_stream(w, prec, 4)
@@ -97,7 +104,7 @@ def test_c1_workload_fp64():
     print("c1 fp64 worst relative errors:", worst)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "f16x3-fused", "f16x3-split"])
 def test_c2_shaped(prec):
     """c2's shape (J=88, R=10, +1 row per slice, +10 slices) at K0=300."""
     w = workload("c2", K0=300, init_rows=("uniform", 50, 300), new_slice_rows=("uniform", 50, 100),
@@ -117,7 +124,7 @@ def _state_from_oracle(w, prec, lam):
     return O.init_helpers_p(X0, U, W, V)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3-fused", "f16x3-split"])
 def test_ragged_edge_batch_from_oracle_state(prec):
     """One update from an oracle state with: a slice split in two segments,
     untouched slices (λ decay only), a 1-row segment, a segment longer than
@@ -163,7 +170,7 @@ def test_rank_deficient_gram_uses_the_pseudo_inverse(prec):
         assert rel(got[k], Uo[k]) <= tol
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3-fused", "f16x3-split"])
 def test_zero_weight_entries_take_the_general_lemma1_path(prec):
     """A slice whose S_k has zero entries: S (S Γ S)⁺ ≠ Γ⁻¹ S⁻¹ (in the
     fused kernel this is its in-kernel FP64 fallback)."""
@@ -186,7 +193,7 @@ def test_zero_weight_entries_take_the_general_lemma1_path(prec):
         assert rel(got[k], Uo[k]) <= tol
 
 
-@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "f16x3-fused", "f16x3-split"])
 def test_fused_tiles_span_many_slices_and_ctas(prec):
     """A few thousand small slices of 1-64 rows (c4's update shape at small J
     and R): many tiles per CTA, big and split slices on the chunked path in
@@ -197,7 +204,7 @@ def test_fused_tiles_span_many_slices_and_ctas(prec):
     print(f"many-slice {prec} worst relative errors:", worst)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3-fused", "f16x3-split"])
 def test_c4_shape_small_k(prec):
     """c4's J = 512 and R = 32 (full register tiles of the MMA path) at
     K0 = 300 slices."""
@@ -251,7 +258,7 @@ def test_capacity_and_argument_errors_leave_state_unchanged():
     assert m.K == 1
 
 
-@pytest.mark.parametrize("prec", ["fp64", "f16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "f16x3-fused", "f16x3-split"])
 def test_local_errors_match_definitions(prec):
     """Definitions 1-2 on the last update's rows: se per slice, te, and the
     direct batch fitness, against the oracle's slice_error / tensor_error /
