@@ -62,7 +62,7 @@ static void prof_collect(dash_model *m) {
     }
     m->prof.pending.clear();
     if (m->prof.d_phase) {
-        unsigned long long c[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        unsigned long long c[kPhaseSlots] = {};
         if (cudaMemcpy(c, m->prof.d_phase, sizeof c, cudaMemcpyDeviceToHost) == cudaSuccess) {
             // phases: average per SM; epilogue sub-phases: average per warp;
             // milliseconds at the device clock
@@ -76,6 +76,13 @@ static void prof_collect(dash_model *m) {
                 const double per = m->prof.q_lt_warps > 0 ? m->prof.q_lt_warps : 1.0;
                 m->prof.ms[KK_QLT_QR + i] += (double)c[7 + i] / per / m->prof.clock_khz;
                 if (c[7 + i]) m->prof.launches[KK_QLT_QR + i] += 1;
+            }
+            // streaming kernels: cycles waiting on / computing stages, summed
+            // over their warps, reported per warp
+            for (int i = 0; i < 4; ++i) {
+                const double w = i < 2 ? m->prof.xq_warps : m->prof.ft_warps;
+                m->prof.ms[KK_XQ_WAIT + i] += (double)c[11 + i] / (w > 0 ? w : 1.0) / m->prof.clock_khz;
+                if (c[11 + i]) m->prof.launches[KK_XQ_WAIT + i] += 1;
             }
             cudaMemset(m->prof.d_phase, 0, sizeof c);
         }
@@ -91,10 +98,10 @@ extern "C" dash_status dash_profile_enable(dash_model *m, int32_t on) {
     if (!m) return DASH_EINVAL;
     if (!m->prof.d_phase) {
         void *p = nullptr;
-        if (cudaMalloc(&p, 11 * sizeof(unsigned long long)) == cudaSuccess) {
+        if (cudaMalloc(&p, kPhaseSlots * sizeof(unsigned long long)) == cudaSuccess) {
             m->prof.d_phase = (unsigned long long *)p;
             m->allocs.push_back(p);
-            cudaMemset(p, 0, 11 * sizeof(unsigned long long));
+            cudaMemset(p, 0, kPhaseSlots * sizeof(unsigned long long));
             int dev = 0, khz = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
@@ -281,9 +288,8 @@ static dash_status init_alloc(dash_model *m) {
     DALLOC(m->xq_frag, (size_t)((J + 15) / 16) * ((R + 7) / 8) * 32 * 16, "Q_V fragments");
     DALLOC(m->xq_bexp, 4, "Q_V fragment scale");
     if (m->fused_ok) {
-        DALLOC(m->Ut, (size_t)Nm * 8 * ((R + 7) / 8) * 4, "U o w rows");
+        DALLOC(m->Ut, (size_t)(Nm / 16 + 2) * ft_ublk((R + 7) / 8) * 4, "U o w fragments");
         DALLOC(m->xe, (size_t)(Nm + 16) * 4, "row exponents");
-        DALLOC(m->gex, (size_t)(Nm / 16 + 2) * 8, "group exponents");
     }
     // FP64 fallback workspace: one slot per warp of a grid of at most 2 CTAs per SM
     DALLOC(m->wsp, (size_t)2 * m->n_sm * FU_WARPS * fu_wsp_doubles((int)R) * 8, "fallback workspace");
@@ -426,8 +432,7 @@ static dash_status refresh_gamma(dash_model *m) {
     else
         LAUNCH(KK_CAST, k_cast<float><<<(n + 255) / 256, 256, 0, m->stream>>>(m->st.V, (float *)m->VT, n));
     LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, m->stream>>>(m->st.V, J, R, m->st.Gam));
-    const size_t sm = (size_t)(3 * R * (R + 1) + (R + 1)) * 8;
-    LAUNCH(KK_PINV, k_pinv_small<<<1, 32, sm, m->stream>>>(m->st.Gam, R, m->rtol, m->st.GamP, m->st.gam_ok));
+    if (dash_status e = launch_pinv(m, m->st.Gam, m->st.GamP, m->st.gam_ok)) return e;
     int ok = 0;
     CK(cudaMemcpyAsync(&ok, m->st.gam_ok, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
     CK(cudaStreamSynchronize(m->stream));

@@ -21,7 +21,8 @@ enum KernelKind {
     KK_EPI_SCALE,
     KK_Q_BEGIN, KK_Q_AROWS, KK_Q_Y, KK_Q_LT, KK_Q_H, KK_Q_VPART, KK_Q_V, KK_Q_PW, KK_Q_W,
     KK_Q_OUT, KK_Q_FIT, KK_QLT_QR, KK_QLT_PRE, KK_QLT_PASS, KK_QLT_TAIL,
-    KK_XQ_PREP, KK_XQ_TC, KK_F_TC, KK_UTILDE, KK_COUNT
+    KK_XQ_PREP, KK_XQ_TC, KK_F_TC, KK_UTILDE, KK_XQ_WAIT, KK_XQ_BUSY, KK_FT_WAIT, KK_FT_BUSY,
+    KK_COUNT
 };
 static const char *const kKernelNames[KK_COUNT] = {
     "k_begin_new", "k_rowmap", "k_xv", "k_slices", "k_f", "k_f_reduce", "k_g_reduce",
@@ -32,7 +33,8 @@ static const char *const kKernelNames[KK_COUNT] = {
     "k_rows_fused.epilogue.scale",
     "k_q_begin_new", "k_q_arows", "k_q_y", "k_q_lt", "k_q_h", "k_q_vpart", "k_q_v", "k_q_pw",
     "k_q_w", "k_q_out", "k_q_fit", "k_q_lt.qr", "k_q_lt.fp32_pass", "k_q_lt.passes",
-    "k_q_lt.tail", "k_xq_bfrag", "k_xq_tc", "k_f_tc", "k_utilde"};
+    "k_q_lt.tail", "k_xq_bfrag", "k_xq_tc", "k_f_tc", "k_utilde", "k_xq_tc.wait", "k_xq_tc.loop",
+    "k_f_tc.wait", "k_f_tc.loop"};
 
 struct Profiler {
     bool on = false;
@@ -46,8 +48,10 @@ struct Profiler {
     double clock_khz = 1.0;
     int n_sm = 1;
     double q_lt_warps = 0.0;    // warps of the last profiled k_q_lt launch
+    double xq_warps = 0.0, ft_warps = 0.0;   // warps of the streaming kernels' last launch
 };
 
+constexpr int kPhaseSlots = 15;        // in-kernel cycle counters of the profiler
 constexpr int kFBlocksMax = 1024;       // max row chunks of the F-partial kernel
 constexpr int kSliceBlocksMax = 1216;   // max CTAs of the per-slice kernel (8 per SM)
 constexpr bool kAutoSplit = true;       // DASH_ROWS_AUTO takes the split row pipeline
@@ -116,9 +120,8 @@ struct dash_model {
     bool split_active = false;
     uint4 *xq_frag = nullptr;         // Q_V split into MMA fragments
     int *xq_bexp = nullptr;           // power-of-two scale of those fragments
-    float *Ut = nullptr;              // Ũ = U ∘ w_new rows, group-scaled (pitch 8·⌈R/8⌉)
+    uint32_t *Ut = nullptr;           // Ũ = U ∘ w_new as MMA fragment blocks of 16 rows
     int *xe = nullptr;                // exponent of each general row's max |x|
-    int2 *gex = nullptr;              // per 16-row group: {X exponent, Ũ exponent}
     // general rows: runs of consecutive rows left to the general kernels
     int64_t *d_run_g0 = nullptr, *d_run_row0 = nullptr;
     int64_t *h_run_g0 = nullptr, *h_run_row0 = nullptr;

@@ -1192,8 +1192,7 @@ __device__ __forceinline__ void big_chunk(const FusedArgs &a, const BigArgs &bg,
 
 static __global__ void __launch_bounds__(256, 2) k_big_b(FusedArgs a, BigArgs bg) {
     __shared__ __align__(16) float Us[FU_WARPS][32][FU_RP];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int R = a.R;
+    const int warp = threadIdx.x >> 5;
     for (int ch = blockIdx.x * FU_WARPS + warp; ch < bg.n_chunks; ch += gridDim.x * FU_WARPS) {
         big_chunk(a, bg, ch, Us[warp]);
     }

@@ -469,6 +469,82 @@ static __global__ void k_pinv_small(const double *__restrict__ Min, int R, doubl
     if (ok && lane == 0) *ok = chol ? 1 : 0;
 }
 
+// G⁺ (or Γ⁺) of a symmetric PSD R×R matrix, R <= 32, spread over R CTAs of
+// one warp (each on its own SM: the FP64 pipe is per SM).  Every CTA factors
+// A = L Lᵀ in registers (lane l = row l, right-looking, pivots broadcast by
+// shuffles); when every pivot exceeds 100·rtol·max(diag), CTA c writes
+// column c of A⁻¹ by two triangular solves (forward from registers,
+// backward from L in shared memory).  Otherwise CTA 0 alone takes the eigen
+// path of k_pinv_small for the whole matrix.  ok (optional) receives 1 for
+// the Cholesky path.  Dynamic shared memory: as k_pinv_small.
+static __global__ void __launch_bounds__(32) k_pinv_cols(const double *__restrict__ Min, int R,
+                                                         double rtol, double *__restrict__ Mout,
+                                                         int *ok) {
+    extern __shared__ double sm[];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, ld = R + 1;
+    const bool act = lane < R;
+    double row[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) row[q] = (act && q < R) ? Min[lane * R + q] : 0.0;
+    double md = 0.0;
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+        if (q == lane) md = fabs(row[q]);
+    md = warp_max(md);
+    const double tol = 100.0 * rtol * md;
+    bool chol = md > 0.0;
+    double myinv = 0.0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        if (j < R) {
+            const double piv = __shfl_sync(full, row[j], j);
+            chol = chol && (piv > tol);
+            const double inv = 1.0 / sqrt(piv > 0.0 ? piv : 1.0);
+            const double lij = (lane == j) ? piv * inv : row[j] * inv;
+            row[j] = lij;
+            if (lane == j) myinv = inv;
+#pragma unroll
+            for (int q = j + 1; q < 32; ++q) {
+                const double lqj = __shfl_sync(full, lij, q);
+                if (q < R) row[q] = fma(-lij, lqj, row[q]);
+            }
+        }
+    }
+    if (chol) {
+        double *Ls = sm;                       // L, row l at Ls[l·ld]
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+            if (act && q < R && q <= lane) Ls[lane * ld + q] = row[q];
+        __syncwarp();
+        const int c = blockIdx.x;
+        double y = (lane == c) ? 1.0 : 0.0;    // L y = e_c
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j < R) {
+                const double yj = __shfl_sync(full, y * myinv, j);
+                if (lane == j) y = yj;
+                else if (lane > j && act) y = fma(-row[j], yj, y);
+            }
+        }
+        for (int j = R - 1; j >= 0; --j) {     // Lᵀ x = y
+            const double xj = __shfl_sync(full, y * myinv, j);
+            if (lane == j) y = xj;
+            else if (lane < j) y = fma(-Ls[j * ld + lane], xj, y);
+        }
+        if (act) Mout[lane * R + c] = y;
+        if (ok && c == 0 && lane == 0) *ok = 1;
+        return;
+    }
+    if (blockIdx.x != 0) return;
+    double *A = sm, *E = A + R * ld, *out = E + R * ld, *f = out + R * ld;
+    for (int i = lane; i < R * R; i += 32) A[(i / R) * ld + (i % R)] = Min[i];
+    __syncwarp();
+    warp_psd_pinv(A, E, f, out, R, ld, rtol, 1, false);
+    for (int i = lane; i < R * R; i += 32) Mout[i] = out[(i / R) * ld + (i % R)];
+    if (ok && lane == 0) *ok = 0;
+}
+
 // P9: V = F G⁺ (Eq. 17), one row per warp, plus V in T for the kernels and
 // the fitness cross term Σ V ∗ F_inc per CTA.
 template <typename T>

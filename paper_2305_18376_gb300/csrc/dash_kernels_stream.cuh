@@ -14,10 +14,12 @@
 // k-steps with one scale) starts a fresh MMA accumulator, which is scaled
 // back and added to the FP32 running sum with a rounded FMA.
 //
-// Data movement: each thread copies exactly the float4s it will later read
-// into its own shared-memory slots with cp.async, several stages ahead, and
-// waits only on its own copy groups (cp.async.wait_group): deep memory-level
-// parallelism without register cost and without any cross-thread wait.
+// Data movement: each warp streams its own stages of X (16 rows × 64
+// columns) through a ring in shared memory with 1-D bulk copies (one copy per
+// row segment, issued by up to 32 lanes at once), each stage completing on
+// its own mbarrier.  The warp is both producer and consumer of its ring, so
+// no wait depends on another warp; every wait is bounded.  Rows are padded
+// in shared memory so that the fragment reads are free of bank conflicts.
 //
 // A sum over a contraction index does not depend on the order of its terms,
 // so each kernel assigns the MMA's k (and m/n) slots to columns or rows in
@@ -32,11 +34,6 @@
 #include "dash_kernels_p.cuh"
 
 namespace dash {
-
-constexpr int XQ_THREADS = 256;
-constexpr int XQ_WARPS = XQ_THREADS / 32;
-constexpr int XQ_KU = 4;                  // k-steps per stage (one scale per row)
-constexpr int XQ_S = 4;                   // stages in flight per warp
 
 __device__ __forceinline__ uint32_t xq_h2(float a, float b) {
     const __half2 h = __floats2half2_rn(a, b);
@@ -57,6 +54,15 @@ __device__ __forceinline__ void xq_mma(float (&d)[4], uint32_t a0, uint32_t a1, 
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
+// d = a·b (fresh accumulator: C is the constant 0)
+__device__ __forceinline__ void xq_mma0(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                        uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%10,%10,%10,%10};"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(0.f));
+}
 // 2^e as a float, for -126 <= e <= 127
 __device__ __forceinline__ float xq_pow2(int e) { return __int_as_float((127 + e) << 23); }
 // e with m = f·2^e, f in [0.5, 1), for finite m >= 0, clamped below at -60 (a
@@ -73,28 +79,38 @@ __device__ __forceinline__ float4 f4scale(float4 v, float s) {
     return make_float4(v.x * s, v.y * s, v.z * s, v.w * s);
 }
 
-// per-thread asynchronous copies global → shared; `valid` false fills zeros
-// (source size 0, nothing read)
-__device__ __forceinline__ void cpa16(void *dst, const void *src, bool valid) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
-                 "r"(valid ? 16 : 0)
-                 : "memory");
+// Bounded wait of a whole warp on its own stage barrier: false after ~1 s
+// (counted once in err).
+__device__ __forceinline__ bool sb_wait(uint64_t *bar, uint32_t parity, int *err) {
+    bool got = true;
+    if (!mbar_try_wait(bar, parity)) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(bar, parity)) {
+            if (clock64() - t0 > 2000000000LL) {
+                got = false;
+                break;
+            }
+        }
+    }
+    got = __all_sync(0xffffffffu, got);
+    if (!got && (threadIdx.x & 31) == 0) atomicAdd(err, 1);
+    return got;
 }
-__device__ __forceinline__ void cpa8(void *dst, const void *src, bool valid) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src),
-                 "r"(valid ? 8 : 0)
-                 : "memory");
+
+// Row g of the general rows: one run (the split plan: every row of the batch,
+// in order) maps with an add, otherwise gen_row's search.
+__device__ __forceinline__ int64_t run0_of(const BatchDev &b) {
+    return b.n_runs == 1 ? b.run_row0[0] : -1;
 }
-__device__ __forceinline__ void cpa4(void *dst, const void *src, bool valid) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src),
-                 "r"(valid ? 4 : 0)
-                 : "memory");
+__device__ __forceinline__ int64_t gen_row_fast(const BatchDev &b, int64_t run0, int64_t g) {
+    return run0 >= 0 ? run0 + g : gen_row(b, g);
 }
-__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cpa_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
+
+// X scale exponent from a row (or row group) max |x| = f·2^ex, f in [0.5, 1):
+// none while max |x| lies in [2^3, 2^14) (the FP16 split of unscaled X then
+// keeps ~28 bits relative to the group's max: a lo half below FP16's normal
+// range is under 2^-25, hi stays below 2^14), else 2^(10 - ex).
+__host__ __device__ inline int ft_xscale_exp(int ex) { return (ex >= 4 && ex <= 14) ? 0 : 10 - ex; }
 
 // Power-of-two exponent bexp that brings max |B| into [512, 1024), clamped
 // to [-40, 40]; B is J×R.  One warp.
@@ -136,79 +152,77 @@ static __global__ void k_xq_bfrag(const float *__restrict__ B, int J, int R,
     frag[i] = f;
 }
 
-// Row g of the general rows: one run (the split plan: every row of the batch,
-// in order) maps with an add, otherwise gen_row's search.
-__device__ __forceinline__ int64_t run0_of(const BatchDev &b) {
-    return b.n_runs == 1 ? b.run_row0[0] : -1;
-}
-__device__ __forceinline__ int64_t gen_row_fast(const BatchDev &b, int64_t run0, int64_t g) {
-    return run0 >= 0 ? run0 + g : gen_row(b, g);
-}
+// ---------------------------------------------------------------------------
+// k_xq_tc.  A warp takes 16-row tiles of the general rows; a stage is the
+// tile's next 64 columns (4 k-steps, one scale per row).  Lane (g = lane/4,
+// tg = lane%4) holds rows g and g+8; in k-step kk its k-slots 2tg, 2tg+1,
+// 2tg+8, 2tg+9 are columns 16kk + 4tg + {0, 1, 2, 3} (one float4 per row).
+constexpr int XQ_THREADS = 512;
+constexpr int XQ_WARPS = XQ_THREADS / 32;
+constexpr int XQ_KU = 4;                  // k-steps per stage
+constexpr int XQ_S = 2;                   // stages per warp ring (a power of 2)
+constexpr int XQ_XP = 80;                 // floats per staged row (≡ 16 mod 32: conflict-free)
+constexpr int XQ_STAGE = 16 * XQ_XP;      // floats per stage
 
-// Dynamic shared memory of k_xq_tc: the B fragments, then per warp XQ_S
-// stages of XQ_KU k-steps × 2 rows of float4 per lane.
+// Dynamic shared memory of k_xq_tc: the B fragments, the warps' rings, their
+// stage barriers.
 __host__ __device__ inline size_t xq_smem(int J, int R) {
     return (size_t)((J + 15) / 16) * ((R + 7) / 8) * 32 * 16 +
-           (size_t)XQ_WARPS * XQ_S * XQ_KU * 2 * 32 * 16;
+           (size_t)XQ_WARPS * XQ_S * XQ_STAGE * 4 + (size_t)XQ_WARPS * XQ_S * 8;
 }
 
 // P(row, :) = X(row, :)·B for the N_gen general rows (general row g lives at
 // gen_row(b, g)); per-CTA partial of Σ ‖x‖² in xn_part[blockIdx.x]; xe[g] =
-// the exponent e of the row's max |x| (max = f·2^e, f in [0.5, 1)).  A warp
-// takes 16-row tiles.  Lane (g = lane/4, tg = lane%4) holds rows g and g+8
-// of the tile; in k-step kk its k-slots 2tg, 2tg+1, 2tg+8, 2tg+9 are columns
-// 16kk + 4tg + {0, 1, 2, 3} (one float4 per row).  A stage is XQ_KU k-steps;
-// each row is scaled once per stage (max over its 64 columns).
+// the exponent e of the row's max |x| (max = f·2^e, f in [0.5, 1)).
 // Requires J % 4 == 0, 16-byte aligned rows and R <= 32.
 static __global__ void __launch_bounds__(XQ_THREADS, 1)
     k_xq_tc(const float *__restrict__ X, BatchDev b, int J, int R, const uint4 *__restrict__ frag,
             const int *__restrict__ bexp_p, float *__restrict__ P, double *__restrict__ xn_part,
-            int *__restrict__ xe) {
-    extern __shared__ uint4 xq_sm[];
+            int *__restrict__ xe, int *__restrict__ err, unsigned long long *__restrict__ pc) {
+    extern __shared__ __align__(16) uint4 xq_sm[];
     const int nks = (J + 15) / 16, nnt = (R + 7) / 8;
     const int nfr = nks * nnt * 32;
-    for (int i = threadIdx.x; i < nfr; i += XQ_THREADS) xq_sm[i] = frag[i];
-    __syncthreads();
-    const float bunscale = xq_pow2(-*bexp_p);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, tg = lane & 3;
-    float4 *ring = reinterpret_cast<float4 *>(xq_sm + nfr) + (size_t)warp * XQ_S * XQ_KU * 2 * 32 + lane;
+    float *ring = reinterpret_cast<float *>(xq_sm + nfr) + (size_t)warp * XQ_S * XQ_STAGE;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<float *>(xq_sm + nfr) +
+                                                  (size_t)XQ_WARPS * XQ_S * XQ_STAGE) + warp * XQ_S;
+    for (int i = threadIdx.x; i < nfr; i += XQ_THREADS) xq_sm[i] = frag[i];
+    if (lane == 0) {
+        for (int s = 0; s < XQ_S; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const float bunscale = xq_pow2(-*bexp_p);
     const int64_t run0 = run0_of(b);
     const int64_t Ng = b.N_gen;
     const int64_t ntile = (Ng + 15) / 16;
     const int64_t t0 = (int64_t)blockIdx.x * XQ_WARPS + warp, tstride = (int64_t)gridDim.x * XQ_WARPS;
-    const int nkg = (nks + XQ_KU - 1) / XQ_KU;
+    const int nkg = (J + 63) / 64;
     const int ntw = t0 < ntile ? (int)((ntile - 1 - t0) / tstride + 1) : 0;
     const int total = ntw * nkg;
-    // stage cursor of the copies (runs XQ_S - 1 stages ahead): tile, k-group
+    // copy cursor (runs XQ_S - 1 stages ahead of the compute): stage, tile, k-group
     int is = 0, itile = 0, ikg = 0;
-    const float *xa = X, *xb = X;
-    bool iva = false, ivb = false;
+    const float *isrc = X;                 // this lane's row (lanes 0..15) of the copy tile
+    int inv = 0;                           // valid rows of the copy tile
     auto issue = [&]() {
-        if (is < total) {
-            if (ikg == 0) {
-                const int64_t ga = 16 * (t0 + (int64_t)itile * tstride) + g, gb = ga + 8;
-                iva = ga < Ng;
-                ivb = gb < Ng;
-                xa = X + (iva ? gen_row_fast(b, run0, ga) : 0) * (int64_t)J + 4 * tg;
-                xb = X + (ivb ? gen_row_fast(b, run0, gb) : 0) * (int64_t)J + 4 * tg;
-            }
-            float4 *slot = ring + (is & (XQ_S - 1)) * XQ_KU * 2 * 32;
-#pragma unroll
-            for (int u = 0; u < XQ_KU; ++u) {
-                const int kk = ikg * XQ_KU + u;
-                const int j0 = 16 * kk;
-                const bool c = kk < nks && j0 + 4 * tg < J;
-                cpa16(slot + (2 * u) * 32, (iva && c) ? xa + j0 : X, iva && c);
-                cpa16(slot + (2 * u + 1) * 32, (ivb && c) ? xb + j0 : X, ivb && c);
-            }
-            if (++ikg == nkg) {
-                ikg = 0;
-                ++itile;
-            }
+        if (is >= total) return;
+        if (ikg == 0) {
+            const int64_t r0 = 16 * (t0 + (int64_t)itile * tstride);
+            inv = (int)(Ng - r0 < 16 ? Ng - r0 : 16);
+            isrc = X + (lane < inv ? gen_row_fast(b, run0, r0 + lane) : 0) * (int64_t)J;
+        }
+        const int s = is & (XQ_S - 1);
+        const uint32_t rb = (uint32_t)min(64, J - 64 * ikg) * 4;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (lane == 0) mbar_expect_tx(&bars[s], rb * (uint32_t)inv);
+        __syncwarp();
+        if (lane < inv) bulk_g2s(ring + (size_t)s * XQ_STAGE + lane * XQ_XP, isrc + 64 * ikg, rb, &bars[s]);
+        if (++ikg == nkg) {
+            ikg = 0;
+            ++itile;
         }
         ++is;
-        cpa_commit();
     };
 #pragma unroll
     for (int i = 0; i < XQ_S - 1; ++i) issue();
@@ -216,9 +230,19 @@ static __global__ void __launch_bounds__(XQ_THREADS, 1)
     float xnf = 0.f, rm0 = 0.f, rm1 = 0.f;
     float acc[4][4];
     int ctile = 0, kg = 0;
-    for (int i = 0; i < total; ++i) {
+    bool aborted = false;
+    int i = 0;
+    long long cw = 0;                      // profiling: cycles waiting on stages
+    const long long c0 = pc ? clock64() : 0;
+    for (; i < total; ++i) {
         issue();
-        cpa_wait<XQ_S - 1>();
+        const int s = i & (XQ_S - 1);
+        const long long w0 = pc ? clock64() : 0;
+        if (!sb_wait(&bars[s], (uint32_t)(i / XQ_S) & 1u, err)) {
+            aborted = true;
+            break;
+        }
+        if (pc) cw += clock64() - w0;
         if (kg == 0) {
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt)
@@ -227,27 +251,42 @@ static __global__ void __launch_bounds__(XQ_THREADS, 1)
             xnf = 0.f;
             rm0 = rm1 = 0.f;
         }
-        const float4 *slot = ring + (i & (XQ_S - 1)) * XQ_KU * 2 * 32;
+        const int64_t ga = 16 * (t0 + (int64_t)ctile * tstride) + g, gb = ga + 8;
+        const bool va = ga < Ng, vb = gb < Ng;
+        const float *st = ring + (size_t)s * XQ_STAGE;
         float4 xv[XQ_KU][2];
         float m0 = 0.f, m1 = 0.f;
 #pragma unroll
         for (int u = 0; u < XQ_KU; ++u) {
-            xv[u][0] = slot[(2 * u) * 32];
-            xv[u][1] = slot[(2 * u + 1) * 32];
+            const int col = 64 * kg + 16 * u + 4 * tg;
+            const bool c = col < J;
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            xv[u][0] = (va && c) ? *reinterpret_cast<const float4 *>(st + g * XQ_XP + 16 * u + 4 * tg) : z;
+            xv[u][1] = (vb && c) ? *reinterpret_cast<const float4 *>(st + (g + 8) * XQ_XP + 16 * u + 4 * tg) : z;
             const float4 p = xv[u][0], q = xv[u][1];
             xnf += p.x * p.x + p.y * p.y + p.z * p.z + p.w * p.w +
                    q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
             m0 = fmaxf(m0, fmax4(p));
             m1 = fmaxf(m1, fmax4(q));
         }
+        __syncwarp();                      // stage s is read: free for its next copy
         m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 1));
         m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 2));
         m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 1));
         m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 2));
         rm0 = fmaxf(rm0, m0);
         rm1 = fmaxf(rm1, m1);
-        const int e0 = xq_exp(m0), e1 = xq_exp(m1);
-        const float s0 = xq_pow2(10 - e0), s1 = xq_pow2(10 - e1);
+        // rows whose max lies in [2^3, 2^14) go unscaled (see ft_xscale_exp);
+        // the multiplies are skipped when that holds for the warp's 16 rows
+        const int x0 = ft_xscale_exp(xq_exp(m0)), x1 = ft_xscale_exp(xq_exp(m1));
+        if (__any_sync(0xffffffffu, (x0 | x1) != 0)) {
+            const float s0 = xq_pow2(x0), s1 = xq_pow2(x1);
+#pragma unroll
+            for (int u = 0; u < XQ_KU; ++u) {
+                xv[u][0] = f4scale(xv[u][0], s0);
+                xv[u][1] = f4scale(xv[u][1], s1);
+            }
+        }
         float d[4][4];
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt)
@@ -257,7 +296,7 @@ static __global__ void __launch_bounds__(XQ_THREADS, 1)
         for (int u = 0; u < XQ_KU; ++u) {
             const int kk = kg * XQ_KU + u;
             if (kk < nks) {
-                const float4 p = f4scale(xv[u][0], s0), q = f4scale(xv[u][1], s1);
+                const float4 p = xv[u][0], q = xv[u][1];
                 uint32_t a0h, a0l, a1h, a1l, a2h, a2l, a3h, a3l;
                 xq_split(p.x, p.y, a0h, a0l);      // row g,   k 2tg, 2tg+1
                 xq_split(q.x, q.y, a1h, a1l);      // row g+8
@@ -275,7 +314,7 @@ static __global__ void __launch_bounds__(XQ_THREADS, 1)
                 }
             }
         }
-        const float u0 = xq_pow2(e0 - 10), u1 = xq_pow2(e1 - 10);
+        const float u0 = xq_pow2(-x0), u1 = xq_pow2(-x1);
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
             acc[nt][0] = fmaf(d[nt][0], u0, acc[nt][0]);
@@ -285,10 +324,8 @@ static __global__ void __launch_bounds__(XQ_THREADS, 1)
         }
         if (++kg == nkg) {
             kg = 0;
-            xn += (double)xnf;
-            const int64_t ga = 16 * (t0 + (int64_t)ctile * tstride) + g, gb = ga + 8;
             ++ctile;
-            const bool va = ga < Ng, vb = gb < Ng;
+            xn += (double)xnf;
             const int64_t ra = va ? gen_row_fast(b, run0, ga) : 0, rb = vb ? gen_row_fast(b, run0, gb) : 0;
             if (tg == 0) {
                 if (va) xe[ga] = xq_exp(rm0);
@@ -305,67 +342,84 @@ static __global__ void __launch_bounds__(XQ_THREADS, 1)
             }
         }
     }
-    cpa_wait<0>();
+    if (aborted) {                         // let the copies already issued land
+        for (int k = i; k < is; ++k) sb_wait(&bars[k & (XQ_S - 1)], (uint32_t)(k / XQ_S) & 1u, err);
+    }
+    if (pc && lane == 0) {
+        atomicAdd(&pc[0], (unsigned long long)cw);
+        atomicAdd(&pc[1], (unsigned long long)(clock64() - c0));
+    }
     xn = warp_sum(xn);
     __shared__ double red[XQ_WARPS];
     if (lane == 0) red[warp] = xn;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < XQ_WARPS; ++w) s += red[w];
-        xn_part[blockIdx.x] = s;
+        double sum = 0.0;
+        for (int w = 0; w < XQ_WARPS; ++w) sum += red[w];
+        xn_part[blockIdx.x] = sum;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Ũ for k_f_tc, one CTA of 128 threads per 16-row group G of the general
-// rows: Ũ(g, :) = U(row, :) ∘ w_k,new (rounded once from the FP64 product),
-// scaled by 2^(10 - eu) with eu the exponent of the group's max |Ũ|, in FP32
-// with row pitch `pitch` (8·⌈R/8⌉; columns R.. zero); gex[G] = {ex, eu} with
-// ex the largest row exponent xe of the group's rows (the X scale k_f_tc
-// applies to all 16 rows).  Thread t: row 16G + t/8, columns 4(t%8) ...
-static __global__ void __launch_bounds__(128) k_utilde(BatchDev b, int R, int pitch,
-                                                       const float *__restrict__ U,
-                                                       const double *__restrict__ W,
-                                                       const int *__restrict__ xe,
-                                                       float *__restrict__ Ut, int2 *__restrict__ gex) {
-    __shared__ float smx[4];
-    __shared__ int sex[4];
-    const int t = threadIdx.x, q = t & 7;
-    const int64_t gg = 16 * (int64_t)blockIdx.x + (t >> 3);
-    const bool rowok = gg < b.N_gen;
-    const bool ok = rowok && 4 * q < pitch;
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
+// Ũ for k_f_tc as MMA B fragments, one warp per 16-row group G of the
+// general rows.  Ũ(g, r) = U(row, r)·w_k,new(r) (rounded once from the FP64
+// product) is scaled by 2^(10 - eu), eu the exponent of the group's max |Ũ|,
+// and split into FP16 hi + lo.  Block G (ft_ublk(NT) 32-bit words at
+// Uf + G·ft_ublk(NT)) holds, for n-tile nt and lane L = (g, tg), the word
+// quadruple {bh0, bh1, bl0, bl1} at words 4(32nt + L) ..: bh0 packs the hi
+// halves of Ũ(16G + 2tg, NT·g + nt) and Ũ(16G + 2tg + 1, ·), bh1 those of
+// rows 2tg + 8 and 2tg + 9, bl0/bl1 the lo halves; then the record
+// {sxe, eu, 0, 0}, sxe the X scale exponent of the group (ft_xscale_exp of
+// its largest row exponent xe).  Rows past N_gen and columns past R are 0.
+__host__ __device__ constexpr int ft_ublk(int NT) { return 128 * NT + 4; }
+
+template <int NT>
+__global__ void __launch_bounds__(256) k_utilde(BatchDev b, int R, const float *__restrict__ U,
+                                                const double *__restrict__ W,
+                                                const int *__restrict__ xe,
+                                                uint32_t *__restrict__ Uf) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, tg = lane & 3;
+    const int64_t G = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (16 * G >= b.N_gen) return;
+    const int64_t run0 = run0_of(b);
+    const int roff[4] = {2 * tg, 2 * tg + 1, 2 * tg + 8, 2 * tg + 9};
+    float v[4][NT];
+    float m = 0.f;
     int ex = -60;
-    if (rowok) ex = xe[gg];
-    if (ok) {
-        const int64_t row = gen_row_fast(b, run0_of(b), gg);
-        const int k = b.row_slice[row];
+    if (lane < 16 && 16 * G + lane < b.N_gen) ex = xe[16 * G + lane];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int r = 4 * q + c;
-            v[c] = r < R ? (float)((double)U[row * R + r] * W[(int64_t)k * R + r]) : 0.f;
+    for (int p = 0; p < 4; ++p) {
+        const int64_t gg = 16 * G + roff[p];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) v[p][nt] = 0.f;
+        if (gg < b.N_gen) {
+            const int64_t row = gen_row_fast(b, run0, gg);
+            const int k = b.row_slice[row];
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int r = NT * g + nt;
+                if (r < R) v[p][nt] = (float)((double)U[row * R + r] * W[(int64_t)k * R + r]);
+                m = fmaxf(m, fabsf(v[p][nt]));
+            }
         }
     }
-    float m = fmaxf(fmaxf(fabsf(v[0]), fabsf(v[1])), fmaxf(fabsf(v[2]), fabsf(v[3])));
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
     }
-    if ((t & 31) == 0) {
-        smx[t >> 5] = m;
-        sex[t >> 5] = ex;
-    }
-    __syncthreads();
-    const float mx = fmaxf(fmaxf(smx[0], smx[1]), fmaxf(smx[2], smx[3]));
-    const int exg = max(max(sex[0], sex[1]), max(sex[2], sex[3]));
-    const int eu = xq_exp(mx);
+    const int eu = xq_exp(m);
     const float ts = xq_pow2(10 - eu);
-    if (ok)
-        reinterpret_cast<float4 *>(Ut + gg * pitch)[q] =
-            make_float4(v[0] * ts, v[1] * ts, v[2] * ts, v[3] * ts);
-    if (t == 0) gex[blockIdx.x] = make_int2(exg, eu);
+    uint32_t *blk = Uf + G * ft_ublk(NT);
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        uint4 f;
+        xq_split(v[0][nt] * ts, v[1][nt] * ts, f.x, f.z);
+        xq_split(v[2][nt] * ts, v[3][nt] * ts, f.y, f.w);
+        reinterpret_cast<uint4 *>(blk)[32 * nt + lane] = f;
+    }
+    if (lane == 0) reinterpret_cast<int4 *>(blk)[32 * NT] = make_int4(ft_xscale_exp(ex), eu, 0, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -374,31 +428,44 @@ static __global__ void __launch_bounds__(128) k_utilde(BatchDev b, int R, int pi
 // k_utilde's groups) and the columns [512·by, 512·by + 512).  Warp w takes
 // column group jg = w % njg (64 columns) and the k-steps (16 rows)
 // ks ≡ w / njg (mod nrs) of the CTA's rows, njg = column groups of this CTA,
-// nrs = FT_WARPS / njg.
+// nrs = FT_WARPS / njg.  A stage holds a k-step's 16 X row segments (64
+// columns) and its Ũ fragment block.
 //
 // MMA orientation: D (16 j × 8 r) += Xᵀ (16 j × 16 rows) · Ũ (16 rows × 8 r).
 // Lane (g, tg) holds the k-slots (rows) 2tg, 2tg+1, 2tg+8, 2tg+9 of the
 // k-step; for m-tile t its m-slots g and g+8 are columns
 // jg0 + 32(t/2) + 4g + 2(t%2) + {0, 1}, so the lane reads each row as two
 // float4s (columns jg0 + 4g and jg0 + 32 + 4g); n-slot g of n-tile nt is
-// rank column NT·g + nt, so the lane reads Ũ(row, NT·g .. NT·g + NT - 1).
-// The k-step's X is scaled by 2^(10 - ex), its Ũ comes scaled by 2^(10 - eu)
-// ({ex, eu} from k_utilde), and its product is scaled back by 2^(ex + eu - 20).
+// rank column NT·g + nt (the order of k_utilde's fragments).  The k-step's X
+// is scaled by 2^sxe, its Ũ comes split and scaled by 2^(10 - eu), and its
+// product is scaled back by 2^(eu - 10 - sxe).
 constexpr int FT_THREADS = 256;
 constexpr int FT_WARPS = FT_THREADS / 32;
-constexpr int FT_S = 4;                   // k-steps in flight per warp (a power of 2)
+constexpr int FT_S = 4;                   // stages per warp ring (a power of 2)
 constexpr int FT_JCTA = 512;              // columns per CTA (8 groups of 64)
-constexpr int FT_SLOT = 13;               // float4 per lane per stage: 8 of X, 4 of Ũ, 1 scale
+constexpr int FT_XP = 68;                 // floats per staged X row (≡ 4 mod 8: conflict-free)
 
-__host__ __device__ inline size_t ft_smem() { return (size_t)FT_WARPS * FT_S * FT_SLOT * 32 * 16; }
+__host__ __device__ constexpr int ft_stage(int NT) { return 16 * FT_XP + ft_ublk(NT); }
+__host__ __device__ inline size_t ft_smem(int NT) {
+    return (size_t)FT_WARPS * FT_S * ft_stage(NT) * 4 + (size_t)FT_WARPS * FT_S * 8;
+}
 
 template <int NT>
 __global__ void __launch_bounds__(FT_THREADS, 1)
-    k_f_tc(const float *__restrict__ X, BatchDev b, int J, int R, const float *__restrict__ Ut,
-           const int2 *__restrict__ gex, int64_t rows_per_cta, float *__restrict__ Fpart) {
-    extern __shared__ float4 ft_sm[];
+    k_f_tc(const float *__restrict__ X, BatchDev b, int J, int R, const uint32_t *__restrict__ Uf,
+           int64_t rows_per_cta, float *__restrict__ Fpart, int *__restrict__ err,
+           unsigned long long *__restrict__ pc) {
+    extern __shared__ __align__(16) float ft_sm[];
+    constexpr int STG = ft_stage(NT), UB = ft_ublk(NT);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, tg = lane & 3;
+    float *ring = ft_sm + (size_t)warp * FT_S * STG;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ft_sm + (size_t)FT_WARPS * FT_S * STG) + warp * FT_S;
+    if (lane == 0) {
+        for (int s = 0; s < FT_S; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
     const int jc0 = FT_JCTA * blockIdx.y;
     const int jcn = min(FT_JCTA, J - jc0);
     const int njg = (jcn + 63) / 64;
@@ -407,41 +474,29 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
     const bool active = rs < nrs;
     const int jg0 = jc0 + 64 * jg;
     const bool c0ok = jg0 + 4 * g < J, c1ok = jg0 + 32 + 4 * g < J;
+    const uint32_t xbytes = (uint32_t)min(64, J - jg0) * 4;
     const int64_t run0 = run0_of(b);
     const int64_t gbeg = (int64_t)blockIdx.x * rows_per_cta;
     const int64_t gend = b.N_gen < gbeg + rows_per_cta ? b.N_gen : gbeg + rows_per_cta;
     const int nks = (int)((gend - gbeg + 15) / 16);
     const int my_n = (active && rs < nks) ? (nks - 1 - rs) / nrs + 1 : 0;
-    float4 *ring = ft_sm + (size_t)warp * FT_S * FT_SLOT * 32 + lane;
-    const int roff[4] = {2 * tg, 2 * tg + 1, 2 * tg + 8, 2 * tg + 9};
     int is = 0;
     int64_t ig0 = gbeg + 16 * rs;             // first row of the next k-step to copy
     auto issue = [&]() {
-        if (is < my_n) {
-            float4 *slot = ring + (is & (FT_S - 1)) * FT_SLOT * 32;
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const int64_t gr = ig0 + roff[p];
-                const bool rv = gr < gend;
-                const float *xr = X + (rv ? gen_row_fast(b, run0, gr) : 0) * (int64_t)J + jg0 + 4 * g;
-                cpa16(slot + (2 * p) * 32, (rv && c0ok) ? xr : X, rv && c0ok);
-                cpa16(slot + (2 * p + 1) * 32, (rv && c1ok) ? xr + 32 : X, rv && c1ok);
-                const float *ur = rv ? Ut + gr * (8 * NT) + NT * g : Ut;
-                float *ud = reinterpret_cast<float *>(slot + (8 + p) * 32);
-                if constexpr (NT == 4) {
-                    cpa16(ud, ur, rv);
-                } else if constexpr (NT == 2) {
-                    cpa8(ud, ur, rv);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < NT; ++c) cpa4(ud + c, rv ? ur + c : Ut, rv);
-                }
-            }
-            cpa8(slot + 12 * 32, gex + ig0 / 16, true);
-            ig0 += 16 * nrs;
+        if (is >= my_n) return;
+        const int s = is & (FT_S - 1);
+        const int nv = (int)(gend - ig0 < 16 ? gend - ig0 : 16);
+        float *st = ring + (size_t)s * STG;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (lane == 0) mbar_expect_tx(&bars[s], (uint32_t)nv * xbytes + (uint32_t)UB * 4);
+        __syncwarp();
+        if (lane < nv) {
+            const int64_t row = gen_row_fast(b, run0, ig0 + lane);
+            bulk_g2s(st + lane * FT_XP, X + row * (int64_t)J + jg0, xbytes, &bars[s]);
         }
+        if (lane == 31) bulk_g2s(st + 16 * FT_XP, Uf + (ig0 / 16) * UB, (uint32_t)UB * 4, &bars[s]);
+        ig0 += 16 * nrs;
         ++is;
-        cpa_commit();
     };
 #pragma unroll
     for (int i = 0; i < FT_S - 1; ++i) issue();
@@ -452,29 +507,56 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
         for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[t][nt][e] = 0.f;
-    for (int i = 0; i < my_n; ++i) {
+    const int roff[4] = {2 * tg, 2 * tg + 1, 2 * tg + 8, 2 * tg + 9};
+    bool aborted = false;
+    int i = 0;
+    int64_t cg0 = gbeg + 16 * rs;             // first row of the k-step being computed
+    long long cw = 0;                         // profiling: cycles waiting on stages
+    const long long c0 = pc ? clock64() : 0;
+    for (; i < my_n; ++i) {
         issue();
-        cpa_wait<FT_S - 1>();
-        const float4 *slot = ring + (i & (FT_S - 1)) * FT_SLOT * 32;
-        const int2 sc = *reinterpret_cast<const int2 *>(slot + 12 * 32);
-        const float sx = xq_pow2(10 - sc.x), tu = xq_pow2(sc.x - 10) * xq_pow2(sc.y - 10);
-        float4 xv[4][2];
-        float4 uv[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            xv[p][0] = f4scale(slot[(2 * p) * 32], sx);
-            xv[p][1] = f4scale(slot[(2 * p + 1) * 32], sx);
-            uv[p] = slot[(8 + p) * 32];
+        const int s = i & (FT_S - 1);
+        const long long w0 = pc ? clock64() : 0;
+        if (!sb_wait(&bars[s], (uint32_t)(i / FT_S) & 1u, err)) {
+            aborted = true;
+            break;
         }
-        uint32_t bh[NT][2], bl[NT][2];
+        if (pc) cw += clock64() - w0;
+        const float *st = ring + (size_t)s * STG;
+        const uint4 *ub = reinterpret_cast<const uint4 *>(st + 16 * FT_XP);
+        const int nv = (int)(gend - cg0 < 16 ? gend - cg0 : 16);
+        cg0 += 16 * nrs;
+        const int4 sc = *reinterpret_cast<const int4 *>(ub + 32 * NT);
+        const float tu = xq_pow2(sc.y - 10) * xq_pow2(-sc.x);
+        float4 xv[4][2];
+        uint4 bf[NT];                      // {bh0, bh1, bl0, bl1} of n-tile nt
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (nv == 16 && c0ok && c1ok) {
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const float u0 = nt == 0 ? uv[0].x : nt == 1 ? uv[0].y : nt == 2 ? uv[0].z : uv[0].w;
-            const float u1 = nt == 0 ? uv[1].x : nt == 1 ? uv[1].y : nt == 2 ? uv[1].z : uv[1].w;
-            const float u2 = nt == 0 ? uv[2].x : nt == 1 ? uv[2].y : nt == 2 ? uv[2].z : uv[2].w;
-            const float u3 = nt == 0 ? uv[3].x : nt == 1 ? uv[3].y : nt == 2 ? uv[3].z : uv[3].w;
-            xq_split(u0, u1, bh[nt][0], bl[nt][0]);
-            xq_split(u2, u3, bh[nt][1], bl[nt][1]);
+            for (int p = 0; p < 4; ++p) {
+                const float *xr = st + roff[p] * FT_XP + 4 * g;
+                xv[p][0] = *reinterpret_cast<const float4 *>(xr);
+                xv[p][1] = *reinterpret_cast<const float4 *>(xr + 32);
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const bool rv = roff[p] < nv;
+                const float *xr = st + roff[p] * FT_XP + 4 * g;
+                xv[p][0] = (rv && c0ok) ? *reinterpret_cast<const float4 *>(xr) : z;
+                xv[p][1] = (rv && c1ok) ? *reinterpret_cast<const float4 *>(xr + 32) : z;
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) bf[nt] = ub[32 * nt + lane];
+        __syncwarp();                      // stage s is read: free for its next copy
+        if (sc.x != 0) {                   // X outside the unscaled range: 2^sxe
+            const float sx = xq_pow2(sc.x);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                xv[p][0] = f4scale(xv[p][0], sx);
+                xv[p][1] = f4scale(xv[p][1], sx);
+            }
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -493,19 +575,25 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
             xq_split(v[2][1], v[3][1], a3h, a3l);     // m g+8
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
-                float d[4] = {0.f, 0.f, 0.f, 0.f};
-                xq_mma(d, a0h, a1h, a2h, a3h, bh[nt][0], bh[nt][1]);
-                xq_mma(d, a0h, a1h, a2h, a3h, bl[nt][0], bl[nt][1]);
-                xq_mma(d, a0l, a1l, a2l, a3l, bh[nt][0], bh[nt][1]);
+                float d[4];
+                xq_mma0(d, a0h, a1h, a2h, a3h, bf[nt].x, bf[nt].y);
+                xq_mma(d, a0h, a1h, a2h, a3h, bf[nt].z, bf[nt].w);
+                xq_mma(d, a0l, a1l, a2l, a3l, bf[nt].x, bf[nt].y);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[t][nt][e] = fmaf(d[e], tu, acc[t][nt][e]);
             }
         }
     }
-    cpa_wait<0>();
+    if (aborted) {                         // let the copies already issued land
+        for (int k = i; k < is; ++k) sb_wait(&bars[k & (FT_S - 1)], (uint32_t)(k / FT_S) & 1u, err);
+    }
+    if (pc && lane == 0) {
+        atomicAdd(&pc[0], (unsigned long long)cw);
+        atomicAdd(&pc[1], (unsigned long long)(clock64() - c0));
+    }
     // warps of one column group (row subgroups 1.., in order) add into row
     // subgroup 0, which writes the CTA's partial; the rings are free now
-    float *red_all = reinterpret_cast<float *>(ft_sm);
+    float *red_all = ft_sm;
     for (int rr = 1; rr < nrs; ++rr) {
         __syncthreads();
         float *red = red_all + jg * 512 * NT;

@@ -97,7 +97,9 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
             CK(cudaFuncSetAttribute(k_xq_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             LAUNCH(KK_XQ_TC, k_xq_tc<<<n_xn, XQ_THREADS, smem, st>>>((const float *)X, b, J, R, m->xq_frag,
                                                                      m->xq_bexp, (float *)m->P,
-                                                                     m->xn_part + g_f, m->xe));
+                                                                     m->xn_part + g_f, m->xe, m->d_err,
+                                                                     m->prof.on ? m->prof.d_phase + 11 : nullptr));
+            m->prof.xq_warps = (double)n_xn * XQ_WARPS;
         } else {
             n_xn = (int)((Ng + XV_ROWS - 1) / XV_ROWS);
             LAUNCH(KK_XV, k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, b, J, R, Vmul, (T *)m->P,
@@ -163,20 +165,24 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
         // Ũ = U ∘ w_new, then the F partials on the tensor cores: one CTA per
         // SM, rows in equal shares
         const int NT = (R + 7) / 8;
-        LAUNCH(KK_UTILDE, k_utilde<<<(unsigned)((Ng + 15) / 16), 128, 0, st>>>(b, R, 8 * NT, (const float *)m->U,
-                                                                              s.W, m->xe, m->Ut, m->gex));
         nfb = (int)std::min<int64_t>(m->n_sm, (Ng + 127) / 128);
         const int64_t rpc = ((Ng + nfb - 1) / nfb + 15) / 16 * 16;
         nfb = (int)((Ng + rpc - 1) / rpc);
         dim3 grid(nfb, (J + FT_JCTA - 1) / FT_JCTA);
         float *Fo = (float *)m->Fpart + (size_t)g_f * J * R;
         const float *Xf = (const float *)X;
-        const size_t fsm = ft_smem();
+        m->prof.ft_warps = (double)grid.x * grid.y * FT_WARPS;
+        const unsigned nug = (unsigned)((Ng + 127) / 128);
+        unsigned long long *pc = m->prof.on ? m->prof.d_phase + 13 : nullptr;
         switch (NT) {
 #define FTC(n)                                                                                       \
     case n:                                                                                          \
-        CK(cudaFuncSetAttribute(k_f_tc<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));  \
-        LAUNCH(KK_F_TC, k_f_tc<n><<<grid, FT_THREADS, fsm, st>>>(Xf, b, J, R, m->Ut, m->gex, rpc, Fo));       \
+        LAUNCH(KK_UTILDE, k_utilde<n><<<nug, 256, 0, st>>>(b, R, (const float *)m->U, s.W, m->xe,   \
+                                                            m->Ut));                                 \
+        CK(cudaFuncSetAttribute(k_f_tc<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
+                                (int)ft_smem(n)));                                                   \
+        LAUNCH(KK_F_TC, k_f_tc<n><<<grid, FT_THREADS, ft_smem(n), st>>>(Xf, b, J, R, m->Ut, rpc,    \
+                                                                        Fo, m->d_err, pc));          \
         break;
             FTC(1)
             FTC(2)
@@ -198,12 +204,11 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     LAUNCH(KK_F_REDUCE, k_f_reduce<T><<<((int64_t)J * R + 255) / 256, 256, 0, st>>>((const T *)m->Fpart, g_f + nfb, J, R, lam,
                                                                 s.F, m->Finc));
     LAUNCH(KK_G_REDUCE, k_g_reduce<<<(R * R + 7) / 8, 256, 0, st>>>(m->Gpart, g_f + nsb, R, lam, s.G, m->Ginc));
-    const size_t psm = (size_t)(3 * R * (R + 1) + (R + 1)) * 8;
-    LAUNCH(KK_PINV, k_pinv_small<<<1, 32, psm, st>>>(s.G, R, m->rtol, m->GP, nullptr));
+    if (dash_status e = launch_pinv(m, s.G, m->GP, nullptr)) return e;
     LAUNCH(KK_VUPDATE, k_vupdate<T><<<(J + 7) / 8, 256, 0, st>>>(s.F, m->GP, m->Finc, J, R, s.V, (T *)m->VT,
                                                m->cross_part));
     LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(s.V, J, R, s.Gam));
-    LAUNCH(KK_PINV, k_pinv_small<<<1, 32, psm, st>>>(s.Gam, R, m->rtol, s.GamP, s.gam_ok));
+    if (dash_status e = launch_pinv(m, s.Gam, s.GamP, s.gam_ok)) return e;
     LAUNCH(KK_FITNESS, k_fitness<<<1, 32, 0, st>>>(m->xn_part, g_f + n_xn, m->cross_part, (J + 7) / 8, s.Gam, m->Ginc, R,
                                 s.gam_ok, m->fit));
     CK(cudaMemcpyAsync(m->h_fit, m->fit, 4 * 8, cudaMemcpyDeviceToHost, st));
