@@ -290,6 +290,7 @@ static dash_status init_alloc(dash_model *m) {
     if (m->fused_ok) {
         DALLOC(m->Ut, (size_t)(Nm / 16 + 2) * ft_ublk((R + 7) / 8) * 4, "U o w fragments");
         DALLOC(m->xe, (size_t)(Nm + 16) * 4, "row exponents");
+        DALLOC(m->Wf, (size_t)Km * R * 4, "w_new (FP32)");
     }
     // FP64 fallback workspace: one slot per warp of a grid of at most 2 CTAs per SM
     DALLOC(m->wsp, (size_t)2 * m->n_sm * FU_WARPS * fu_wsp_doubles((int)R) * 8, "fallback workspace");

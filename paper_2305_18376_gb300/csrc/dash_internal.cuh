@@ -122,6 +122,7 @@ struct dash_model {
     int *xq_bexp = nullptr;           // power-of-two scale of those fragments
     uint32_t *Ut = nullptr;           // Ũ = U ∘ w_new as MMA fragment blocks of 16 rows
     int *xe = nullptr;                // exponent of each general row's max |x|
+    float *Wf = nullptr;              // FP32 copy of the finished slices' new weights
     // general rows: runs of consecutive rows left to the general kernels
     int64_t *d_run_g0 = nullptr, *d_run_row0 = nullptr;
     int64_t *h_run_g0 = nullptr, *h_run_row0 = nullptr;

@@ -66,6 +66,7 @@ struct FusedArgs {
     const int64_t *seg_row;
     const int *seg_slice;
     double *W;                // K×R
+    float *Wf;                // K×R FP32 copy of the new weights (optional)
     df *c;                    // K×R
     df *D;                    // K×R×R
     float *U;                 // N×R output rows
@@ -241,9 +242,10 @@ __device__ __forceinline__ float chol_solve_reg(const float (&row)[FU_RP], const
 // row), A = Γ ∗ D_k is kept as double-float pairs, and the Cholesky factor is
 // formed right-looking with the pivot column broadcast by shuffles.  Lw (a
 // per-warp R×FU_LD float block) only carries L for the backward solve.
+template <bool GSM = false>
 __device__ __forceinline__ float slice_finish(const FusedArgs &a, int k, const float (&dd)[FU_RP],
                                               float dc, float (&gacc)[FU_RP], const df *Gs,
-                                              float *Lw, df *xw, double *wsp) {
+                                              float *Lw, df *xw, double *wsp, float *gsm = nullptr) {
     (void)xw;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -346,11 +348,16 @@ __device__ __forceinline__ float slice_finish(const FusedArgs &a, int k, const f
         if (lane == 0) atomicAdd(&a.err[1], 1);
     }
     if (act) a.W[(int64_t)k * R + lane] = wnew_d;
+    if (act && a.Wf) a.Wf[(int64_t)k * R + lane] = (float)wnew_d;
     const float wnew = (float)wnew_d;
 #pragma unroll
     for (int q = 0; q < FU_RP; ++q) {
         const float wq = __shfl_sync(full, wnew, q);
-        if (act && q < R) gacc[q] = fmaf(wnew * dd[q], wq, gacc[q]);
+        if constexpr (GSM) {               // row `lane` of the warp's block (pitch FU_LD)
+            if (act && q < R) gsm[lane * FU_LD + q] = fmaf(wnew * dd[q], wq, gsm[lane * FU_LD + q]);
+        } else {
+            if (act && q < R) gacc[q] = fmaf(wnew * dd[q], wq, gacc[q]);
+        }
     }
     __syncwarp();
     return wnew;
@@ -1198,19 +1205,38 @@ static __global__ void __launch_bounds__(256, 2) k_big_b(FusedArgs a, BigArgs bg
     }
 }
 
-static __global__ void __launch_bounds__(256) k_big_c(FusedArgs a, BigArgs bg, double *Gpart_out) {
+// (two CTAs per SM: each warp keeps its G partial in shared memory, not in
+// registers)
+static __global__ void __launch_bounds__(256, 2) k_big_c(FusedArgs a, BigArgs bg, double *Gpart_out) {
     __shared__ df Gs[FU_RP * FU_RP];
-    __shared__ __align__(16) float Lw_all[FU_WARPS][FU_RP * FU_LD];   // also the G reduction
+    __shared__ __align__(16) float Lw_all[FU_WARPS][FU_RP * FU_LD];
+    __shared__ float G_all[FU_WARPS][FU_RP * FU_LD];                  // per-warp G partials
     __shared__ df xw_all[FU_WARPS][FU_RP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = a.R;
     for (int i = threadIdx.x; i < R * R; i += blockDim.x) Gs[(i / R) * FU_RP + (i % R)] = a.Gdf[i];
+    for (int i = threadIdx.x; i < FU_WARPS * FU_RP * FU_LD; i += blockDim.x) (&G_all[0][0])[i] = 0.f;
     __syncthreads();
-    float gacc[FU_RP];
-#pragma unroll
-    for (int q = 0; q < FU_RP; ++q) gacc[q] = 0.f;
+    float gacc[FU_RP];                      // unused: the partials live in G_all
     double *wsp = a.wsp + (size_t)(blockIdx.x * FU_WARPS + warp) * fu_wsp_doubles(R);
+    // bring the next slice's state (D_k, c_k, W(k,:)) and chunk partials into
+    // L2 while this one is finished
+    auto prefetch = [&](int f2) {
+        if (f2 >= bg.n_fin) return;
+        const int k2 = bg.fin_k[f2];
+        const char *dk = reinterpret_cast<const char *>(a.D + (int64_t)k2 * R * R);
+        for (int l = lane; l < (R * R * 8 + 127) / 128; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(dk + 128 * l));
+        if (lane == 0) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(a.c + (int64_t)k2 * R)));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(a.W + (int64_t)k2 * R)));
+        }
+        const int c0 = bg.fin_c0[f2], c1 = bg.fin_c0[f2 + 1];
+        const char *dp = reinterpret_cast<const char *>(bg.dpart + (size_t)c0 * (R * R + R));
+        const int nl = (int)(((size_t)(c1 - c0) * (R * R + R) * 4 + 127) / 128);
+        for (int l = lane; l < nl; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(dp + 128 * l));
+    };
     for (int f = blockIdx.x * FU_WARPS + warp; f < bg.n_fin; f += gridDim.x * FU_WARPS) {
+        prefetch(f + gridDim.x * FU_WARPS);
         const int k = bg.fin_k[f];
         float dd[FU_RP];
 #pragma unroll
@@ -1225,17 +1251,13 @@ static __global__ void __launch_bounds__(256) k_big_c(FusedArgs a, BigArgs bg, d
                 dc += in[R * R + lane];
             }
         }
-        slice_finish(a, k, dd, dc, gacc, Gs, Lw_all[warp], xw_all[warp], wsp);
+        slice_finish<true>(a, k, dd, dc, gacc, Gs, Lw_all[warp], xw_all[warp], wsp, G_all[warp]);
     }
-    __syncthreads();
-    float *gsm = &Lw_all[0][0];             // FU_WARPS × FU_RP × FU_RP floats fit in Lw_all
-#pragma unroll
-    for (int q = 0; q < FU_RP; ++q) gsm[(warp * FU_RP + lane) * FU_RP + q] = gacc[q];
     __syncthreads();
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
         const int r = e / R, q = e % R;
         double s = 0.0;
-        for (int w = 0; w < FU_WARPS; ++w) s += (double)gsm[(w * FU_RP + r) * FU_RP + q];
+        for (int w = 0; w < FU_WARPS; ++w) s += (double)G_all[w][r * FU_LD + q];
         Gpart_out[(int64_t)blockIdx.x * R * R + e] = s;
     }
 }

@@ -362,8 +362,9 @@ static __global__ void __launch_bounds__(XQ_THREADS, 1)
 
 // ---------------------------------------------------------------------------
 // Ũ for k_f_tc as MMA B fragments, one warp per 16-row group G of the
-// general rows.  Ũ(g, r) = U(row, r)·w_k,new(r) (rounded once from the FP64
-// product) is scaled by 2^(10 - eu), eu the exponent of the group's max |Ũ|,
+// general rows.  Ũ(g, r) = U(row, r)·w_k,new(r) (FP32 product with the FP32
+// copy of w_new: the FP64 pipe is far too narrow for a per-row product) is
+// scaled by 2^(10 - eu), eu the exponent of the group's max |Ũ|,
 // and split into FP16 hi + lo.  Block G (ft_ublk(NT) 32-bit words at
 // Uf + G·ft_ublk(NT)) holds, for n-tile nt and lane L = (g, tg), the word
 // quadruple {bh0, bh1, bl0, bl1} at words 4(32nt + L) ..: bh0 packs the hi
@@ -375,7 +376,7 @@ __host__ __device__ constexpr int ft_ublk(int NT) { return 128 * NT + 4; }
 
 template <int NT>
 __global__ void __launch_bounds__(256) k_utilde(BatchDev b, int R, const float *__restrict__ U,
-                                                const double *__restrict__ W,
+                                                const float *__restrict__ Wf,
                                                 const int *__restrict__ xe,
                                                 uint32_t *__restrict__ Uf) {
     const int lane = threadIdx.x & 31;
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(256) k_utilde(BatchDev b, int R, const float *
     float v[4][NT];
     float m = 0.f;
     int ex = -60;
-    if (lane < 16 && 16 * G + lane < b.N_gen) ex = xe[16 * G + lane];
+    if (lane < 16 && 16 * G + lane < b.N_gen) ex = __ldcg(xe + 16 * G + lane);
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const int64_t gg = 16 * G + roff[p];
@@ -395,13 +396,23 @@ __global__ void __launch_bounds__(256) k_utilde(BatchDev b, int R, const float *
         for (int nt = 0; nt < NT; ++nt) v[p][nt] = 0.f;
         if (gg < b.N_gen) {
             const int64_t row = gen_row_fast(b, run0, gg);
-            const int k = b.row_slice[row];
+            const int k = __ldcg(b.row_slice + row);
+            if (NT == 4 && R == 32) {      // 16-byte aligned: one float4 of U, one of w
+                const float4 u4 = __ldcg(reinterpret_cast<const float4 *>(U + row * 32 + 4 * g));
+                const float4 w4 = __ldcg(reinterpret_cast<const float4 *>(Wf + (int64_t)k * 32 + 4 * g));
+                v[p][0] = u4.x * w4.x;
+                v[p][1] = u4.y * w4.y;
+                v[p][2] = u4.z * w4.z;
+                v[p][3] = u4.w * w4.w;
+            } else {
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const int r = NT * g + nt;
-                if (r < R) v[p][nt] = (float)((double)U[row * R + r] * W[(int64_t)k * R + r]);
-                m = fmaxf(m, fabsf(v[p][nt]));
+                for (int nt = 0; nt < NT; ++nt) {
+                    const int r = NT * g + nt;
+                    if (r < R) v[p][nt] = U[row * R + r] * Wf[(int64_t)k * R + r];
+                }
             }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) m = fmaxf(m, fabsf(v[p][nt]));
         }
     }
 #pragma unroll

@@ -38,7 +38,7 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
         }
         if (m->fused_active && m->n_tiles > 0) {
             g_f = std::min(m->n_sm, m->n_tiles);
-            FusedArgs fa;
+            FusedArgs fa{};
             fa.X = X;
             fa.J = J;
             fa.R = R;
@@ -122,6 +122,7 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
             fa.Gam = s.Gam;
             fa.gam_ok = s.gam_ok;
             fa.W = s.W;
+            fa.Wf = split ? m->Wf : nullptr;
             fa.c = reinterpret_cast<df *>(s.c);
             fa.D = reinterpret_cast<df *>(s.D);
             fa.U = (float *)m->U;
@@ -177,7 +178,7 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
         switch (NT) {
 #define FTC(n)                                                                                       \
     case n:                                                                                          \
-        LAUNCH(KK_UTILDE, k_utilde<n><<<nug, 256, 0, st>>>(b, R, (const float *)m->U, s.W, m->xe,   \
+        LAUNCH(KK_UTILDE, k_utilde<n><<<nug, 256, 0, st>>>(b, R, (const float *)m->U, m->Wf, m->xe, \
                                                             m->Ut));                                 \
         CK(cudaFuncSetAttribute(k_f_tc<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
                                 (int)ft_smem(n)));                                                   \
