@@ -385,6 +385,7 @@ extern "C" dash_status dash_init(const dash_config *cfg, dash_model **out) {
     }
     cudaEventCreate(&m->ev0);
     cudaEventCreate(&m->ev1);
+    cudaEventCreateWithFlags(&m->ev_meta, cudaEventDisableTiming);
     st = init_alloc(m);
     if (st != DASH_OK) {
         fprintf(stderr, "dash_init: %s\n", m->err.c_str());
@@ -410,6 +411,7 @@ extern "C" void dash_destroy(dash_model *m) {
     free_all(m);
     cudaEventDestroy(m->ev0);
     cudaEventDestroy(m->ev1);
+    if (m->ev_meta) cudaEventDestroy(m->ev_meta);
     if (m->own_stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -900,16 +902,21 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
                               const int64_t *rp /* n_seg+1 absolute */, int64_t K_old,
                               int64_t n_new, const void *X, bool allow_fused, BatchDev *b) {
     const int64_t K_all = K_old + n_new;
-    CK(cudaStreamSynchronize(m->stream));   // pinned metadata buffers are reused
-    m->gam_ok_host = m->h_fit[3] != 0.0;
-    if (m->h_err[0] > 0) return fail(m, DASH_ETIMEOUT, "a bounded device wait timed out");
-    if (m->h_err[2] > 0)
-        return fail(m, DASH_ENUMERIC, "%d slice factors came out non-finite", m->h_err[2]);
+    // The pinned metadata buffers are rewritten below: wait until the last
+    // batch's copies out of them have run (they open that update, so this
+    // seldom waits).  The host planning then overlaps the previous update on
+    // the GPU.  It assumes the last known state of Γ (nonsingular or not) and
+    // is redone in the rare case that the previous update changed it.
+    CK(cudaEventSynchronize(m->ev_meta));
+    bool gam_ok = m->gam_ok_host;
+    int n_touch = 0, nt = 0, nr = 0;
+    int64_t ng = 0;
+    for (int pass = 0;; ++pass) {
     int *tslot = m->h_tslot;
     for (int64_t k = 0; k < K_all; ++k) tslot[k] = -1;
     std::vector<int> cnt;
     cnt.reserve(1024);
-    int n_touch = 0;
+    n_touch = 0;
     for (int64_t s = 0; s < n_seg; ++s) {
         const int64_t k = ids[s];
         if (tslot[k] < 0) {
@@ -919,8 +926,7 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
         cnt[tslot[k]] += 1;
     }
     // which segments the fused kernel finishes
-    const bool fused = allow_fused && m->fused_ok && m->gam_ok_host &&
-                       ((uintptr_t)X % 16) == 0;
+    const bool fused = allow_fused && m->fused_ok && gam_ok && ((uintptr_t)X % 16) == 0;
     // split: no tiles, every touched slice through the chunked path
     const bool split = fused && m->cfg.precision == DASH_PREC_F16X3 &&
                        (m->row_path == DASH_ROWS_SPLIT || (m->row_path == DASH_ROWS_AUTO && kAutoSplit));
@@ -994,17 +1000,10 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
         m->h_fin_c0[nf] = nc;
         m->n_chunks = nc;
         m->n_fin = nf;
-        if (nc > 0) {
-            CK(cudaMemcpyAsync(m->d_ch_row0, m->h_ch_row0, nc * 8, cudaMemcpyHostToDevice, m->stream));
-            CK(cudaMemcpyAsync(m->d_ch_n, m->h_ch_n, nc * 4, cudaMemcpyHostToDevice, m->stream));
-            CK(cudaMemcpyAsync(m->d_ch_k, m->h_ch_k, nc * 4, cudaMemcpyHostToDevice, m->stream));
-        }
-        if (nf > 0) CK(cudaMemcpyAsync(m->d_fin_k, m->h_fin_k, nf * 4, cudaMemcpyHostToDevice, m->stream));
-        CK(cudaMemcpyAsync(m->d_fin_c0, m->h_fin_c0, (nf + 1) * 4, cudaMemcpyHostToDevice, m->stream));
     }
     for (int64_t s = 0; s <= n_seg; ++s) m->h_seg_row[s] = rp[s];
     // tiles: runs of consecutive fused segments with <= FU_TILE_MAX rows
-    int nt = 0;
+    nt = 0;
     {
         int64_t s = 0;
         while (s < n_seg) {
@@ -1033,8 +1032,8 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
         m->plan_tiles = nt;
     }
     // general runs: maximal runs of consecutive non-fused segments
-    int nr = 0;
-    int64_t ng = 0;
+    nr = 0;
+    ng = 0;
     {
         int64_t s = 0;
         while (s < n_seg) {
@@ -1054,6 +1053,30 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
     // with the fused path on, the rows outside tiles go through the chunked path
     m->plan_chunk_rows = fused ? ng : 0;
     m->plan_general_rows = fused ? 0 : ng;
+    if (pass == 0) {
+        CK(cudaStreamSynchronize(m->stream));   // the previous update has finished
+        m->gam_ok_host = m->h_fit[3] != 0.0;
+        if (m->h_err[0] > 0) return fail(m, DASH_ETIMEOUT, "a bounded device wait timed out");
+        if (m->h_err[2] > 0)
+            return fail(m, DASH_ENUMERIC, "%d slice factors came out non-finite", m->h_err[2]);
+        if (m->gam_ok_host != gam_ok) {
+            gam_ok = m->gam_ok_host;
+            continue;
+        }
+    }
+    break;
+    }
+    if (m->n_chunks > 0) {
+        const int nc = m->n_chunks;
+        CK(cudaMemcpyAsync(m->d_ch_row0, m->h_ch_row0, nc * 8, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->d_ch_n, m->h_ch_n, nc * 4, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->d_ch_k, m->h_ch_k, nc * 4, cudaMemcpyHostToDevice, m->stream));
+    }
+    if (m->fused_active) {
+        const int nf = m->n_fin;
+        if (nf > 0) CK(cudaMemcpyAsync(m->d_fin_k, m->h_fin_k, nf * 4, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->d_fin_c0, m->h_fin_c0, (nf + 1) * 4, cudaMemcpyHostToDevice, m->stream));
+    }
     if (n_seg > 0) {
         CK(cudaMemcpyAsync(m->d_seg_slice, m->h_seg_slice, n_seg * 4, cudaMemcpyHostToDevice, m->stream));
         CK(cudaMemcpyAsync(m->d_tseg_idx, m->h_tseg_idx, n_seg * 4, cudaMemcpyHostToDevice, m->stream));
@@ -1067,6 +1090,7 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
     }
     CK(cudaMemcpyAsync(m->d_run_g0, m->h_run_g0, (nr + 1) * 8, cudaMemcpyHostToDevice, m->stream));
     if (nr > 0) CK(cudaMemcpyAsync(m->d_run_row0, m->h_run_row0, nr * 8, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaEventRecord(m->ev_meta, m->stream));
     const int64_t N = n_seg ? rp[n_seg] : 0;
     b->n_seg = (int)n_seg;
     b->n_touch = n_touch;

@@ -64,6 +64,7 @@ struct dash_model {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev_meta = nullptr;    // after a batch's metadata copies (pinned buffers free)
     double rtol = 0.0;
     size_t tsize = 4;                 // bytes of the product arithmetic type
     bool df_state = false;            // c, D stored as double-float pairs

@@ -11,8 +11,9 @@
 // are scaled by powers of two so that their maxima lie in [512, 1024): then a
 // lo half that leaves FP16's normal range is below 2^-35 of the maximum, and
 // each operand keeps ~22 significant bits.  Every k-step (or group of
-// k-steps with one scale) starts a fresh MMA accumulator, which is scaled
-// back and added to the FP32 running sum with a rounded FMA.
+// k-steps with one scale) starts fresh MMA accumulators, one for the hi·hi
+// terms and one for the two correction terms, which are scaled back and added
+// to the FP32 running sum with rounded FP32 arithmetic.
 //
 // Data movement: each warp streams its own stages of X (16 rows × 64
 // columns) through a ring in shared memory with 1-D bulk copies (one copy per
@@ -107,10 +108,8 @@ __device__ __forceinline__ int64_t gen_row_fast(const BatchDev &b, int64_t run0,
 }
 
 // X scale exponent from a row (or row group) max |x| = f·2^ex, f in [0.5, 1):
-// none while max |x| lies in [2^3, 2^14) (the FP16 split of unscaled X then
-// keeps ~28 bits relative to the group's max: a lo half below FP16's normal
-// range is under 2^-25, hi stays below 2^14), else 2^(10 - ex).
-__host__ __device__ inline int ft_xscale_exp(int ex) { return (ex >= 4 && ex <= 14) ? 0 : 10 - ex; }
+// the scale 2^(10 - ex) brings that max into [512, 1024).
+__host__ __device__ inline int ft_xscale_exp(int ex) { return 10 - ex; }
 
 // Power-of-two exponent bexp that brings max |B| into [512, 1024), clamped
 // to [-40, 40]; B is J×R.  One warp.
@@ -276,10 +275,8 @@ static __global__ void __launch_bounds__(XQ_THREADS, 1)
         m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 2));
         rm0 = fmaxf(rm0, m0);
         rm1 = fmaxf(rm1, m1);
-        // rows whose max lies in [2^3, 2^14) go unscaled (see ft_xscale_exp);
-        // the multiplies are skipped when that holds for the warp's 16 rows
         const int x0 = ft_xscale_exp(xq_exp(m0)), x1 = ft_xscale_exp(xq_exp(m1));
-        if (__any_sync(0xffffffffu, (x0 | x1) != 0)) {
+        {
             const float s0 = xq_pow2(x0), s1 = xq_pow2(x1);
 #pragma unroll
             for (int u = 0; u < XQ_KU; ++u) {
@@ -287,11 +284,14 @@ static __global__ void __launch_bounds__(XQ_THREADS, 1)
                 xv[u][1] = f4scale(xv[u][1], s1);
             }
         }
-        float d[4][4];
+        // main (hi·hi) and correction (hi·lo + lo·hi) terms in separate MMA
+        // accumulators, added in FP32 after the stage: the small corrections
+        // never pass through the accumulator that holds the large terms
+        float d[4][4], dc[4][4];
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) d[nt][e] = 0.f;
+            for (int e = 0; e < 4; ++e) d[nt][e] = dc[nt][e] = 0.f;
 #pragma unroll
         for (int u = 0; u < XQ_KU; ++u) {
             const int kk = kg * XQ_KU + u;
@@ -308,8 +308,8 @@ static __global__ void __launch_bounds__(XQ_THREADS, 1)
                     if (nt < nnt) {
                         const uint4 f = fr[nt * 32];
                         xq_mma(d[nt], a0h, a1h, a2h, a3h, f.x, f.y);
-                        xq_mma(d[nt], a0h, a1h, a2h, a3h, f.z, f.w);
-                        xq_mma(d[nt], a0l, a1l, a2l, a3l, f.x, f.y);
+                        xq_mma(dc[nt], a0h, a1h, a2h, a3h, f.z, f.w);
+                        xq_mma(dc[nt], a0l, a1l, a2l, a3l, f.x, f.y);
                     }
                 }
             }
@@ -317,10 +317,10 @@ static __global__ void __launch_bounds__(XQ_THREADS, 1)
         const float u0 = xq_pow2(-x0), u1 = xq_pow2(-x1);
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
-            acc[nt][0] = fmaf(d[nt][0], u0, acc[nt][0]);
-            acc[nt][1] = fmaf(d[nt][1], u0, acc[nt][1]);
-            acc[nt][2] = fmaf(d[nt][2], u1, acc[nt][2]);
-            acc[nt][3] = fmaf(d[nt][3], u1, acc[nt][3]);
+            acc[nt][0] = fmaf(d[nt][0] + dc[nt][0], u0, acc[nt][0]);
+            acc[nt][1] = fmaf(d[nt][1] + dc[nt][1], u0, acc[nt][1]);
+            acc[nt][2] = fmaf(d[nt][2] + dc[nt][2], u1, acc[nt][2]);
+            acc[nt][3] = fmaf(d[nt][3] + dc[nt][3], u1, acc[nt][3]);
         }
         if (++kg == nkg) {
             kg = 0;
@@ -452,13 +452,16 @@ __global__ void __launch_bounds__(256) k_utilde(BatchDev b, int R, const float *
 // product is scaled back by 2^(eu - 10 - sxe).
 constexpr int FT_THREADS = 256;
 constexpr int FT_WARPS = FT_THREADS / 32;
-constexpr int FT_S = 4;                   // stages per warp ring (a power of 2)
+constexpr int FT_S = 3;                   // stages per warp ring
 constexpr int FT_JCTA = 512;              // columns per CTA (8 groups of 64)
 constexpr int FT_XP = 68;                 // floats per staged X row (≡ 4 mod 8: conflict-free)
+constexpr int FT_FLUSH = 16;              // k-steps summed in registers before the smem sum
 
 __host__ __device__ constexpr int ft_stage(int NT) { return 16 * FT_XP + ft_ublk(NT); }
+// rings, then per warp its FP32 accumulator (512·NT floats), then the barriers
 __host__ __device__ inline size_t ft_smem(int NT) {
-    return (size_t)FT_WARPS * FT_S * ft_stage(NT) * 4 + (size_t)FT_WARPS * FT_S * 8;
+    return (size_t)FT_WARPS * FT_S * ft_stage(NT) * 4 + (size_t)FT_WARPS * 512 * NT * 4 +
+           (size_t)FT_WARPS * FT_S * 8;
 }
 
 template <int NT>
@@ -471,11 +474,17 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, tg = lane & 3;
     float *ring = ft_sm + (size_t)warp * FT_S * STG;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(ft_sm + (size_t)FT_WARPS * FT_S * STG) + warp * FT_S;
+    // Two-level sum: FT_FLUSH k-steps in registers, then into the warp's FP32
+    // block in shared memory (slot ((t·NT + nt)·4 + e)·32 + lane), so no FP32
+    // running sum takes more than a few dozen terms.
+    float *wacc = ft_sm + (size_t)FT_WARPS * FT_S * STG + (size_t)warp * 512 * NT;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ft_sm + (size_t)FT_WARPS * FT_S * STG +
+                                                  (size_t)FT_WARPS * 512 * NT) + warp * FT_S;
     if (lane == 0) {
         for (int s = 0; s < FT_S; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int e = lane; e < 512 * NT; e += 32) wacc[e] = 0.f;
     __syncwarp();
     const int jc0 = FT_JCTA * blockIdx.y;
     const int jcn = min(FT_JCTA, J - jc0);
@@ -495,7 +504,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
     int64_t ig0 = gbeg + 16 * rs;             // first row of the next k-step to copy
     auto issue = [&]() {
         if (is >= my_n) return;
-        const int s = is & (FT_S - 1);
+        const int s = is % FT_S;
         const int nv = (int)(gend - ig0 < 16 ? gend - ig0 : 16);
         float *st = ring + (size_t)s * STG;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -526,7 +535,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
     const long long c0 = pc ? clock64() : 0;
     for (; i < my_n; ++i) {
         issue();
-        const int s = i & (FT_S - 1);
+        const int s = i % FT_S;
         const long long w0 = pc ? clock64() : 0;
         if (!sb_wait(&bars[s], (uint32_t)(i / FT_S) & 1u, err)) {
             aborted = true;
@@ -561,7 +570,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) bf[nt] = ub[32 * nt + lane];
         __syncwarp();                      // stage s is read: free for its next copy
-        if (sc.x != 0) {                   // X outside the unscaled range: 2^sxe
+        {                                  // X scale of the group: 2^sxe
             const float sx = xq_pow2(sc.x);
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
@@ -585,23 +594,41 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
             xq_split(v[2][0], v[3][0], a2h, a2l);     // m g,   k 2tg+8, 2tg+9
             xq_split(v[2][1], v[3][1], a3h, a3l);     // m g+8
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                float d[4];
+            for (int nt = 0; nt < NT; ++nt) {   // main and correction terms apart
+                float d[4], dc[4];
                 xq_mma0(d, a0h, a1h, a2h, a3h, bf[nt].x, bf[nt].y);
-                xq_mma(d, a0h, a1h, a2h, a3h, bf[nt].z, bf[nt].w);
-                xq_mma(d, a0l, a1l, a2l, a3l, bf[nt].x, bf[nt].y);
+                xq_mma0(dc, a0h, a1h, a2h, a3h, bf[nt].z, bf[nt].w);
+                xq_mma(dc, a0l, a1l, a2l, a3l, bf[nt].x, bf[nt].y);
 #pragma unroll
-                for (int e = 0; e < 4; ++e) acc[t][nt][e] = fmaf(d[e], tu, acc[t][nt][e]);
+                for (int e = 0; e < 4; ++e) acc[t][nt][e] = fmaf(d[e] + dc[e], tu, acc[t][nt][e]);
             }
+        }
+        if ((i + 1) % FT_FLUSH == 0 || i + 1 == my_n) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        float &w = wacc[((t * NT + nt) * 4 + e) * 32 + lane];
+                        w += acc[t][nt][e];
+                        acc[t][nt][e] = 0.f;
+                    }
         }
     }
     if (aborted) {                         // let the copies already issued land
-        for (int k = i; k < is; ++k) sb_wait(&bars[k & (FT_S - 1)], (uint32_t)(k / FT_S) & 1u, err);
+        for (int k = i; k < is; ++k) sb_wait(&bars[k % FT_S], (uint32_t)(k / FT_S) & 1u, err);
     }
     if (pc && lane == 0) {
         atomicAdd(&pc[0], (unsigned long long)cw);
         atomicAdd(&pc[1], (unsigned long long)(clock64() - c0));
     }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[t][nt][e] = wacc[((t * NT + nt) * 4 + e) * 32 + lane];
     // warps of one column group (row subgroups 1.., in order) add into row
     // subgroup 0, which writes the CTA's partial; the rings are free now
     float *red_all = ft_sm;
