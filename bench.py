@@ -134,8 +134,9 @@ def algorithmic(kernel: str, plan: dict, N: int, K_all: int, J: int, R: int, tsi
         return tr * J * isize + tr * R * 4 + ts * per_slice, 4 * tr * J * R
     if kernel == "k_xq_tc":              # X read, P' written (chunked-path rows)
         return cr * J * isize + cr * R * 4, 2 * cr * J * R
-    if kernel == "k_f_tc":               # X and U read, the row's slice id
-        return cr * J * isize + cr * R * 4 + cr * 4, 2 * cr * J * R
+    if kernel == "k_f_tc":               # X read, Ũ fragment blocks (16 rows each) read
+        nt = -(-R // 8)
+        return cr * J * isize + -(-cr // 16) * (512 * nt + 16), 2 * cr * J * R
     if kernel == "k_utilde":             # U read, U ∘ w written (rank padded to 8)
         return cr * R * 4 + cr * (-(-R // 8) * 8) * 4, cr * R
     if kernel == "k_xv":
@@ -441,10 +442,14 @@ def run_ours(a):
         t0 = time.perf_counter()
         h2d = d2h = 0
         erows = 0
+        b, hx = hosts[0]
+        m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), hx)
         for i in range(len(timed)):
             b, hx = hosts[i % len(hosts)]
-            m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), hx)
             m.update()
+            if i + 1 < len(timed):                # the next step's copy overlaps this update
+                nb, nhx = hosts[(i + 1) % len(hosts)]
+                m.append_batch(nb.slice_ids.numpy(), nb.row_ptr.numpy(), nhx)
             m.fitness()                           # D2H read of the step's result
             h2d += hx.numel() * hx.element_size() + 16 * b.slice_ids.numel()
             d2h += 24

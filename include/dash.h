@@ -78,8 +78,9 @@ typedef struct dash_config {
     int64_t max_rows;       /* capacity of rows per update (scratch sizing)      */
     int64_t max_segments;   /* capacity of segments per update                   */
     void *stream;           /* cudaStream_t to run on; NULL = a private stream   */
-    int64_t max_staged_rows;/* rows the append_* staging buffer holds; 0 = max_rows
-                               (device-resident batches need no staging)       */
+    int64_t max_staged_rows;/* rows each of the two append_* staging buffers
+                               holds; 0 = max_rows (device-resident batches
+                               need no staging)                                */
 } dash_config;
 
 /* Fill *cfg with defaults for (J, R, λ): mode P, FP32 products, FP32 input,
@@ -151,7 +152,10 @@ dash_status dash_append_slices(dash_model *m, int64_t L, const int64_t *I,
  * create new slices, which must be numbered consecutively and appear in
  * ascending order.  slice_ids and row_ptr are host arrays; X is at `where`
  * and is copied (host → device with cudaMemcpyAsync; pinned memory lets
- * it overlap). */
+ * it overlap).  Staging alternates between two device buffers, so a batch
+ * may be appended while the previous update still runs; a host X of 64 MiB
+ * or more is split over several copy streams and copied in the background:
+ * keep it unchanged until the next dash_update() returns. */
 dash_status dash_append_batch(dash_model *m, int64_t n_seg, const int64_t *slice_ids,
                               const int64_t *row_ptr, const void *X, int32_t where);
 

@@ -260,7 +260,9 @@ static dash_status init_alloc(dash_model *m) {
     }
     // staging and batch metadata
     m->stage_cap = c.max_staged_rows > 0 ? std::min<int64_t>(c.max_staged_rows, Nm) : Nm;
-    DALLOC(m->Xs, m->stage_cap * J * ie, "staged X");
+    DALLOC(m->Xs_buf[0], m->stage_cap * J * ie, "staged X");
+    DALLOC(m->Xs_buf[1], m->stage_cap * J * ie, "staged X");
+    m->Xs = m->Xs_buf[0];
     DALLOC(m->d_seg_slice, Sm * 4, "segment ids");
     DALLOC(m->d_seg_row, (Sm + 1) * 8, "segment rows");
     DALLOC(m->d_tslot, Km * 4, "slice slots");
@@ -386,6 +388,14 @@ extern "C" dash_status dash_init(const dash_config *cfg, dash_model **out) {
     cudaEventCreate(&m->ev0);
     cudaEventCreate(&m->ev1);
     cudaEventCreateWithFlags(&m->ev_meta, cudaEventDisableTiming);
+    for (int i = 0; i < kCopyStreams; ++i) {
+        if (cudaStreamCreateWithFlags(&m->copy_streams[i], cudaStreamNonBlocking) != cudaSuccess)
+            m->copy_streams[i] = nullptr;
+    }
+    for (int i = 0; i <= kCopyStreams; ++i) cudaEventCreateWithFlags(&m->copy_ev[i], cudaEventDisableTiming);
+    for (int i = 0; i < 2; ++i) cudaEventCreateWithFlags(&m->buf_free[i], cudaEventDisableTiming);
+    if (!m->copy_streams[kCopyStreams - 1]) m->copy_streams[0] = nullptr;   // all or none
+    cudaGetLastError();
     st = init_alloc(m);
     if (st != DASH_OK) {
         fprintf(stderr, "dash_init: %s\n", m->err.c_str());
@@ -408,10 +418,18 @@ extern "C" void dash_destroy(dash_model *m) {
     if (m->err_rows) cudaFree(m->err_rows);
     if (m->err_segs) cudaFree(m->err_segs);
     for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
+    for (int c = 0; c < kCopyStreams; ++c)      // split host copies still in flight
+        if (m->copy_streams[c]) cudaStreamSynchronize(m->copy_streams[c]);
     free_all(m);
     cudaEventDestroy(m->ev0);
     cudaEventDestroy(m->ev1);
     if (m->ev_meta) cudaEventDestroy(m->ev_meta);
+    for (int i = 0; i < kCopyStreams; ++i)
+        if (m->copy_streams[i]) cudaStreamDestroy(m->copy_streams[i]);
+    for (int i = 0; i <= kCopyStreams; ++i)
+        if (m->copy_ev[i]) cudaEventDestroy(m->copy_ev[i]);
+    for (int i = 0; i < 2; ++i)
+        if (m->buf_free[i]) cudaEventDestroy(m->buf_free[i]);
     if (m->own_stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -876,9 +894,29 @@ extern "C" dash_status dash_append_batch(dash_model *m, int64_t n_seg, const int
     const size_t ie = (m->cfg.input_dtype == DASH_F64) ? 8 : 4;
     if (N > 0) {
         char *dst = (char *)m->Xs + (size_t)m->st_rows * m->cfg.J * ie;
-        CK(cudaMemcpyAsync(dst, X, (size_t)N * m->cfg.J * ie,
-                           where == DASH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                           m->stream));
+        const size_t bytes = (size_t)N * m->cfg.J * ie;
+        if (where == DASH_HOST && bytes >= kSplitCopyBytes && m->copy_streams[0]) {
+            // a large host batch: one copy per part on the copy streams, so
+            // several copy engines share it.  The parts wait only until the
+            // last update that read this staging buffer is done, so they
+            // overlap an update in flight on the other buffer; the next
+            // update makes the model's stream wait for them.
+            const size_t part = (bytes / kCopyStreams + 4095) / 4096 * 4096;
+            for (int i = 0; i < kCopyStreams; ++i) {
+                const size_t off = (size_t)i * part;
+                const size_t nb = off >= bytes ? 0 : (bytes - off < part ? bytes - off : part);
+                CK(cudaStreamWaitEvent(m->copy_streams[i], m->buf_free[m->st_buf], 0));
+                if (nb > 0)
+                    CK(cudaMemcpyAsync(dst + off, (const char *)X + off, nb, cudaMemcpyHostToDevice,
+                                       m->copy_streams[i]));
+                CK(cudaEventRecord(m->copy_ev[i], m->copy_streams[i]));
+            }
+            m->copies_pending = true;
+        } else {
+            CK(cudaMemcpyAsync(dst, X, bytes,
+                               where == DASH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                               m->stream));
+        }
     }
     const int64_t base = m->st_rows;
     for (int64_t q = 0; q < n_seg; ++q) {
@@ -1144,11 +1182,31 @@ static void clear_staging(dash_model *m) {
     m->st_new = 0;
 }
 
+// The model's stream waits for split host copies into the staging buffer.
+static dash_status join_copies(dash_model *m) {
+    if (m->copies_pending) {
+        for (int i = 0; i < kCopyStreams; ++i) CK(cudaStreamWaitEvent(m->stream, m->copy_ev[i], 0));
+        m->copies_pending = false;
+    }
+    return DASH_OK;
+}
+
+// After an update that read the staging buffer: mark it free once that work
+// is done, and stage the next rows into the other buffer.
+static dash_status flip_staging(dash_model *m) {
+    CK(cudaEventRecord(m->buf_free[m->st_buf], m->stream));
+    m->st_buf ^= 1;
+    m->Xs = m->Xs_buf[m->st_buf];
+    clear_staging(m);
+    return DASH_OK;
+}
+
 extern "C" dash_status dash_update(dash_model *m) {
     if (!m) return DASH_EINVAL;
     const int64_t n_seg = m->st_segs();
+    if (dash_status e = join_copies(m)) return e;
     dash_status s = update_common(m, n_seg, m->st_slice.data(), m->st_row.data(), m->Xs, m->st_new);
-    if (s == DASH_OK) clear_staging(m);
+    if (s == DASH_OK) return flip_staging(m);
     return s;
 }
 
@@ -1215,9 +1273,10 @@ static dash_status fit_common(dash_model *m, int64_t n_seg, const int64_t *ids,
 
 extern "C" dash_status dash_fit_initial(dash_model *m, int32_t n_iter) {
     if (!m) return DASH_EINVAL;
+    if (dash_status e = join_copies(m)) return e;
     dash_status s = fit_common(m, m->st_segs(), m->st_slice.data(), m->st_row.data(), m->Xs,
                                m->st_new, n_iter);
-    if (s == DASH_OK) clear_staging(m);
+    if (s == DASH_OK) return flip_staging(m);
     return s;
 }
 

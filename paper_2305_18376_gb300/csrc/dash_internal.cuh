@@ -52,6 +52,8 @@ struct Profiler {
 };
 
 constexpr int kPhaseSlots = 15;        // in-kernel cycle counters of the profiler
+constexpr int kCopyStreams = 2;         // streams sharing a large host-to-device append
+constexpr size_t kSplitCopyBytes = 64u << 20;   // appends from this size are split
 constexpr int kFBlocksMax = 1024;       // max row chunks of the F-partial kernel
 constexpr int kSliceBlocksMax = 1216;   // max CTAs of the per-slice kernel (8 per SM)
 constexpr bool kAutoSplit = true;       // DASH_ROWS_AUTO takes the split row pipeline
@@ -65,6 +67,8 @@ struct dash_model {
     bool own_stream = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t ev_meta = nullptr;    // after a batch's metadata copies (pinned buffers free)
+    cudaStream_t copy_streams[dash::kCopyStreams] = {};   // parts of large host appends
+    cudaEvent_t copy_ev[dash::kCopyStreams + 1] = {};
     double rtol = 0.0;
     size_t tsize = 4;                 // bytes of the product arithmetic type
     bool df_state = false;            // c, D stored as double-float pairs
@@ -80,9 +84,14 @@ struct dash_model {
     double *GP = nullptr;             // G⁺
     double *Finc = nullptr, *Ginc = nullptr, *fit = nullptr;
 
-    // staging: rows copied in by the append calls
-    void *Xs = nullptr;
-    int64_t stage_cap = 0;            // rows the staging buffer holds
+    // staging: rows copied in by the append calls, into one of two buffers
+    // (the other may still be read by the update in flight)
+    void *Xs = nullptr;               // the buffer being filled: Xs_buf[st_buf]
+    void *Xs_buf[2] = {nullptr, nullptr};
+    int st_buf = 0;
+    cudaEvent_t buf_free[2] = {};     // after the last update that read the buffer
+    bool copies_pending = false;      // split host copies the next update must wait for
+    int64_t stage_cap = 0;            // rows a staging buffer holds
     int64_t st_rows = 0, st_new = 0;
     std::vector<int64_t> st_slice;    // slice id per staged segment
     std::vector<int64_t> st_row{0};   // row offsets, size = segments + 1

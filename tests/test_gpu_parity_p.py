@@ -294,3 +294,37 @@ def test_local_errors_match_definitions(prec):
         # the direct fitness agrees with the Gram-form fitness of the update
         assert abs(m.fitness()[0] - fd) <= (1e-9 if prec == "fp64" else 1e-3)
     m.close()
+
+
+def test_large_host_appends_overlap_and_match_device_updates():
+    """Host batches of >= 64 MB are split over several copy streams into a
+    double-buffered staging area; the next batch is appended while the
+    previous update runs.  The result is bit-identical to device-resident
+    updates of the same batches."""
+    w = tiny(K0=600, J=512, R=8, steps=3, sigma=0.05, lam=0.9, rows=("uniform", 40, 80),
+             new=4, new_rows=("uniform", 100, 300), init_rows=("uniform", 40, 80))
+    s = PlantedStream(w)
+    bs = [s.batch(t) for t in range(4)]
+    assert min(b.n_rows for b in bs[1:]) * w.J * 4 >= 64 << 20    # the split-copy path
+    kw = dict(max_slices=w.K0 + 64, max_rows=max(b.n_rows for b in bs) + 8, max_segments=4096)
+    ma = _model(w.J, w.R, w.lam, "f16x3", **kw)
+    mb = _model(w.J, w.R, w.lam, "f16x3", **kw)
+    V0 = np.random.default_rng(2).random((w.J, w.R))
+    for m in (ma, mb):
+        m.set_factors(V0)
+        m.update_device(bs[0].slice_ids.numpy(), bs[0].row_ptr.numpy(), bs[0].X.float().cuda())
+    pinned = [torch.empty(b.X.shape, dtype=torch.float32, pin_memory=True).copy_(b.X.float())
+              for b in bs]
+    ma.append_batch(bs[1].slice_ids.numpy(), bs[1].row_ptr.numpy(), pinned[1])
+    for t in (1, 2, 3):
+        ma.update()
+        if t < 3:                       # next batch's copy overlaps this update
+            ma.append_batch(bs[t + 1].slice_ids.numpy(), bs[t + 1].row_ptr.numpy(), pinned[t + 1])
+        fa = ma.fitness()[0]
+        mb.update_device(bs[t].slice_ids.numpy(), bs[t].row_ptr.numpy(), bs[t].X.float().cuda())
+        assert fa == mb.fitness()[0]
+    ga, gb = ma.get_state_p(), mb.get_state_p()
+    for k in ga:
+        assert np.array_equal(ga[k], gb[k]), k
+    ma.close()
+    mb.close()
