@@ -52,6 +52,12 @@ def parse():
     ap.add_argument("--q-steps", type=int, default=4,
                     help="timed updates of the constrained-mode (Q) measurement; 0 skips it")
     ap.add_argument("--q-init-iters", type=int, default=2)
+    ap.add_argument("--cycle-scan", action="store_true",
+                    help="update time against update size for the dual-way, rows-only and "
+                    "slices-only streaming settings (prints one JSON line; not the bench line)")
+    ap.add_argument("--lambda-sweep", action="store_true",
+                    help="local and global errors of a drifting stream for several forgetting "
+                    "factors (prints one JSON line; not the bench line)")
     return ap.parse_args()
 
 
@@ -610,10 +616,165 @@ def measure_mode_q(a, w, mq, batches, stream, K_total, step_rows, max_seg, pk, i
     return out
 
 
+# ---------------------------------------------------------------------------
+# Extra workloads: update-cycle scan (the paper's settings 2-4 and Fig. 5's
+# linearity) and the forgetting-factor sweep (§4.4)
+# ---------------------------------------------------------------------------
+def derive_batch(b, K_cur, scale, rows=True, slices=True):
+    """A batch derived from planted batch b: each segment keeps its first
+    ceil(scale·n) rows; rows=False drops the segments of existing slices,
+    slices=False drops the new slices (new slices are renumbered from K_cur).
+    Returns (slice_ids, row_ptr, X) with X on b.X's device."""
+    import math
+    import torch
+    ids, rp = b.slice_ids.tolist(), b.row_ptr.tolist()
+    keep_ids, take, nxt = [], [], K_cur
+    for q, k in enumerate(ids):
+        n = rp[q + 1] - rp[q]
+        is_new = k >= b.K_before
+        if (is_new and not slices) or (not is_new and (not rows or k >= K_cur)):
+            continue
+        m = min(n, max(1 if is_new else 0, math.ceil(scale * n)))
+        if is_new:
+            keep_ids.append(nxt)
+            nxt += 1
+        else:
+            keep_ids.append(k)
+        take.append((rp[q], m))
+    import numpy as np
+    starts = np.array([r0 for r0, _ in take], dtype=np.int64)
+    counts = np.array([m for _, m in take], dtype=np.int64)
+    row_ptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    idx = np.repeat(starts - row_ptr[:-1], counts) + np.arange(int(row_ptr[-1]), dtype=np.int64)
+    X = b.X.index_select(0, torch.from_numpy(idx).to(b.X.device)).contiguous()
+    return keep_ids, row_ptr.tolist(), X, nxt - K_cur
+
+
+def run_cycle_scan(a):
+    import numpy as np
+    import torch
+
+    from paper_2305_18376_gb300 import DashModel
+    from synth.planted import PlantedStream, workload
+
+    w = workload(a.workload)
+    if a.k0:
+        w = type(w)(**{**w.__dict__, "K0": a.k0})
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = PlantedStream(w, device="cuda", dtype=torch.float32, seed=w.seed + 1000)
+    b0 = s.batch(0)
+    batches = [s.batch(t) for t in range(1, 6)]
+    max_rows = max([b0.n_rows] + [b.n_rows for b in batches])
+    max_seg = max(b.slice_ids.numel() for b in [b0] + batches) + 8
+    K_total = w.K0 + 5 * w.new_slices_per_step + 8
+
+    def model():
+        return DashModel(w.J, w.R, w.lam, precision=a.precision, input_dtype="f32",
+                         max_slices=K_total, max_rows=max_rows, max_segments=max_seg,
+                         stream=stream.cuda_stream, max_staged_rows=1)
+    m = model()
+    m.set_row_path(a.row_path)
+    m.set_factors(np.random.default_rng(7).random((w.J, w.R)))
+    m.fit_initial_device(b0.slice_ids.numpy(), b0.row_ptr.numpy(), b0.X, a.init_iters)
+    m.sync()
+    snap, K_snap = m.get_state_p(), m.K
+    m.close()
+    del b0
+    out = {}
+    for variant, rows, slices in (("dual-way", True, True), ("rows-only", True, False),
+                                  ("slices-only", False, True)):
+        pts = []
+        for scale in (0.2, 0.4, 0.6, 0.8, 1.0):
+            mm = model()
+            mm.set_row_path(a.row_path)
+            mm.set_state_p(**snap)
+            K, times, nrows = K_snap, [], []
+            for t, b in enumerate(batches):
+                ids, rp, X, n_new = derive_batch(b, K, scale, rows, slices)
+                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ea.record(stream)
+                mm.update_device(np.asarray(ids), np.asarray(rp), X)
+                eb.record(stream)
+                K += n_new
+                if t >= 1:                 # the first update is a warm-up
+                    times.append((ea, eb))
+                    nrows.append(rp[-1])
+            torch.cuda.synchronize()
+            ms = [ea.elapsed_time(eb) for ea, eb in times]
+            pts.append({"scale": scale, "rows_per_update": float(np.mean(nrows)),
+                        "ms_per_update": float(np.median(ms))})
+            mm.close()
+        x = np.array([p["rows_per_update"] for p in pts])
+        y = np.array([p["ms_per_update"] for p in pts])
+        slope, icpt = np.polyfit(x, y, 1)
+        r2 = 1.0 - float(np.sum((y - (slope * x + icpt)) ** 2) / max(np.sum((y - y.mean()) ** 2), 1e-30))
+        out[variant] = {"points": pts, "linear_fit": {"ms_per_million_rows": float(slope * 1e6),
+                                                      "intercept_ms": float(icpt), "r2": r2}}
+    print(json.dumps({"metric": "update time vs update size (update cycle scan)",
+                      "workload": workload_config(w, a)["workload"],
+                      "row_path": a.row_path, "precision": a.precision, "settings": out}))
+
+
+def run_lambda_sweep(a):
+    import numpy as np
+    import torch
+
+    from paper_2305_18376_gb300 import DashModel
+    from synth.planted import PlantedStream, workload
+
+    w = workload("c2", K0=300, init_rows=("uniform", 50, 300), new_slice_rows=("uniform", 50, 100),
+                 steps=20, drift=0.02)
+    lams = (0.1, 0.3, 0.5, 0.7, 0.9)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    res = {}
+    for lam in lams:
+        s = PlantedStream(w, device="cuda", dtype=torch.float32, seed=w.seed + 1000)
+        bs = [s.batch(t) for t in range(w.steps + 1)]
+        m = DashModel(w.J, w.R, lam, precision=a.precision, input_dtype="f32",
+                      max_slices=w.K0 + w.new_slices_per_step * w.steps + 8,
+                      max_rows=max(b.n_rows for b in bs), max_segments=4096,
+                      stream=stream.cuda_stream, max_staged_rows=1)
+        m.set_factors(np.random.default_rng(7).random((w.J, w.R)))
+        m.fit_initial_device(bs[0].slice_ids.numpy(), bs[0].row_ptr.numpy(), bs[0].X, a.init_iters)
+        ids_all, rp_all, X_all, U_all = [], [0], [], []
+
+        def add(b, U):
+            rp = b.row_ptr.tolist()
+            for q, k in enumerate(b.slice_ids.tolist()):
+                ids_all.append(k)
+                rp_all.append(rp_all[-1] + rp[q + 1] - rp[q])
+            X_all.append(b.X)
+            U_all.append(torch.from_numpy(U))
+        add(bs[0], m.new_rows())
+        loc, glo = [], []
+        for t in range(1, w.steps + 1):
+            b = bs[t]
+            m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X)
+            _, fd, _ = m.local_errors()
+            loc.append((1.0 - fd) ** 2)            # Σ||X_new − X̂||² / Σ||X_new||²
+            add(b, m.new_rows())
+            e2, x2, _ = m.rows_error(ids_all, rp_all, torch.cat(X_all), torch.cat(U_all).cuda())
+            glo.append(e2 / x2)
+        res[str(lam)] = {"local_error_mean": float(np.mean(loc)), "global_error_mean": float(np.mean(glo)),
+                         "local_error_last": loc[-1], "global_error_last": glo[-1]}
+        m.close()
+    print(json.dumps({"metric": "forgetting-factor sweep: mean local and global relative squared error",
+                      "workload": (f"c2-shaped drifting stream: K0={w.K0}, J={w.J}, R={w.R}, "
+                                   f"{w.steps} updates, +1 row per slice and +{w.new_slices_per_step} "
+                                   f"slices per update, drift {w.drift}, sigma {w.sigma}"),
+                      "precision": a.precision, "lambda": res}))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.cycle_scan:
+        run_cycle_scan(a)
+    elif a.lambda_sweep:
+        run_lambda_sweep(a)
     else:
         run_ours(a)
 

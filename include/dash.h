@@ -234,6 +234,21 @@ dash_status dash_fitness(const dash_model *m, double *fit_batch, double *x_norm2
 dash_status dash_local_errors(dash_model *m, double *te, double *fit_direct, double *se,
                               int64_t se_len);
 
+/* Reconstruction error of any rows against the factors as they are now (the
+ * paper's global error of §4.1 when the rows are the whole accumulated
+ * tensor; Definitions 1-2 use the same residual):
+ *   sq_err = Σ_i ||x_i − x̂_i||²,  sq_x = Σ_i ||x_i||²,  abs_err = Σ_i |x_i − x̂_i|_1
+ * with x̂_i = u_i S_k Vᵀ (mode P) or u_i H S_k Vᵀ (mode Q).  Segment s covers
+ * rows row_ptr[s]..row_ptr[s+1]-1 (row_ptr[0] = 0, ascending; host array)
+ * and belongs to slice slice_ids[s] (host array, 0 <= id < the slice count).
+ * X (device, input_dtype, row-major N×J) holds the rows and `rows` (device,
+ * FP64, row-major N×R) their factor rows: U_k rows in mode P, Q_k rows in
+ * mode Q, as the updates that saw them produced them (dash_new_rows).  Any
+ * output may be NULL.  DASH_EINVAL for bad segments; synchronises the stream. */
+dash_status dash_rows_error(dash_model *m, int64_t n_seg, const int64_t *slice_ids,
+                            const int64_t *row_ptr, const void *X, const double *rows,
+                            double *sq_err, double *sq_x, double *abs_err);
+
 /* Wait for all work issued on the model's stream. */
 dash_status dash_sync(dash_model *m);
 

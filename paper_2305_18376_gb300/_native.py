@@ -73,6 +73,7 @@ SIGNATURES = [
     ("dash_profile_get", C.c_int, [P, I32, C.POINTER(C.c_char_p), PI64, PD]),
     ("dash_last_plan", C.c_int, [P, PI64, PI64, PI64, PI64, PI64]),
     ("dash_set_row_path", C.c_int, [P, I32]),
+    ("dash_rows_error", C.c_int, [P, I64, PI64, PI64, P, P, PD, PD, PD]),
     ("dash_local_errors", C.c_int, [P, PD, PD, PD, I64]),
     ("dash_f_increment_noalloc", C.c_int, [P, P, I64, I32, I32, P, P, I64, P, P, P]),
     ("dash_counters", C.c_int, [P, PI64, PI64]),
@@ -222,6 +223,22 @@ class DashModel:
         self._ck(self._lib.dash_last_plan(self._h, *(C.byref(x) for x in v)))
         return dict(zip(("tile_rows", "tile_slices", "tiles", "chunk_rows", "general_rows"),
                         (x.value for x in v)))
+
+    def rows_error(self, slice_ids, row_ptr, X, rows):
+        """(Σ||x − x̂||², Σ||x||², Σ|x − x̂|) of the rows of X (a CUDA tensor of
+        the input dtype) with factor rows `rows` (CUDA FP64, N×R) against the
+        current factors; segments as in append_batch."""
+        import torch
+        ids, rp = _i64(slice_ids), _i64(row_ptr)
+        xp, where, keep = self._ptr(X)
+        if where != DEVICE or not (isinstance(rows, torch.Tensor) and rows.is_cuda):
+            raise TypeError("rows_error needs CUDA tensors for X and rows")
+        rows = rows.to(torch.float64).contiguous()
+        e2, x2, ea = C.c_double(), C.c_double(), C.c_double()
+        self._ck(self._lib.dash_rows_error(self._h, len(ids), ids.ctypes.data_as(PI64),
+                                           rp.ctypes.data_as(PI64), xp, C.c_void_p(rows.data_ptr()),
+                                           C.byref(e2), C.byref(x2), C.byref(ea)))
+        return e2.value, x2.value, ea.value
 
     ROW_PATHS = {"auto": 0, "fused": 1, "split": 2}
 

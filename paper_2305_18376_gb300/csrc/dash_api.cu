@@ -417,6 +417,8 @@ extern "C" void dash_destroy(dash_model *m) {
     prof_collect(m);
     if (m->err_rows) cudaFree(m->err_rows);
     if (m->err_segs) cudaFree(m->err_segs);
+    if (m->re_seg_row) cudaFree(m->re_seg_row);
+    if (m->re_seg_slice) cudaFree(m->re_seg_slice);
     for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
     for (int c = 0; c < kCopyStreams; ++c)      // split host copies still in flight
         if (m->copy_streams[c]) cudaStreamSynchronize(m->copy_streams[c]);
@@ -784,6 +786,85 @@ extern "C" dash_status dash_local_errors(dash_model *m, double *te, double *fit_
     }
     if (te) *te = tcount ? tsum / (double)tcount : 0.0;
     if (fit_direct) *fit_direct = xn > 0.0 ? 1.0 - std::sqrt(sq / xn) : 1.0;
+    return DASH_OK;
+}
+
+// Reconstruction error of arbitrary rows (the global error over an
+// accumulated tensor) against the current factors.
+template <typename TI>
+static dash_status launch_rows_error(dash_model *m, int64_t N, int n_seg, const void *X,
+                                     const double *rows) {
+    const int J = m->cfg.J, R = m->cfg.R;
+    const size_t smem = err_smem<double>(R, J);
+    CK(cudaFuncSetAttribute(k_resid_rows<TI, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (int)std::min<int64_t>((N + 7) / 8, 4 * (int64_t)m->n_sm);
+    LAUNCH(KK_Q_OUT, (k_resid_rows<TI, double><<<grid, 256, smem, m->stream>>>(
+                         N, J, R, n_seg, m->re_seg_row, m->re_seg_slice, (const TI *)X, rows,
+                         m->cfg.mode == DASH_MODE_Q ? m->qH : nullptr, m->st.W, m->st.V,
+                         m->err_rows)));
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_rows_error(dash_model *m, int64_t n_seg, const int64_t *slice_ids,
+                                       const int64_t *row_ptr, const void *X, const double *rows,
+                                       double *sq_err, double *sq_x, double *abs_err) {
+    if (!m) return DASH_EINVAL;
+    if (m->broken) return fail(m, DASH_ESTATE, "model is unusable after a CUDA error");
+    if (n_seg < 0 || (n_seg > 0 && (!slice_ids || !row_ptr)))
+        return fail(m, DASH_EINVAL, "bad segment arrays");
+    if (n_seg > INT32_MAX) return fail(m, DASH_EINVAL, "too many segments");
+    if (n_seg > 0 && row_ptr[0] != 0) return fail(m, DASH_EINVAL, "row_ptr[0] must be 0");
+    for (int64_t q = 0; q < n_seg; ++q) {
+        if (row_ptr[q + 1] < row_ptr[q]) return fail(m, DASH_EINVAL, "row_ptr is not ascending");
+        if (slice_ids[q] < 0 || slice_ids[q] >= m->K)
+            return fail(m, DASH_EINVAL, "slice id %lld is not in the model", (long long)slice_ids[q]);
+    }
+    const int64_t N = n_seg ? row_ptr[n_seg] : 0;
+    if (N > 0 && (!X || !rows)) return fail(m, DASH_EINVAL, "X or rows is null");
+    double e2 = 0.0, x2 = 0.0, ea = 0.0;
+    if (N > 0) {
+        if (m->err_rows_cap < N) {
+            if (m->err_rows) cudaFree(m->err_rows);
+            m->err_rows = nullptr;
+            CK(cudaMalloc(&m->err_rows, (size_t)N * 3 * 8));
+            m->err_rows_cap = N;
+        }
+        if (m->err_segs_cap < n_seg) {
+            if (m->err_segs) cudaFree(m->err_segs);
+            m->err_segs = nullptr;
+            CK(cudaMalloc(&m->err_segs, (size_t)n_seg * 3 * 8));
+            m->err_segs_cap = n_seg;
+        }
+        if (m->re_cap < n_seg) {
+            if (m->re_seg_row) cudaFree(m->re_seg_row);
+            if (m->re_seg_slice) cudaFree(m->re_seg_slice);
+            m->re_seg_row = nullptr;
+            m->re_seg_slice = nullptr;
+            CK(cudaMalloc(&m->re_seg_row, (size_t)(n_seg + 1) * 8));
+            CK(cudaMalloc(&m->re_seg_slice, (size_t)n_seg * 4));
+            m->re_cap = n_seg;
+        }
+        std::vector<int> ids32(slice_ids, slice_ids + n_seg);
+        CK(cudaMemcpyAsync(m->re_seg_row, row_ptr, (size_t)(n_seg + 1) * 8, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->re_seg_slice, ids32.data(), (size_t)n_seg * 4, cudaMemcpyHostToDevice, m->stream));
+        const dash_status st = m->cfg.input_dtype == DASH_F64
+                                   ? launch_rows_error<double>(m, N, (int)n_seg, X, rows)
+                                   : launch_rows_error<float>(m, N, (int)n_seg, X, rows);
+        if (st) return st;
+        LAUNCH(KK_Q_FIT, (k_resid_segs<<<(unsigned)((n_seg + 127) / 128), 128, 0, m->stream>>>(
+                             (int)n_seg, m->re_seg_row, m->err_rows, m->err_segs)));
+        std::vector<double> seg((size_t)n_seg * 3);
+        CK(cudaMemcpyAsync(seg.data(), m->err_segs, seg.size() * 8, cudaMemcpyDeviceToHost, m->stream));
+        CK(cudaStreamSynchronize(m->stream));    // also keeps ids32 alive for its copy
+        for (int64_t q = 0; q < n_seg; ++q) {
+            ea += seg[(size_t)q * 3];
+            e2 += seg[(size_t)q * 3 + 1];
+            x2 += seg[(size_t)q * 3 + 2];
+        }
+    }
+    if (sq_err) *sq_err = e2;
+    if (sq_x) *sq_x = x2;
+    if (abs_err) *abs_err = ea;
     return DASH_OK;
 }
 

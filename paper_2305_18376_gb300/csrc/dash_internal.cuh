@@ -163,6 +163,9 @@ struct dash_model {
     std::vector<int64_t> last_ids, last_rp;
     double *err_rows = nullptr, *err_segs = nullptr;
     int64_t err_rows_cap = 0, err_segs_cap = 0;
+    int64_t *re_seg_row = nullptr;    // segments of dash_rows_error
+    int *re_seg_slice = nullptr;
+    int64_t re_cap = 0;
 
     // plan of the last batch (dash_last_plan)
     int64_t plan_tile_rows = 0, plan_tile_slices = 0, plan_tiles = 0, plan_chunk_rows = 0,

@@ -12,7 +12,8 @@ Planted model (one recipe for every workload):
     with its columns' signs fixed so that diag(R̃) > 0, drawn at the slice's
     *final* length and revealed by row prefix, so new rows continue the same
     planted slice;
-  * X_k = Q_k H diag(w_k) Vᵀ + σ·N(0,1)  (absolute noise level σ).
+  * X_k = Q_k H diag(w_k) Vᵀ + σ·N(0,1)  (absolute noise level σ);
+  * a drifting stream (drift > 0) uses V + drift·t·V_d for update t's rows.
 
 Row counts are drawn up front from the workload's distributions, so the
 stream is a pure function of (workload, seed, device).  The CPU and CUDA
@@ -45,6 +46,7 @@ class Workload:
     sigma: float               # absolute Gaussian noise level
     lam: float                 # forgetting factor used by this workload
     seed: int
+    drift: float = 0.0         # V of update t is V + drift·t·V_d (a drifting stream)
 
 
 def _w(name, idx, **kw):
@@ -165,6 +167,9 @@ class PlantedStream:
         self.V = torch.rand(J, R, **kw)
         self.W = torch.rand(self.K_total, R, **kw)
         self.Q = self._planted_q(final, dg)
+        # a drifting stream moves V along a fixed random direction (drawn last,
+        # so streams without drift are unchanged)
+        self.Vd = torch.rand(J, R, **kw) if w.drift else None
         self._next = 0
 
     # -- planted orthonormal Q_k, bucketed by length ---------------------------
@@ -240,12 +245,13 @@ class PlantedStream:
         src = start.repeat_interleave(rows) + within
         self._revealed[:k_count] += rows
         X = torch.empty(N, w.J, device=self.device, dtype=self.dtype)
+        Vt = self.V if self.Vd is None else self.V + (w.drift * t) * self.Vd
         chunk = 1 << 21
         for c0 in range(0, N, chunk):
             c1 = min(N, c0 + chunk)
             q = self.Q.index_select(0, src[c0:c1].to(self.device))
             wk = self.W.index_select(0, seg_of_row[c0:c1].to(self.device))
-            torch.matmul((q @ self.H) * wk, self.V.T, out=X[c0:c1])
+            torch.matmul((q @ self.H) * wk, Vt.T, out=X[c0:c1])
             if w.sigma:
                 X[c0:c1].add_(torch.randn(c1 - c0, w.J, generator=self._dgen,
                                           device=self.device, dtype=self.dtype), alpha=w.sigma)

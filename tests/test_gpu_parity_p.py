@@ -328,3 +328,50 @@ def test_large_host_appends_overlap_and_match_device_updates():
         assert np.array_equal(ga[k], gb[k]), k
     ma.close()
     mb.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f16x3"])
+def test_rows_error_is_the_global_error_of_accumulated_rows(prec):
+    """dash_rows_error over every row of several updates (each with the U rows
+    its update produced) against the oracle's Σ ||X_k − U_k S_k Vᵀ||² with the
+    current S_k and V: the global error of §4.1."""
+    _, tdt = PREC_DTYPE[prec]
+    w = tiny(K0=7, J=10, R=3, steps=3, sigma=0.05, lam=0.9, new=2)
+    s = PlantedStream(w)
+    rng = np.random.default_rng(4)
+    b0 = s.batch(0)
+    X0 = [x for _, x in segs_np(b0, tdt)]
+    U, W, V = O.static_als_p(X0, rng.random((w.J, w.R)), np.ones((len(X0), w.R)), 2)
+    st = O.init_helpers_p(X0, U, W, V)
+    m = _model(w.J, w.R, w.lam, prec, max_slices=64, max_rows=1024, max_segments=256)
+    m.set_state_p(st.V, st.W, st.c, st.D, st.F, st.G)
+    ids_all, rows_all, X_all, U_gpu, U_orc = [], [0], [], [], []
+    for t in (1, 2, 3):
+        b = s.batch(t)
+        X = O._group(segs_np(b, tdt), st.K, b.n_new, w.J)
+        st, Uo = O.dash_update_p(st, list(X.items()), b.n_new, w.lam)
+        m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.to(tdt).cuda())
+        U_gpu.append(m.new_rows())
+        rp = b.row_ptr.tolist()
+        for q, k in enumerate(b.slice_ids.tolist()):
+            ids_all.append(k)
+            rows_all.append(rows_all[-1] + rp[q + 1] - rp[q])
+            U_orc.append(Uo[k][: rp[q + 1] - rp[q]] if k in Uo else np.zeros((0, w.R)))
+        X_all.append(b.X.to(tdt))
+        # the oracle side: every accumulated segment with the current factors
+        e2_o = x2_o = 0.0
+        Xc = torch.cat(X_all).numpy().astype(np.float64)
+        for q, k in enumerate(ids_all):
+            xs = Xc[rows_all[q]:rows_all[q + 1]]
+            xh = O.reconstruct_p(U_orc[q], st.W[k], st.V)
+            e2_o += float(np.sum((xs - xh) ** 2))
+            x2_o += float(np.sum(xs ** 2))
+        e2, x2, ea = m.rows_error(ids_all, rows_all, torch.cat(X_all).cuda(),
+                                  torch.from_numpy(np.concatenate(U_gpu)).cuda())
+        # the mixed path's X̂ is within ~1e-5 of |X|; the residual is ~σ, so
+        # its sum of squares carries that error amplified by |X|/σ
+        tol = 1e-8 if prec == "fp64" else 5e-3
+        assert abs(x2 - x2_o) <= 1e-12 * x2_o
+        assert abs(e2 - e2_o) <= tol * e2_o, (t, e2, e2_o)
+        assert ea > 0
+    m.close()
