@@ -3,6 +3,8 @@
 // update on the model's CUDA stream.
 #include <cuda_runtime.h>
 
+#include <chrono>
+
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -1026,6 +1028,7 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
     // seldom waits).  The host planning then overlaps the previous update on
     // the GPU.  It assumes the last known state of Γ (nonsingular or not) and
     // is redone in the rare case that the previous update changed it.
+    m->prof.t_plan0 = std::chrono::steady_clock::now();
     CK(cudaEventSynchronize(m->ev_meta));
     bool gam_ok = m->gam_ok_host;
     int n_touch = 0, nt = 0, nr = 0;
@@ -1173,7 +1176,15 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
     m->plan_chunk_rows = fused ? ng : 0;
     m->plan_general_rows = fused ? 0 : ng;
     if (pass == 0) {
+        const auto th0 = std::chrono::steady_clock::now();
         CK(cudaStreamSynchronize(m->stream));   // the previous update has finished
+        if (m->prof.on) {
+            const auto th1 = std::chrono::steady_clock::now();
+            m->prof.ms[KK_HOST_PLAN] += std::chrono::duration<double, std::milli>(th0 - m->prof.t_plan0).count();
+            m->prof.ms[KK_HOST_WAIT] += std::chrono::duration<double, std::milli>(th1 - th0).count();
+            m->prof.launches[KK_HOST_PLAN] += 1;
+            m->prof.launches[KK_HOST_WAIT] += 1;
+        }
         m->gam_ok_host = m->h_fit[3] != 0.0;
         if (m->h_err[0] > 0) return fail(m, DASH_ETIMEOUT, "a bounded device wait timed out");
         if (m->h_err[2] > 0)
@@ -1244,8 +1255,14 @@ static dash_status update_common(dash_model *m, int64_t n_seg, const int64_t *id
     dash_status s = plan_batch(m, n_seg, ids, rp, m->K, n_new, X, true, &b);
     if (s) return s;
     CK(cudaEventRecord(m->ev0, m->stream));
+    const auto tl0 = std::chrono::steady_clock::now();
     s = run_update(m, b, X, m->cfg.lambda, true);
     if (s) return s;
+    if (m->prof.on) {
+        m->prof.ms[KK_HOST_LAUNCH] +=
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tl0).count();
+        m->prof.launches[KK_HOST_LAUNCH] += 1;
+    }
     CK(cudaEventRecord(m->ev1, m->stream));
     m->K += n_new;
     m->last_N = b.N;

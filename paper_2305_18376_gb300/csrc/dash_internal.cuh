@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -22,7 +23,7 @@ enum KernelKind {
     KK_Q_BEGIN, KK_Q_AROWS, KK_Q_Y, KK_Q_LT, KK_Q_H, KK_Q_VPART, KK_Q_V, KK_Q_PW, KK_Q_W,
     KK_Q_OUT, KK_Q_FIT, KK_QLT_QR, KK_QLT_PRE, KK_QLT_PASS, KK_QLT_TAIL,
     KK_XQ_PREP, KK_XQ_TC, KK_F_TC, KK_UTILDE, KK_XQ_WAIT, KK_XQ_BUSY, KK_FT_WAIT, KK_FT_BUSY,
-    KK_COUNT
+    KK_HOST_PLAN, KK_HOST_WAIT, KK_HOST_LAUNCH, KK_COUNT
 };
 static const char *const kKernelNames[KK_COUNT] = {
     "k_begin_new", "k_rowmap", "k_xv", "k_slices", "k_f", "k_f_reduce", "k_g_reduce",
@@ -34,7 +35,7 @@ static const char *const kKernelNames[KK_COUNT] = {
     "k_q_begin_new", "k_q_arows", "k_q_y", "k_q_lt", "k_q_h", "k_q_vpart", "k_q_v", "k_q_pw",
     "k_q_w", "k_q_out", "k_q_fit", "k_q_lt.qr", "k_q_lt.fp32_pass", "k_q_lt.passes",
     "k_q_lt.tail", "k_xq_bfrag", "k_xq_tc", "k_f_tc", "k_utilde", "k_xq_tc.wait", "k_xq_tc.loop",
-    "k_f_tc.wait", "k_f_tc.loop"};
+    "k_f_tc.wait", "k_f_tc.loop", "host.plan", "host.wait_previous", "host.launch"};
 
 struct Profiler {
     bool on = false;
@@ -49,6 +50,7 @@ struct Profiler {
     int n_sm = 1;
     double q_lt_warps = 0.0;    // warps of the last profiled k_q_lt launch
     double xq_warps = 0.0, ft_warps = 0.0;   // warps of the streaming kernels' last launch
+    std::chrono::steady_clock::time_point t_plan0;   // start of the current batch's planning
 };
 
 constexpr int kPhaseSlots = 15;        // in-kernel cycle counters of the profiler
