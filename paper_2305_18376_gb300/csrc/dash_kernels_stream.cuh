@@ -668,4 +668,211 @@ __global__ void __launch_bounds__(FT_THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// k_big_b_tc: the chunked path's per-chunk products on the tensor cores (the
+// split row pipeline).  One warp per chunk of <= 256 rows of one slice:
+//   U = (P'·R_V⁻ᵀ)·S_k⁻¹ (Lemma 1's fast path, Eq. 11), written out;
+//   ΔD = UᵀU and Δc = diag(ΔD S_k Γ) (Eqs. 15-16), the chunk's partials.
+// Both products use the FP16 split with the main and correction terms in
+// separate accumulators, 16 rows at a time: U's tile goes through a padded
+// shared block (pitch BT_UP, conflict-free) to become both MMA operands of
+// ΔD (A = Uᵀ and B = U read the same values).  Chunks of slices that need
+// the general map (a zero weight, or a singular Γ) take big_chunk's SIMT
+// path.  R <= 32, R even (8-byte aligned P' and U pairs for the float2 accesses).
+constexpr int BT_UP = 36;                 // staged U tile pitch (≡ 4 mod 32 words: 8tg + g banks)
+
+static __global__ void __launch_bounds__(256, 2) k_big_b_tc(FusedArgs a, BigArgs bg) {
+    __shared__ __align__(16) float Us[FU_WARPS][32][FU_RP];      // SIMT fallback
+    __shared__ __align__(16) float Tw[FU_WARPS][32 * BT_UP];     // U tile / ΔD staging
+    __shared__ float Wi_all[FU_WARPS][32];                        // 1/w_k of the chunk's slice
+    __shared__ uint4 Mf_all[FU_WARPS][8][32];                     // R_V⁻ᵀ fragments per lane
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tg = lane & 3;
+    const int R = a.R;
+    const unsigned full = 0xffffffffu;
+    float *T = Tw[warp];
+    float *Wi = Wi_all[warp];
+    uint4 (*Mf)[32] = Mf_all[warp];
+    const bool gam_ok = *a.gam_ok != 0;
+    // R_V⁻ᵀ as B fragments (k = t, n = c), scaled by 2^bm: the same for every
+    // chunk of the update (U = (P'·R_V⁻ᵀ) ∘ 1/w_k column by column, so S_k⁻¹
+    // is applied to the output columns)
+    float mmax = 0.f;
+    for (int e0 = 0; e0 < R * R; e0 += 32)
+        if (e0 + lane < R * R) mmax = fmaxf(mmax, fabsf(a.GPf[e0 + lane]));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mmax = fmaxf(mmax, __shfl_xor_sync(full, mmax, o));
+    const int bm = 10 - xq_exp(mmax);
+    const float bsc = xq_pow2(bm);
+    // {b0hi, b1hi, b0lo, b1lo} of n-tile nt, k-step ks at Mf[2nt + ks][lane]
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        const int c = 8 * nt + g;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = 16 * ks + 2 * tg + (u & 1) + 8 * (u >> 1);
+                v[u] = (t < R && c < R) ? a.GPf[t * R + c] * bsc : 0.f;
+            }
+            uint4 f;
+            xq_split(v[0], v[1], f.x, f.z);
+            xq_split(v[2], v[3], f.y, f.w);
+            Mf[2 * nt + ks][lane] = f;
+        }
+    }
+    for (int ch = blockIdx.x * FU_WARPS + warp; ch < bg.n_chunks; ch += gridDim.x * FU_WARPS) {
+        const int k = bg.ch_k[ch];
+        const double wold_d = lane < R ? a.W[(int64_t)k * R + lane] : 1.0;
+        const bool fast = gam_ok && __all_sync(full, wold_d != 0.0);
+        if (!fast) {
+            big_chunk(a, bg, ch, Us[warp]);
+            continue;
+        }
+        const int64_t row0 = bg.ch_row0[ch];
+        const int n = bg.ch_n[ch];
+        __syncwarp();
+        Wi[lane] = lane < R ? 1.0f / (float)wold_d : 0.f;   // 1/w_k (zero past R)
+        __syncwarp();
+        float dd[2][4][4];                        // ΔD in the MMA C layout: [mt][nt][e]
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dd[mt][nt][e] = 0.f;
+        for (int i0 = 0; i0 < n; i0 += 16) {
+            const int m = min(16, n - i0);
+            const bool va = g < m, vb = g + 8 < m;
+            const float *ya = bg.Y + (row0 + i0 + g) * R, *yb = ya + 8 * R;
+            // P' A fragments (rows g, g+8; k-slots 2tg, 2tg+1, 2tg+8, 2tg+9)
+            float2 p[2][4];
+            float pm0 = 0.f, pm1 = 0.f;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const int c0 = 16 * ks + 2 * tg, c1 = c0 + 8;
+                const float2 z = make_float2(0.f, 0.f);
+                p[ks][0] = (va && c0 < R) ? *reinterpret_cast<const float2 *>(ya + c0) : z;
+                p[ks][1] = (vb && c0 < R) ? *reinterpret_cast<const float2 *>(yb + c0) : z;
+                p[ks][2] = (va && c1 < R) ? *reinterpret_cast<const float2 *>(ya + c1) : z;
+                p[ks][3] = (vb && c1 < R) ? *reinterpret_cast<const float2 *>(yb + c1) : z;
+                pm0 = fmaxf(pm0, fmaxf(fmaxf(fabsf(p[ks][0].x), fabsf(p[ks][0].y)),
+                                       fmaxf(fabsf(p[ks][2].x), fabsf(p[ks][2].y))));
+                pm1 = fmaxf(pm1, fmaxf(fmaxf(fabsf(p[ks][1].x), fabsf(p[ks][1].y)),
+                                       fmaxf(fabsf(p[ks][3].x), fabsf(p[ks][3].y))));
+            }
+            pm0 = fmaxf(pm0, __shfl_xor_sync(full, pm0, 1));
+            pm0 = fmaxf(pm0, __shfl_xor_sync(full, pm0, 2));
+            pm1 = fmaxf(pm1, __shfl_xor_sync(full, pm1, 1));
+            pm1 = fmaxf(pm1, __shfl_xor_sync(full, pm1, 2));
+            const int x0 = ft_xscale_exp(xq_exp(pm0)), x1 = ft_xscale_exp(xq_exp(pm1));
+            const float s0 = xq_pow2(x0), s1 = xq_pow2(x1);
+            float um[4][4], uc[4][4];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) um[nt][e] = uc[nt][e] = 0.f;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                uint32_t ah[4], al[4];
+                xq_split(p[ks][0].x * s0, p[ks][0].y * s0, ah[0], al[0]);
+                xq_split(p[ks][1].x * s1, p[ks][1].y * s1, ah[1], al[1]);
+                xq_split(p[ks][2].x * s0, p[ks][2].y * s0, ah[2], al[2]);
+                xq_split(p[ks][3].x * s1, p[ks][3].y * s1, ah[3], al[3]);
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    const uint4 f = Mf[2 * nt + ks][lane];
+                    xq_mma(um[nt], ah[0], ah[1], ah[2], ah[3], f.x, f.y);
+                    xq_mma(uc[nt], ah[0], ah[1], ah[2], ah[3], f.z, f.w);
+                    xq_mma(uc[nt], al[0], al[1], al[2], al[3], f.x, f.y);
+                }
+            }
+            // U rows: scale back (row scale and M's 2^bm), write out, stage in T
+            const float r0s = xq_pow2(-x0) * xq_pow2(-bm), r1s = xq_pow2(-x1) * xq_pow2(-bm);
+            __syncwarp();
+            float umax = 0.f;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int c = 8 * nt + 2 * tg;
+                const float w0 = Wi[c], w1 = Wi[c + 1];
+                const float u00 = (um[nt][0] + uc[nt][0]) * r0s * w0;
+                const float u01 = (um[nt][1] + uc[nt][1]) * r0s * w1;
+                const float u10 = (um[nt][2] + uc[nt][2]) * r1s * w0;
+                const float u11 = (um[nt][3] + uc[nt][3]) * r1s * w1;
+                const bool cv = c < R;
+                T[g * BT_UP + c] = (va && cv) ? u00 : 0.f;
+                T[g * BT_UP + c + 1] = (va && cv) ? u01 : 0.f;
+                T[(g + 8) * BT_UP + c] = (vb && cv) ? u10 : 0.f;
+                T[(g + 8) * BT_UP + c + 1] = (vb && cv) ? u11 : 0.f;
+                if (va && cv) *reinterpret_cast<float2 *>(a.U + (row0 + i0 + g) * R + c) = make_float2(u00, u01);
+                if (vb && cv) *reinterpret_cast<float2 *>(a.U + (row0 + i0 + g + 8) * R + c) = make_float2(u10, u11);
+                if (va && cv) umax = fmaxf(umax, fmaxf(fabsf(u00), fabsf(u01)));
+                if (vb && cv) umax = fmaxf(umax, fmaxf(fabsf(u10), fabsf(u11)));
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) umax = fmaxf(umax, __shfl_xor_sync(full, umax, o));
+            const int eu = xq_exp(umax);
+            const float su = xq_pow2(10 - eu);
+            __syncwarp();
+            // ΔD += UᵀU for this tile: u(row, col) pairs at rows 2tg, 2tg+1 (b0)
+            // and 2tg+8, 2tg+9 (b1), column 8nt + g; A = Uᵀ's fragments for
+            // m-tile mt are those of n-tiles 2mt, 2mt+1
+            uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int c = 8 * nt + g;
+                xq_split(T[(2 * tg) * BT_UP + c] * su, T[(2 * tg + 1) * BT_UP + c] * su, bh[nt][0], bl[nt][0]);
+                xq_split(T[(2 * tg + 8) * BT_UP + c] * su, T[(2 * tg + 9) * BT_UP + c] * su, bh[nt][1], bl[nt][1]);
+            }
+            const float uu = xq_pow2(eu - 10) * xq_pow2(eu - 10);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    float d[4], dc[4];
+                    xq_mma0(d, bh[2 * mt][0], bh[2 * mt + 1][0], bh[2 * mt][1], bh[2 * mt + 1][1],
+                            bh[nt][0], bh[nt][1]);
+                    xq_mma0(dc, bh[2 * mt][0], bh[2 * mt + 1][0], bh[2 * mt][1], bh[2 * mt + 1][1],
+                            bl[nt][0], bl[nt][1]);
+                    xq_mma(dc, bl[2 * mt][0], bl[2 * mt + 1][0], bl[2 * mt][1], bl[2 * mt + 1][1],
+                           bh[nt][0], bh[nt][1]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) dd[mt][nt][e] = fmaf(d[e] + dc[e], uu, dd[mt][nt][e]);
+                }
+            }
+        }
+        // ΔD (C layout: row 16mt + g (+8), column 8nt + 2tg (+1)) → staging,
+        // then Δc = diag(ΔD S Γ) with lane = row, and the chunk's partials
+        __syncwarp();
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int r = 16 * mt + g, c = 8 * nt + 2 * tg;
+                T[r * 33 + c] = dd[mt][nt][0];
+                T[r * 33 + c + 1] = dd[mt][nt][1];
+                T[(r + 8) * 33 + c] = dd[mt][nt][2];
+                T[(r + 8) * 33 + c + 1] = dd[mt][nt][3];
+            }
+        __syncwarp();
+        const bool act = lane < R;
+        const float wl = act ? (float)wold_d : 0.f;
+        float sacc = 0.f;
+        float *out = bg.dpart + (size_t)ch * (R * R + R);
+#pragma unroll 4
+        for (int q = 0; q < R; ++q) {
+            const float wq = __shfl_sync(full, wl, q);
+            // ΔD is symmetric; the MMA's two halves may differ in the last bit
+            const float dq = 0.5f * (T[q * 33 + lane] + T[lane * 33 + q]);
+            if (act) {
+                sacc = fmaf(dq * wq, a.Gdf[q * R + lane].hi, sacc);   // (float)Γ
+                out[q * R + lane] = dq;
+            }
+        }
+        if (act) out[R * R + lane] = sacc;
+        __syncwarp();
+    }
+}
+
 }  // namespace dash

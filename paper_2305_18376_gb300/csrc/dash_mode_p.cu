@@ -141,7 +141,10 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
             // both grids stay within the 2-CTAs-per-SM workspace (persistent warps)
             if (m->n_chunks > 0) {
                 const int gb = std::min(2 * m->n_sm, (m->n_chunks + FU_WARPS - 1) / FU_WARPS);
-                LAUNCH(KK_BIG_B, k_big_b<<<gb, 256, 0, st>>>(fa, bg));
+                if (split && (R % 2) == 0)
+                    LAUNCH(KK_BIG_B, k_big_b_tc<<<gb, 256, 0, st>>>(fa, bg));
+                else
+                    LAUNCH(KK_BIG_B, k_big_b<<<gb, 256, 0, st>>>(fa, bg));
             }
             if (m->n_fin > 0) {
                 nsb = std::min(2 * m->n_sm, (m->n_fin + FU_WARPS - 1) / FU_WARPS);
