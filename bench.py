@@ -472,7 +472,10 @@ def run_ours(a):
     pk, pk_kind = peaks()
     Nm = int(statistics.mean(b.n_rows for b in timed))
     K_all = w.K0 + w.new_slices_per_step * (a.warmup + len(timed))
-    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    # the dominant kernel: by time, among launched kernels (not the in-kernel
+    # phase counters "kernel.phase" nor the host timers "host.*")
+    launched = {k: v for k, v in prof.items() if "." not in k}
+    top = max(launched.items(), key=lambda kv: kv[1][1]) if launched else None
     roof = None
     kernels = {}
     plan = {k: statistics.mean(p[k] for p in plans) for k in plans[0]}
