@@ -165,17 +165,27 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
         if (mode == 0)
             for (int i = lane; i < R * R; i += 32) Lg[k * RR + i] = Lw[(i / R) * ld + (i % R)];
         if (q.phase) { const long long c1 = clock64(); pc[0] += c1 - c0k; c0k = c1; }
-        {
+        if (R <= 32) {
+            // register-resident one-sided Jacobi: FP32 sweeps, E re-orthogonalised
+            // to the working type, then sweeps in the working type
+            if (!std::is_same<S, float>::value) {
+                warp_eig_os<float, S>(Lw, Ew, nullptr, R, ld, 8, 1e-6f);
+                warp_newton_schulz2<S>(Ew, Gw, Mw, R, ld);
+            }
+            if (q.phase) { const long long c1 = clock64(); pc[1] += c1 - c0k; c0k = c1; }
+            warp_eig_os<S, S>(Lw, Ew, mu, R, ld, passes, jac_tol);
+            if (q.phase) { const long long c1 = clock64(); pc[2] += c1 - c0k; c0k = c1; }
+        } else {
             // FP32 pre-pass (float scratch in G and M), then the working-type passes
             float *f0 = reinterpret_cast<float *>(Gw);
             const int fs = R * ld;
             if (!std::is_same<S, float>::value)
                 warp_eig_prepass_f32<S>(Lw, Ew, f0, f0 + fs, f0 + 2 * fs, f0 + 3 * fs,
                                         reinterpret_cast<float *>(mu), Gw, Mw, R, ld, 6);
+            if (q.phase) { const long long c1 = clock64(); pc[1] += c1 - c0k; c0k = c1; }
+            warp_eig_factor(Lw, Ew, Gw, Mw, mu, R, ld, passes, jac_tol, 40, 1e-7f);
+            if (q.phase) { const long long c1 = clock64(); pc[2] += c1 - c0k; c0k = c1; }
         }
-        if (q.phase) { const long long c1 = clock64(); pc[1] += c1 - c0k; c0k = c1; }
-        warp_eig_factor(Lw, Ew, Gw, Mw, mu, R, ld, passes, jac_tol, 40, 1e-7f);
-        if (q.phase) { const long long c1 = clock64(); pc[2] += c1 - c0k; c0k = c1; }
         {
             // a non-finite factor or eigenvalue must not pass silently
             bool ok = true;

@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "df.cuh"
 
 namespace dash {
@@ -273,7 +275,8 @@ __device__ int warp_eig_factor(const S *L, S *E, S *G, S *M, S *mu, int R, int l
 }
 
 template <class A, class B> __device__ __forceinline__ B rt_cast(A a) {
-    return RT<B>::from_d(RT<A>::to_d(a));
+    if constexpr (std::is_same<A, B>::value) return a;
+    else return RT<B>::from_d(RT<A>::to_d(a));
 }
 template <> __device__ __forceinline__ float rt_cast<df, float>(df a) { return a.hi + a.lo; }
 template <> __device__ __forceinline__ df rt_cast<float, df>(float a) { return {a, 0.f}; }
@@ -323,6 +326,146 @@ __device__ void warp_eig_prepass_f32(const S *L, S *E, float *Lf, float *Ef, flo
     for (int i = lane; i < R * R; i += 32) E[(i / R) * ld + (i % R)] = Ms[(i / R) * ld + (i % R)];
     __syncwarp();
     }
+}
+
+// Two Newton–Schulz steps E ← E (3I − EᵀE)/2 re-orthogonalise E to the
+// precision of S (each step squares EᵀE − I).  Gs, Ms: R×ld S scratch.
+template <class S>
+__device__ void warp_newton_schulz2(S *E, S *Gs, S *Ms, int R, int ld) {
+    using O = RT<S>;
+    const int lane = threadIdx.x & 31;
+    for (int step = 0; step < 2; ++step) {
+        for (int b = lane; b < R; b += 32)
+            for (int a = 0; a < R; ++a) {
+                S acc = O::zero();
+                for (int i = 0; i < R; ++i) acc = O::fma(acc, E[i * ld + a], E[i * ld + b]);
+                Gs[a * ld + b] = acc;
+            }
+        __syncwarp();
+        for (int c = lane; c < R; c += 32)
+            for (int r = 0; r < R; ++r) {
+                S acc = O::zero();
+                for (int k = 0; k < R; ++k) {
+                    const S pk = (k == c) ? O::sub(O::from_f(3.f), Gs[k * ld + c]) : O::sub(O::zero(), Gs[k * ld + c]);
+                    acc = O::fma(acc, E[r * ld + k], pk);
+                }
+                Ms[r * ld + c] = O::mulf(acc, 0.5f);
+            }
+        __syncwarp();
+        for (int i = lane; i < R * R; i += 32) E[(i / R) * ld + (i % R)] = Ms[(i / R) * ld + (i % R)];
+        __syncwarp();
+    }
+}
+
+// One-sided (Hestenes) Jacobi for the eigen-decomposition of B = LᵀL, R <= 32,
+// register-resident: lane c holds column c of G = L·E and of E in the
+// working type W (S, or float for a cheap first pass).  A sweep pairs every
+// column with every other once: in round m (1..31) lane c meets lane c^m
+// (a perfect matching; pair (i, j) meets in round i^j), and each pair is
+// rotated so that its two columns of G become orthogonal: with α = |g_i|²,
+// β = |g_j|², γ = g_i·g_j (i < j), θ = (β − α)/(2γ),
+// t = sign(θ)/(|θ| + sqrt(1 + θ²)), c = 1/sqrt(1 + t²), s = c·t,
+// g_i ← c g_i − s g_j, g_j ← s g_i + c g_j, and the same on E's columns.
+// The lower lane of the pair computes t (in FP32: the angle need only be
+// close, the pair (c, s) in W is exactly orthogonal) and passes it to its
+// partner, so both apply one rotation.  Sweeps stop when every
+// |γ| <= tol·sqrt(αβ) or after max_sweeps.  On exit the columns of G are
+// orthogonal: E (smem, S) holds the eigenvectors and mu[c] = |g_c|² (S)
+// the eigenvalues.  Rotating G itself, never forming LᵀL, keeps the
+// relative accuracy of one-sided Jacobi (Demmel and Veselić 1992).  L (smem,
+// S, upper triangular) is read only.  Returns the sweeps run.
+template <class W, class S>
+__device__ int warp_eig_os(const S *L, S *E, S *mu, int R, int ld, int max_sweeps, float tol) {
+    using O = RT<W>;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < R;
+    W g[32], e[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) e[i] = (act && i < R) ? rt_cast<S, W>(E[i * ld + lane]) : O::zero();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        W a = O::zero();
+        if (i < R)
+#pragma unroll
+            for (int k = i; k < 32; ++k)
+                if (k < R) a = O::fma(a, rt_cast<S, W>(L[i * ld + k]), e[k]);
+        g[i] = a;
+    }
+    // Columns whose squared norm is below tol²·‖L‖_F² count as zero and are not
+    // rotated: in a rank-deficient L such a column stays collinear with a
+    // large one, so the cosine test alone would keep rotating it until it
+    // underflows (and a denormal γ would turn θ into 0·∞).
+    float fro = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) fro = fmaf(O::hi(g[i]), O::hi(g[i]), fro);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) fro += __shfl_xor_sync(full, fro, o);
+    const float flo = tol * tol * fro;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        float off = 0.f;
+        for (int m = 1; m < 32; ++m) {
+            const int p = lane ^ m;
+            W dot = O::zero(), nn = O::zero();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const W gp = O::shfl_xor(g[i], m);
+                dot = O::fma(dot, g[i], gp);
+                nn = O::fma(nn, g[i], g[i]);
+            }
+            const float np = __shfl_xor_sync(full, O::hi(nn), m);
+            const bool lo = lane < p;
+            float t = 0.f;
+            const float al = O::hi(nn), be = np;
+            if (lo && act && p < R && al > flo && be > flo) {   // this lane is i, the partner j
+                const float ga = O::hi(dot);
+                const float sc = sqrtf(al) * sqrtf(be);
+                if (fabsf(ga) > tol * sc) {
+                    off = fmaxf(off, fabsf(ga) / sc);
+                    const float df = be - al;
+                    const float th = df == 0.f ? 0.f : df * __frcp_rn(2.0f * ga);
+                    if (fabsf(th) > 1e18f) t = 0.5f * __frcp_rn(th);
+                    else {
+                        const float h = fmaf(th, th, 1.0f);
+                        t = copysignf(__frcp_rn(fabsf(th) + h * rsqrtf(h)), th);
+                    }
+                }
+            }
+            const float tp = __shfl_xor_sync(full, t, m);
+            t = lo ? t : tp;
+            if (__any_sync(full, t != 0.f)) {
+                const W tt = O::from_f(t);
+                const W c = O::rsqrt_(O::fma(O::one(), tt, tt));
+                const W sg = O::mulf(c, lo ? -t : t);     // i: c g_i − s g_j; j: c g_j + s g_i
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const W gp = O::shfl_xor(g[i], m);
+                    g[i] = O::fma(O::mul(c, g[i]), sg, gp);
+                }
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const W ep = O::shfl_xor(e[i], m);
+                    e[i] = O::fma(O::mul(c, e[i]), sg, ep);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) off = fmaxf(off, __shfl_xor_sync(full, off, o));
+        if (off == 0.f) break;
+    }
+    W nn = O::zero();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) nn = O::fma(nn, g[i], g[i]);
+    __syncwarp();
+    if (act) {
+        if (mu) mu[lane] = rt_cast<W, S>(nn);
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (i < R) E[i * ld + lane] = rt_cast<W, S>(e[i]);
+    }
+    __syncwarp();
+    return sweep;
 }
 
 // Spectral weights of B^{-1/2} and B^{1/2} from the eigenvalues mu:
