@@ -296,8 +296,8 @@ static dash_status init_alloc(dash_model *m) {
         DALLOC(m->xe, (size_t)(Nm + 16) * 4, "row exponents");
         DALLOC(m->Wf, (size_t)Km * R * 4, "w_new (FP32)");
     }
-    // FP64 fallback workspace: one slot per warp of a grid of at most 2 CTAs per SM
-    DALLOC(m->wsp, (size_t)2 * m->n_sm * FU_WARPS * fu_wsp_doubles((int)R) * 8, "fallback workspace");
+    // FP64 fallback workspace: one slot per warp of a grid of at most kBigCBlocksPerSM CTAs per SM
+    DALLOC(m->wsp, (size_t)kBigCBlocksPerSM * m->n_sm * FU_WARPS * fu_wsp_doubles((int)R) * 8, "fallback workspace");
     DALLOC(m->d_err, 4 * sizeof(int), "error counters");
     m->max_chunks = Nm / FU_TILE_MAX + Sm + 1;
     DALLOC(m->d_ch_row0, m->max_chunks * 8, "chunks");

@@ -38,6 +38,7 @@ namespace dash {
 
 constexpr int FU_THREADS = 256;
 constexpr int FU_WARPS = 8;
+constexpr int kBigCBlocksPerSM = 3;   // CTAs per SM of k_big_c (and slots of the FP64 workspace)
 constexpr int FU_TILE_MAX = 256;     // rows per tile (and max rows of a fused slice)
 constexpr int FU_NBUF = 3;           // ring slots
 constexpr int FU_SLOT_BYTES = 32768; // bytes per ring slot
@@ -242,10 +243,9 @@ __device__ __forceinline__ float chol_solve_reg(const float (&row)[FU_RP], const
 // row), A = Γ ∗ D_k is kept as double-float pairs, and the Cholesky factor is
 // formed right-looking with the pivot column broadcast by shuffles.  Lw (a
 // per-warp R×FU_LD float block) only carries L for the backward solve.
-template <bool GSM = false>
 __device__ __forceinline__ float slice_finish(const FusedArgs &a, int k, const float (&dd)[FU_RP],
                                               float dc, float (&gacc)[FU_RP], const df *Gs,
-                                              float *Lw, df *xw, double *wsp, float *gsm = nullptr) {
+                                              float *Lw, df *xw, double *wsp) {
     (void)xw;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -353,11 +353,7 @@ __device__ __forceinline__ float slice_finish(const FusedArgs &a, int k, const f
 #pragma unroll
     for (int q = 0; q < FU_RP; ++q) {
         const float wq = __shfl_sync(full, wnew, q);
-        if constexpr (GSM) {               // row `lane` of the warp's block (pitch FU_LD)
-            if (act && q < R) gsm[lane * FU_LD + q] = fmaf(wnew * dd[q], wq, gsm[lane * FU_LD + q]);
-        } else {
-            if (act && q < R) gacc[q] = fmaf(wnew * dd[q], wq, gacc[q]);
-        }
+        if (act && q < R) gacc[q] = fmaf(wnew * dd[q], wq, gacc[q]);
     }
     __syncwarp();
     return wnew;
@@ -1205,19 +1201,202 @@ static __global__ void __launch_bounds__(256, 2) k_big_b(FusedArgs a, BigArgs bg
     }
 }
 
-// (two CTAs per SM: each warp keeps its G partial in shared memory, not in
-// registers)
-static __global__ void __launch_bounds__(256, 2) k_big_c(FusedArgs a, BigArgs bg, double *Gpart_out) {
-    __shared__ df Gs[FU_RP * FU_RP];
+// chol_solve_reg with L read from the warp's shared block (Lw[l][j], pitch
+// FU_LD) in both sweeps: the same operations in the same order, in rolled
+// loops (k_big_c keeps its straight-line code short).
+__device__ __forceinline__ float chol_solve_smem(const float *Lw, float myinv, bool act, float b) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float y = act ? b : 0.f;
+#pragma unroll 4
+    for (int j = 0; j < FU_RP; ++j) {
+        const float yj = __shfl_sync(full, y * myinv, j);
+        if (lane == j) y = yj;
+        else if (lane > j) y = fmaf(-Lw[lane * FU_LD + j], yj, y);
+    }
+#pragma unroll 4
+    for (int j = FU_RP - 1; j >= 0; --j) {
+        const float xj = __shfl_sync(full, y * myinv, j);
+        if (lane == j) y = xj;
+        else if (lane < j) y = fmaf(-Lw[j * FU_LD + lane], xj, y);
+    }
+    return act ? y : 0.f;
+}
+
+// FP64 pseudo-inverse solve of W(k,:) (rare: the FP32 factor broke down):
+// A = Γ ∗ D_k, b = c_k.  Returns w_k,new[lane].
+static __device__ __forceinline__ double big_c_fallback(const FusedArgs &a, const df *Dk, df cnew, double *wsp) {
+    const int lane = threadIdx.x & 31;
+    const int R = a.R;
+    double *Aw = wsp, *Lf = Aw + R * (R + 1), *Ew = Lf + R * (R + 1);
+    double *bw = Ew + R * (R + 1), *fw = bw + (R + 1);
+    const int ld = R + 1;
+    __syncwarp();
+    for (int e = lane; e < R * R; e += 32) {
+        const int r = e / R, q = e % R;
+        Aw[r * ld + q] = a.Gam[e] * df_to_double(Dk[e]);
+    }
+    if (lane < R) bw[lane] = df_to_double(cnew);
+    __syncwarp();
+    warp_psd_solve(Aw, Lf, Ew, bw, fw, R, ld, a.rtol);
+    __syncwarp();
+    if (lane == 0) atomicAdd(&a.err[1], 1);
+    return lane < R ? bw[lane] : 0.0;
+}
+
+#ifndef BC_DB
+#define BC_DB 4
+#endif
+// k_big_c's slice finish: the arithmetic of slice_finish (Eqs. 12, 15-16,
+// 21) arranged so that a single R×R block lives in registers across the solve
+// and three CTAs fit on an SM.  ΔD is summed from the slice's chunk partials
+// once for the D_k update and once more, in the same order (so to the same
+// bits), for the slice's share S_k ΔD S_k of G_inc; Γ is read through L1;
+// D_k moves as float2 pairs.  gsm is the warp's G block (row `lane`, pitch
+// FU_LD).  Called by all 32 lanes of a warp.
+__device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &bg, int f,
+                                             float *Lw, float *gsm, double *wsp) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int R = a.R;
+    const bool act = lane < R;
+    const int k = bg.fin_k[f];
+    const int c0 = bg.fin_c0[f], c1 = bg.fin_c0[f + 1];
+    const size_t cst = (size_t)R * R + R;
+    const float2 *G2 = reinterpret_cast<const float2 *>(a.Gdf);
+    df *Dk = a.D + (int64_t)k * R * R;
+    float2 *D2 = reinterpret_cast<float2 *>(Dk);
+    const df lamdf = df_from_double(a.lam);
+    const bool keep_old = a.lam != 0.0;
+    // ΔD row `lane` (its column: ΔD is symmetric) and Δc[lane]
+    float dd[FU_RP];
+#pragma unroll
+    for (int q = 0; q < FU_RP; ++q) dd[q] = 0.f;
+    float dc = 0.f;
+    for (int c = c0; c < c1; ++c) {
+        const float *in = bg.dpart + (size_t)c * cst;
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < FU_RP; ++q)
+                if (q < R) dd[q] += in[q * R + lane];
+            dc += in[R * R + lane];
+        }
+    }
+    df cnew = {0.f, 0.f};
+    if (act) {
+        const df cold = a.c[(int64_t)k * R + lane];
+        cnew = df_add(keep_old ? df_mul(lamdf, cold) : df{0.f, 0.f}, df_make(dc));
+        a.c[(int64_t)k * R + lane] = cnew;
+    }
+    // D_k ← λD_k + ΔD and row `lane` of A = Γ ∗ D_k (hi parts); rows and
+    // columns >= R stay zero, so the factorisation runs over all 32 unguarded
+    float row[FU_RP];
+    float mydiag = 0.f;
+#pragma unroll
+    for (int r0 = 0; r0 < FU_RP; r0 += BC_DB) {
+        float2 dold[BC_DB];
+#pragma unroll
+        for (int u = 0; u < BC_DB; ++u)
+            dold[u] = (r0 + u < R && act && keep_old) ? D2[(r0 + u) * R + lane] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < BC_DB; ++u) {
+            const int r = r0 + u;
+            row[r] = 0.f;
+            if (r < R && act) {
+                const df dn = df_add(keep_old ? df_mul(lamdf, df{dold[u].x, dold[u].y}) : df{0.f, 0.f},
+                                     df_make(dd[r]));
+                D2[r * R + lane] = make_float2(dn.hi, dn.lo);
+                const float2 g = __ldg(G2 + r * R + lane);
+                row[r] = df_mul(df{g.x, g.y}, dn).hi;
+                if (r == lane) mydiag = row[r];
+            }
+        }
+    }
+    const float amax = warp_max_f(fabsf(mydiag));
+    // right-looking Cholesky of A (hi parts), lane l = row l
+    const float tol = 1e-6f * amax;
+    bool ok = amax > 0.f;
+    float myinv = 0.f;
+#pragma unroll 32
+    for (int j = 0; j < FU_RP; ++j) {
+        const float piv = __shfl_sync(full, row[j], j);
+        if (j < R) ok = ok && (piv > tol);
+        const float inv = rsqrtf(fmaxf(piv, 1e-30f));
+        const float lij = (lane == j) ? piv * inv : row[j] * inv;
+        row[j] = lij;
+        if (lane == j) myinv = inv;
+#pragma unroll 31
+        for (int q = j + 1; q < FU_RP; ++q) {
+            const float lqj = __shfl_sync(full, lij, q);
+            row[q] = fmaf(-lij, lqj, row[q]);
+        }
+    }
+    df x = {0.f, 0.f};
+    if (ok) {
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < FU_RP; ++j) Lw[lane * FU_LD + j] = row[j];
+        __syncwarp();
+        const float x0 = chol_solve_smem(Lw, myinv, act, cnew.hi);
+        // one refinement step: res = c − A x0 in double-float, A re-formed
+        // from the D_k just written
+        df res = cnew;
+#pragma unroll 4
+        for (int r = 0; r < R; ++r) {
+            const float xr = __shfl_sync(full, x0, r);
+            if (act) {
+                const float2 g = __ldg(G2 + r * R + lane);
+                const float2 d = D2[r * R + lane];
+                const df av = df_mul(df{g.x, g.y}, df{d.x, d.y});
+                res = df_sub(res, df_mul_f(av, xr));
+            }
+        }
+        const float dx = chol_solve_smem(Lw, myinv, act, res.hi);
+        x = df_add(df_make(x0), df_make(dx));
+        ok = __all_sync(full, isfinite(x.hi));
+    }
+    double wnew_d;
+    if (ok) {
+        wnew_d = act ? df_to_double(x) : 0.0;
+    } else {
+        wnew_d = big_c_fallback(a, Dk, cnew, wsp);
+    }
+    if (act) a.W[(int64_t)k * R + lane] = wnew_d;
+    if (act && a.Wf) a.Wf[(int64_t)k * R + lane] = (float)wnew_d;
+    const float wnew = (float)wnew_d;
+    // S_k ΔD S_k, row `lane`, into the warp's G block: ΔD summed again
+#pragma unroll 1
+    for (int q0 = 0; q0 < R; q0 += 8) {
+        float sd[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sd[u] = 0.f;
+        for (int c = c0; c < c1; ++c) {
+            const float *in = bg.dpart + (size_t)c * cst;
+            if (act)
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (q0 + u < R) sd[u] += in[(q0 + u) * R + lane];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u;
+            const float wq = __shfl_sync(full, wnew, q);
+            if (act && q < R) gsm[lane * FU_LD + q] = fmaf(wnew * sd[u], wq, gsm[lane * FU_LD + q]);
+        }
+    }
+    __syncwarp();
+}
+
+// Three CTAs of eight warps per SM (at most 80 registers a thread); each warp
+// finishes whole slices and keeps its G partial in shared memory, the CTA
+// sums the eight partials in a fixed order.
+static __global__ void __launch_bounds__(256, kBigCBlocksPerSM) k_big_c(FusedArgs a, BigArgs bg, double *Gpart_out) {
     __shared__ __align__(16) float Lw_all[FU_WARPS][FU_RP * FU_LD];
     __shared__ float G_all[FU_WARPS][FU_RP * FU_LD];                  // per-warp G partials
-    __shared__ df xw_all[FU_WARPS][FU_RP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = a.R;
-    for (int i = threadIdx.x; i < R * R; i += blockDim.x) Gs[(i / R) * FU_RP + (i % R)] = a.Gdf[i];
     for (int i = threadIdx.x; i < FU_WARPS * FU_RP * FU_LD; i += blockDim.x) (&G_all[0][0])[i] = 0.f;
     __syncthreads();
-    float gacc[FU_RP];                      // unused: the partials live in G_all
     double *wsp = a.wsp + (size_t)(blockIdx.x * FU_WARPS + warp) * fu_wsp_doubles(R);
     // bring the next slice's state (D_k, c_k, W(k,:)) and chunk partials into
     // L2 while this one is finished
@@ -1237,21 +1416,7 @@ static __global__ void __launch_bounds__(256, 2) k_big_c(FusedArgs a, BigArgs bg
     };
     for (int f = blockIdx.x * FU_WARPS + warp; f < bg.n_fin; f += gridDim.x * FU_WARPS) {
         prefetch(f + gridDim.x * FU_WARPS);
-        const int k = bg.fin_k[f];
-        float dd[FU_RP];
-#pragma unroll
-        for (int q = 0; q < FU_RP; ++q) dd[q] = 0.f;
-        float dc = 0.f;
-        for (int c = bg.fin_c0[f]; c < bg.fin_c0[f + 1]; ++c) {
-            const float *in = bg.dpart + (size_t)c * (R * R + R);
-            if (lane < R) {                 // symmetric: column `lane`, coalesced
-#pragma unroll
-                for (int q = 0; q < FU_RP; ++q)
-                    if (q < R) dd[q] += in[q * R + lane];
-                dc += in[R * R + lane];
-            }
-        }
-        slice_finish<true>(a, k, dd, dc, gacc, Gs, Lw_all[warp], xw_all[warp], wsp, G_all[warp]);
+        big_c_finish(a, bg, f, Lw_all[warp], G_all[warp], wsp);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {

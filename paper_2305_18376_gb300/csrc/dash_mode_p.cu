@@ -147,7 +147,11 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
                     LAUNCH(KK_BIG_B, k_big_b<<<gb, 256, 0, st>>>(fa, bg));
             }
             if (m->n_fin > 0) {
-                nsb = std::min(2 * m->n_sm, (m->n_fin + FU_WARPS - 1) / FU_WARPS);
+                nsb = std::min(kBigCBlocksPerSM * m->n_sm, (m->n_fin + FU_WARPS - 1) / FU_WARPS);
+                // the whole unified L1/shared array as shared memory, so that
+                // kBigCBlocksPerSM CTAs fit on an SM
+                CK(cudaFuncSetAttribute(k_big_c, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
                 LAUNCH(KK_BIG_C, k_big_c<<<nsb, 256, 0, st>>>(fa, bg, m->Gpart + (size_t)g_f * R * R));
             }
             finished = true;
