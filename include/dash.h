@@ -252,6 +252,21 @@ dash_status dash_rows_error(dash_model *m, int64_t n_seg, const int64_t *slice_i
 /* Wait for all work issued on the model's stream. */
 dash_status dash_sync(dash_model *m);
 
+/* Device memory (serving admission; the paper has no counterpart).
+ * dash_config_bytes(): the device and pinned host bytes dash_init would
+ * allocate for *cfg (each allocation rounded up to 512 bytes), computed
+ * without allocating anything; DASH_EINVAL (and no sizes) for a config
+ * dash_init would reject.  dash_device_bytes(): the device bytes the handle
+ * owns (0 for NULL); the same figure as dash_config_bytes() for its config.
+ * Either pointer may be NULL. */
+dash_status dash_config_bytes(const dash_config *cfg, int64_t *device_bytes, int64_t *host_bytes);
+int64_t dash_device_bytes(const dash_model *m);
+
+/* Non-blocking completion test: *idle = 1 when every copy and kernel the
+ * model has issued (its stream and its copy streams) has finished, else 0.
+ * Never waits.  DASH_ECUDA if a stream reports an error. */
+dash_status dash_query(const dash_model *m, int32_t *idle);
+
 /* Per-update device time of the last dash_update (CUDA events, ms). */
 dash_status dash_last_update_ms(const dash_model *m, float *ms);
 

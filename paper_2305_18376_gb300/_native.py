@@ -66,6 +66,9 @@ SIGNATURES = [
     ("dash_new_rows", C.c_int, [P, PD, PI64]),
     ("dash_fitness", C.c_int, [P, PD, PD]),
     ("dash_sync", C.c_int, [P]),
+    ("dash_config_bytes", C.c_int, [C.POINTER(Config), PI64, PI64]),
+    ("dash_device_bytes", I64, [P]),
+    ("dash_query", C.c_int, [P, C.POINTER(C.c_int32)]),
     ("dash_last_update_ms", C.c_int, [P, C.POINTER(C.c_float)]),
     ("dash_launch_count", I64, [P]),
     ("dash_profile_enable", C.c_int, [P, I32]),
@@ -113,6 +116,34 @@ def _i64(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
 
 
+def _config(lib, J: int, R: int, lam: float, mode: str = "P", precision: str = "fp32",
+            input_dtype: str = "f32", max_slices: int = 1 << 16, max_rows: int = 1 << 20,
+            max_segments: int = 1 << 17, pinv_rtol: float = 0.0, stream=None,
+            max_staged_rows: int = 0) -> Config:
+    cfg = Config()
+    lib.dash_config_default(C.byref(cfg), J, R, lam)
+    cfg.mode = DASH_MODE_P if mode == "P" else DASH_MODE_Q
+    cfg.precision = PREC[precision]
+    cfg.input_dtype = DTYPE[input_dtype]
+    cfg.max_slices, cfg.max_rows, cfg.max_segments = max_slices, max_rows, max_segments
+    cfg.pinv_rtol = pinv_rtol
+    cfg.stream = stream
+    cfg.max_staged_rows = max_staged_rows
+    return cfg
+
+
+def config_bytes(J: int, R: int, lam: float, **kw) -> tuple:
+    """(device bytes, pinned host bytes) that a DashModel with these
+    arguments allocates, computed without allocating (dash_config_bytes)."""
+    lib = load()
+    cfg = _config(lib, J, R, lam, **kw)
+    dev, host = C.c_int64(), C.c_int64()
+    st = lib.dash_config_bytes(C.byref(cfg), C.byref(dev), C.byref(host))
+    if st != 0:
+        raise DashError(st, "dash_config_bytes rejected the configuration")
+    return dev.value, host.value
+
+
 class DashModel:
     """One streaming PARAFAC2 model behind the C ABI (dash_init ...)."""
 
@@ -121,15 +152,8 @@ class DashModel:
                  max_segments: int = 1 << 17, pinv_rtol: float = 0.0, stream=None,
                  max_staged_rows: int = 0):
         lib = load()
-        cfg = Config()
-        lib.dash_config_default(C.byref(cfg), J, R, lam)
-        cfg.mode = DASH_MODE_P if mode == "P" else DASH_MODE_Q
-        cfg.precision = PREC[precision]
-        cfg.input_dtype = DTYPE[input_dtype]
-        cfg.max_slices, cfg.max_rows, cfg.max_segments = max_slices, max_rows, max_segments
-        cfg.pinv_rtol = pinv_rtol
-        cfg.stream = stream
-        cfg.max_staged_rows = max_staged_rows
+        cfg = _config(lib, J, R, lam, mode, precision, input_dtype, max_slices, max_rows,
+                      max_segments, pinv_rtol, stream, max_staged_rows)
         h = P()
         st = lib.dash_init(C.byref(cfg), C.byref(h))
         if st != 0:
@@ -284,6 +308,16 @@ class DashModel:
 
     def sync(self):
         self._ck(self._lib.dash_sync(self._h))
+
+    def device_bytes(self) -> int:
+        """Device memory the model owns."""
+        return int(self._lib.dash_device_bytes(self._h))
+
+    def idle(self) -> bool:
+        """True when all work the model has issued has finished (never waits)."""
+        v = C.c_int32()
+        self._ck(self._lib.dash_query(self._h, C.byref(v)))
+        return bool(v.value)
 
     # ---- staging -------------------------------------------------------------
     def _ptr(self, X):

@@ -183,8 +183,16 @@ extern "C" void dash_config_default(dash_config *cfg, int32_t J, int32_t R, doub
 // ---------------------------------------------------------------------------
 // allocation helpers
 // ---------------------------------------------------------------------------
+// cudaMalloc's granularity for the footprint accounting
+static int64_t alloc_rounded(size_t bytes) { return (int64_t)((bytes + 511) / 512 * 512); }
+
 static dash_status dalloc(dash_model *m, void **p, size_t bytes, const char *what) {
     if (bytes == 0) bytes = 16;
+    m->dev_bytes += alloc_rounded(bytes);
+    if (m->dry) {
+        *p = nullptr;
+        return DASH_OK;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -211,6 +219,11 @@ static void free_all(dash_model *m) {
 
 static dash_status halloc(dash_model *m, void **p, size_t bytes) {
     if (bytes == 0) bytes = 16;
+    m->host_bytes += alloc_rounded(bytes);
+    if (m->dry) {
+        *p = nullptr;
+        return DASH_OK;
+    }
     cudaError_t e = cudaMallocHost(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -327,16 +340,14 @@ static dash_status init_alloc(dash_model *m) {
     if ((s = halloc(m, (void **)&m->h_ch_k, m->max_chunks * 4))) return s;
     if ((s = halloc(m, (void **)&m->h_fin_k, Km * 4))) return s;
     if ((s = halloc(m, (void **)&m->h_fin_c0, (Km + 1) * 4))) return s;
+    if (m->dry) return DASH_OK;
     memset(m->h_err, 0, 4 * sizeof(int));
     cudaMemsetAsync(m->d_err, 0, 4 * sizeof(int), m->stream);
     return DASH_OK;
 }
 
-extern "C" dash_status dash_init(const dash_config *cfg, dash_model **out) {
-    if (!cfg || !out) return DASH_EINVAL;
-    *out = nullptr;
-    dash_model *m = new dash_model();
-    m->cfg = *cfg;
+// Validate m->cfg and derive the sizes init_alloc uses (no CUDA allocation).
+static dash_status init_check(dash_model *m) {
     const dash_config &c = m->cfg;
     auto bad = [&](const char *msg) {
         fail(m, DASH_EINVAL, "%s", msg);
@@ -353,13 +364,7 @@ extern "C" dash_status dash_init(const dash_config *cfg, dash_model **out) {
     else if (c.n_sweeps != 1) st = bad("only n_sweeps = 1 is supported");
     else if (c.max_slices < 1 || c.max_rows < 1 || c.max_segments < 1) st = bad("capacities must be positive");
     else if (c.max_slices > INT32_MAX / 2 || c.max_segments > INT32_MAX / 2) st = bad("capacity too large");
-    if (st != DASH_OK) {
-        // keep the message reachable through a static copy
-        static thread_local std::string last;
-        last = m->err;
-        delete m;
-        return st;
-    }
+    if (st != DASH_OK) return st;
     m->rtol = c.pinv_rtol > 0.0 ? c.pinv_rtol : (double)c.R * DBL_EPSILON;
     m->tsize = (c.precision == DASH_PREC_FP64) ? 8 : 4;
     m->df_state = c.precision != DASH_PREC_FP64;
@@ -376,6 +381,33 @@ extern "C" dash_status dash_init(const dash_config *cfg, dash_model **out) {
     m->st.R = c.R;
     m->st.lam = c.lambda;
     m->st.rtol = m->rtol;
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_config_bytes(const dash_config *cfg, int64_t *device_bytes, int64_t *host_bytes) {
+    if (!cfg) return DASH_EINVAL;
+    dash_model m;
+    m.cfg = *cfg;
+    m.dry = true;
+    dash_status st = init_check(&m);
+    if (st == DASH_OK) st = init_alloc(&m);
+    if (st != DASH_OK) return st;
+    if (device_bytes) *device_bytes = m.dev_bytes;
+    if (host_bytes) *host_bytes = m.host_bytes;
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_init(const dash_config *cfg, dash_model **out) {
+    if (!cfg || !out) return DASH_EINVAL;
+    *out = nullptr;
+    dash_model *m = new dash_model();
+    m->cfg = *cfg;
+    const dash_config &c = m->cfg;
+    dash_status st = init_check(m);
+    if (st != DASH_OK) {
+        delete m;
+        return st;
+    }
     if (c.stream) {
         m->stream = (cudaStream_t)c.stream;
         m->own_stream = false;
@@ -439,6 +471,29 @@ extern "C" void dash_destroy(dash_model *m) {
 }
 
 extern "C" int64_t dash_num_slices(const dash_model *m) { return m ? m->K : -1; }
+
+extern "C" int64_t dash_device_bytes(const dash_model *m) { return m ? m->dev_bytes : 0; }
+
+extern "C" dash_status dash_query(const dash_model *mc, int32_t *idle) {
+    if (!mc || !idle) return DASH_EINVAL;
+    dash_model *m = const_cast<dash_model *>(mc);
+    int32_t done = 1;
+    cudaStream_t sts[1 + kCopyStreams] = {m->stream};
+    for (int i = 0; i < kCopyStreams; ++i) sts[1 + i] = m->copy_streams[i];
+    for (int i = 0; i <= kCopyStreams; ++i) {
+        const cudaStream_t s = sts[i];
+        if (i > 0 && !s) continue;                   // no copy streams on this model
+        const cudaError_t e = cudaStreamQuery(s);
+        if (e == cudaErrorNotReady) {
+            done = 0;
+        } else if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(m, DASH_ECUDA, "cudaStreamQuery: %s", cudaGetErrorString(e));
+        }
+    }
+    *idle = done;
+    return DASH_OK;
+}
 
 extern "C" dash_status dash_sync(dash_model *m) {
     if (!m) return DASH_EINVAL;

@@ -180,4 +180,6 @@ struct dash_model {
     dash::Profiler prof;
 
     std::vector<void *> allocs, host_allocs;
+    bool dry = false;                      // init_alloc only counts bytes (dash_config_bytes)
+    int64_t dev_bytes = 0, host_bytes = 0; // owned device / pinned host memory
 };

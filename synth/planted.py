@@ -47,6 +47,9 @@ class Workload:
     lam: float                 # forgetting factor used by this workload
     seed: int
     drift: float = 0.0         # V of update t is V + drift·t·V_d (a drifting stream)
+    touch: Tuple = ()          # () every existing slice gets rows; ("uniform", lo, hi): per
+                               # update a fraction f ~ U(lo, hi) of them, each with prob. f
+    new_slices_dist: Tuple = ()  # () new_slices_per_step per update; else L drawn per update
 
 
 def _w(name, idx, **kw):
@@ -134,16 +137,34 @@ class PlantedStream:
         self.dtype = dtype
         seed = w.seed if seed is None else seed
         g = torch.Generator(device="cpu").manual_seed(seed)
-        L, T = w.new_slices_per_step, w.steps
-        self.K_total = w.K0 + L * T
+        T = w.steps
+        # new slices per update (extra draws only for a drawn L, so streams
+        # with a fixed L are unchanged)
+        if w.new_slices_dist:
+            self.L_t = [0] + _draw_counts(w.new_slices_dist, T, g).tolist()
+        else:
+            self.L_t = [0] + [w.new_slices_per_step] * T
+        self.K_before_t = [0] * (T + 1)
+        for t in range(2, T + 1):
+            self.K_before_t[t] = self.K_before_t[t - 1] + self.L_t[t - 1]
+        for t in range(1, T + 1):
+            self.K_before_t[t] += w.K0
+        self.K_total = w.K0 + sum(self.L_t)
         # ---- row counts (host, int64) --------------------------------------
         born = torch.zeros(self.K_total, dtype=torch.int64)   # arrival update
         first = torch.empty(self.K_total, dtype=torch.int64)  # rows at arrival
         first[: w.K0] = _draw_counts(w.init_rows, w.K0, g)
         self.step_rows: List[torch.Tensor] = [first[: w.K0].clone()]
         for t in range(1, T + 1):
-            k_exist = w.K0 + L * (t - 1)
+            k_exist = self.K_before_t[t]
+            L = self.L_t[t]
             grow = _draw_counts(w.rows_per_step, k_exist, g)
+            if w.touch:                        # a random fraction of the slices
+                kind, flo, fhi = w.touch
+                if kind != "uniform":
+                    raise ValueError(f"unknown touch distribution {w.touch!r}")
+                f = flo + (fhi - flo) * float(torch.rand(1, generator=g, dtype=torch.float64))
+                grow = grow * (torch.rand(k_exist, generator=g, dtype=torch.float64) < f)
             lo = k_exist
             first[lo: lo + L] = _draw_counts(w.new_slice_rows, L, g)
             born[lo: lo + L] = t
@@ -232,8 +253,8 @@ class PlantedStream:
         w = self.w
         rows = self.step_rows[t]
         k_count = rows.numel()
-        K_before = 0 if t == 0 else w.K0 + w.new_slices_per_step * (t - 1)
-        n_new = w.K0 if t == 0 else w.new_slices_per_step
+        K_before = 0 if t == 0 else self.K_before_t[t]
+        n_new = w.K0 if t == 0 else self.L_t[t]
         ids = torch.arange(k_count, dtype=torch.int64)
         row_ptr = torch.zeros(k_count + 1, dtype=torch.int64)
         row_ptr[1:] = torch.cumsum(rows, 0)
@@ -255,6 +276,11 @@ class PlantedStream:
             if w.sigma:
                 X[c0:c1].add_(torch.randn(c1 - c0, w.J, generator=self._dgen,
                                           device=self.device, dtype=self.dtype), alpha=w.sigma)
+        if w.touch and t > 0:                  # list only the touched old slices
+            keep = (rows > 0) | (ids >= K_before)
+            ids = ids[keep]
+            row_ptr = torch.zeros(ids.numel() + 1, dtype=torch.int64)
+            row_ptr[1:] = torch.cumsum(rows[keep], 0)
         return Batch(slice_ids=ids, row_ptr=row_ptr, X=X,
                      K_before=K_before, n_new=n_new)
 
