@@ -58,6 +58,15 @@ def parse():
     ap.add_argument("--lambda-sweep", action="store_true",
                     help="local and global errors of a drifting stream for several forgetting "
                     "factors (prints one JSON line; not the bench line)")
+    ap.add_argument("--serving", action="store_true",
+                    help="the serving loop on many independent streams with Poisson arrivals: "
+                    "p50/p99 update latency and rows/s, mixed and FP64 (prints one JSON line; "
+                    "not the bench line)")
+    ap.add_argument("--serve-streams", type=int, default=8)
+    ap.add_argument("--serve-seconds", type=float, default=0.5)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-k0-max", type=int, default=1000)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     return ap.parse_args()
 
 
@@ -770,6 +779,102 @@ def run_lambda_sweep(a):
                       "precision": a.precision, "lambda": res}))
 
 
+def _replay_requests(load, s, b0, pool, K0, tdt, Request):
+    """Stream s's requests: its initial fit, then one update per arrival,
+    replaying the pool of planted batches in turn.  Old slices keep their
+    ids (the pool's old ids exist by the time a batch is replayed); new
+    slices are renumbered to follow the stream's current slice count."""
+    import numpy as np
+    reqs = [Request(stream=s, arrival=0.0, kind="init", slice_ids=b0.slice_ids.numpy(),
+                    row_ptr=b0.row_ptr.numpy(), X=b0.X, init_iters=1, rows=b0.n_rows)]
+    K = K0
+    i = 0
+    for (t_arr, s2, _) in load.arrivals:
+        if s2 != s:
+            continue
+        b = pool[i % len(pool)]
+        i += 1
+        ids = b.slice_ids.numpy().copy()
+        new = ids >= b.K_before
+        ids[new] = K + (ids[new] - b.K_before)
+        K += b.n_new
+        reqs.append(Request(stream=s, arrival=t_arr, kind="update", slice_ids=ids,
+                            row_ptr=b.row_ptr.numpy(), X=b.X, rows=b.n_rows))
+    return reqs, K
+
+
+def run_serving(a):
+    """Serving loop (paper_2305_18376_gb300.serving) over the serving workload
+    (synth.serving): independent planted streams, update batches arriving as
+    one Poisson process.  Each stream's update batches come from a pool of
+    three planted batches generated on the device and replayed in turn.
+    Initial fits run first, untimed; the updates are then served in real
+    time.  Reports the latency (arrival to completion) and rows/s of the
+    updates, for the mixed and the FP64 paths."""
+    import numpy as np
+    import torch
+
+    from paper_2305_18376_gb300.serving import Request, ServingLoop, latency_summary
+    from synth.planted import PlantedStream, scaled
+    from synth.serving import serving_load
+
+    load = serving_load(n_streams=a.serve_streams, duration=a.serve_seconds, rate=a.serve_rate,
+                        K0_range=(500, a.serve_k0_max))
+    out = {"metric": "serving: update latency (arrival to completion) and rows/s",
+           "streams": a.serve_streams, "arrivals": len(load.arrivals), "rate_per_s": a.serve_rate,
+           "seconds": a.serve_seconds, "data": "synthetic",
+           "config": {"workload": f"serving: {a.serve_streams} planted streams, J in (64, 128, 256), "
+                                  f"R in (8, 16, 32), K0 in [500, {a.serve_k0_max}], Poisson arrivals "
+                                  f"{a.serve_rate:g}/s for {a.serve_seconds:g} s, each batch touching a "
+                                  "fraction U(0,1] of the slices with U{1..256} rows plus U{0..50} new "
+                                  "slices; batches replayed from a pool of 3 per stream, device-resident"}}
+    for prec, tdt, idt in (("f16x3", torch.float32, "f32"), ("fp64", torch.float64, "f64")):
+        specs, reqs_init, reqs_upd, V0 = {}, [], [], {}
+        for s, w in enumerate(load.streams):
+            ps = PlantedStream(scaled(w, steps=3), device="cuda", dtype=tdt)
+            b0 = ps.batch(0)
+            pool = [ps.batch(t) for t in range(1, 4)]
+            reqs, K_end = _replay_requests(load, s, b0, pool, w.K0, tdt, Request)
+            reqs_init.append(reqs[0])
+            reqs_upd.extend(reqs[1:])
+            specs[s] = dict(J=w.J, R=w.R, lam=w.lam, precision=prec, input_dtype=idt,
+                            max_slices=K_end + 8,
+                            max_rows=max([b0.n_rows] + [b.n_rows for b in pool]) + 16,
+                            max_segments=max(b.slice_ids.numel() for b in [b0] + pool) + 8)
+            V0[s] = np.random.default_rng(s).random((w.J, w.R))
+        torch.cuda.synchronize()
+        counters = {}
+        loop = ServingLoop(specs, int(a.serve_budget_gb * 1e9), max_inflight=max(2, a.serve_streams),
+                           prepare=lambda s, m: m.set_factors(V0[s]),
+                           on_retire=lambda s, m: counters.setdefault(s, (m.counters(), m.K)))
+        loop.run(reqs_init, realtime=False)
+        torch.cuda.synchronize()
+        loop.run(reqs_upd, realtime=True)
+        summ = latency_summary(reqs_upd)
+        summ["peak_resident_gb"] = loop.peak_resident / 1e9
+        loop.close()
+        # per stream: queueing (arrival to admission) against service (admission
+        # to completion), and the numerical counters
+        per = []
+        for s, w in enumerate(load.streams):
+            rs = [r for r in reqs_upd if r.stream == s]
+            if not rs:
+                continue
+            svc = np.array([r.done - r.admitted for r in rs]) * 1e3
+            lat = np.array([r.latency for r in rs]) * 1e3
+            (timeouts, fallbacks), K_end = counters.get(s, ((None, None), None))
+            per.append({"stream": s, "J": w.J, "R": w.R, "K0": w.K0, "K_end": K_end,
+                        "updates": len(rs), "rows": int(sum(r.rows for r in rs)),
+                        "service_ms_median": float(np.median(svc)), "service_ms_max": float(svc.max()),
+                        "latency_ms_max": float(lat.max()), "wait_timeouts": timeouts,
+                        "fp64_fallback_solves": fallbacks})
+        summ["per_stream"] = per
+        out["mixed" if prec == "f16x3" else "fp64"] = summ
+        del reqs_init, reqs_upd
+        torch.cuda.empty_cache()
+    print(json.dumps(out))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -778,6 +883,8 @@ def main():
         run_cycle_scan(a)
     elif a.lambda_sweep:
         run_lambda_sweep(a)
+    elif a.serving:
+        run_serving(a)
     else:
         run_ours(a)
 
