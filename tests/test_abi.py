@@ -72,3 +72,35 @@ def test_init_rejects_bad_arguments_before_touching_the_device(lib):
         h = C.c_void_p()
         assert lib.dash_init(C.byref(cfg), C.byref(h)) == 1, field
         assert not h.value
+
+
+def test_config_bytes_counts_the_allocation_list_without_a_device(lib):
+    """dash_config_bytes runs dash_init's allocation list in a counting mode:
+    no device is touched, bad configs are rejected like dash_init rejects
+    them, and the count grows with the capacities as the per-slice and
+    per-row buffers say (D_k, c_k, W(k,:) in 8-byte words; staged X in the
+    input dtype, twice for the double staging)."""
+    from paper_2305_18376_gb300 import _native
+
+    def count(**kw):
+        cfg = _native._config(lib, **{"J": 64, "R": 8, "lam": 0.9, "precision": "f16x3", **kw})
+        dev, host = C.c_int64(), C.c_int64()
+        assert lib.dash_config_bytes(C.byref(cfg), C.byref(dev), C.byref(host)) == 0
+        return dev.value, host.value
+
+    base = dict(max_slices=4096, max_rows=8192, max_segments=4096)
+    d0, h0 = count(**base)
+    assert d0 > 0 and h0 > 0
+    # 4096 more slices: D (R·R), c (R), W (R) in 8 bytes, plus small per-slice words
+    d1, _ = count(**{**base, "max_slices": 8192})
+    per_slice = (d1 - d0) / 4096
+    assert 8 * (8 * 8 + 2 * 8) <= per_slice < 8 * (8 * 8 + 2 * 8) + 128
+    # 8192 more rows: at least the two staging buffers of J FP32 values a row
+    d2, _ = count(**{**base, "max_rows": 16384})
+    assert (d2 - d0) / 8192 >= 2 * 64 * 4
+    # FP64 input doubles the two staging buffers and nothing else (FP64 products)
+    d4, _ = count(**base, precision="fp64", input_dtype="f32")
+    d5, _ = count(**base, precision="fp64", input_dtype="f64")
+    assert d5 - d4 == 2 * 8192 * 64 * 4
+    cfg = _native._config(lib, J=64, R=65, lam=0.9)
+    assert lib.dash_config_bytes(C.byref(cfg), None, None) == 1
