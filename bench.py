@@ -27,7 +27,7 @@ if ROOT not in sys.path:
 
 METRIC = "Dash update rows/s & p50/p99 latency, mixed-prec vs FP64 on 1 GB300"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-FP64_FMA_TFLOPS = 1.20     # measured FMA-loop FP64 rate of this machine's GB300
+FP64_FMA_TFLOPS = 1.20     # FP64 FMA rate of a GB300, measured with an independent-FMA loop kernel
 
 
 def parse():
@@ -133,7 +133,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work ("Roofline")
+# algorithmic work: the bytes (or flops) each kernel must move per launch
 # ---------------------------------------------------------------------------
 def algorithmic(kernel: str, plan: dict, N: int, K_all: int, J: int, R: int, tsize: int,
                 isize: int):
@@ -506,7 +506,7 @@ def run_ours(a):
                 roof = {"bound": "alu", "achieved": fl / per / 1e12, "peak": FP64_FMA_TFLOPS,
                         "unit": "TFLOP/s", "frac": fl / per / 1e12 / FP64_FMA_TFLOPS,
                         "traffic": ncu_traffic(name), "kernel": name,
-                        "peak_source": "FP64 FMA-loop measurement (DESIGN.md)"}
+                        "peak_source": "FP64 FMA-loop measurement on a GB300"}
             else:
                 roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                         "frac": ach / hbm, "traffic": ncu_traffic(name), "kernel": name,

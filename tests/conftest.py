@@ -14,7 +14,7 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    # GPU tests cannot run without a device: skip them (they run on the GPU machine)
+    # GPU tests cannot run without a device: skip them here
     try:
         import torch
         has_gpu = torch.cuda.is_available()
