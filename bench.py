@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--init-iters", type=int, default=3)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-slices", type=int, default=200,
+    ap.add_argument("--cpu-slices", type=int, default=50,
                     help="slices in the oracle's bounded CPU sample")
     ap.add_argument("--profile-out", default="", help="write the per-kernel profile here")
     ap.add_argument("--k0", type=int, default=0, help="override the initial slice count "
@@ -224,7 +224,18 @@ def ncu_traffic(kernel: str):
 # ---------------------------------------------------------------------------
 # CPU baseline / reference arm: the FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample(wname: str, n_slices: int, n_updates: int, warm: int = 0):
+def oracle_sample(wname: str, n_slices: int, n_updates: int, warm: int = 0, init_iters: int = 3):
+    """Time the FP64 oracle's mode-P update (Algorithm 1) on a bounded sample
+    of workload `wname`: the same stream recipe with n_slices initial slices
+    (new slices per update scaled down in proportion).
+
+    The starting state is fitted the way the GPU arm fits its own: the
+    workload's initial row recipe, then `init_iters` static ALS iterations
+    from V0 ~ U(0,1), W0 = 1, each one oracle update on empty helpers (λ = 0,
+    which equals one static ALS iteration), then the helpers of the final
+    factors (Eqs. 6-9).  Algorithm 1 fixes no scale between S_k and V, so from
+    an unfitted start (one iteration, or slices of a few rows) W grows and V
+    shrinks without bound within a few updates; a fitted start stays put."""
     import numpy as np
     import torch
     from oracle import dash_oracle as O
@@ -235,17 +246,18 @@ def oracle_sample(wname: str, n_slices: int, n_updates: int, warm: int = 0):
     except Exception:
         blas = os.cpu_count() or 1
     w = workload(wname)
-    # the update's cost depends on the new rows and on K, not on the history:
-    # the untimed initial tensor of the sample keeps R..2R rows per slice
     w = type(w)(**{**w.__dict__, "K0": n_slices, "steps": warm + n_updates,
-                   "init_rows": ("uniform", w.R, 2 * w.R),
                    "new_slices_per_step": max(1, w.new_slices_per_step * n_slices // w.K0)})
     s = PlantedStream(w, dtype=torch.float32)
     b0 = s.batch(0)
-    X0 = [x.double().numpy() for _, x in b0.segments()]
-    V0 = np.random.default_rng(0).random((w.J, w.R))
-    U, W, V = O.static_als_p(X0, V0, np.ones((len(X0), w.R)), 1)
-    st = O.init_helpers_p(X0, U, W, V)
+    segs0 = [(k, x.double().numpy()) for k, x in b0.segments()]
+    t_init = time.perf_counter()
+    st = O.empty_state_p(np.random.default_rng(0).random((w.J, w.R)))
+    U = {}
+    for it in range(init_iters):
+        st, U = O.dash_update_p(st, segs0, b0.n_new if it == 0 else 0, 0.0)
+    st = O.init_helpers_p([x for _, x in segs0], [U[k] for k in range(len(segs0))], st.W, st.V)
+    t_init = time.perf_counter() - t_init
     times, rows = [], []
     for t in range(1, warm + n_updates + 1):
         b = s.batch(t)
@@ -256,10 +268,14 @@ def oracle_sample(wname: str, n_slices: int, n_updates: int, warm: int = 0):
         if t > warm:
             times.append(dt)
             rows.append(b.n_rows)
+    if not all(np.isfinite(st.V).ravel()) or not all(np.isfinite(st.W).ravel()):
+        raise RuntimeError("oracle sample state went non-finite")
     return {"rows": rows, "times": times, "cores": blas, "nproc": os.cpu_count(),
-            "sample": f"{wname} update recipe on K0={n_slices} slices (J={w.J}, R={w.R}; "
-                      f"untimed initial tensor of R..2R rows per slice), {n_updates} timed "
-                      f"updates, oracle mode P in numpy float64"}
+            "init_s": t_init, "max_abs_W": float(np.abs(st.W).max()),
+            "sample": f"{wname} update recipe on K0={n_slices} slices (J={w.J}, R={w.R}, the "
+                      f"workload's initial row recipe, {b0.n_rows} rows, fitted by "
+                      f"{init_iters} untimed static ALS iterations), {n_updates} timed "
+                      f"updates after {warm} untimed, oracle mode P in numpy float64"}
 
 
 def run_reference(a):
@@ -268,7 +284,8 @@ def run_reference(a):
         return
     from synth.planted import workload
     w = workload(a.workload)
-    r = oracle_sample(a.workload, a.cpu_slices, a.steps, warm=a.warmup)
+    r = oracle_sample(a.workload, a.cpu_slices, a.steps, warm=a.warmup,
+                      init_iters=a.init_iters)
     tot_rows, tot_t = sum(r["rows"]), sum(r["times"])
     v = tot_rows / tot_t
     lat = sorted(r["times"])
@@ -518,7 +535,7 @@ def run_ours(a):
         mq.close()
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
-        r = oracle_sample(a.workload, a.cpu_slices, 2)
+        r = oracle_sample(a.workload, a.cpu_slices, 12, init_iters=a.init_iters)
         cpu = {"value": sum(r["rows"]) / sum(r["times"]), "unit": "rows/s", "cores": r["cores"],
                "kind": "oracle", "sample": r["sample"], "nproc": r["nproc"]}
     if rank == 0:

@@ -36,8 +36,10 @@ Parity pins (tests/test_oracle_*.py): Lemma 1–3 optimality against direct
 least squares, the Khatri–Rao identity of Appendix A.2, λ = 1 exactness of
 the streamed summaries, the replay identity for c_k, F, G, single-batch
 equality with static ALS written independently, noiseless planted recovery,
-the R = 1 reduction to a power iteration, orthonormal Q_k, and a worked
-example derived by hand (tests/golden/).
+the R = 1 reduction to a power iteration, orthonormal Q_k, a two-update
+worked example carried out by hand in exact fractions, the fitness's root
+on a hand value, and the constrained-mode initial helpers against their
+entry-by-entry definition.
 """
 from __future__ import annotations
 

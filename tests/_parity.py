@@ -22,6 +22,39 @@ def rel(a, b) -> float:
     return float(np.max(np.abs(a - b))) / scale
 
 
+def rel_rows(a, b) -> float:
+    """Largest normwise relative error over the leading index (per slice for
+    W, c and D): a slice whose own entries are small relative to the largest
+    slice is judged at its own scale.  A slice whose reference is exactly zero
+    is judged against the global scale."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if b.size == 0:
+        return 0.0
+    a2 = a.reshape(a.shape[0], -1)
+    b2 = b.reshape(b.shape[0], -1)
+    gscale = max(float(np.max(np.abs(b2))), 1e-300)
+    scale = np.max(np.abs(b2), axis=1)
+    scale = np.where(scale > 0.0, scale, gscale)
+    return float(np.max(np.max(np.abs(a2 - b2), axis=1) / scale))
+
+
+def record(step: str, errors: dict, limits=None):
+    """Append one parity record (the measured errors and the limits applied)
+    of the running test to the JSON-lines file named by DASH_PARITY_RECORD,
+    if set."""
+    import json
+    import os
+    path = os.environ.get("DASH_PARITY_RECORD")
+    if not path:
+        return
+    test = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+    fl = lambda d: {k: float(v) for k, v in d.items()} if isinstance(d, dict) else d
+    with open(path, "a") as f:
+        f.write(json.dumps({"test": test, "step": step, "errors": fl(errors),
+                            "limits": fl(limits)}) + "\n")
+
+
 def segs_np(batch, dtype):
     """(k, X) pairs with X rounded to the GPU's input dtype (the oracle sees
     exactly the values the kernels read)."""
@@ -29,6 +62,21 @@ def segs_np(batch, dtype):
     for k, x in batch.segments():
         out.append((k, x.to(dtype).to(torch.float64).numpy()))
     return out
+
+
+def oracle_fit_p(segs, V0, n_iter: int) -> "O.StateP":
+    """The static initial fit as the library runs it (§3.2.1 with our own
+    static ALS): n_iter oracle updates on empty helpers (λ = 0), each one
+    static ALS iteration (pinned against lstsq in the CPU tests), then the
+    helpers of the final factors (Eqs. 6-9).  segs: (k, X_k) of every
+    initial slice, k = 0..K0-1 in order."""
+    st = O.empty_state_p(V0)
+    U = {}
+    for it in range(n_iter):
+        st, U = O.dash_update_p(st, segs, len(segs) if it == 0 else 0, 0.0)
+    X = [x for _, x in segs]
+    R = V0.shape[1]
+    return O.init_helpers_p(X, [U.get(k, np.zeros((0, R))) for k in range(len(X))], st.W, st.V)
 
 
 def oracle_batch_fitness_p(state, U, X):
@@ -47,9 +95,13 @@ def gpu_rows_by_slice(rows: np.ndarray, batch):
 
 
 def compare_state_p(gpu: dict, st: "O.StateP", tol: float, what=""):
+    """Normwise relative error of every factor and helper, plus the same per
+    slice for W, c and D (each slice at its own scale), all within tol."""
     errs = {
         "V": rel(gpu["V"], st.V), "W": rel(gpu["W"], st.W), "c": rel(gpu["c"], st.c),
         "D": rel(gpu["D"], st.D), "F": rel(gpu["F"], st.F), "G": rel(gpu["G"], st.G),
+        "W_slice": rel_rows(gpu["W"], st.W), "c_slice": rel_rows(gpu["c"], st.c),
+        "D_slice": rel_rows(gpu["D"], st.D),
     }
     bad = {k: v for k, v in errs.items() if not v <= tol}
     assert not bad, f"{what} state mismatch (tol {tol:g}): {errs}"

@@ -11,7 +11,7 @@ import torch
 from oracle import dash_oracle as O
 from synth.planted import PlantedStream, ragged_batch, tiny, workload
 from tests._parity import (FIT_TOL, TOL, compare_state_p, gpu_rows_by_slice, oracle_batch_fitness_p,
-                           rel, segs_np)
+                           oracle_fit_p, record, rel, segs_np)
 
 pytestmark = pytest.mark.gpu
 
@@ -39,15 +39,13 @@ def _run_stream(w, prec, n_steps, init_iters=3, via="batch", seed_v=1):
     rng = np.random.default_rng(seed_v)
     V0 = rng.random((w.J, w.R))
     b0 = s.batch(0)
-    X0 = [x for _, x in segs_np(b0, tdt)]
-    U, W, V = O.static_als_p(X0, V0, np.ones((len(X0), w.R)), init_iters)
-    st = O.init_helpers_p(X0, U, W, V)
+    st = oracle_fit_p(segs_np(b0, tdt), V0, init_iters)
     m = _model(w.J, w.R, w.lam, prec, max_slices=w.K0 + w.new_slices_per_step * n_steps + 8,
                max_rows=max(4096, b0.n_rows * 2), max_segments=4096)
     m.set_factors(V0)
     m.append_batch(b0.slice_ids.numpy(), b0.row_ptr.numpy(), b0.X.to(tdt).numpy())
     m.fit_initial(init_iters)
-    compare_state_p(m.get_state_p(), st, TOL[prec] * (10 if prec == "fp64" else 1), "init")
+    record("init", compare_state_p(m.get_state_p(), st, TOL[prec], "init"), TOL[prec])
     worst = {}
     for t in range(1, n_steps + 1):
         b = s.batch(t)
@@ -78,6 +76,8 @@ def _run_stream(w, prec, n_steps, init_iters=3, via="batch", seed_v=1):
         assert errs["U"] <= TOL[prec], errs
         fit_g, xn = m.fitness()
         fit_o = oracle_batch_fitness_p(st, Uo, X)
+        errs["fit"] = abs(fit_g - fit_o)
+        record(f"update {t}", errs, TOL[prec])
         assert abs(fit_g - fit_o) <= FIT_TOL[prec], (fit_g, fit_o)
         for k, v in errs.items():
             worst[k] = max(worst.get(k, 0.0), v)
@@ -163,8 +163,8 @@ def test_rank_deficient_gram_uses_the_pseudo_inverse(prec):
     m.set_factors(V0)
     m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.numpy())
     m.update()
-    tol = 1e-9 if prec == "fp64" else 1e-4
-    compare_state_p(m.get_state_p(), st, tol, "J<R")
+    tol = TOL[prec]
+    record("J<R", compare_state_p(m.get_state_p(), st, tol, "J<R"), tol)
     got = gpu_rows_by_slice(m.new_rows(), b)
     for k in Uo:
         assert rel(got[k], Uo[k]) <= tol
@@ -186,8 +186,8 @@ def test_zero_weight_entries_take_the_general_lemma1_path(prec):
     m.set_state_p(st.V, st.W, st.c, st.D, st.F, st.G)
     m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.numpy())
     m.update()
-    tol = 1e-9 if prec == "fp64" else 1e-4
-    compare_state_p(m.get_state_p(), st2, tol, "zero w")
+    tol = TOL[prec]
+    record("zero w", compare_state_p(m.get_state_p(), st2, tol, "zero w"), tol)
     got = gpu_rows_by_slice(m.new_rows(), b)
     for k in Uo:
         assert rel(got[k], Uo[k]) <= tol
@@ -284,14 +284,24 @@ def test_local_errors_match_definitions(prec):
         se_o = {k: O.slice_error(X[k], Xh[k]) for k in ks if X[k].shape[0] > 0}
         te_o = O.tensor_error([X[k] for k in se_o], [Xh[k] for k in se_o])
         fit_o = O.fitness([X[k] for k in ks], [Xh[k] for k in ks])
-        tol = TOL[prec] * 10
-        assert abs(te - te_o) <= tol * max(te_o, 1e-30), (te, te_o)
+        # se and te are means of |x - x̂| with x̂ ≈ x: the factors' relative
+        # error TOL moves each x̂ by at most about TOL·|x̂| ≤ TOL·max|X|, so
+        # the stated bar applies to se and te at the scale of the data, not
+        # of the (much smaller) residual
+        xmax = max(float(np.max(np.abs(X[k]))) for k in se_o)
+        tol = TOL[prec] * xmax
+        record(f"local errors {t}", {"te": abs(te - te_o) / xmax,
+                                     "se": max(abs(se[k] - v) for k, v in se_o.items()) / xmax,
+                                     "fit": abs(fd - fit_o)}, TOL[prec])
+        assert abs(te - te_o) <= tol, (te, te_o)
         assert abs(fd - fit_o) <= FIT_TOL[prec], (fd, fit_o)
         for k, v in se_o.items():
-            assert abs(se[k] - v) <= tol * max(v, 1e-30), (k, se[k], v)
+            assert abs(se[k] - v) <= tol, (k, se[k], v)
         untouched = [k for k in range(st.K) if k not in se_o]
         assert all(np.isnan(se[k]) for k in untouched)
         # the direct fitness agrees with the Gram-form fitness of the update
+        # (GPU against GPU: the Gram form ||X||² − 2·cross + ||X̂||² cancels
+        # to about 1e-8 relative of ||X||² at σ = 0.05, hence 1e-9 there)
         assert abs(m.fitness()[0] - fd) <= (1e-9 if prec == "fp64" else 1e-3)
     m.close()
 

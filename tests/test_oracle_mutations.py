@@ -49,6 +49,17 @@ def _polar_via_transpose(L, rtol=None):
     return _ORIG_INV_SQRT_F(L.T, rtol)                          # factor transposed
 
 
+def _fitness_without_root(X, Xhat):
+    num = sum(float(np.sum((a - b) ** 2)) for a, b in zip(X, Xhat))
+    den = sum(float(np.sum(a ** 2)) for a in X)
+    return 1.0 - num / den if den > 0 else 1.0                 # sqrt dropped
+
+
+def _init_helpers_q_without_s(X, H, V, W, a_noise=None):
+    return _ORIG_INIT_Q(X, H, V, np.ones_like(np.asarray(W)), a_noise)   # S_k dropped from A_k
+
+
+_ORIG_INIT_Q = O.init_helpers_q
 _ORIG_R_FACTOR = O.r_factor
 _ORIG_INV_SQRT_F = O.inv_sqrt_from_factor
 
@@ -62,6 +73,8 @@ CASES = [
     ("r_factor", _r_factor_unsquared, [lambda: P.test_mode_q_summaries_exact_and_q_orthonormal(0.8)]),
     ("inv_sqrt_from_factor", _polar_via_transpose,
      [P.test_mode_q_single_batch_equals_parafac2_als_iteration]),
+    ("fitness", _fitness_without_root, [P.test_fitness_takes_the_root_of_the_pooled_residual_ratio]),
+    ("init_helpers_q", _init_helpers_q_without_s, [P.test_init_helpers_q_follow_their_definition]),
 ]
 
 

@@ -532,3 +532,47 @@ def test_slice_and_tensor_errors_by_hand():
     assert O.tensor_error([a, b], [ah, bh]) == (0.375 + 1.0) / 2
     assert O.fitness([a], [a]) == 1.0
     assert abs(O.fitness([a], [np.zeros_like(a)])) < 1e-15
+
+
+def test_fitness_takes_the_root_of_the_pooled_residual_ratio():
+    """fit = 1 - ||X - X̂||_F / ||X||_F worked by hand.  X = [[3, 4]] against
+    X̂ = [[3, 0]] leaves a residual of norm 4 against ||X||_F = 5: fit = 0.2
+    (the squared ratio would give 0.36).  Over several matrices the squared
+    sums pool before the root: residual² 4 + 0 over ||X||² 9 + 16 gives
+    1 - 2/5 = 0.6 (the mean of per-matrix fits would give 2/3)."""
+    assert abs(O.fitness([np.array([[3.0, 4.0]])], [np.array([[3.0, 0.0]])]) - 0.2) < 1e-15
+    X = [np.array([[1.0, 2.0], [2.0, 0.0]]), np.array([[0.0, 4.0]])]
+    Xh = [np.array([[1.0, 2.0], [0.0, 0.0]]), np.array([[0.0, 4.0]])]
+    assert abs(O.fitness(X, Xh) - 0.6) < 1e-15
+
+
+def test_init_helpers_q_follow_their_definition():
+    """Constrained-mode helpers of an initial tensor (the Q_k H S_k form of
+    §2.1, helpers as in Eqs. 6-9): with A_k = X_k V S_k Hᵀ formed entry by
+    entry, L_k is upper triangular with a non-negative diagonal and
+    L_kᵀL_k = A_kᵀA_k, i.e. L_k is the transposed Cholesky factor of A_kᵀA_k;
+    and Z_k = A_kᵀX_k entry by entry.  Weights away from 1 keep S_k visible."""
+    rng = np.random.default_rng(7)
+    J, R = 5, 3
+    X = [rng.standard_normal((n, J)) for n in (7, 4, 3)]    # I_k = R included
+    V = rng.random((J, R))
+    H = rng.random((R, R))
+    W = rng.random((3, R)) + 0.5
+    st = O.init_helpers_q(X, H, V, W)
+    for k, Xk in enumerate(X):
+        I = Xk.shape[0]
+        A = np.zeros((I, R))
+        for i in range(I):
+            for r in range(R):
+                A[i, r] = sum(Xk[i, j] * V[j, s] * W[k, s] * H[r, s]
+                              for j in range(J) for s in range(R))
+        Z = np.zeros((R, J))
+        for r in range(R):
+            for j in range(J):
+                Z[r, j] = sum(A[i, r] * Xk[i, j] for i in range(I))
+        L = st.L[k]
+        assert np.all(np.tril(L, -1) == 0.0)
+        assert np.all(np.diag(L) >= 0.0)
+        assert _rel(L.T @ L, A.T @ A) < 1e-12
+        assert _rel(L, np.linalg.cholesky(A.T @ A).T) < 1e-10
+        assert _rel(st.Z[k], Z) < 1e-13
