@@ -38,9 +38,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c4")
     ap.add_argument("--precision", default="f16x3", choices=["fp32", "f16x3"])
-    ap.add_argument("--row-path", default="auto", choices=["auto", "fused", "split"],
+    ap.add_argument("--row-path", default="auto", choices=["auto", "fused", "split", "split-warp"],
                     help="mode-P row pipeline (f16x3 only)")
     ap.add_argument("--init-iters", type=int, default=3)
+    ap.add_argument("--graph", action="store_true",
+                    help="submit each update as one CUDA graph (no per-kernel profile then)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=50,
@@ -147,11 +149,15 @@ def algorithmic(kernel: str, plan: dict, N: int, K_all: int, J: int, R: int, tsi
     cr, gr = plan.get("chunk_rows", 0), plan.get("general_rows", 0)
     if kernel == "k_rows_fused":         # one read of every tile row, U written
         return tr * J * isize + tr * R * 4 + ts * per_slice, 4 * tr * J * R
-    if kernel == "k_xq_tc":              # X read, P' written (chunked-path rows)
+    if kernel in ("k_xq_tc", "k_xq_umma"):   # X read, P' written (chunked-path rows)
         return cr * J * isize + cr * R * 4, 2 * cr * J * R
     if kernel == "k_f_tc":               # X read, Ũ fragment blocks (16 rows each) read
         nt = -(-R // 8)
         return cr * J * isize + -(-cr // 16) * (512 * nt + 16), 2 * cr * J * R
+    if kernel == "k_f_umma":             # X read, Ũ TF32 blocks (32 rows, 8 KB each) read
+        return cr * J * isize + -(-cr // 32) * 8192, 2 * cr * J * R
+    if kernel == "k_utilde_tf32":        # U read, Ũ TF32 blocks written
+        return cr * R * 4 + -(-cr // 32) * 8192, cr * R
     if kernel == "k_utilde":             # U read, U ∘ w written (rank padded to 8)
         return cr * R * 4 + cr * (-(-R // 8) * 8) * 4, cr * R
     if kernel == "k_xv":
@@ -355,6 +361,8 @@ def run_ours(a):
                   max_slices=K_total + 8, max_rows=max_rows, max_segments=max_seg + 8,
                   stream=stream.cuda_stream, max_staged_rows=step_rows)
     m.set_row_path(a.row_path)
+    if a.graph:
+        m.set_graph(True)
     V0 = np.random.default_rng(7).random((w.J, w.R))
     m.set_factors(V0)
     t0 = time.perf_counter()
@@ -383,7 +391,7 @@ def run_ours(a):
     # ---- timed region (device-resident inputs) ----------------------------
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in timed]
-    m.profile(True)
+    m.profile(not a.graph)
     l0 = m.launch_count()
     fits = []
     sampler = ClockSampler(local)

@@ -71,7 +71,8 @@ typedef struct dash_config {
     int32_t mode;           /* DASH_MODE_P or DASH_MODE_Q                        */
     int32_t precision;      /* DASH_PREC_*                                       */
     int32_t input_dtype;    /* DASH_F64 or DASH_F32: element type of X           */
-    int32_t n_sweeps;       /* passes of Algorithm 1 per update; must be 1       */
+    int32_t n_sweeps;       /* passes of Algorithm 1 per update, 1..64 (mode P;
+                               mode Q runs one)                                */
     double pinv_rtol;       /* pseudo-inverse cut-off relative to the largest
                                singular value; <= 0 selects R·DBL_EPSILON      */
     int64_t max_slices;     /* capacity K_max of slices over the model's life    */
@@ -218,6 +219,39 @@ dash_status dash_new_rows(const dash_model *m, double *out, int64_t *n_rows);
  * ||X_new||²_F. */
 dash_status dash_fitness(const dash_model *m, double *fit_batch, double *x_norm2);
 
+/* λ-weighted fitness of every row absorbed so far (mode P), in the form that
+ * Lemma 3's V step minimises (Eqs. 17, 20-21): each row x keeps the product
+ * u·S_k that its own update produced (U_k,new S_k,new, frozen like the rows
+ * of F and G) and is weighted by λ^age, age = updates since it arrived:
+ *   fit_λ = 1 − sqrt(Σ λ^age ||x − (u∘w)Vᵀ||² / Σ λ^age ||x||²)
+ * with the current V, evaluated from the helpers alone as
+ *   Σ λ^age ||x − (u∘w)Vᵀ||² = xx − 2 tr(VᵀF) + tr(VᵀV G),  xx = Σ λ^age ||x||².
+ * xx is tracked from every update's ||X_new||² (xx ← λ·xx + ||X_new||²),
+ * starting at ||X_0||² after dash_fit_initial(); after dash_set_state_p() it
+ * is unknown until dash_set_weighted_norm() supplies it (DASH_ESTATE until
+ * then).  x_norm2_lambda (may be NULL) receives xx.  Mode Q: DASH_ESTATE.
+ * Synchronises the stream. */
+dash_status dash_fitness_lambda(const dash_model *m, double *fit_lambda, double *x_norm2_lambda);
+/* Set xx = Σ λ^age ||x||² of the rows a loaded state summarises (part of the
+ * resumable state together with dash_set_state_p()).  DASH_EINVAL if it is
+ * negative or not finite. */
+dash_status dash_set_weighted_norm(dash_model *m, double x_norm2_lambda);
+
+/* Save the model's resumable state to a file: the configuration it was
+ * created with (capacities included, the stream excluded), the slice count,
+ * and the helpers an update reads as "old" (§3.2.1): mode P V, W, c_k, D_k,
+ * F, G and xx; mode Q V, H, W, L_k, Y_k and each slice's eigenbasis and
+ * B_k^{1/2} (so that the next update continues bit for bit), all as FP64,
+ * followed by a checksum.  Nothing may be staged (DASH_ESTATE).  DASH_EINVAL
+ * if the file cannot be written.  Synchronises the stream. */
+dash_status dash_save(const dash_model *m, const char *path);
+/* Create a model from a file written by dash_save(), on `stream` (a
+ * cudaStream_t; NULL = a private stream), and load its state.  The next
+ * update of the loaded model equals the next update the saved model would
+ * have run.  DASH_EINVAL for a missing, truncated or corrupted file (bad
+ * magic, version, sizes or checksum); allocation errors as dash_init(). */
+dash_status dash_load(const char *path, void *stream, dash_model **out);
+
 /* Reconstruction errors of the last update's new data with the updated
  * factors, from a second read of its rows (the paper's slice-level and
  * tensor-level reconstruction errors, Definitions 1-2, also its local error
@@ -300,18 +334,53 @@ dash_status dash_last_plan(const dash_model *m, int64_t *tile_rows, int64_t *til
                            int64_t *tiles, int64_t *chunk_rows, int64_t *general_rows);
 
 /* Row pipeline of a mode-P update with FP32 input and DASH_PREC_F16X3
- * products (the paper has no counterpart: both compute Algorithm 1's P2-P7
+ * products (the paper has no counterpart: all compute Algorithm 1's P2-P7
  * on the same rows, in different kernels).
  *   DASH_ROWS_FUSED  tiles of single-segment slices (at most 256 new rows)
  *                    in one fused row kernel; other slices in row chunks.
  *   DASH_ROWS_SPLIT  every slice in row chunks: X·Q_V and the F increment
  *                    (Eq. 20) as two streaming tensor-core passes over X,
- *                    the per-slice work (P4, P6, P7) in between.
+ *                    the per-slice work (P4, P6, P7) in between.  The X·Q_V
+ *                    pass runs on tcgen05 MMAs fed by TMA (3-term TF32
+ *                    split) where the shape allows it (J % 4 == 0, J <= 512,
+ *                    R <= 32, 16-byte aligned rows), else as warp-level MMAs.
+ *   DASH_ROWS_SPLIT_WARP  the same split pipeline with warp-level MMAs
+ *                    (FP16 split) for both passes.
  *   DASH_ROWS_AUTO   the library's choice (currently DASH_ROWS_SPLIT).
  * Takes effect at the next update; other paths ignore it.  DASH_EINVAL for
  * an unknown value. */
-enum { DASH_ROWS_AUTO = 0, DASH_ROWS_FUSED = 1, DASH_ROWS_SPLIT = 2 };
+enum { DASH_ROWS_AUTO = 0, DASH_ROWS_FUSED = 1, DASH_ROWS_SPLIT = 2, DASH_ROWS_SPLIT_WARP = 3 };
 dash_status dash_set_row_path(dash_model *m, int32_t path);
+
+/* Bounded device waits (the paper has no counterpart).  Every wait of the
+ * streaming kernels on their copy pipeline gives up after a limit; the
+ * update is then dropped by its own kernels: the ones that write the state
+ * (c_k, D_k, W, F, G, V, VᵀV) see the flag and leave it as it was.  The next
+ * synchronising call (dash_sync, a getter, or the planning of the next
+ * update) returns DASH_ETIMEOUT once; the slice count returns to its value
+ * before the dropped update, the dropped batch is gone, and the model stays
+ * usable.
+ * dash_set_wait_limit(): the limit of the tcgen05 streaming kernels, in SM
+ * clock cycles (default 2·10⁹, about a second; the warp-level kernels keep
+ * that default).  DASH_EINVAL below 1000.
+ * dash_inject_wait_fault(): a test hook: in the next update, the first
+ * thread block of the tcgen05 X·Q_V pass never issues the copy of its first
+ * stage, so that its wait runs out.  DASH_ESTATE when this configuration has
+ * no such pass (mode Q, FP64 or FP32 products, shapes it does not take). */
+dash_status dash_set_wait_limit(dash_model *m, int64_t cycles);
+dash_status dash_inject_wait_fault(dash_model *m);
+
+/* Launch each update (dash_update, dash_update_device) as one CUDA graph
+ * (the paper has no counterpart: the same kernels with the same arguments,
+ * submitted at once).  The update's launch sequence is captured from the
+ * model's stream; while its topology matches the previous update's (the same
+ * kernels in the same order, as for batches of similar shape) the captured
+ * arguments update the instantiated graph, otherwise it is instantiated
+ * anew.  Off by default; ignored while profiling is on.  Results are
+ * bit-identical either way.  dash_graph_stats() counts instantiations and
+ * in-place updates (either pointer may be NULL).  Synchronises the stream. */
+dash_status dash_set_graph(dash_model *m, int32_t on);
+dash_status dash_graph_stats(const dash_model *m, int64_t *instantiations, int64_t *updates);
 
 /* Allocation-free F increment.  (The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory.)

@@ -444,6 +444,21 @@ def fitness(X: Sequence[np.ndarray], Xhat: Sequence[np.ndarray]) -> float:
     return 1.0 - np.sqrt(num / den) if den > 0 else 1.0
 
 
+def weighted_fitness_p(rows, V: np.ndarray, lam: float) -> float:
+    """λ-weighted fitness of stored rows with the current V: every row block
+    keeps the U_k,new and the S_k,new (its diagonal w) that its own update
+    produced, the products that enter F and G (Eqs. 20-21) and that Lemma 3's
+    V step fits (Eq. 17), and counts with weight λ^age:
+        1 − sqrt(Σ λ^age ||X − U diag(w) Vᵀ||² / Σ λ^age ||X||²).
+    rows: iterable of (age, X, U, w)."""
+    num = den = 0.0
+    for age, X, U, w in rows:
+        a = lam ** age
+        num += a * float(np.sum((X - reconstruct_p(U, w, V)) ** 2))
+        den += a * float(np.sum(X ** 2))
+    return 1.0 - np.sqrt(num / den) if den > 0 else 1.0
+
+
 def slice_error(X_new: np.ndarray, Xhat_new: np.ndarray) -> float:
     """Definition 1 (Eq. 22): mean absolute reconstruction error of a slice's
     new rows, se = Σ|X - X̂| / (I_k,new J)."""
@@ -503,7 +518,7 @@ class OracleStream:
         while len(self.rows) < self.state.K:
             self.rows.append([])
         for k, Xk in X.items():
-            self.rows[k].append((self.t, Xk, keep[k]))
+            self.rows[k].append((self.t, Xk, keep[k], np.array(self.state.W[k])))
         self.t += 1
         self.last_new, self.last_X = new, X
         return new

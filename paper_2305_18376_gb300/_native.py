@@ -80,6 +80,14 @@ SIGNATURES = [
     ("dash_local_errors", C.c_int, [P, PD, PD, PD, I64]),
     ("dash_f_increment_noalloc", C.c_int, [P, P, I64, I32, I32, P, P, I64, P, P, P]),
     ("dash_counters", C.c_int, [P, PI64, PI64]),
+    ("dash_fitness_lambda", C.c_int, [P, PD, PD]),
+    ("dash_set_weighted_norm", C.c_int, [P, D]),
+    ("dash_save", C.c_int, [P, C.c_char_p]),
+    ("dash_load", C.c_int, [C.c_char_p, P, C.POINTER(P)]),
+    ("dash_set_graph", C.c_int, [P, I32]),
+    ("dash_set_wait_limit", C.c_int, [P, I64]),
+    ("dash_inject_wait_fault", C.c_int, [P]),
+    ("dash_graph_stats", C.c_int, [P, PI64, PI64]),
 ]
 
 
@@ -119,9 +127,10 @@ def _i64(a) -> np.ndarray:
 def _config(lib, J: int, R: int, lam: float, mode: str = "P", precision: str = "fp32",
             input_dtype: str = "f32", max_slices: int = 1 << 16, max_rows: int = 1 << 20,
             max_segments: int = 1 << 17, pinv_rtol: float = 0.0, stream=None,
-            max_staged_rows: int = 0) -> Config:
+            max_staged_rows: int = 0, n_sweeps: int = 1) -> Config:
     cfg = Config()
     lib.dash_config_default(C.byref(cfg), J, R, lam)
+    cfg.n_sweeps = n_sweeps
     cfg.mode = DASH_MODE_P if mode == "P" else DASH_MODE_Q
     cfg.precision = PREC[precision]
     cfg.input_dtype = DTYPE[input_dtype]
@@ -150,17 +159,59 @@ class DashModel:
     def __init__(self, J: int, R: int, lam: float, mode: str = "P", precision: str = "fp32",
                  input_dtype: str = "f32", max_slices: int = 1 << 16, max_rows: int = 1 << 20,
                  max_segments: int = 1 << 17, pinv_rtol: float = 0.0, stream=None,
-                 max_staged_rows: int = 0):
+                 max_staged_rows: int = 0, n_sweeps: int = 1, _handle=None):
         lib = load()
-        cfg = _config(lib, J, R, lam, mode, precision, input_dtype, max_slices, max_rows,
-                      max_segments, pinv_rtol, stream, max_staged_rows)
-        h = P()
-        st = lib.dash_init(C.byref(cfg), C.byref(h))
-        if st != 0:
-            raise DashError(st, "dash_init failed")
+        if _handle is None:
+            cfg = _config(lib, J, R, lam, mode, precision, input_dtype, max_slices, max_rows,
+                          max_segments, pinv_rtol, stream, max_staged_rows, n_sweeps)
+            h = P()
+            st = lib.dash_init(C.byref(cfg), C.byref(h))
+            if st != 0:
+                raise DashError(st, "dash_init failed")
+        else:
+            h = _handle
         self._lib, self._h = lib, h
         self.J, self.R, self.lam, self.mode = J, R, lam, mode
         self.np_dtype = np.float64 if input_dtype == "f64" else np.float32
+
+    @classmethod
+    def load_file(cls, path: str, J: int, R: int, lam: float, mode: str = "P",
+                  input_dtype: str = "f32", stream=None) -> "DashModel":
+        """dash_load(): a model resumed from a dash_save() file (the shape
+        arguments describe it to the binding; the file sizes the model)."""
+        lib = load()
+        h = P()
+        st = lib.dash_load(os.fsencode(path), stream, C.byref(h))
+        if st != 0:
+            raise DashError(st, f"dash_load({path}) failed")
+        return cls(J, R, lam, mode=mode, input_dtype=input_dtype, _handle=h)
+
+    def save(self, path: str) -> None:
+        self._ck(self._lib.dash_save(self._h, os.fsencode(path)))
+
+    def fitness_lambda(self):
+        """(λ-weighted fitness of every absorbed row, Σ λ^age ||x||²)."""
+        f, x = C.c_double(), C.c_double()
+        self._ck(self._lib.dash_fitness_lambda(self._h, C.byref(f), C.byref(x)))
+        return f.value, x.value
+
+    def set_wait_limit(self, cycles: int) -> None:
+        self._ck(self._lib.dash_set_wait_limit(self._h, int(cycles)))
+
+    def inject_wait_fault(self) -> None:
+        self._ck(self._lib.dash_inject_wait_fault(self._h))
+
+    def set_graph(self, on: bool) -> None:
+        self._ck(self._lib.dash_set_graph(self._h, 1 if on else 0))
+
+    def graph_stats(self):
+        """(graph instantiations, in-place graph updates) since dash_init."""
+        a, b = C.c_int64(), C.c_int64()
+        self._ck(self._lib.dash_graph_stats(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def set_weighted_norm(self, xx: float) -> None:
+        self._ck(self._lib.dash_set_weighted_norm(self._h, float(xx)))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -264,7 +315,7 @@ class DashModel:
                                            C.byref(e2), C.byref(x2), C.byref(ea)))
         return e2.value, x2.value, ea.value
 
-    ROW_PATHS = {"auto": 0, "fused": 1, "split": 2}
+    ROW_PATHS = {"auto": 0, "fused": 1, "split": 2, "split-warp": 3}
 
     def set_row_path(self, path: str) -> None:
         """Mode-P row pipeline for the next updates: "fused", "split" or

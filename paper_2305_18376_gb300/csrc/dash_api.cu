@@ -86,6 +86,14 @@ static void prof_collect(dash_model *m) {
                 m->prof.ms[KK_XQ_WAIT + i] += (double)c[11 + i] / (w > 0 ? w : 1.0) / m->prof.clock_khz;
                 if (c[11 + i]) m->prof.launches[KK_XQ_WAIT + i] += 1;
             }
+            // k_xq_umma: cycles each role waited (producer and MMA issuer: one
+            // thread per CTA; converters and epilogue: summed over their 8
+            // warps) and each CTA's lifetime, reported per CTA
+            for (int i = 0; i < 5; ++i) {
+                const double per = (m->prof.xu_ctas > 0 ? m->prof.xu_ctas : 1.0) * ((i == 2 || i == 3) ? 8.0 : 1.0);
+                m->prof.ms[KK_XU_WAIT_P + i] += (double)c[15 + i] / per / m->prof.clock_khz;
+                if (c[15 + i]) m->prof.launches[KK_XU_WAIT_P + i] += 1;
+            }
             cudaMemset(m->prof.d_phase, 0, sizeof c);
         }
     }
@@ -250,10 +258,16 @@ static dash_status init_alloc(dash_model *m) {
     DALLOC(m->GP, R * R * 8, "G+");
     DALLOC(m->Finc, J * R * 8, "F_inc");
     DALLOC(m->Ginc, R * R * 8, "G_inc");
-    DALLOC(m->fit, 4 * 8, "fitness");
+    DALLOC(m->fit, 6 * 8, "fitness");       // batch fitness [4], λ-weighted fitness [2]
     if (c.mode == DASH_MODE_P) {
         DALLOC(m->st.c, Km * R * 8, "c");
         DALLOC(m->st.D, Km * R * R * 8, "D");
+        if (c.n_sweeps > 1) {
+            DALLOC(m->sw_c, Km * R * 8, "c (sweep start)");
+            DALLOC(m->sw_D, Km * R * R * 8, "D (sweep start)");
+            DALLOC(m->sw_F, J * R * 8, "F (sweep start)");
+            DALLOC(m->sw_G, R * R * 8, "G (sweep start)");
+        }
     } else {
         DALLOC(m->qL, Km * R * R * 8, "L_k");
         DALLOC(m->qE, Km * R * R * 8, "E_k");
@@ -304,6 +318,10 @@ static dash_status init_alloc(dash_model *m) {
     DALLOC(m->Gdf, R * R * 8, "Gamma (double-float)");
     DALLOC(m->xq_frag, (size_t)((J + 15) / 16) * ((R + 7) / 8) * 32 * 16, "Q_V fragments");
     DALLOC(m->xq_bexp, 4, "Q_V fragment scale");
+    if (m->xu_nst > 0) {
+        DALLOC(m->qv_slabs, (size_t)((J + 31) / 32) * XU_SLAB_BYTES, "Q_V TF32 slabs");
+        DALLOC(m->ub_tf32, (size_t)(Nm / 32 + 2) * FB_UBLK, "U o w TF32 blocks");
+    }
     if (m->fused_ok) {
         DALLOC(m->Ut, (size_t)(Nm / 16 + 2) * ft_ublk((R + 7) / 8) * 4, "U o w fragments");
         DALLOC(m->xe, (size_t)(Nm + 16) * 4, "row exponents");
@@ -361,7 +379,8 @@ static dash_status init_check(dash_model *m) {
     else if (c.precision != DASH_PREC_FP64 && c.precision != DASH_PREC_FP32 &&
              c.precision != DASH_PREC_F16X3) st = bad("unknown precision");
     else if (c.input_dtype != DASH_F64 && c.input_dtype != DASH_F32) st = bad("unknown input dtype");
-    else if (c.n_sweeps != 1) st = bad("only n_sweeps = 1 is supported");
+    else if (c.n_sweeps < 1 || c.n_sweeps > 64) st = bad("n_sweeps must be in 1..64");
+    else if (c.n_sweeps != 1 && c.mode != DASH_MODE_P) st = bad("mode Q runs one sweep per update (n_sweeps = 1)");
     else if (c.max_slices < 1 || c.max_rows < 1 || c.max_segments < 1) st = bad("capacities must be positive");
     else if (c.max_slices > INT32_MAX / 2 || c.max_segments > INT32_MAX / 2) st = bad("capacity too large");
     if (st != DASH_OK) return st;
@@ -377,6 +396,7 @@ static dash_status init_check(dash_model *m) {
     }
     m->fused_ok = m->df_state && c.input_dtype == DASH_F32 && c.R <= FU_RP &&
                   c.J <= FU_WARPS * FU_JG && (c.J % 4) == 0 && c.mode == DASH_MODE_P;
+    m->xu_nst = (m->fused_ok && c.precision == DASH_PREC_F16X3 && c.R <= 32) ? xu_stages(c.J) : 0;
     m->st.J = c.J;
     m->st.R = c.R;
     m->st.lam = c.lambda;
@@ -456,6 +476,7 @@ extern "C" void dash_destroy(dash_model *m) {
     for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
     for (int c = 0; c < kCopyStreams; ++c)      // split host copies still in flight
         if (m->copy_streams[c]) cudaStreamSynchronize(m->copy_streams[c]);
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
     free_all(m);
     cudaEventDestroy(m->ev0);
     cudaEventDestroy(m->ev1);
@@ -495,10 +516,32 @@ extern "C" dash_status dash_query(const dash_model *mc, int32_t *idle) {
     return DASH_OK;
 }
 
+// After a synchronisation: an update whose bounded wait timed out was
+// dropped by its own kernels (flag err[3], copied back at the end of the
+// update); the host then forgets it too and reports it once.
+static dash_status check_abandoned(dash_model *m) {
+    if (m->h_err[3] == 0) return DASH_OK;
+    m->h_err[3] = 0;
+    m->K = m->K_prev;
+    m->has_last = false;
+    m->xx_pending = false;
+    return fail(m, DASH_ETIMEOUT, "a bounded device wait timed out: the last update was dropped "
+                                  "and the state is unchanged");
+}
+
+// After a synchronisation: the device counter of non-finite per-slice
+// results (copied back at the end of every update) must be zero.
+static dash_status check_numeric(dash_model *m) {
+    if (dash_status a = check_abandoned(m)) return a;
+    if (m->h_err[2] > 0)
+        return fail(m, DASH_ENUMERIC, "%d slice factors came out non-finite", m->h_err[2]);
+    return DASH_OK;
+}
+
 extern "C" dash_status dash_sync(dash_model *m) {
     if (!m) return DASH_EINVAL;
     CK(cudaStreamSynchronize(m->stream));
-    return DASH_OK;
+    return check_abandoned(m);
 }
 
 // ---------------------------------------------------------------------------
@@ -511,8 +554,8 @@ static dash_status refresh_gamma(dash_model *m) {
         LAUNCH(KK_CAST, k_cast<double><<<(n + 255) / 256, 256, 0, m->stream>>>(m->st.V, (double *)m->VT, n));
     else
         LAUNCH(KK_CAST, k_cast<float><<<(n + 255) / 256, 256, 0, m->stream>>>(m->st.V, (float *)m->VT, n));
-    LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, m->stream>>>(m->st.V, J, R, m->st.Gam));
-    if (dash_status e = launch_pinv(m, m->st.Gam, m->st.GamP, m->st.gam_ok)) return e;
+    LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, m->stream>>>(m->st.V, J, R, m->st.Gam, nullptr));
+    if (dash_status e = launch_pinv(m, m->st.Gam, m->st.GamP, m->st.gam_ok, nullptr)) return e;
     int ok = 0;
     CK(cudaMemcpyAsync(&ok, m->st.gam_ok, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
     CK(cudaStreamSynchronize(m->stream));
@@ -606,6 +649,8 @@ extern "C" dash_status dash_set_state_p(dash_model *m, int64_t K, const double *
     if (s) return s;
     m->v_set = true;
     m->has_last = false;
+    m->xx_valid = false;           // until dash_set_weighted_norm()
+    m->xx_pending = false;
     return DASH_OK;
 }
 
@@ -614,8 +659,9 @@ extern "C" dash_status dash_get_state_p(const dash_model *mc, double *V, double 
     dash_model *m = const_cast<dash_model *>(mc);
     if (!m) return DASH_EINVAL;
     if (m->cfg.mode != DASH_MODE_P) return fail(m, DASH_ESTATE, "model is not in mode P");
-    const int64_t J = m->cfg.J, R = m->cfg.R, K = m->K;
     CK(cudaStreamSynchronize(m->stream));
+    if (dash_status a = check_abandoned(m)) return a;
+    const int64_t J = m->cfg.J, R = m->cfg.R, K = m->K;
     if (V) CK(cudaMemcpy(V, m->st.V, J * R * 8, cudaMemcpyDeviceToHost));
     if (W && K) CK(cudaMemcpy(W, m->st.W, K * R * 8, cudaMemcpyDeviceToHost));
     if (c && K) { dash_status s1 = get_summ(m, c, m->st.c, (size_t)K * R); if (s1) return s1; }
@@ -668,12 +714,12 @@ extern "C" dash_status dash_set_state_q(dash_model *m, int64_t K, const double *
     return DASH_OK;
 }
 
-// After a synchronisation: the device counter of non-finite per-slice
-// results (copied back at the end of every update) must be zero.
-static dash_status check_numeric(dash_model *m) {
-    if (m->h_err[2] > 0)
-        return fail(m, DASH_ENUMERIC, "%d slice factors came out non-finite", m->h_err[2]);
-    return DASH_OK;
+// Fold the last finished update's ||X_new||² (h_fit[1]) into xx.  Call only
+// after the model's stream has been synchronised.
+static void fold_xx(dash_model *m) {
+    if (!m->xx_pending) return;
+    m->xx = m->xx_lam * m->xx + m->h_fit[1];
+    m->xx_pending = false;
 }
 
 extern "C" dash_status dash_get_state_q(const dash_model *mc, double *V, double *H, double *W,
@@ -747,6 +793,37 @@ extern "C" dash_status dash_fitness(const dash_model *mc, double *fit_batch, dou
     return DASH_OK;
 }
 
+extern "C" dash_status dash_fitness_lambda(const dash_model *mc, double *fit_lambda, double *x_norm2_lambda) {
+    dash_model *m = const_cast<dash_model *>(mc);
+    if (!m) return DASH_EINVAL;
+    if (m->cfg.mode != DASH_MODE_P) return fail(m, DASH_ESTATE, "the lambda-weighted fitness is defined in mode P");
+    CK(cudaStreamSynchronize(m->stream));
+    if (dash_status sn = check_numeric(m)) return sn;
+    fold_xx(m);
+    if (!m->xx_valid)
+        return fail(m, DASH_ESTATE, "the weighted norm of the absorbed rows is unknown (dash_set_weighted_norm)");
+    const int J = m->cfg.J, R = m->cfg.R;
+    LAUNCH(KK_FIT_LAMBDA, k_fit_lambda<<<1, 32, 0, m->stream>>>(m->st.V, m->st.F, m->st.Gam, m->st.G, J, R, m->xx,
+                                                                m->fit + 4));
+    double out[2];
+    CK(cudaMemcpyAsync(out, m->fit + 4, 2 * 8, cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    if (fit_lambda) *fit_lambda = out[0];
+    if (x_norm2_lambda) *x_norm2_lambda = m->xx;
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_set_weighted_norm(dash_model *m, double x_norm2_lambda) {
+    if (!m) return DASH_EINVAL;
+    if (!(x_norm2_lambda >= 0.0) || !std::isfinite(x_norm2_lambda))
+        return fail(m, DASH_EINVAL, "the weighted norm must be finite and >= 0");
+    CK(cudaStreamSynchronize(m->stream));
+    fold_xx(m);
+    m->xx = x_norm2_lambda;
+    m->xx_valid = true;
+    return DASH_OK;
+}
+
 extern "C" dash_status dash_last_plan(const dash_model *mc, int64_t *tile_rows,
                                       int64_t *tile_slices, int64_t *tiles, int64_t *chunk_rows,
                                       int64_t *general_rows) {
@@ -761,9 +838,44 @@ extern "C" dash_status dash_last_plan(const dash_model *mc, int64_t *tile_rows,
     return DASH_OK;
 }
 
+extern "C" dash_status dash_set_wait_limit(dash_model *m, int64_t cycles) {
+    if (!m) return DASH_EINVAL;
+    if (cycles < 1000) return fail(m, DASH_EINVAL, "wait limit below 1000 cycles");
+    m->wait_limit = cycles;
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_inject_wait_fault(dash_model *m) {
+    if (!m) return DASH_EINVAL;
+    if (m->cfg.mode != DASH_MODE_P || m->xu_nst == 0)
+        return fail(m, DASH_ESTATE, "no tcgen05 X·Q_V pass in this configuration");
+    m->inject_wait_fault = 1;
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_set_graph(dash_model *m, int32_t on) {
+    if (!m) return DASH_EINVAL;
+    if (on != 0 && on != 1) return fail(m, DASH_EINVAL, "graph switch must be 0 or 1");
+    CK(cudaStreamSynchronize(m->stream));
+    m->use_graph = on != 0;
+    if (!m->use_graph && m->gexec) {
+        cudaGraphExecDestroy(m->gexec);
+        m->gexec = nullptr;
+    }
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_graph_stats(const dash_model *m, int64_t *instantiations, int64_t *updates) {
+    if (!m) return DASH_EINVAL;
+    if (instantiations) *instantiations = m->graph_instantiations;
+    if (updates) *updates = m->graph_updates;
+    return DASH_OK;
+}
+
 extern "C" dash_status dash_set_row_path(dash_model *m, int32_t path) {
     if (!m) return DASH_EINVAL;
-    if (path != DASH_ROWS_AUTO && path != DASH_ROWS_FUSED && path != DASH_ROWS_SPLIT)
+    if (path != DASH_ROWS_AUTO && path != DASH_ROWS_FUSED && path != DASH_ROWS_SPLIT &&
+        path != DASH_ROWS_SPLIT_WARP)
         return fail(m, DASH_EINVAL, "unknown row path %d", path);
     m->row_path = path;
     return DASH_OK;
@@ -1106,7 +1218,8 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
     const bool fused = allow_fused && m->fused_ok && gam_ok && ((uintptr_t)X % 16) == 0;
     // split: no tiles, every touched slice through the chunked path
     const bool split = fused && m->cfg.precision == DASH_PREC_F16X3 &&
-                       (m->row_path == DASH_ROWS_SPLIT || (m->row_path == DASH_ROWS_AUTO && kAutoSplit));
+                       (m->row_path == DASH_ROWS_SPLIT || m->row_path == DASH_ROWS_SPLIT_WARP ||
+                        (m->row_path == DASH_ROWS_AUTO && kAutoSplit));
     m->split_active = split;
     std::vector<char> fz(n_seg, 0);
     if (fused && !split) {
@@ -1233,6 +1346,7 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
     if (pass == 0) {
         const auto th0 = std::chrono::steady_clock::now();
         CK(cudaStreamSynchronize(m->stream));   // the previous update has finished
+        fold_xx(m);
         if (m->prof.on) {
             const auto th1 = std::chrono::steady_clock::now();
             m->prof.ms[KK_HOST_PLAN] += std::chrono::duration<double, std::milli>(th0 - m->prof.t_plan0).count();
@@ -1241,7 +1355,7 @@ static dash_status plan_batch(dash_model *m, int64_t n_seg, const int64_t *ids,
             m->prof.launches[KK_HOST_WAIT] += 1;
         }
         m->gam_ok_host = m->h_fit[3] != 0.0;
-        if (m->h_err[0] > 0) return fail(m, DASH_ETIMEOUT, "a bounded device wait timed out");
+        if (dash_status a = check_abandoned(m)) return a;
         if (m->h_err[2] > 0)
             return fail(m, DASH_ENUMERIC, "%d slice factors came out non-finite", m->h_err[2]);
         if (m->gam_ok_host != gam_ok) {
@@ -1301,6 +1415,39 @@ static dash_status run_update(dash_model *m, const BatchDev &b, const void *X, d
     return run_update_p(m, b, X, lam, begin_new);
 }
 
+// The kernels of one update: Algorithm 1 once, or n_sweeps times over the
+// same new rows with the old helpers restored before every further pass.
+static dash_status launch_sweeps(dash_model *m, const BatchDev &b, const void *X) {
+    dash_status s;
+    const int nsw = m->cfg.mode == DASH_MODE_P ? m->cfg.n_sweeps : 1;
+    if (nsw > 1) {
+        // the old helpers every pass starts from (new slices start at zero)
+        const int64_t R = m->cfg.R;
+        CK(cudaMemcpyAsync(m->sw_c, m->st.c, m->K * R * 8, cudaMemcpyDeviceToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->sw_D, m->st.D, m->K * R * R * 8, cudaMemcpyDeviceToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->sw_F, m->st.F, (size_t)m->cfg.J * R * 8, cudaMemcpyDeviceToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->sw_G, m->st.G, R * R * 8, cudaMemcpyDeviceToDevice, m->stream));
+    }
+    s = run_update(m, b, X, m->cfg.lambda, true);
+    if (s) return s;
+    for (int sw = 1; sw < nsw; ++sw) {
+        // Algorithm 1 again on the same rows with the factors of the last
+        // pass and the old helpers held fixed
+        const int64_t R = m->cfg.R, Ka = b.K_all;
+        CK(cudaMemcpyAsync(m->st.c, m->sw_c, m->K * R * 8, cudaMemcpyDeviceToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->st.D, m->sw_D, m->K * R * R * 8, cudaMemcpyDeviceToDevice, m->stream));
+        if (Ka > m->K) {
+            CK(cudaMemsetAsync(m->st.c + m->K * R, 0, (Ka - m->K) * R * 8, m->stream));
+            CK(cudaMemsetAsync(m->st.D + m->K * R * R, 0, (Ka - m->K) * R * R * 8, m->stream));
+        }
+        CK(cudaMemcpyAsync(m->st.F, m->sw_F, (size_t)m->cfg.J * R * 8, cudaMemcpyDeviceToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->st.G, m->sw_G, R * R * 8, cudaMemcpyDeviceToDevice, m->stream));
+        s = run_update(m, b, X, m->cfg.lambda, false);
+        if (s) return s;
+    }
+    return DASH_OK;
+}
+
 static dash_status update_common(dash_model *m, int64_t n_seg, const int64_t *ids,
                                  const int64_t *rp, const void *X, int64_t n_new) {
     if (!m->v_set) return fail(m, DASH_ESTATE, "V is not set (dash_set_factors)");
@@ -1309,10 +1456,44 @@ static dash_status update_common(dash_model *m, int64_t n_seg, const int64_t *id
     BatchDev b;
     dash_status s = plan_batch(m, n_seg, ids, rp, m->K, n_new, X, true, &b);
     if (s) return s;
+    CK(cudaMemsetAsync(m->d_err + 3, 0, sizeof(int), m->stream));
+    m->K_prev = m->K;
     CK(cudaEventRecord(m->ev0, m->stream));
     const auto tl0 = std::chrono::steady_clock::now();
-    s = run_update(m, b, X, m->cfg.lambda, true);
-    if (s) return s;
+    const bool graph = m->use_graph && !m->prof.on;
+    if (graph) CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+    s = launch_sweeps(m, b, X);
+    if (graph) {
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(m->stream, &g);
+        if (s || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            if (s) return s;
+            CK(ec);
+        }
+        if (m->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(m->gexec, g, &info) == cudaSuccess) {
+                ++m->graph_updates;
+            } else {                   // another launch topology: instantiate anew
+                cudaGetLastError();
+                cudaGraphExecDestroy(m->gexec);
+                m->gexec = nullptr;
+            }
+        }
+        if (!m->gexec) {
+            const cudaError_t ei = cudaGraphInstantiate(&m->gexec, g, 0);
+            cudaGraphDestroy(g);
+            g = nullptr;
+            CK(ei);
+            ++m->graph_instantiations;
+        }
+        if (g) cudaGraphDestroy(g);
+        CK(cudaGraphLaunch(m->gexec, m->stream));
+    } else if (s) {
+        return s;
+    }
     if (m->prof.on) {
         m->prof.ms[KK_HOST_LAUNCH] +=
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tl0).count();
@@ -1322,6 +1503,8 @@ static dash_status update_common(dash_model *m, int64_t n_seg, const int64_t *id
     m->K += n_new;
     m->last_N = b.N;
     m->has_last = true;
+    m->xx_pending = true;
+    m->xx_lam = m->cfg.lambda;
     m->last_X = X;
     m->last_ids.assign(ids, ids + n_seg);
     m->last_rp.assign(rp, rp + n_seg + 1);
@@ -1390,6 +1573,8 @@ static dash_status fit_common(dash_model *m, int64_t n_seg, const int64_t *ids,
     BatchDev b;
     dash_status s = plan_batch(m, n_seg, ids, rp, 0, n_new, X, true, &b);
     if (s) return s;
+    CK(cudaMemsetAsync(m->d_err + 3, 0, sizeof(int), m->stream));
+    m->K_prev = 0;
     CK(cudaEventRecord(m->ev0, m->stream));
     // iteration 1: the slices are new (S_k = I); later iterations: the same
     // rows with the helpers of the previous iteration dropped (λ = 0), which
@@ -1416,6 +1601,10 @@ static dash_status fit_common(dash_model *m, int64_t n_seg, const int64_t *ids,
     }
     CK(cudaEventRecord(m->ev1, m->stream));
     m->K = n_new;
+    m->xx = 0.0;
+    m->xx_valid = true;
+    m->xx_pending = true;          // the last iteration's ||X||² is ||X_0||²
+    m->xx_lam = 0.0;
     m->last_N = b.N;
     m->has_last = true;
     m->last_X = X;
@@ -1447,4 +1636,164 @@ extern "C" dash_status dash_fit_initial_device(dash_model *m, int64_t n_seg,
     if (n_new > m->cfg.max_slices) return fail(m, DASH_ENOMEM, "slices would exceed max_slices");
     if (N > 0 && !X) return fail(m, DASH_EINVAL, "X is null");
     return fit_common(m, n_seg, slice_ids, row_ptr, X, n_new, n_iter);
+}
+
+// ---------------------------------------------------------------------------
+// save / load: the resumable state of §3.2.1 (the helpers an update reads as
+// "old"), with the configuration that sized the model
+// ---------------------------------------------------------------------------
+namespace {
+constexpr char kSaveMagic[8] = {'D', 'A', 'S', 'H', 'S', 'A', 'V', '1'};
+
+struct SaveHeader {
+    char magic[8];
+    int32_t version, mode, J, R, precision, input_dtype, n_sweeps, xx_valid;
+    double lambda, pinv_rtol, xx;
+    int64_t max_slices, max_rows, max_segments, max_staged_rows, K;
+};
+
+uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
+struct Arrays {
+    std::vector<double> a[7];
+};
+
+// Sizes of the saved arrays: mode P {V, W, c, D, F, G}; mode Q {V, H, W, L,
+// Y, E, B^{1/2}} (the eigenbasis and square root of B_k kept with L_k so that
+// a resumed model continues bit for bit).
+void array_sizes(int mode, int64_t J, int64_t R, int64_t K, size_t *n, int *count) {
+    if (mode == DASH_MODE_P) {
+        const size_t s[6] = {(size_t)(J * R), (size_t)(K * R), (size_t)(K * R), (size_t)(K * R * R),
+                             (size_t)(J * R), (size_t)(R * R)};
+        for (int i = 0; i < 6; ++i) n[i] = s[i];
+        *count = 6;
+    } else {
+        const size_t s[7] = {(size_t)(J * R), (size_t)(R * R), (size_t)(K * R), (size_t)(K * R * R),
+                             (size_t)(K * R * J), (size_t)(K * R * R), (size_t)(K * R * R)};
+        for (int i = 0; i < 7; ++i) n[i] = s[i];
+        *count = 7;
+    }
+}
+}  // namespace
+
+extern "C" dash_status dash_save(const dash_model *mc, const char *path) {
+    dash_model *m = const_cast<dash_model *>(mc);
+    if (!m) return DASH_EINVAL;
+    if (!path) return fail(m, DASH_EINVAL, "path is null");
+    if (!m->v_set) return fail(m, DASH_ESTATE, "V is not set: nothing to save");
+    if (m->st_segs() > 0) return fail(m, DASH_ESTATE, "rows are staged; update first");
+    CK(cudaStreamSynchronize(m->stream));
+    if (dash_status sn = check_numeric(m)) return sn;
+    fold_xx(m);
+    const dash_config &c = m->cfg;
+    SaveHeader h{};
+    memcpy(h.magic, kSaveMagic, 8);
+    h.version = 1;
+    h.mode = c.mode;
+    h.J = c.J;
+    h.R = c.R;
+    h.precision = c.precision;
+    h.input_dtype = c.input_dtype;
+    h.n_sweeps = c.n_sweeps;
+    h.xx_valid = m->xx_valid ? 1 : 0;
+    h.lambda = c.lambda;
+    h.pinv_rtol = c.pinv_rtol;
+    h.xx = m->xx;
+    h.max_slices = c.max_slices;
+    h.max_rows = c.max_rows;
+    h.max_segments = c.max_segments;
+    h.max_staged_rows = c.max_staged_rows;
+    h.K = m->K;
+    size_t n[7];
+    int cnt = 0;
+    array_sizes(c.mode, c.J, c.R, m->K, n, &cnt);
+    Arrays A;
+    for (int i = 0; i < cnt; ++i) A.a[i].resize(n[i]);
+    dash_status s;
+    if (c.mode == DASH_MODE_P) {
+        s = dash_get_state_p(m, A.a[0].data(), A.a[1].data(), A.a[2].data(), A.a[3].data(), A.a[4].data(),
+                             A.a[5].data());
+    } else {
+        s = dash_get_state_q(m, A.a[0].data(), A.a[1].data(), A.a[2].data(), A.a[3].data(), A.a[4].data());
+        if (!s && m->K > 0) s = get_summ(m, A.a[5].data(), m->qE, n[5]);
+        if (!s && m->K > 0) s = get_summ(m, A.a[6].data(), m->qBh, n[6]);
+    }
+    if (s) return s;
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(m, DASH_EINVAL, "cannot open %s for writing", path);
+    uint64_t hash = fnv1a(1469598103934665603ull, &h, sizeof h);
+    bool ok = fwrite(&h, sizeof h, 1, f) == 1;
+    for (int i = 0; i < cnt && ok; ++i) {
+        if (n[i] == 0) continue;
+        ok = fwrite(A.a[i].data(), 8, n[i], f) == n[i];
+        hash = fnv1a(hash, A.a[i].data(), n[i] * 8);
+    }
+    ok = ok && fwrite(&hash, 8, 1, f) == 1;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return fail(m, DASH_EINVAL, "writing %s failed", path);
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_load(const char *path, void *stream, dash_model **out) {
+    if (!path || !out) return DASH_EINVAL;
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) return DASH_EINVAL;
+    SaveHeader h{};
+    bool ok = fread(&h, sizeof h, 1, f) == 1 && memcmp(h.magic, kSaveMagic, 8) == 0 && h.version == 1 &&
+              (h.mode == DASH_MODE_P || h.mode == DASH_MODE_Q) && h.J > 0 && h.R > 0 && h.R <= kMaxR &&
+              h.K >= 0 && h.K <= h.max_slices;
+    size_t n[7] = {};
+    int cnt = 0;
+    Arrays A;
+    uint64_t hash = fnv1a(1469598103934665603ull, &h, sizeof h);
+    if (ok) {
+        array_sizes(h.mode, h.J, h.R, h.K, n, &cnt);
+        for (int i = 0; i < cnt && ok; ++i) {
+            A.a[i].resize(n[i]);
+            if (n[i] == 0) continue;
+            ok = fread(A.a[i].data(), 8, n[i], f) == n[i];
+            hash = fnv1a(hash, A.a[i].data(), n[i] * 8);
+        }
+        uint64_t stored = 0;
+        ok = ok && fread(&stored, 8, 1, f) == 1 && stored == hash;
+    }
+    fclose(f);
+    if (!ok) return DASH_EINVAL;
+    dash_config c;
+    dash_config_default(&c, h.J, h.R, h.lambda);
+    c.mode = h.mode;
+    c.precision = h.precision;
+    c.input_dtype = h.input_dtype;
+    c.n_sweeps = h.n_sweeps;
+    c.pinv_rtol = h.pinv_rtol;
+    c.max_slices = h.max_slices;
+    c.max_rows = h.max_rows;
+    c.max_segments = h.max_segments;
+    c.max_staged_rows = h.max_staged_rows;
+    c.stream = stream;
+    dash_model *m = nullptr;
+    dash_status s = dash_init(&c, &m);
+    if (s) return s;
+    if (h.mode == DASH_MODE_P) {
+        s = dash_set_state_p(m, h.K, A.a[0].data(), A.a[1].data(), A.a[2].data(), A.a[3].data(),
+                             A.a[4].data(), A.a[5].data());
+    } else {
+        s = dash_set_state_q(m, h.K, A.a[0].data(), A.a[1].data(), A.a[2].data(), A.a[3].data(),
+                             A.a[4].data());
+        if (!s && h.K > 0) s = put_summ(m, m->qE, A.a[5].data(), n[5]);
+        if (!s && h.K > 0) s = put_summ(m, m->qBh, A.a[6].data(), n[6]);
+    }
+    if (s) {
+        dash_destroy(m);
+        return s;
+    }
+    m->xx = h.xx;
+    m->xx_valid = h.xx_valid != 0;
+    *out = m;
+    return DASH_OK;
 }

@@ -66,13 +66,15 @@ dash_status prepare_q(dash_model *m);
 namespace dash {
 // Launch the R×R PSD pseudo-inverse (G⁺ or Γ⁺) on the model's stream: the
 // column-parallel Cholesky kernel for R <= 32, the one-warp kernel above.
-inline dash_status launch_pinv(dash_model *m, const double *in, double *out, int *ok) {
+// abandoned (may be null): see k_f_reduce.
+inline dash_status launch_pinv(dash_model *m, const double *in, double *out, int *ok,
+                               const int *abandoned) {
     const int R = m->cfg.R;
     const size_t psm = (size_t)(3 * R * (R + 1) + (R + 1)) * 8;
     if (R <= 32)
-        LAUNCH(KK_PINV, k_pinv_cols<<<R, 32, psm, m->stream>>>(in, R, m->rtol, out, ok));
+        LAUNCH(KK_PINV, k_pinv_cols<<<R, 32, psm, m->stream>>>(in, R, m->rtol, out, ok, abandoned));
     else
-        LAUNCH(KK_PINV, k_pinv_small<<<1, 32, psm, m->stream>>>(in, R, m->rtol, out, ok));
+        LAUNCH(KK_PINV, k_pinv_small<<<1, 32, psm, m->stream>>>(in, R, m->rtol, out, ok, abandoned));
     return DASH_OK;
 }
 }  // namespace dash

@@ -12,6 +12,7 @@
 #include "dash_kernels_q.cuh"
 #include "dash_kernels_err.cuh"
 #include "dash_kernels_stream.cuh"
+#include "dash_kernels_tc05.cuh"
 
 namespace dash {
 // kernel kinds for the per-kernel profiler
@@ -23,6 +24,8 @@ enum KernelKind {
     KK_Q_BEGIN, KK_Q_AROWS, KK_Q_Y, KK_Q_LT, KK_Q_H, KK_Q_VPART, KK_Q_V, KK_Q_PW, KK_Q_W,
     KK_Q_OUT, KK_Q_FIT, KK_QLT_QR, KK_QLT_PRE, KK_QLT_PASS, KK_QLT_TAIL,
     KK_XQ_PREP, KK_XQ_TC, KK_F_TC, KK_UTILDE, KK_XQ_WAIT, KK_XQ_BUSY, KK_FT_WAIT, KK_FT_BUSY,
+    KK_QV_TF32, KK_XQ_UMMA, KK_UTILDE_TF32, KK_F_UMMA, KK_FIT_LAMBDA,
+    KK_XU_WAIT_P, KK_XU_WAIT_M, KK_XU_WAIT_C, KK_XU_WAIT_E, KK_XU_CYCLES,
     KK_HOST_PLAN, KK_HOST_WAIT, KK_HOST_LAUNCH, KK_COUNT
 };
 static const char *const kKernelNames[KK_COUNT] = {
@@ -35,7 +38,9 @@ static const char *const kKernelNames[KK_COUNT] = {
     "k_q_begin_new", "k_q_arows", "k_q_y", "k_q_lt", "k_q_h", "k_q_vpart", "k_q_v", "k_q_pw",
     "k_q_w", "k_q_out", "k_q_fit", "k_q_lt.qr", "k_q_lt.fp32_pass", "k_q_lt.passes",
     "k_q_lt.tail", "k_xq_bfrag", "k_xq_tc", "k_f_tc", "k_utilde", "k_xq_tc.wait", "k_xq_tc.loop",
-    "k_f_tc.wait", "k_f_tc.loop", "host.plan", "host.wait_previous", "host.launch"};
+    "k_f_tc.wait", "k_f_tc.loop", "k_qv_tf32", "k_xq_umma", "k_utilde_tf32", "k_f_umma", "k_fit_lambda",
+    "k_xq_umma.producer_wait", "k_xq_umma.mma_wait", "k_xq_umma.converter_wait", "k_xq_umma.epilogue_wait",
+    "k_xq_umma.cta", "host.plan", "host.wait_previous", "host.launch"};
 
 struct Profiler {
     bool on = false;
@@ -50,10 +55,11 @@ struct Profiler {
     int n_sm = 1;
     double q_lt_warps = 0.0;    // warps of the last profiled k_q_lt launch
     double xq_warps = 0.0, ft_warps = 0.0;   // warps of the streaming kernels' last launch
+    double xu_ctas = 0.0;                     // CTAs of the last k_xq_umma launch
     std::chrono::steady_clock::time_point t_plan0;   // start of the current batch's planning
 };
 
-constexpr int kPhaseSlots = 15;        // in-kernel cycle counters of the profiler
+constexpr int kPhaseSlots = 20;        // in-kernel cycle counters of the profiler
 constexpr int kCopyStreams = 2;         // streams sharing a large host-to-device append
 constexpr size_t kSplitCopyBytes = 64u << 20;   // appends from this size are split
 constexpr int kFBlocksMax = 1024;       // max row chunks of the F-partial kernel
@@ -129,11 +135,27 @@ struct dash_model {
     // every slice through the chunked path, with the streaming tensor-core
     // kernels for P' = X Q_V and the F partials
     int row_path = 0;
+    // updates launched as one CUDA graph: the launch sequence is captured
+    // from the model's stream and, while its topology (kernel kinds, order,
+    // copies) matches the previous update's, applied to the instantiated
+    // graph as a parameter update (cudaGraphExecUpdate) instead of a new
+    // instantiation
+    bool use_graph = false;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_instantiations = 0, graph_updates = 0;
     bool split_active = false;
     uint4 *xq_frag = nullptr;         // Q_V split into MMA fragments
     int *xq_bexp = nullptr;           // power-of-two scale of those fragments
     uint32_t *Ut = nullptr;           // Ũ = U ∘ w_new as MMA fragment blocks of 16 rows
     int *xe = nullptr;                // exponent of each general row's max |x|
+    // tcgen05 streaming X·Q_V (k_xq_umma): Q_V's TF32 slabs and the ring
+    // depth for this J (0: the shape takes the warp-level kernel)
+    float *qv_slabs = nullptr;
+    int xu_nst = 0;
+    float *ub_tf32 = nullptr;         // Ũ blocks of the tcgen05 F pass (k_utilde_tf32)
+    long long wait_limit = 2000000000LL;   // cycles before a bounded device wait gives up
+    int inject_wait_fault = 0;        // test hook: the next tcgen05 X·Q_V pass skips one copy
+    int64_t K_prev = 0;               // slices before the last update (restored if it is dropped)
     float *Wf = nullptr;              // FP32 copy of the finished slices' new weights
     // general rows: runs of consecutive rows left to the general kernels
     int64_t *d_run_g0 = nullptr, *d_run_row0 = nullptr;
@@ -176,6 +198,15 @@ struct dash_model {
     // last update
     int64_t last_N = 0;
     bool has_last = false;
+
+    // xx = Σ λ^age ||x||² over every absorbed row (the λ-weighted fitness'
+    // denominator): folded on the host from each update's ||X_new||² once
+    // the update has finished (xx ← xx_lam·xx + ||X_new||²)
+    double xx = 0.0;
+    bool xx_valid = false, xx_pending = false;
+    double xx_lam = 0.0;
+    // n_sweeps > 1 (mode P): the old helpers each extra pass starts from
+    double *sw_c = nullptr, *sw_D = nullptr, *sw_F = nullptr, *sw_G = nullptr;
 
     dash::Profiler prof;
 

@@ -139,12 +139,14 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 
 // Bounded wait on an mbarrier phase: gives up after ~2·10⁹ cycles (≈ 1 s)
-// and reports the timeout instead of hanging.
+// and reports the timeout instead of hanging: err[0] counts timeouts, err[3]
+// marks the update as abandoned.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > 2000000000LL) {
             atomicAdd(err, 1);
+            err[3] = 1;
             return false;
         }
     }
@@ -1393,6 +1395,7 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
 static __global__ void __launch_bounds__(256, kBigCBlocksPerSM) k_big_c(FusedArgs a, BigArgs bg, double *Gpart_out) {
     __shared__ __align__(16) float Lw_all[FU_WARPS][FU_RP * FU_LD];
     __shared__ float G_all[FU_WARPS][FU_RP * FU_LD];                  // per-warp G partials
+    if (a.err[3]) return;        // a bounded wait of this update timed out: state untouched
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = a.R;
     for (int i = threadIdx.x; i < FU_WARPS * FU_RP * FU_LD; i += blockDim.x) (&G_all[0][0])[i] = 0.f;

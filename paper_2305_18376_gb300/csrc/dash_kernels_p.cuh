@@ -419,10 +419,16 @@ __global__ void __launch_bounds__(256) k_f(const TI *__restrict__ X, BatchDev b,
     }
 }
 
+// The kernels below that write the model's state take `abandoned` (may be
+// null): when *abandoned != 0 a bounded wait of this update timed out, the
+// update is dropped and they leave the state as it was.
+
 // P8: F ← λF + Σ_b Fpart[b] (Eq. 20); F_inc kept for the fitness.
 template <typename T>
 __global__ void k_f_reduce(const T *__restrict__ Fpart, int nb, int J, int R, double lam,
-                           double *__restrict__ F, double *__restrict__ Finc) {
+                           double *__restrict__ F, double *__restrict__ Finc,
+                           const int *__restrict__ abandoned) {
+    if (abandoned && *abandoned) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)J * R) return;
     double a = 0.0;
@@ -433,7 +439,9 @@ __global__ void k_f_reduce(const T *__restrict__ Fpart, int nb, int J, int R, do
 
 // P8: G ← λG + Σ partials (Eq. 21), one warp per entry, fixed lane order.
 static __global__ void k_g_reduce(const double *__restrict__ Gpart, int nb, int R, double lam,
-                           double *__restrict__ G, double *__restrict__ Ginc) {
+                           double *__restrict__ G, double *__restrict__ Ginc,
+                           const int *__restrict__ abandoned) {
+    if (abandoned && *abandoned) return;
     const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (e >= R * R) return;
@@ -449,7 +457,8 @@ static __global__ void k_g_reduce(const double *__restrict__ Gpart, int nb, int 
 // G⁺ (or Γ⁺) of a symmetric PSD R×R matrix by one warp; ok (optional)
 // receives 1 when the Cholesky path was taken.
 static __global__ void k_pinv_small(const double *__restrict__ Min, int R, double rtol,
-                             double *__restrict__ Mout, int *ok) {
+                             double *__restrict__ Mout, int *ok, const int *__restrict__ abandoned) {
+    if (abandoned && *abandoned) return;
     extern __shared__ double sm[];
     const int ld = R + 1, lane = threadIdx.x & 31;
     double *A = sm, *E = A + R * ld, *out = E + R * ld, *f = out + R * ld;
@@ -479,7 +488,8 @@ static __global__ void k_pinv_small(const double *__restrict__ Min, int R, doubl
 // the Cholesky path.  Dynamic shared memory: as k_pinv_small.
 static __global__ void __launch_bounds__(32) k_pinv_cols(const double *__restrict__ Min, int R,
                                                          double rtol, double *__restrict__ Mout,
-                                                         int *ok) {
+                                                         int *ok, const int *__restrict__ abandoned) {
+    if (abandoned && *abandoned) return;
     extern __shared__ double sm[];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, ld = R + 1;
@@ -550,7 +560,9 @@ static __global__ void __launch_bounds__(32) k_pinv_cols(const double *__restric
 template <typename T>
 __global__ void k_vupdate(const double *__restrict__ F, const double *__restrict__ GP,
                           const double *__restrict__ Finc, int J, int R, double *__restrict__ V,
-                          T *__restrict__ VT, double *__restrict__ cross_part) {
+                          T *__restrict__ VT, double *__restrict__ cross_part,
+                          const int *__restrict__ abandoned) {
+    if (abandoned && *abandoned) return;
     __shared__ double red[8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int j = blockIdx.x * 8 + wid;
@@ -575,7 +587,9 @@ __global__ void k_vupdate(const double *__restrict__ F, const double *__restrict
 }
 
 // P1: Γ = VᵀV, one warp per entry (r, q), lanes over j.
-static __global__ void k_gamma(const double *__restrict__ V, int J, int R, double *__restrict__ Gam) {
+static __global__ void k_gamma(const double *__restrict__ V, int J, int R, double *__restrict__ Gam,
+                               const int *__restrict__ abandoned) {
+    if (abandoned && *abandoned) return;
     const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (e >= R * R) return;
@@ -614,6 +628,26 @@ static __global__ void k_fitness(const double *__restrict__ xn_part, int n_xn,
         out[1] = xn;
         out[2] = res;
         out[3] = (double)*gam_ok;
+    }
+}
+
+// λ-weighted fitness of every row absorbed so far, each with the U_k,new
+// S_k,new its update produced (the frozen products that enter F and G,
+// Eqs. 20-21) and the current V: the residual Σ λ^age ||x − (u∘w)Vᵀ||² is
+// xx − 2 tr(VᵀF) + tr(VᵀV G), xx = Σ λ^age ||x||².  One warp.
+static __global__ void k_fit_lambda(const double *__restrict__ V, const double *__restrict__ F,
+                                    const double *__restrict__ Gam, const double *__restrict__ G,
+                                    int J, int R, double xx, double *__restrict__ out /* [fit, resid2] */) {
+    const int lane = threadIdx.x & 31;
+    double a = 0.0, q = 0.0;
+    for (int i = lane; i < J * R; i += 32) a += V[i] * F[i];
+    for (int i = lane; i < R * R; i += 32) q += Gam[i] * G[i];
+    a = warp_sum(a);
+    q = warp_sum(q);
+    if (lane == 0) {
+        const double res = fmax(0.0, xx - 2.0 * a + q);
+        out[0] = xx > 0.0 ? 1.0 - sqrt(res / xx) : 1.0;
+        out[1] = res;
     }
 }
 

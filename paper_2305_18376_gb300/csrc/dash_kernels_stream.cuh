@@ -81,7 +81,7 @@ __device__ __forceinline__ float4 f4scale(float4 v, float s) {
 }
 
 // Bounded wait of a whole warp on its own stage barrier: false after ~1 s
-// (counted once in err).
+// (counted once in err[0]; err[3] marks the update as abandoned).
 __device__ __forceinline__ bool sb_wait(uint64_t *bar, uint32_t parity, int *err) {
     bool got = true;
     if (!mbar_try_wait(bar, parity)) {
@@ -94,7 +94,10 @@ __device__ __forceinline__ bool sb_wait(uint64_t *bar, uint32_t parity, int *err
         }
     }
     got = __all_sync(0xffffffffu, got);
-    if (!got && (threadIdx.x & 31) == 0) atomicAdd(err, 1);
+    if (!got && (threadIdx.x & 31) == 0) {
+        atomicAdd(err, 1);
+        err[3] = 1;
+    }
     return got;
 }
 

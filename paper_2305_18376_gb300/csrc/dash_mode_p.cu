@@ -2,6 +2,8 @@
 // the fused row kernel over tiles of single-segment slices, the chunked path
 // for large or split slices, the general kernels, and the global reductions
 // and solves (Eqs. 11-21).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -10,6 +12,39 @@
 #include "dash_host.cuh"
 
 namespace dash {
+
+// cuTensorMapEncodeTiled from the driver, looked up once (no link against
+// libcuda); null if the driver does not provide it.
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of the rows [0, rows) of a row-major FP32 matrix with J columns
+// (16-byte aligned base, J % 4 == 0), boxes of box_x columns × box_y rows,
+// zero fill past the edges: 32 × 128 with the 128-byte swizzle for the X·Q_V
+// pass, 128 × 32 unswizzled for the F pass.  False if the driver refuses it.
+static bool x_tensor_map(CUtensorMap *map, const float *base, int J, int64_t rows, int box_x, int box_y,
+                         bool swizzle) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc || rows <= 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || (J % 4) != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)J, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)J * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 template <typename TI, typename T>
 static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void *Xv, double lam,
@@ -76,6 +111,9 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
         }
     }
     int n_xn = 0;
+    // the tcgen05 passes of the split pipeline: their tensor maps over X
+    CUtensorMap tmx, tmxf;
+    bool tc05 = false;
     // P = X V for the general kernels; P' = X Q_V for the chunked path
     const T *Vmul = (const T *)m->VT;
     if constexpr (std::is_same<T, float>::value) {
@@ -85,7 +123,25 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     if constexpr (std::is_same<T, float>::value && std::is_same<TI, float>::value) split = m->split_active;
     if (Ng > 0) {
         LAUNCH(KK_ROWMAP, k_rowmap<<<(N + 255) / 256, 256, 0, st>>>(b));
-        if (split) {
+        if (split && m->xu_nst > 0 && m->row_path != DASH_ROWS_SPLIT_WARP && b.n_runs == 1) {
+            const float *X0 = (const float *)X + m->h_run_row0[0] * J;
+            tc05 = x_tensor_map(&tmx, X0, J, Ng, 32, 128, true) && x_tensor_map(&tmxf, X0, J, Ng, 128, 32, false);
+        }
+        if (tc05) {
+            // P' = X Q_V on tcgen05 MMAs, X tiles by TMA, Q_V as TF32 slabs
+            const int nslab = (J + 31) / 32;
+            LAUNCH(KK_QV_TF32, k_qv_tf32<<<(nslab * 2048 + 255) / 256, 256, 0, st>>>(m->QV, J, R, m->qv_slabs));
+            n_xn = (int)std::min<int64_t>(m->n_sm, (Ng + 127) / 128);
+            XuArgs xa{m->qv_slabs, (float *)m->P, m->xn_part + g_f, m->d_err, Ng, m->h_run_row0[0],
+                      J, R, m->xu_nst, m->wait_limit, m->inject_wait_fault,
+                      m->prof.on ? m->prof.d_phase + 15 : nullptr};
+            m->inject_wait_fault = 0;
+            const size_t smem = xu_smem(J, m->xu_nst);
+            CK(cudaFuncSetAttribute(k_xq_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            LAUNCH(KK_XQ_UMMA, k_xq_umma<<<n_xn, XU_THREADS, smem, st>>>(tmx, xa));
+            m->prof.xq_warps = (double)n_xn * (XU_THREADS / 32);
+            m->prof.xu_ctas = n_xn;
+        } else if (split) {
             // P' = X Q_V on the tensor cores, Q_V pre-split into fragments
             const int nfr = ((J + 15) / 16) * ((R + 7) / 8) * 32;
             LAUNCH(KK_XQ_PREP, k_xq_bscale<<<1, 32, 0, st>>>(m->QV, J * R, m->xq_bexp));
@@ -169,7 +225,20 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     }
     // F partials of the general rows
     int nfb = 0;
-    if (Ng > 0 && split) {
+    if (Ng > 0 && tc05) {
+        // Ũ = U ∘ w_new as TF32 blocks, then the F partials on tcgen05 MMAs:
+        // about one CTA per SM, row chunks × 128-column tiles
+        LAUNCH(KK_UTILDE_TF32, k_utilde_tf32<<<(unsigned)((Ng + 31) / 32), 256, 0, st>>>(b, R, (const float *)m->U,
+                                                                                       m->Wf, m->ub_tf32));
+        const int nmt = (J + 127) / 128;
+        nfb = std::max(1, m->n_sm / nmt);
+        const int64_t rpc = ((Ng + nfb - 1) / nfb + 31) / 32 * 32;
+        nfb = (int)((Ng + rpc - 1) / rpc);
+        FbArgs fb{m->ub_tf32, (float *)m->Fpart + (size_t)g_f * J * R, m->d_err, Ng, rpc, J, R, m->wait_limit};
+        CK(cudaFuncSetAttribute(k_f_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem()));
+        LAUNCH(KK_F_UMMA, k_f_umma<<<dim3(nfb, nmt), FB_THREADS, fb_smem(), st>>>(tmxf, fb));
+        m->prof.ft_warps = (double)nfb * nmt * (FB_THREADS / 32);
+    } else if (Ng > 0 && split) {
         // Ũ = U ∘ w_new, then the F partials on the tensor cores: one CTA per
         // SM, rows in equal shares
         const int NT = (R + 7) / 8;
@@ -210,13 +279,14 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
                                                      (T *)m->Fpart + (size_t)g_f * J * R));
     }
     LAUNCH(KK_F_REDUCE, k_f_reduce<T><<<((int64_t)J * R + 255) / 256, 256, 0, st>>>((const T *)m->Fpart, g_f + nfb, J, R, lam,
-                                                                s.F, m->Finc));
-    LAUNCH(KK_G_REDUCE, k_g_reduce<<<(R * R + 7) / 8, 256, 0, st>>>(m->Gpart, g_f + nsb, R, lam, s.G, m->Ginc));
-    if (dash_status e = launch_pinv(m, s.G, m->GP, nullptr)) return e;
+                                                                s.F, m->Finc, m->d_err + 3));
+    LAUNCH(KK_G_REDUCE, k_g_reduce<<<(R * R + 7) / 8, 256, 0, st>>>(m->Gpart, g_f + nsb, R, lam, s.G, m->Ginc,
+                                                                  m->d_err + 3));
+    if (dash_status e = launch_pinv(m, s.G, m->GP, nullptr, m->d_err + 3)) return e;
     LAUNCH(KK_VUPDATE, k_vupdate<T><<<(J + 7) / 8, 256, 0, st>>>(s.F, m->GP, m->Finc, J, R, s.V, (T *)m->VT,
-                                               m->cross_part));
-    LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(s.V, J, R, s.Gam));
-    if (dash_status e = launch_pinv(m, s.Gam, s.GamP, s.gam_ok)) return e;
+                                               m->cross_part, m->d_err + 3));
+    LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(s.V, J, R, s.Gam, m->d_err + 3));
+    if (dash_status e = launch_pinv(m, s.Gam, s.GamP, s.gam_ok, m->d_err + 3)) return e;
     LAUNCH(KK_FITNESS, k_fitness<<<1, 32, 0, st>>>(m->xn_part, g_f + n_xn, m->cross_part, (J + 7) / 8, s.Gam, m->Ginc, R,
                                 s.gam_ok, m->fit));
     CK(cudaMemcpyAsync(m->h_fit, m->fit, 4 * 8, cudaMemcpyDeviceToHost, st));

@@ -109,7 +109,7 @@ static dash_status launch_update_q(dash_model *m, const BatchDev &b, const void 
             LAUNCH(KK_Q_VPART, (k_q_vpart<T, 64><<<gv, QV_THREADS, 0, st>>>(b.K_all, q, Y, m->qslots)));
         LAUNCH(KK_Q_V, (k_q_v<T><<<(J + 7) / 8, 256, 0, st>>>(m->qslots, gv, m->qPV, J, R, m->st.V,
                                                                (T *)m->VT)));
-        LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(m->st.V, J, R, m->st.Gam));
+        LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(m->st.V, J, R, m->st.Gam, nullptr));
         LAUNCH(KK_Q_PW, (k_q_pw<<<1, 32, (size_t)(3 * R * ld + R) * 8, st>>>(q, m->qPW)));
         if (b.K_all > 0) {
             const int gw = std::min(b.K_all, 4 * m->n_sm);

@@ -9,8 +9,10 @@ from oracle import dash_oracle as O
 
 # tolerances (relative, normwise max): FP64 products ≤ 1e-10; FP32 / mixed
 # products ≤ 1e-4 with batch fitness within 1e-3
-TOL = {"fp64": 1e-10, "fp32": 1e-4, "f16x3": 1e-4, "f16x3-fused": 1e-4, "f16x3-split": 1e-4}
-FIT_TOL = {"fp64": 1e-10, "fp32": 1e-3, "f16x3": 1e-3, "f16x3-fused": 1e-3, "f16x3-split": 1e-3}
+TOL = {"fp64": 1e-10, "fp32": 1e-4, "f16x3": 1e-4, "f16x3-fused": 1e-4, "f16x3-split": 1e-4,
+       "f16x3-split-warp": 1e-4}
+FIT_TOL = {"fp64": 1e-10, "fp32": 1e-3, "f16x3": 1e-3, "f16x3-fused": 1e-3, "f16x3-split": 1e-3,
+           "f16x3-split-warp": 1e-3}
 
 
 def rel(a, b) -> float:

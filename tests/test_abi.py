@@ -65,7 +65,7 @@ def test_status_strings_and_default_config(lib):
 def test_init_rejects_bad_arguments_before_touching_the_device(lib):
     from paper_2305_18376_gb300 import _native
     for field, value in [("J", 0), ("R", 65), ("R", 0), ("lambda_", 0.0), ("lambda_", 1.5),
-                         ("n_sweeps", 2), ("mode", 7), ("precision", 9)]:
+                         ("n_sweeps", 0), ("n_sweeps", 65), ("mode", 7), ("precision", 9)]:
         cfg = _native.Config()
         lib.dash_config_default(C.byref(cfg), 8, 3, 0.9)
         setattr(cfg, field, value)

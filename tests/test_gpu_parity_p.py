@@ -11,18 +11,18 @@ import torch
 from oracle import dash_oracle as O
 from synth.planted import PlantedStream, ragged_batch, tiny, workload
 from tests._parity import (FIT_TOL, TOL, compare_state_p, gpu_rows_by_slice, oracle_batch_fitness_p,
-                           oracle_fit_p, record, rel, segs_np)
+                           oracle_fit_p, perturb, record, rel, segs_np)
 
 pytestmark = pytest.mark.gpu
 
 PREC_DTYPE = {"fp64": ("f64", torch.float64), "fp32": ("f32", torch.float32),
               "f16x3": ("f32", torch.float32), "f16x3-fused": ("f32", torch.float32),
-              "f16x3-split": ("f32", torch.float32)}
+              "f16x3-split": ("f32", torch.float32), "f16x3-split-warp": ("f32", torch.float32)}
 
 
 def _model(J, R, lam, prec, **kw):
-    """prec: a precision, or "f16x3-fused" / "f16x3-split" for the tensor-core
-    products with that row pipeline."""
+    """prec: a precision, or "f16x3-fused" / "f16x3-split" / "f16x3-split-warp"
+    for the tensor-core products with that row pipeline."""
     from paper_2305_18376_gb300 import DashModel
     idt, _ = PREC_DTYPE[prec]
     base, _, path = prec.partition("-")
@@ -85,7 +85,7 @@ def _run_stream(w, prec, n_steps, init_iters=3, via="batch", seed_v=1):
     return worst
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3-fused", "f16x3-split"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3-fused", "f16x3-split", "f16x3-split-warp"])
 def test_small_stream_parity(prec):
     w = tiny(K0=6, J=9, R=3, steps=4, sigma=0.05, lam=0.9)
     _run_stream(w, prec, 4)
@@ -193,7 +193,7 @@ def test_zero_weight_entries_take_the_general_lemma1_path(prec):
         assert rel(got[k], Uo[k]) <= tol
 
 
-@pytest.mark.parametrize("prec", ["fp32", "f16x3-fused", "f16x3-split"])
+@pytest.mark.parametrize("prec", ["fp32", "f16x3-fused", "f16x3-split", "f16x3-split-warp"])
 def test_fused_tiles_span_many_slices_and_ctas(prec):
     """A few thousand small slices of 1-64 rows (c4's update shape at small J
     and R): many tiles per CTA, big and split slices on the chunked path in
@@ -204,7 +204,7 @@ def test_fused_tiles_span_many_slices_and_ctas(prec):
     print(f"many-slice {prec} worst relative errors:", worst)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3-fused", "f16x3-split"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3-fused", "f16x3-split", "f16x3-split-warp"])
 def test_c4_shape_small_k(prec):
     """c4's J = 512 and R = 32 (full register tiles of the MMA path) at
     K0 = 300 slices."""
@@ -385,3 +385,107 @@ def test_rows_error_is_the_global_error_of_accumulated_rows(prec):
         assert abs(e2 - e2_o) <= tol * e2_o, (t, e2, e2_o)
         assert ea > 0
     m.close()
+
+
+def test_long_stream_from_an_unfitted_start_tracks_the_oracle():
+    """Algorithm 1 fixes no scale between S_k and V (Eqs. 11-17 are invariant
+    under S_k → αS_k, V → V/α).  From an unfitted start (one static iteration
+    on slices of R..2R rows, c4's update recipe at K0 = 200) the W rows grow
+    and V shrinks update after update, until G overflows.  The FP64 path
+    follows the oracle update by update:
+      * while the state is well scaled (max |W| < 2): within 1e-10;
+      * while the systems it inverts stay well posed (cond of G and of VᵀV
+        below 1e10, far inside the pseudo-inverse cut-off 1/(R·ε)): within
+        1e-10 or 16× the spread of a shadow oracle stream started one FP64
+        rounding per entry away, whichever is larger — the drifting update
+        map amplifies rounding-sized differences in the oracle itself;
+      * after that the pseudo-inverses' rank decisions are themselves
+        ill-posed, and the GPU state must have drifted the same way (max |W|
+        above 1e3) or been reported non-finite."""
+    w = workload("c4", K0=200, steps=14, init_rows=("uniform", 32, 64), new_slices_per_step=1)
+    s = PlantedStream(w)
+    V0 = np.random.default_rng(0).random((w.J, w.R))
+    b0 = s.batch(0)
+    st = oracle_fit_p(segs_np(b0, torch.float64), V0, 1)
+    prng = np.random.default_rng(5)
+    sh = O.StateP(*(perturb(getattr(st, f), 2.0 ** -53, prng) for f in ("V", "W", "c", "D", "F", "G")))
+    m = _model(w.J, w.R, w.lam, "fp64", max_slices=w.K0 + 64, max_rows=b0.n_rows + 8192,
+               max_segments=4096)
+    m.set_factors(V0)
+    m.append_batch(b0.slice_ids.numpy(), b0.row_ptr.numpy(), b0.X.double().numpy())
+    m.fit_initial(1)
+    compare_state_p(m.get_state_p(), st, TOL["fp64"], "init")
+    drifted = compared = False
+    for t in range(1, 15):
+        b = s.batch(t)
+        segs = segs_np(b, torch.float64)
+        try:
+            with np.errstate(all="ignore"):
+                st, _ = O.dash_update_p(st, segs, b.n_new, w.lam)
+                sh, _ = O.dash_update_p(sh, segs, b.n_new, w.lam)
+            o_ok = all(np.all(np.isfinite(getattr(x, f))) for x in (st, sh) for f in ("V", "W", "G"))
+        except np.linalg.LinAlgError:
+            o_ok = False
+        m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.double().cuda())
+        try:
+            g = m.get_state_p()
+            g_ok = bool(np.all(np.isfinite(g["W"])) and np.all(np.isfinite(g["V"])))
+        except Exception:          # DASH_ENUMERIC: the library saw the overflow
+            g, g_ok = None, False
+        if not o_ok:
+            print(f"  update {t}: oracle state no longer finite; GPU finite: {g_ok}")
+            if g_ok:
+                assert float(np.max(np.abs(g["W"]))) > 1e3, "GPU state did not drift with the oracle"
+            drifted = True
+            break
+        wmax = float(np.max(np.abs(st.W)))
+        cond = max(np.linalg.cond(st.G), np.linalg.cond(st.V.T @ st.V))
+        if cond >= 1e10:
+            gw = float(np.max(np.abs(g["W"]))) if g_ok else float("inf")
+            print(f"  update {t}: max|W| {wmax:.3g}, cond {cond:.3g}: ill-posed; GPU max|W| {gw:.3g}")
+            record(f"drift {t}", {"wmax": wmax, "cond": cond, "gpu_wmax": gw}, None)
+            assert gw > 1e3, "GPU state did not drift with the oracle"
+            drifted = True
+            continue
+        assert g_ok, f"update {t}: GPU state non-finite while the oracle's is finite and well posed"
+        errs = {k: rel(g[k], getattr(st, k)) for k in "VWcDFG"}
+        spread = max(rel(getattr(sh, k), getattr(st, k)) for k in "VWcDFG")
+        limit = TOL["fp64"] if wmax < 2.0 else max(TOL["fp64"], 16.0 * spread)
+        print(f"  update {t}: max|W| {wmax:.3g} cond {cond:.3g} errors {errs} shadow spread {spread:.3g} "
+              f"limit {limit:.3g}")
+        record(f"drift {t}", {**errs, "shadow_spread": spread, "wmax": wmax, "cond": cond}, limit)
+        assert max(errs.values()) <= limit, (t, errs, limit)
+        compared = True
+        drifted = drifted or wmax > 1e3
+    m.close()
+    assert compared and drifted, "the stream did not drift: the test no longer covers the unnormalised regime"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f16x3"])
+def test_graph_launched_updates_are_bit_identical(prec):
+    """Updates submitted as one captured CUDA graph (re-used across batches of
+    the same launch topology) give the same bits as plain launches."""
+    _, tdt = PREC_DTYPE[prec]
+    w = workload("c2", K0=300, steps=4, init_rows=("uniform", 50, 300),
+                 new_slice_rows=("uniform", 50, 100))
+    s = PlantedStream(w)
+    b0 = s.batch(0)
+    st = oracle_fit_p(segs_np(b0, tdt), np.random.default_rng(1).random((w.J, w.R)), 2)
+    ms = []
+    for graph in (False, True):
+        m = _model(w.J, w.R, w.lam, prec, max_slices=w.K0 + 64, max_rows=8192, max_segments=4096)
+        m.set_state_p(st.V, st.W, st.c, st.D, st.F, st.G)
+        m.set_graph(graph)
+        ms.append(m)
+    for t in range(1, 5):
+        b = s.batch(t)
+        for m in ms:
+            m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.to(tdt).cuda())
+        ga, gb = ms[0].get_state_p(), ms[1].get_state_p()
+        for k in ga:
+            assert np.array_equal(ga[k], gb[k]), (t, k)
+        assert ms[0].fitness()[0] == ms[1].fitness()[0]
+    inst, upd = ms[1].graph_stats()
+    assert inst >= 1 and upd >= 1 and inst + upd == 4, (inst, upd)
+    for m in ms:
+        m.close()

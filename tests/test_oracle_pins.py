@@ -576,3 +576,40 @@ def test_init_helpers_q_follow_their_definition():
         assert _rel(L.T @ L, A.T @ A) < 1e-12
         assert _rel(L, np.linalg.cholesky(A.T @ A).T) < 1e-10
         assert _rel(st.Z[k], Z) < 1e-13
+
+
+def test_weighted_fitness_by_hand_and_as_a_batch_fitness():
+    """The λ-weighted fitness: a hand case (ages 0 and 1, λ = 1/4) and the
+    single-batch special case, where it is the batch fitness."""
+    V = np.eye(2)
+    rows = [(0, np.array([[3.0, 4.0]]), np.array([[3.0, 0.0]]), np.array([1.0, 1.0])),
+            (1, np.array([[0.0, 2.0]]), np.array([[0.0, 1.0]]), np.array([1.0, 2.0]))]
+    # residuals 16 (age 0) and 0; norms 25 + 4/4
+    assert abs(O.weighted_fitness_p(rows, V, 0.25) - (1.0 - np.sqrt(16.0 / 26.0))) < 1e-15
+    X = RNG.standard_normal((6, 4))
+    U = RNG.standard_normal((6, 2))
+    w = RNG.random(2) + 0.5
+    Vr = RNG.standard_normal((4, 2))
+    assert abs(O.weighted_fitness_p([(0, X, U, w)], Vr, 0.7)
+               - O.fitness([X], [O.reconstruct_p(U, w, Vr)])) < 1e-14
+
+
+@pytest.mark.parametrize("lam", [1.0, 0.8])
+def test_weighted_fitness_equals_the_helper_form(lam):
+    """Over a stream, Σ λ^age ||x − (u∘w)Vᵀ||² computed from every stored row
+    equals xx − 2 tr(VᵀF) + tr(VᵀV G) from the streamed helpers (Eqs. 20-21),
+    xx = Σ λ^age ||x||²: the form the library evaluates."""
+    w = tiny(K0=6, J=7, R=3, steps=3, sigma=0.05, lam=lam, new=2)
+    s = PlantedStream(w)
+    ost = O.OracleStream("P", RNG.random((w.J, w.R)), lam)
+    for t in range(4):
+        b = s.batch(t)
+        ost.update(_segs(b), b.n_new)
+    st = ost.state
+    T = ost.t
+    rows = [(T - 1 - p[0], p[1], p[2], p[3]) for parts in ost.rows for p in parts]
+    num = sum(lam ** a * np.sum((X - O.reconstruct_p(U, wv, st.V)) ** 2) for a, X, U, wv in rows)
+    xx = sum(lam ** a * np.sum(X ** 2) for a, X, _, _ in rows)
+    helper = xx - 2.0 * np.sum(st.V * st.F) + np.sum((st.V.T @ st.V) * st.G)
+    assert abs(num - helper) <= 1e-10 * xx
+    assert abs(O.weighted_fitness_p(rows, st.V, lam) - (1.0 - np.sqrt(helper / xx))) < 1e-8
