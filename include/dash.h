@@ -382,6 +382,14 @@ dash_status dash_inject_wait_fault(dash_model *m);
 dash_status dash_set_graph(dash_model *m, int32_t on);
 dash_status dash_graph_stats(const dash_model *m, int64_t *instantiations, int64_t *updates);
 
+/* Measured FP64 FMA rate of the current device (FMAs per second; one FMA is
+ * two flops): independent FMA chains on every SM, best of three timed runs
+ * after a warm-up.  The FP64-product path and the per-slice R×R solves are
+ * bound by this pipe; it is the denominator of their roofline.  Allocates a
+ * few bytes (the paper has no counterpart).  DASH_ECUDA if the device
+ * cannot be used. */
+dash_status dash_measure_fp64_fma(double *fma_per_second);
+
 /* Allocation-free F increment.  (The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory.)
  *
@@ -403,12 +411,14 @@ dash_status dash_graph_stats(const dash_model *m, int64_t *instantiations, int64
  * Nothing is allocated: per-block partial sums go to one static device
  * array of 2^21 floats (8 MiB) that every GPU loading this library holds
  * until the process exits.  J·R above 2^21 returns DASH_ENOMEM; bad
- * arguments DASH_EINVAL; a failed lookup or launch DASH_ECUDA.  The first
- * call on a device looks up that array's device address (with the device
- * current) and caches it: make that first call before any stream capture.
- * Calls share the array, so calls that overlap on the GPU race; serialise
- * them (e.g. one stream).  Each call writes every partial it reads, so what
- * an earlier call left there is never used. */
+ * arguments DASH_EINVAL; a failed lookup or launch DASH_ECUDA.  A call on a
+ * stream that is not being captured looks that array's device address up
+ * (with the device current) and caches it, so a context created anew after
+ * cudaDeviceReset is followed; a call on a stream under capture uses the
+ * cached address: make the first call on each device before any capture
+ * (else DASH_ECUDA).  Calls share the array, so calls that overlap on the
+ * GPU race; serialise them (e.g. one stream).  Each call writes every
+ * partial it reads, so what an earlier call left there is never used. */
 dash_status dash_f_increment_noalloc(const float *X, const float *U, int64_t N, int32_t J,
                                      int32_t R, const int64_t *seg_row, const int32_t *seg_slice,
                                      int64_t n_seg, const double *W, double *F_inc,

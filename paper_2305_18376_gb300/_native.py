@@ -85,6 +85,7 @@ SIGNATURES = [
     ("dash_save", C.c_int, [P, C.c_char_p]),
     ("dash_load", C.c_int, [C.c_char_p, P, C.POINTER(P)]),
     ("dash_set_graph", C.c_int, [P, I32]),
+    ("dash_measure_fp64_fma", C.c_int, [PD]),
     ("dash_set_wait_limit", C.c_int, [P, I64]),
     ("dash_inject_wait_fault", C.c_int, [P]),
     ("dash_graph_stats", C.c_int, [P, PI64, PI64]),
@@ -139,6 +140,16 @@ def _config(lib, J: int, R: int, lam: float, mode: str = "P", precision: str = "
     cfg.stream = stream
     cfg.max_staged_rows = max_staged_rows
     return cfg
+
+
+def measure_fp64_fma() -> float:
+    """FP64 FMAs per second of the current device (dash_measure_fp64_fma)."""
+    lib = load()
+    v = C.c_double()
+    st = lib.dash_measure_fp64_fma(C.byref(v))
+    if st != 0:
+        raise DashError(st, "dash_measure_fp64_fma failed")
+    return v.value
 
 
 def config_bytes(J: int, R: int, lam: float, **kw) -> tuple:

@@ -26,7 +26,7 @@ NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                   "-I" + INCLUDE, "-I" + CSRC, "--expt-relaxed-constexpr"]
 
 # every .cu translation unit of the library
-SOURCES = ["dash_api.cu", "dash_mode_p.cu", "dash_mode_q.cu", "dash_noalloc.cu"]
+SOURCES = ["dash_api.cu", "dash_mode_p.cu", "dash_mode_q.cu", "dash_noalloc.cu", "dash_probe.cu"]
 
 
 def nvcc() -> str:

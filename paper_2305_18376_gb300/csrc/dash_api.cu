@@ -87,10 +87,11 @@ static void prof_collect(dash_model *m) {
                 if (c[11 + i]) m->prof.launches[KK_XQ_WAIT + i] += 1;
             }
             // k_xq_umma: cycles each role waited (producer and MMA issuer: one
-            // thread per CTA; converters and epilogue: summed over their 8
+            // thread per CTA; converters and epilogue: summed over their
             // warps) and each CTA's lifetime, reported per CTA
             for (int i = 0; i < 5; ++i) {
-                const double per = (m->prof.xu_ctas > 0 ? m->prof.xu_ctas : 1.0) * ((i == 2 || i == 3) ? 8.0 : 1.0);
+                const double nw = i == 2 ? 4.0 * XU_CONV_GROUPS : (i == 3 ? 4.0 * XU_EPI_GROUPS : 1.0);
+                const double per = (m->prof.xu_ctas > 0 ? m->prof.xu_ctas : 1.0) * nw;
                 m->prof.ms[KK_XU_WAIT_P + i] += (double)c[15 + i] / per / m->prof.clock_khz;
                 if (c[15 + i]) m->prof.launches[KK_XU_WAIT_P + i] += 1;
             }
@@ -319,8 +320,9 @@ static dash_status init_alloc(dash_model *m) {
     DALLOC(m->xq_frag, (size_t)((J + 15) / 16) * ((R + 7) / 8) * 32 * 16, "Q_V fragments");
     DALLOC(m->xq_bexp, 4, "Q_V fragment scale");
     if (m->xu_nst > 0) {
-        DALLOC(m->qv_slabs, (size_t)((J + 31) / 32) * XU_SLAB_BYTES, "Q_V TF32 slabs");
-        DALLOC(m->ub_tf32, (size_t)(Nm / 32 + 2) * FB_UBLK, "U o w TF32 blocks");
+        DALLOC(m->qv_slabs, (size_t)xu_slabs((int)J) * XU_SLAB_BYTES, "Q_V TF32 slabs");
+        m->ub_blocks = Nm / 32 + 2;
+        DALLOC(m->ub_tf32, (size_t)m->ub_blocks * FB_UBLK, "U o w TF32 blocks");
     }
     if (m->fused_ok) {
         DALLOC(m->Ut, (size_t)(Nm / 16 + 2) * ft_ublk((R + 7) / 8) * 4, "U o w fragments");
@@ -329,7 +331,7 @@ static dash_status init_alloc(dash_model *m) {
     }
     // FP64 fallback workspace: one slot per warp of a grid of at most kBigCBlocksPerSM CTAs per SM
     DALLOC(m->wsp, (size_t)kBigCBlocksPerSM * m->n_sm * FU_WARPS * fu_wsp_doubles((int)R) * 8, "fallback workspace");
-    DALLOC(m->d_err, 4 * sizeof(int), "error counters");
+    DALLOC(m->d_err, kErrSlots * sizeof(int), "error counters");
     m->max_chunks = Nm / FU_TILE_MAX + Sm + 1;
     DALLOC(m->d_ch_row0, m->max_chunks * 8, "chunks");
     DALLOC(m->d_ch_n, m->max_chunks * 4, "chunks");
@@ -352,15 +354,15 @@ static dash_status init_alloc(dash_model *m) {
     if ((s = halloc(m, (void **)&m->h_tile_s1, (Sm + 1) * 4))) return s;
     if ((s = halloc(m, (void **)&m->h_run_g0, (Sm + 2) * 8))) return s;
     if ((s = halloc(m, (void **)&m->h_run_row0, (Sm + 2) * 8))) return s;
-    if ((s = halloc(m, (void **)&m->h_err, 4 * sizeof(int)))) return s;
+    if ((s = halloc(m, (void **)&m->h_err, kErrSlots * sizeof(int)))) return s;
     if ((s = halloc(m, (void **)&m->h_ch_row0, m->max_chunks * 8))) return s;
     if ((s = halloc(m, (void **)&m->h_ch_n, m->max_chunks * 4))) return s;
     if ((s = halloc(m, (void **)&m->h_ch_k, m->max_chunks * 4))) return s;
     if ((s = halloc(m, (void **)&m->h_fin_k, Km * 4))) return s;
     if ((s = halloc(m, (void **)&m->h_fin_c0, (Km + 1) * 4))) return s;
     if (m->dry) return DASH_OK;
-    memset(m->h_err, 0, 4 * sizeof(int));
-    cudaMemsetAsync(m->d_err, 0, 4 * sizeof(int), m->stream);
+    memset(m->h_err, 0, kErrSlots * sizeof(int));
+    cudaMemsetAsync(m->d_err, 0, kErrSlots * sizeof(int), m->stream);
     return DASH_OK;
 }
 
@@ -532,6 +534,9 @@ static dash_status check_abandoned(dash_model *m) {
 // After a synchronisation: the device counter of non-finite per-slice
 // results (copied back at the end of every update) must be zero.
 static dash_status check_numeric(dash_model *m) {
+    if (m->h_err[4] > 0)
+        return fail(m, DASH_ECUDA, "%d index self-checks of the tcgen05 kernels failed (first code %d)",
+                    m->h_err[4], m->h_err[5]);
     if (dash_status a = check_abandoned(m)) return a;
     if (m->h_err[2] > 0)
         return fail(m, DASH_ENUMERIC, "%d slice factors came out non-finite", m->h_err[2]);
@@ -660,7 +665,7 @@ extern "C" dash_status dash_get_state_p(const dash_model *mc, double *V, double 
     if (!m) return DASH_EINVAL;
     if (m->cfg.mode != DASH_MODE_P) return fail(m, DASH_ESTATE, "model is not in mode P");
     CK(cudaStreamSynchronize(m->stream));
-    if (dash_status a = check_abandoned(m)) return a;
+    if (dash_status a = check_numeric(m)) return a;
     const int64_t J = m->cfg.J, R = m->cfg.R, K = m->K;
     if (V) CK(cudaMemcpy(V, m->st.V, J * R * 8, cudaMemcpyDeviceToHost));
     if (W && K) CK(cudaMemcpy(W, m->st.W, K * R * 8, cudaMemcpyDeviceToHost));

@@ -60,6 +60,10 @@ struct Profiler {
 };
 
 constexpr int kPhaseSlots = 20;        // in-kernel cycle counters of the profiler
+// device error slots: [0] timed-out waits, [1] FP64 fallback solves,
+// [2] non-finite slice results, [3] this update abandoned, [4] failed index
+// self-checks of the tcgen05 kernels, [5] the first failed check's code
+constexpr int kErrSlots = 8;
 constexpr int kCopyStreams = 2;         // streams sharing a large host-to-device append
 constexpr size_t kSplitCopyBytes = 64u << 20;   // appends from this size are split
 constexpr int kFBlocksMax = 1024;       // max row chunks of the F-partial kernel
@@ -153,6 +157,7 @@ struct dash_model {
     float *qv_slabs = nullptr;
     int xu_nst = 0;
     float *ub_tf32 = nullptr;         // Ũ blocks of the tcgen05 F pass (k_utilde_tf32)
+    int64_t ub_blocks = 0;            // blocks that buffer holds
     long long wait_limit = 2000000000LL;   // cycles before a bounded device wait gives up
     int inject_wait_fault = 0;        // test hook: the next tcgen05 X·Q_V pass skips one copy
     int64_t K_prev = 0;               // slices before the last update (restored if it is dropped)

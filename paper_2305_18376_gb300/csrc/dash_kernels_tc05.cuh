@@ -13,41 +13,46 @@
 //   k_f_umma   per-chunk partials of F_inc = Σ_rows X(i,:)ᵀ Ũ(i,:) (P5,
 //              Eq. 20) on tcgen05 MMAs, A = Xᵀ from tensor memory
 //
-// Products.  x = big(x) + small(x), big(x) the TF32 value the tensor core
-// takes from x's FP32 bits and small(x) = x − big(x) exactly in FP32; Q_V
-// likewise.  P' = big(X)·big(Q_V) + big(X)·small(Q_V) + small(X)·big(Q_V)
-// (the 3-term TF32 split), each product exact in FP32.  Every 32-column
-// stage (4 MMA k-steps) accumulates into a fresh tensor-memory accumulator,
-// the main term in its columns 0-31 and the two correction terms in 32-63;
-// the epilogue adds main + correction and sums the stages in FP32 registers
-// (rounded to nearest).  The tensor core's own accumulation does not round
-// to nearest, and over all 64 k-steps of a 512-column row a sum with
-// cancelling terms lost ~30× more than the FP16-split kernel; over 4 k-steps
-// it stays below that kernel's error.  TF32 keeps FP32's exponent range, so
+// Products.  x = big(x) + small(x) + O(2^-22 x): big(x) the TF32 value the
+// tensor core takes from x's FP32 bits in shared memory (truncation), small(x)
+// = x − big(x) rounded to TF32; Q_V with both parts rounded to the nearest
+// TF32 value (2^-23).  (Rounding big(x) in place as well measured no gain in
+// accuracy and cost 8 % of the pass.)  P' = big(X)·big(Q_V) + big(X)·small(Q_V) + small(X)·big(Q_V)
+// (the 3-term TF32 split), each product exact in FP32.  Every 32-column box
+// of a stage (4 MMA k-steps) accumulates into a fresh tensor-memory
+// accumulator, the main term in its columns 0-31 and the two correction
+// terms in 32-63; the epilogue adds them and sums in FP32 registers (rounded
+// to nearest).  The tensor core's own accumulation does not round to
+// nearest: over all 64 k-steps of a 512-column row a sum with cancelling
+// terms lost ~30× more than the FP16-split kernel.  TF32 keeps FP32's exponent range, so
 // no operand needs scaling.
 //
-// Kernel structure (one persistent CTA per SM, 18 warps, tiles of 128 rows):
-//   warp 0     TMA producer: Q_V's slabs once, then per tile and 32-column
-//              stage one 128×32 FP32 box of X (SWIZZLE_128B) into a ring of
-//              nst stages, each completing on full[s]
-//   warp 1     MMA issuer: per stage 4 k-steps of 8 columns, each one
+// Kernel structure (one persistent CTA per SM, 14 warps, tiles of 128 rows):
+//   warp 0     TMA producer: per tile and 64-column stage, two 128×32 FP32
+//              boxes of X (SWIZZLE_128B) and the stage's two Q_V slabs (from
+//              L2; holding all of Q_V would leave room for too few stages)
+//              into a ring of nst stages, each completing on full[s] (32 KB
+//              of X per stage: a CTA turns its ring over at most ~2 M stages
+//              per second, so 16 KB stages would cap a pass near 4.8 TB/s)
+//   warp 1     MMA issuer: per stage 8 k-steps of 8 columns, each one
 //              M=128 N=64 MMA of big(X) (shared memory) against Q_V's big and
 //              small rows and one M=128 N=32 MMA of small(X) (tensor memory)
 //              against Q_V's big rows, into accumulator i mod XU_NACC; its
 //              commits free the stage (empty[s]) and publish the
 //              accumulator (accf[a])
-//   warps 2-9  converters, two groups of four taking alternate stages:
-//              thread = row of the tile (its TMEM lane); reads its row's 32
-//              floats of the stage, writes small(x) into the stage's
+//   warps 2-9  converters (XU_CONV_GROUPS groups of four taking alternate
+//              stages): thread = row of the tile (its TMEM lane); reads its
+//              row's 64 floats of the stage, writes small(x) into the stage's
 //              tensor-memory slot, sums x²
-//   warps 10-17 epilogue, two groups of four taking alternate stages: per
-//              stage, reads the accumulator (freeing it through acce[a]) and
-//              adds it to the row's FP32 sums; at a tile's end the second
-//              group hands its sums to the first through tensor memory, which
-//              adds them (fixed order) and writes the P' rows
-// Two groups per role give each converter and epilogue thread two stage
-// times for its chain of shared-memory loads, tensor-memory stores or loads
-// and their waits.
+//   warps 10-13 epilogue (XU_EPI_GROUPS groups of four taking alternate
+//              stages): per stage, reads the accumulator (freeing it through
+//              acce[a]) and adds it to the row's FP32 sums; after a tile's
+//              last stage writes the P' rows.  With two groups, the second
+//              hands its sums to the first through tensor memory at a tile's
+//              end, which adds them in a fixed order.
+// More than one group per role gives each thread several stage times for its
+// chain of loads, tensor-memory accesses and waits, at the price of
+// registers (the whole CTA shares 64 K of them).
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -59,35 +64,64 @@
 
 namespace dash {
 
-constexpr int XU_THREADS = 576;
+constexpr int XU_CONV_GROUPS = 2;            // converter groups (alternate stages)
+constexpr int XU_EPI_GROUPS = 1;             // epilogue groups (alternate stages)
+constexpr int XU_CONV_W0 = 2, XU_EPI_W0 = XU_CONV_W0 + 4 * XU_CONV_GROUPS;
+constexpr int XU_THREADS = 32 * (XU_EPI_W0 + 4 * XU_EPI_GROUPS);
 constexpr int XU_SLAB_BYTES = 64 * 128;      // one Q_V slab: 64 rows × 32 floats
-constexpr int XU_STAGE_BYTES = 128 * 128;    // one X box: 128 rows × 32 floats
-constexpr int XU_TMEM_COLS = 512;            // accumulators 0-255, small(X) slots 256-447, hand-over 480
-constexpr int XU_NACC = 4;                   // accumulator ring (64 columns each)
-constexpr int XU_MAX_STAGES = 6;             // small(X) slots: 256 + 6·32 <= 448
-constexpr uint32_t XU_HAND_COL = 480;        // epilogue hand-over columns 480-511
+constexpr int XU_BOX_BYTES = 128 * 128;      // one X box: 128 rows × 32 floats
+constexpr int XU_XBYTES = 2 * XU_BOX_BYTES;  // a stage's X: two boxes, 64 columns
+constexpr int XU_STAGE_BYTES = XU_XBYTES + 2 * XU_SLAB_BYTES;   // plus its two Q_V slabs
+constexpr int XU_TMEM_COLS = 512;            // accumulators 0-255, small(X) slots 256-511
+constexpr int XU_NACC = 2;                   // accumulator ring: 128 columns per stage, one
+                                             // 64-column accumulator per 32-column box
+constexpr int XU_MAX_STAGES = 4;             // small(X) slots of 64 columns: 256 + 4·64 = 512
+constexpr uint32_t XU_HAND_COL = 480;        // epilogue hand-over (two epilogue groups only;
+                                             // then at most 3 stages)
+// A group that takes every G-th stage must always wait on the same ring slots:
+// an mbarrier parity wait cannot tell phase u from phase u − 2, so a group
+// reaching a slot two phases ahead of its barrier would pass at once.  Ring
+// depths are therefore multiples of the group counts.
+static_assert(XU_MAX_STAGES % XU_CONV_GROUPS == 0, "converter groups must divide the stage ring");
+static_assert(XU_NACC % XU_EPI_GROUPS == 0, "epilogue groups must divide the accumulator ring");
+static_assert(XU_EPI_GROUPS == 1 || 256 + XU_MAX_STAGES * 64 <= (int)XU_HAND_COL,
+              "the hand-over columns must not overlap the small(X) slots");
 
-// big(x): the TF32 value the tensor core uses for an FP32 operand x (its
-// 13 low mantissa bits dropped).  small(x) = x − big(x) is exact in FP32.
-__device__ __forceinline__ float tf32_big(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
-
-// Dynamic shared memory of k_xq_umma for J columns and nst stages:
-// alignment slack, the Q_V slabs, the X ring, barriers and scratch.
-__host__ __device__ inline size_t xu_smem(int J, int nst) {
-    const int nslab = (J + 31) / 32;
-    return 1024 + (size_t)nslab * XU_SLAB_BYTES + (size_t)nst * XU_STAGE_BYTES + 512;
+// tf32_trunc(x): the TF32 value the tensor core takes from an FP32 operand x
+// held in memory (its 13 low mantissa bits dropped).  tf32_rn(x): x rounded
+// to the nearest TF32 value (ties away from zero), which the tensor core then
+// reads unchanged.  A split x = big + small with small = tf32_rn(x − big)
+// keeps x to 2^-22 relative (2^-23 when big = tf32_rn(x) too); a truncated
+// small part would keep only 2^-21.
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+__device__ __forceinline__ float tf32_rn(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
 }
-// Largest ring depth that fits the 227 KB per-CTA limit (0: does not fit).
+
+// Q_V slabs of J columns: one per 32 columns, rounded up to whole stages of
+// two slabs (the slab past J is zero).
+__host__ __device__ inline int xu_slabs(int J) { return ((J + 63) / 64) * 2; }
+// Dynamic shared memory of k_xq_umma for nst stages (each its X boxes and the
+// two Q_V slabs they multiply, which come from L2 again for every tile):
+// alignment slack, the ring, barriers and scratch.
+__host__ __device__ inline size_t xu_smem(int J, int nst) {
+    (void)J;
+    return 1024 + (size_t)nst * XU_STAGE_BYTES + 512;
+}
+// Largest ring depth that fits the 227 KB per-CTA limit and is a multiple of
+// the converter groups (0: none fits).
 inline int xu_stages(int J) {
     const size_t cap = 232448;
-    for (int nst = XU_MAX_STAGES; nst >= 3; --nst)
-        if (xu_smem(J, nst) <= cap) return nst;
+    for (int nst = XU_MAX_STAGES; nst >= 2; --nst)
+        if (nst % XU_CONV_GROUPS == 0 && xu_smem(J, nst) <= cap) return nst;
     return 0;
 }
 
-// Q_V (J×R FP32 row-major) into nslab swizzled slabs (see above).
+// Q_V (J×R FP32 row-major) into xu_slabs(J) swizzled slabs (see above).
 static __global__ void k_qv_tf32(const float *__restrict__ QV, int J, int R, float *__restrict__ out) {
-    const int nslab = (J + 31) / 32;
+    const int nslab = xu_slabs(J);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;      // (slab, row, k)
     if (i >= nslab * 64 * 32) return;
     const int sl = i / 2048, n = (i / 32) % 64, kc = i % 32;
@@ -95,10 +129,16 @@ static __global__ void k_qv_tf32(const float *__restrict__ QV, int J, int R, flo
     float v = 0.f;
     if (j < J && r < R) {
         const float q = QV[(int64_t)j * R + r];
-        const float big = tf32_big(q);
-        v = n < 32 ? big : q - big;
+        const float big = tf32_rn(q);
+        v = n < 32 ? big : tf32_rn(q - big);
     }
     reinterpret_cast<float *>(reinterpret_cast<char *>(out) + (size_t)sl * XU_SLAB_BYTES + umma::swz(n, kc))[0] = v;
+}
+
+// Index self-check: record a failed check (count in err[4], the first code
+// in err[5]) so that the host reports it; the caller skips the access.
+__device__ __forceinline__ void tc05_check_failed(int *err, int code) {
+    if (atomicAdd(err + 4, 1) == 0) err[5] = code;
 }
 
 struct XuArgs {
@@ -121,19 +161,19 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
     k_xq_umma(const __grid_constant__ CUtensorMap tmX, XuArgs a) {
     extern __shared__ uint8_t xu_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(xu_raw) + 1023) & ~(uintptr_t)1023);
-    const int nslab = (a.J + 31) / 32, nst = a.nst;
-    uint8_t *sB = sm;
-    uint8_t *sX = sm + (size_t)nslab * XU_SLAB_BYTES;
+    const int nslab = xu_slabs(a.J), nst = a.nst;
+    const int nstg = nslab / 2;                       // stages per tile (64 columns each)
+    uint8_t *sX = sm;                                 // stage s: X boxes, then its Q_V slabs
     uint64_t *full = reinterpret_cast<uint64_t *>(sX + (size_t)nst * XU_STAGE_BYTES);
     uint64_t *conv = full + nst, *empty = conv + nst;
-    uint64_t *accf = empty + nst, *acce = accf + XU_NACC, *bfull = acce + XU_NACC, *done = bfull + 1;
+    uint64_t *accf = empty + nst, *acce = accf + XU_NACC, *done = acce + XU_NACC;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_f = reinterpret_cast<volatile int *>(tslot + 1);
-    double *red = reinterpret_cast<double *>(tslot + 2);      // 8 converter warps
+    double *red = reinterpret_cast<double *>(tslot + 2);      // one per converter warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_tiles = (a.N_gen + 127) / 128;
     const int my_nt = blockIdx.x < n_tiles ? (int)((n_tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
-    const int total = my_nt * nslab;
+    const int total = my_nt * nstg;
     const long long c_start = xu_clk(a.pc);
     long long c_wait = 0;
     if (threadIdx.x == 0) {
@@ -146,7 +186,6 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
             mbar_init(&accf[b], 1);
             mbar_init(&acce[b], 4);
         }
-        mbar_init(bfull, 1);
         mbar_init(done, 1);
         *abort_f = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -159,10 +198,6 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
     if (warp == 0) {
         // ---- TMA producer ----
         if (lane == 0) {
-            mbar_expect_tx(bfull, (uint32_t)nslab * XU_SLAB_BYTES);
-            for (int sl = 0; sl < nslab; ++sl)
-                bulk_g2s(sB + (size_t)sl * XU_SLAB_BYTES, a.qv_slabs + (size_t)sl * (XU_SLAB_BYTES / 4),
-                         XU_SLAB_BYTES, bfull);
             int issued = 0;
             for (int it = 0; it < total; ++it) {
                 const int s = it % nst, u = it / nst;
@@ -170,11 +205,18 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
                 if (u > 0 && !umma::wait_or_abort(&empty[s], (uint32_t)(u - 1) & 1u, abort_f, a.err, a.wait_limit))
                     break;
                 c_wait += xu_clk(a.pc) - w0;
-                const int64_t tile = blockIdx.x + (int64_t)(it / nslab) * gridDim.x;
+                const int64_t tile = blockIdx.x + (int64_t)(it / nstg) * gridDim.x;
+                const int kk = it % nstg;
+                uint8_t *st = sX + (size_t)s * XU_STAGE_BYTES;
                 mbar_expect_tx(&full[s], XU_STAGE_BYTES);
-                if (!(a.skip_first_copy && blockIdx.x == 0 && it == 0))
-                    umma::tma_load_2d(sX + (size_t)s * XU_STAGE_BYTES, &tmX, 32 * (it % nslab),
-                                      (int)(tile * 128), &full[s]);
+                if (tile * 128 >= a.N_gen || 64 * kk >= a.J + 64 || 2 * kk + 1 >= nslab) {
+                    tc05_check_failed(a.err, 101);
+                } else if (!(a.skip_first_copy && blockIdx.x == 0 && it == 0)) {
+                    umma::tma_load_2d(st, &tmX, 64 * kk, (int)(tile * 128), &full[s]);
+                    umma::tma_load_2d(st + XU_BOX_BYTES, &tmX, 64 * kk + 32, (int)(tile * 128), &full[s]);
+                    bulk_g2s(st + XU_XBYTES, a.qv_slabs + (size_t)(2 * kk) * (XU_SLAB_BYTES / 4),
+                             2 * XU_SLAB_BYTES, &full[s]);
+                }
                 ++issued;
             }
             // copies still in flight land before the CTA exits: the last use
@@ -185,21 +227,17 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
                 while (!mbar_try_wait(&full[s], (uint32_t)u & 1u) && clock64() - t0 < a.wait_limit) {
                 }
             }
-            const long long t0 = clock64();
-            while (!mbar_try_wait(bfull, 0) && clock64() - t0 < a.wait_limit) {
-            }
             if (a.pc) atomicAdd(&a.pc[0], (unsigned long long)c_wait);
         }
     } else if (warp == 1) {
         // ---- MMA issuer ----
-        if (lane == 0 && total > 0 && umma::wait_or_abort(bfull, 0, abort_f, a.err, a.wait_limit)) {
-            umma::fence_after();
+        if (lane == 0 && total > 0) {
             constexpr uint32_t id64 = umma::idesc_tf32(128, 64, 0, 0);
             constexpr uint32_t id32 = umma::idesc_tf32(128, 32, 0, 0);
-            const uint32_t sx0 = smem_u32(sX), sb0 = smem_u32(sB);
+            const uint32_t sx0 = smem_u32(sX);
             for (int it = 0; it < total; ++it) {
                 const int s = it % nst, u = it / nst;
-                const int kk = it % nslab;
+                const int kk = it % nstg;
                 const int ab = it % XU_NACC, v = it / XU_NACC;
                 const long long w0 = xu_clk(a.pc);
                 if (v > 0 && !umma::wait_or_abort(&acce[ab], (uint32_t)(v - 1) & 1u, abort_f, a.err, a.wait_limit))
@@ -207,14 +245,19 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
                 if (!umma::wait_or_abort(&conv[s], (uint32_t)u & 1u, abort_f, a.err, a.wait_limit)) break;
                 c_wait += xu_clk(a.pc) - w0;
                 umma::fence_after();
-                const uint32_t dcol = tmem + (uint32_t)ab * 64u;
-                const uint32_t acol = tmem + 256u + (uint32_t)s * 32u;
+                const uint32_t acol = tmem + 256u + (uint32_t)s * 64u;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint64_t ad = umma::sdesc_sw128(sx0 + (uint32_t)s * XU_STAGE_BYTES + 32u * k, 16, 1024);
-                    const uint64_t bd = umma::sdesc_sw128(sb0 + (uint32_t)kk * XU_SLAB_BYTES + 32u * k, 16, 1024);
-                    umma::mma_ss(dcol, ad, bd, id64, k != 0);
-                    umma::mma_ts(dcol + 32u, acol + 8u * k, bd, id32, 1u);
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t dcol = tmem + (uint32_t)ab * 128u + 64u * h;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t st0 = sx0 + (uint32_t)s * XU_STAGE_BYTES;
+                        const uint64_t ad = umma::sdesc_sw128(st0 + (uint32_t)h * XU_BOX_BYTES + 32u * k, 16, 1024);
+                        const uint64_t bd = umma::sdesc_sw128(
+                            st0 + XU_XBYTES + (uint32_t)h * XU_SLAB_BYTES + 32u * k, 16, 1024);
+                        umma::mma_ss(dcol, ad, bd, id64, k != 0);
+                        umma::mma_ts(dcol + 32u, acol + 32u * h + 8u * k, bd, id32, 1u);
+                    }
                 }
                 umma::commit(&empty[s]);
                 umma::commit(&accf[ab]);
@@ -226,32 +269,35 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
             }
             if (a.pc) atomicAdd(&a.pc[1], (unsigned long long)c_wait);
         }
-    } else if (warp < 10) {
-        // ---- converters: group gr takes stages it ≡ gr (mod 2); thread = tile
-        // row r, TMEM lane r ----
-        const int q = warp & 3, gr = (warp - 2) >> 2, r = 32 * q + lane;
+    } else if (warp < XU_EPI_W0) {
+        // ---- converters: group gr takes stages it ≡ gr (mod XU_CONV_GROUPS);
+        // thread = tile row r, TMEM lane r ----
+        const int q = warp & 3, gr = (warp - XU_CONV_W0) >> 2, r = 32 * q + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
         double xn = 0.0;
-        for (int it = gr; it < total; it += 2) {
+        for (int it = gr; it < total; it += XU_CONV_GROUPS) {
             const int s = it % nst, u = it / nst;
             const long long w0 = xu_clk(a.pc);
             const bool ok = umma::wait_or_abort(&full[s], (uint32_t)u & 1u, abort_f, a.err, a.wait_limit);
             if (!__all_sync(0xffffffffu, ok)) break;
             c_wait += xu_clk(a.pc) - w0;
-            const uint8_t *row = sX + (size_t)s * XU_STAGE_BYTES + (size_t)r * 128;
-            uint32_t sv[32];
             float xs = 0.f;
 #pragma unroll
-            for (int c4 = 0; c4 < 8; ++c4) {
-                const float4 x = *reinterpret_cast<const float4 *>(row + ((c4 ^ (r & 7)) << 4));
-                const float xv[4] = {x.x, x.y, x.z, x.w};
+            for (int h = 0; h < 2; ++h) {
+                const uint8_t *row = sX + (size_t)s * XU_STAGE_BYTES + (size_t)h * XU_BOX_BYTES + (size_t)r * 128;
+                uint32_t sv[32];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    xs = fmaf(xv[e], xv[e], xs);
-                    sv[4 * c4 + e] = __float_as_uint(xv[e] - tf32_big(xv[e]));
+                for (int c4 = 0; c4 < 8; ++c4) {
+                    const float4 x = *reinterpret_cast<const float4 *>(row + ((c4 ^ (r & 7)) << 4));
+                    const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        xs = fmaf(xv[e], xv[e], xs);
+                        sv[4 * c4 + e] = __float_as_uint(tf32_rn(xv[e] - tf32_trunc(xv[e])));
+                    }
                 }
+                umma::tmem_st32(lane_base + 256u + (uint32_t)s * 64u + 32u * h, sv);
             }
-            umma::tmem_st32(lane_base + 256u + (uint32_t)s * 32u, sv);
             xn += (double)xs;
             umma::tmem_st_wait();
             umma::fence_before();
@@ -259,22 +305,23 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
             if (lane == 0) umma::mbar_arrive(&conv[s]);
         }
         xn = warp_sum(xn);
-        if (lane == 0) red[warp - 2] = xn;
+        if (lane == 0) red[warp - XU_CONV_W0] = xn;
         if (a.pc && lane == 0) atomicAdd(&a.pc[2], (unsigned long long)c_wait);
     } else {
-        // ---- epilogue: group gr takes stages it ≡ gr (mod 2); thread = tile
-        // row r.  Every thread runs the same hand-over barriers per tile, also
-        // after an abort (then without waiting or touching tensor memory). ----
-        const int q = warp & 3, gr = (warp - 10) >> 2, r = 32 * q + lane;
+        // ---- epilogue: group gr takes stages it ≡ gr (mod XU_EPI_GROUPS);
+        // thread = tile row r.  With two groups every thread runs the same
+        // hand-over barriers per tile, also after an abort (then without
+        // waiting or touching tensor memory). ----
+        const int q = warp & 3, gr = (warp - XU_EPI_W0) >> 2, r = 32 * q + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
         bool dead = false;
         for (int tc = 0; tc < my_nt; ++tc) {
             float acc[32];
 #pragma unroll
             for (int c = 0; c < 32; ++c) acc[c] = 0.f;
-            for (int kk = 0; kk < nslab; ++kk) {
-                const int it = tc * nslab + kk;
-                if ((it & 1) != gr || dead) continue;
+            for (int kk = 0; kk < nstg; ++kk) {
+                const int it = tc * nstg + kk;
+                if ((it % XU_EPI_GROUPS) != gr || dead) continue;
                 const int ab = it % XU_NACC, v = it / XU_NACC;
                 const long long w0 = xu_clk(a.pc);
                 const bool ok = umma::wait_or_abort(&accf[ab], (uint32_t)v & 1u, abort_f, a.err, a.wait_limit);
@@ -284,36 +331,41 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
                 }
                 c_wait += xu_clk(a.pc) - w0;
                 umma::fence_after();
-                uint32_t t[32];
-                umma::tmem_ld32(lane_base + (uint32_t)ab * 64u, t);
-                umma::tmem_ld_wait();
+                // per box: main terms (columns 0-31), then corrections (32-63),
+                // 16 columns at a time
 #pragma unroll
-                for (int c = 0; c < 32; ++c) acc[c] += __uint_as_float(t[c]);
-                umma::tmem_ld32(lane_base + (uint32_t)ab * 64u + 32u, t);
-                umma::tmem_ld_wait();
+                for (int q4 = 0; q4 < 8; ++q4) {
+                    uint32_t t[16];
+                    umma::tmem_ld16(lane_base + (uint32_t)ab * 128u + 16u * q4, t);
+                    umma::tmem_ld_wait();
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) acc[16 * (q4 & 1) + c] += __uint_as_float(t[c]);
+                }
                 umma::fence_before();
                 __syncwarp();
                 if (lane == 0) umma::mbar_arrive(&acce[ab]);
-#pragma unroll
-                for (int c = 0; c < 32; ++c) acc[c] += __uint_as_float(t[c]);
             }
-            // hand-over: group 1's sums to group 0 through tensor memory
-            if (gr == 1 && !dead) {
-                uint32_t t[32];
+            if (XU_EPI_GROUPS == 2) {
+                // hand-over: group 1's sums to group 0 through tensor memory
+                if (gr == 1 && !dead) {
+                    uint32_t t[32];
 #pragma unroll
-                for (int c = 0; c < 32; ++c) t[c] = __float_as_uint(acc[c]);
-                umma::tmem_st32(lane_base + XU_HAND_COL, t);
-                umma::tmem_st_wait();
+                    for (int c = 0; c < 32; ++c) t[c] = __float_as_uint(acc[c]);
+                    umma::tmem_st32(lane_base + XU_HAND_COL, t);
+                    umma::tmem_st_wait();
+                }
+                umma::fence_before();
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                umma::fence_after();
+                if (gr == 0 && !dead) {
+                    uint32_t t[32];
+                    umma::tmem_ld32(lane_base + XU_HAND_COL, t);
+                    umma::tmem_ld_wait();
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) acc[c] += __uint_as_float(t[c]);
+                }
             }
-            umma::fence_before();
-            asm volatile("bar.sync 1, 256;" ::: "memory");
-            umma::fence_after();
             if (gr == 0 && !dead) {
-                uint32_t t[32];
-                umma::tmem_ld32(lane_base + XU_HAND_COL, t);
-                umma::tmem_ld_wait();
-#pragma unroll
-                for (int c = 0; c < 32; ++c) acc[c] += __uint_as_float(t[c]);
                 const int64_t g = (blockIdx.x + (int64_t)tc * gridDim.x) * 128 + r;
                 if (g < a.N_gen) {
                     float *p = a.P + (a.row0 + g) * a.R;
@@ -329,9 +381,11 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
                     }
                 }
             }
-            umma::fence_before();
-            asm volatile("bar.sync 2, 256;" ::: "memory");
-            umma::fence_after();
+            if (XU_EPI_GROUPS == 2) {
+                umma::fence_before();
+                asm volatile("bar.sync 2, 256;" ::: "memory");
+                umma::fence_after();
+            }
         }
         if (a.pc && lane == 0) atomicAdd(&a.pc[3], (unsigned long long)c_wait);
     }
@@ -339,7 +393,7 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
     __syncthreads();
     if (threadIdx.x == 0) {
         double sum = 0.0;
-        for (int q = 0; q < 8; ++q) sum += red[q];
+        for (int q = 0; q < 4 * XU_CONV_GROUPS; ++q) sum += red[q];
         a.xn_part[blockIdx.x] = sum;
         if (a.pc) atomicAdd(&a.pc[4], (unsigned long long)(clock64() - c_start));
     }
@@ -363,12 +417,14 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
 // register sums (main + correction added in FP32, rounded to nearest): the
 // same split of the sum as the X·Q_V pass.
 constexpr int FB_THREADS = 320;
-constexpr int FB_XSTAGE = 32 * 128 * 4;        // 32 rows × 128 columns of X
+constexpr int FB_ROWS = 64;                    // rows per stage
+constexpr int FB_XSTAGE = FB_ROWS * 128 * 4;   // 64 rows × 128 columns of X
 constexpr int FB_UBLK = 64 * 128;              // Ũ block: 64 rank rows × 32 rows
-constexpr int FB_STAGE = FB_XSTAGE + FB_UBLK;
-constexpr int FB_NST = 4;
-constexpr int FB_NACC = 4;
-constexpr int FB_TMEM_COLS = 512;              // accumulators 0-255, A slots from 256 (64 each)
+constexpr int FB_STAGE = FB_XSTAGE + 2 * FB_UBLK;
+constexpr int FB_NST = 3;
+constexpr int FB_NACC = 2;
+constexpr int FB_FLUSH = 16;                   // stages summed in registers before the outer sum
+constexpr int FB_TMEM_COLS = 512;              // accumulators 0-127, A slots from 128 (128 each)
 
 __host__ __device__ inline size_t fb_smem() { return 1024 + (size_t)FB_NST * FB_STAGE + 512; }
 
@@ -376,11 +432,17 @@ __host__ __device__ inline size_t fb_smem() { return 1024 + (size_t)FB_NST * FB_
 // new weights) for general rows g, split into big + small and written per
 // 32-row block G at Ub + G·FB_UBLK: rank row r (big) and 32 + r (small), K
 // position g mod 32, 128-byte swizzled.  Rows past N_gen and ranks past R
-// are zero.  One CTA of 256 threads per block.
+// are zero (the F pass reads whole stages of two blocks: launch an even
+// number of blocks).  One CTA of 256 threads per block.
 static __global__ void __launch_bounds__(256) k_utilde_tf32(BatchDev b, int R, const float *__restrict__ U,
-                                                           const float *__restrict__ Wf, float *__restrict__ Ub) {
+                                                           const float *__restrict__ Wf, float *__restrict__ Ub,
+                                                           int64_t n_blocks, int *err) {
     __shared__ float t[32][33];
     const int64_t G = blockIdx.x;
+    if (G >= n_blocks) {                        // index self-check (the whole block)
+        if (threadIdx.x == 0) tc05_check_failed(err, 201);
+        return;
+    }
     const int64_t run0 = run0_of(b);
     for (int e = threadIdx.x; e < 32 * 32; e += 256) {
         const int i = e / 32, r = e % 32;           // row in block, rank column
@@ -398,17 +460,19 @@ static __global__ void __launch_bounds__(256) k_utilde_tf32(BatchDev b, int R, c
     for (int e = threadIdx.x; e < 64 * 32; e += 256) {
         const int n = e / 32, i = e % 32;           // rank row of the block, row in block
         const float u = t[i][n & 31];
-        const float big = tf32_big(u);
-        *reinterpret_cast<float *>(blk + umma::swz(n, i)) = n < 32 ? big : u - big;
+        const float big = tf32_rn(u);
+        *reinterpret_cast<float *>(blk + umma::swz(n, i)) = n < 32 ? big : tf32_rn(u - big);
     }
 }
 
 struct FbArgs {
     const float *Ub;         // k_utilde_tf32 blocks
+    int64_t n_ub_blocks;     // blocks written by k_utilde_tf32 for this pass
+    int64_t n_part;          // partial slots available in Fpart
     float *Fpart;            // per row chunk: J×R FP32 partial
     int *err;
     int64_t N_gen;
-    int64_t rows_per_cta;    // a multiple of 32
+    int64_t rows_per_cta;    // a multiple of FB_ROWS
     int J, R;
     long long wait_limit;
 };
@@ -429,7 +493,7 @@ static __global__ void __launch_bounds__(FB_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t g0 = (int64_t)blockIdx.x * a.rows_per_cta;
     const int64_t g1 = min(a.N_gen, g0 + a.rows_per_cta);
-    const int nstage = g1 > g0 ? (int)((g1 - g0 + 31) / 32) : 0;
+    const int nstage = g1 > g0 ? (int)((g1 - g0 + FB_ROWS - 1) / FB_ROWS) : 0;
     const int j0 = 128 * blockIdx.y;
     if (threadIdx.x == 0) {
         for (int s = 0; s < FB_NST; ++s) {
@@ -459,9 +523,14 @@ static __global__ void __launch_bounds__(FB_THREADS, 1)
                 if (u > 0 && !umma::wait_or_abort(&empty[s], (uint32_t)(u - 1) & 1u, abort_f, a.err, a.wait_limit))
                     break;
                 uint8_t *st = sm + (size_t)s * FB_STAGE;
+                const int64_t blk = g0 / 32 + 2 * i;
+                if (blk + 1 >= a.n_ub_blocks || g0 + FB_ROWS * i >= a.N_gen || j0 >= a.J) {
+                    tc05_check_failed(a.err, 301);   // stage skipped: its waits run out
+                    break;
+                }
                 mbar_expect_tx(&full[s], FB_STAGE);
-                umma::tma_load_2d(st, &tmX, j0, (int)(g0 + 32 * i), &full[s]);
-                bulk_g2s(st + FB_XSTAGE, a.Ub + (size_t)(g0 / 32 + i) * (FB_UBLK / 4), FB_UBLK, &full[s]);
+                umma::tma_load_2d(st, &tmX, j0, (int)(g0 + FB_ROWS * i), &full[s]);
+                bulk_g2s(st + FB_XSTAGE, a.Ub + (size_t)blk * (FB_UBLK / 4), 2 * FB_UBLK, &full[s]);
                 ++issued;
             }
             for (int i = issued - 1; i >= 0 && i >= issued - FB_NST; --i) {
@@ -484,13 +553,13 @@ static __global__ void __launch_bounds__(FB_THREADS, 1)
                 if (!umma::wait_or_abort(&conv[s], (uint32_t)u & 1u, abort_f, a.err, a.wait_limit)) break;
                 umma::fence_after();
                 const uint32_t dcol = tmem + (uint32_t)ab * 64u;
-                const uint32_t abig = tmem + 256u + (uint32_t)s * 64u;
+                const uint32_t abig = tmem + 128u + (uint32_t)s * 128u;
                 const uint32_t ub = s0 + (uint32_t)s * FB_STAGE + FB_XSTAGE;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint64_t bd = umma::sdesc_sw128(ub + 32u * k, 16, 1024);
+                for (int k = 0; k < 8; ++k) {
+                    const uint64_t bd = umma::sdesc_sw128(ub + (uint32_t)(k >> 2) * FB_UBLK + 32u * (k & 3), 16, 1024);
                     umma::mma_ts(dcol, abig + 8u * k, bd, id64, k != 0);
-                    umma::mma_ts(dcol + 32u, abig + 32u + 8u * k, bd, id32, 1u);
+                    umma::mma_ts(dcol + 32u, abig + 64u + 8u * k, bd, id32, 1u);
                 }
                 umma::commit(&empty[s]);
                 umma::commit(&accf[ab]);
@@ -509,16 +578,19 @@ static __global__ void __launch_bounds__(FB_THREADS, 1)
             const bool ok = umma::wait_or_abort(&full[s], (uint32_t)u & 1u, abort_f, a.err, a.wait_limit);
             if (!__all_sync(0xffffffffu, ok)) break;
             const float *xs = reinterpret_cast<const float *>(sm + (size_t)s * FB_STAGE) + jl;
-            uint32_t bg[32], sl[32];
 #pragma unroll
-            for (int r = 0; r < 32; ++r) {
-                const float x = xs[r * 128];
-                const float big = tf32_big(x);
-                bg[r] = __float_as_uint(big);
-                sl[r] = __float_as_uint(x - big);
+            for (int h = 0; h < 2; ++h) {
+                uint32_t bg[32], sl[32];
+#pragma unroll
+                for (int r = 0; r < 32; ++r) {
+                    const float x = xs[(32 * h + r) * 128];
+                    const float big = tf32_rn(x);
+                    bg[r] = __float_as_uint(big);
+                    sl[r] = __float_as_uint(tf32_rn(x - big));
+                }
+                umma::tmem_st32(lane_base + 128u + (uint32_t)s * 128u + 32u * h, bg);
+                umma::tmem_st32(lane_base + 128u + (uint32_t)s * 128u + 64u + 32u * h, sl);
             }
-            umma::tmem_st32(lane_base + 256u + (uint32_t)s * 64u, bg);
-            umma::tmem_st32(lane_base + 256u + (uint32_t)s * 64u + 32u, sl);
             umma::tmem_st_wait();
             umma::fence_before();
             __syncwarp();
@@ -528,9 +600,11 @@ static __global__ void __launch_bounds__(FB_THREADS, 1)
         // ---- epilogue: thread = column jl ----
         const int q = warp & 3, jl = 32 * q + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
-        float acc[32];
+        // two-level FP32 sum: FB_FLUSH stages in acc, then into tot, so that
+        // no running sum takes more than a few dozen terms
+        float acc[32], tot[32];
 #pragma unroll
-        for (int r = 0; r < 32; ++r) acc[r] = 0.f;
+        for (int r = 0; r < 32; ++r) acc[r] = tot[r] = 0.f;
         bool ok_all = true;
         for (int i = 0; i < nstage; ++i) {
             const int ab = i % FB_NACC, v = i / FB_NACC;
@@ -549,13 +623,24 @@ static __global__ void __launch_bounds__(FB_THREADS, 1)
             if (lane == 0) umma::mbar_arrive(&acce[ab]);
 #pragma unroll
             for (int r = 0; r < 32; ++r) acc[r] += __uint_as_float(mn[r]) + __uint_as_float(cr[r]);
+            if ((i + 1) % FB_FLUSH == 0) {
+#pragma unroll
+                for (int r = 0; r < 32; ++r) {
+                    tot[r] += acc[r];
+                    acc[r] = 0.f;
+                }
+            }
         }
+#pragma unroll
+        for (int r = 0; r < 32; ++r) tot[r] += acc[r];
         const int j = j0 + jl;
-        if (ok_all && j < a.J) {
+        if (ok_all && j < a.J && blockIdx.x >= a.n_part) {
+            tc05_check_failed(a.err, 302);
+        } else if (ok_all && j < a.J) {
             float *out = a.Fpart + (int64_t)blockIdx.x * a.J * a.R + (int64_t)j * a.R;
 #pragma unroll
             for (int r = 0; r < 32; ++r)
-                if (r < a.R) out[r] = acc[r];
+                if (r < a.R) out[r] = tot[r];
         }
     }
     umma::fence_before();

@@ -125,11 +125,12 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
         LAUNCH(KK_ROWMAP, k_rowmap<<<(N + 255) / 256, 256, 0, st>>>(b));
         if (split && m->xu_nst > 0 && m->row_path != DASH_ROWS_SPLIT_WARP && b.n_runs == 1) {
             const float *X0 = (const float *)X + m->h_run_row0[0] * J;
-            tc05 = x_tensor_map(&tmx, X0, J, Ng, 32, 128, true) && x_tensor_map(&tmxf, X0, J, Ng, 128, 32, false);
+            tc05 = x_tensor_map(&tmx, X0, J, Ng, 32, 128, true) &&
+                   x_tensor_map(&tmxf, X0, J, Ng, 128, FB_ROWS, false);
         }
         if (tc05) {
             // P' = X Q_V on tcgen05 MMAs, X tiles by TMA, Q_V as TF32 slabs
-            const int nslab = (J + 31) / 32;
+            const int nslab = xu_slabs(J);
             LAUNCH(KK_QV_TF32, k_qv_tf32<<<(nslab * 2048 + 255) / 256, 256, 0, st>>>(m->QV, J, R, m->qv_slabs));
             n_xn = (int)std::min<int64_t>(m->n_sm, (Ng + 127) / 128);
             XuArgs xa{m->qv_slabs, (float *)m->P, m->xn_part + g_f, m->d_err, Ng, m->h_run_row0[0],
@@ -228,13 +229,17 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     if (Ng > 0 && tc05) {
         // Ũ = U ∘ w_new as TF32 blocks, then the F partials on tcgen05 MMAs:
         // about one CTA per SM, row chunks × 128-column tiles
-        LAUNCH(KK_UTILDE_TF32, k_utilde_tf32<<<(unsigned)((Ng + 31) / 32), 256, 0, st>>>(b, R, (const float *)m->U,
-                                                                                       m->Wf, m->ub_tf32));
+        const int64_t n_ub = 2 * ((Ng + FB_ROWS - 1) / FB_ROWS);
+        if (n_ub > m->ub_blocks) return fail(m, DASH_ECUDA, "internal: F-pass blocks exceed their buffer");
+        LAUNCH(KK_UTILDE_TF32, k_utilde_tf32<<<(unsigned)n_ub, 256, 0, st>>>(b, R, (const float *)m->U, m->Wf,
+                                                                            m->ub_tf32, m->ub_blocks, m->d_err));
         const int nmt = (J + 127) / 128;
         nfb = std::max(1, m->n_sm / nmt);
-        const int64_t rpc = ((Ng + nfb - 1) / nfb + 31) / 32 * 32;
+        const int64_t rpc = ((Ng + nfb - 1) / nfb + FB_ROWS - 1) / FB_ROWS * FB_ROWS;
         nfb = (int)((Ng + rpc - 1) / rpc);
-        FbArgs fb{m->ub_tf32, (float *)m->Fpart + (size_t)g_f * J * R, m->d_err, Ng, rpc, J, R, m->wait_limit};
+        if (g_f + nfb > m->n_fb_max) return fail(m, DASH_ECUDA, "internal: F partials exceed their buffer");
+        FbArgs fb{m->ub_tf32, n_ub, (int64_t)(m->n_fb_max - g_f), (float *)m->Fpart + (size_t)g_f * J * R, m->d_err,
+                  Ng, rpc, J, R, m->wait_limit};
         CK(cudaFuncSetAttribute(k_f_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem()));
         LAUNCH(KK_F_UMMA, k_f_umma<<<dim3(nfb, nmt), FB_THREADS, fb_smem(), st>>>(tmxf, fb));
         m->prof.ft_warps = (double)nfb * nmt * (FB_THREADS / 32);
@@ -290,7 +295,7 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     LAUNCH(KK_FITNESS, k_fitness<<<1, 32, 0, st>>>(m->xn_part, g_f + n_xn, m->cross_part, (J + 7) / 8, s.Gam, m->Ginc, R,
                                 s.gam_ok, m->fit));
     CK(cudaMemcpyAsync(m->h_fit, m->fit, 4 * 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(m->h_err, m->d_err, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(m->h_err, m->d_err, kErrSlots * sizeof(int), cudaMemcpyDeviceToHost, st));
     return DASH_OK;
 }
 

@@ -130,7 +130,7 @@ static dash_status launch_update_q(dash_model *m, const BatchDev &b, const void 
     }
     LAUNCH(KK_Q_FIT, (k_q_fit<<<1, 32, 0, st>>>(m->qfit, go, m->st.gam_ok, m->fit)));
     CK(cudaMemcpyAsync(m->h_fit, m->fit, 4 * 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(m->h_err, m->d_err, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(m->h_err, m->d_err, kErrSlots * sizeof(int), cudaMemcpyDeviceToHost, st));
     return DASH_OK;
 }
 

@@ -20,9 +20,11 @@
 //
 // In host code the symbol g_noalloc_partials is only a host-side stand-in for
 // the array, not its device address, so the address is looked up with
-// cudaGetSymbolAddress once per device (with that device current) on the first
-// call there and cached.  That first call on each device should therefore be
-// made before any stream capture begins.
+// cudaGetSymbolAddress (with the device current).  A call on a stream that is
+// not being captured looks it up afresh and caches it per device, so a
+// context torn down and created again (cudaDeviceReset) is picked up; a call
+// made while its stream is being captured into a CUDA graph uses the cached
+// address, so the first call on each device must come before any capture.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -43,18 +45,24 @@ constexpr int kMaxDevices = 64;
 std::mutex g_addr_mutex;
 float *g_addr[kMaxDevices] = {};
 
-// Device address of g_noalloc_partials on the current device (looked up once).
-cudaError_t partials_address(float **out) {
+// Device address of g_noalloc_partials on the current device: looked up when
+// `stream` is not being captured (and cached), the cached one during capture.
+cudaError_t partials_address(cudaStream_t stream, float **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_partials);
         if (e != cudaSuccess) return e;
         g_addr[dev] = static_cast<float *>(p);
+    } else if (!g_addr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;   // first call on this device is under capture
     }
     *out = g_addr[dev];
     return cudaSuccess;
@@ -142,12 +150,12 @@ extern "C" dash_status dash_f_increment_noalloc(const float *X, const float *U, 
         return DASH_EINVAL;
     const int64_t JR = (int64_t)J * R;
     if (JR > kNoallocPartialFloats) return DASH_ENOMEM;      // J·R beyond the static array
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     float *partials = nullptr;
-    if (partials_address(&partials) != cudaSuccess) {
+    if (partials_address(st, &partials) != cudaSuccess) {
         cudaGetLastError();
         return DASH_ECUDA;
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     int nb = 0;
     if (N > 0) {
         const int64_t by_size = kNoallocPartialFloats / JR;

@@ -69,6 +69,48 @@ def test_noalloc_f_increment_matches_update():
         m.close()
 
 
+def _f_inc_definition(X, U, seg_row, seg_slice, W):
+    """Σ_k X_k,newᵀ U_k,new S_k (Eq. 20's new term) in FP64, row by row."""
+    F = np.zeros((X.shape[1], U.shape[1]))
+    for s in range(len(seg_slice)):
+        r0, r1 = seg_row[s], seg_row[s + 1]
+        F += X[r0:r1].T @ (U[r0:r1] * W[seg_slice[s]])
+    return F
+
+
+def test_noalloc_large_then_small_call_on_a_side_stream():
+    """A call with every one of the 64 row chunks and J·R = 2^15 (R = 64, the
+    largest rank), then a call with fewer rows, another J and R: each equals
+    the FP64 definition of F_inc (FP32 products: 1e-4), so nothing the first
+    call left in the shared array reaches the second.  Both on a non-default
+    stream."""
+    from paper_2305_18376_gb300 import _native
+    lib = _native.load()
+    rng = np.random.default_rng(5)
+    side = torch.cuda.Stream()
+    for (N, J, R, n_seg) in ((60000, 512, 64, 700), (900, 70, 7, 40)):
+        cuts = np.sort(rng.choice(np.arange(1, N), n_seg - 1, replace=False))
+        seg_row = np.concatenate([[0], cuts, [N]]).astype(np.int64)
+        seg_slice = rng.integers(0, 3 * n_seg, n_seg).astype(np.int32)
+        X = rng.random((N, J)).astype(np.float32)
+        U = (rng.standard_normal((N, R)) * 0.1).astype(np.float32)
+        W = rng.random((3 * n_seg, R)) + 0.5
+        with torch.cuda.stream(side):
+            Xd, Ud = torch.from_numpy(X).cuda(), torch.from_numpy(U).cuda()
+            sr, ss = torch.from_numpy(seg_row).cuda(), torch.from_numpy(seg_slice).cuda()
+            Wd = torch.from_numpy(W).cuda()
+            out = torch.full((J, R), float("nan"), dtype=torch.float64, device="cuda")
+            side.synchronize()
+            stat = lib.dash_f_increment_noalloc(Xd.data_ptr(), Ud.data_ptr(), N, J, R, sr.data_ptr(),
+                                                ss.data_ptr(), n_seg, Wd.data_ptr(), out.data_ptr(),
+                                                C.c_void_p(side.cuda_stream))
+            assert stat == 0
+            side.synchronize()
+        want = _f_inc_definition(X.astype(np.float64), U.astype(np.float64), seg_row, seg_slice, W)
+        err = float(np.max(np.abs(out.cpu().numpy() - want)) / np.max(np.abs(want)))
+        assert err <= 1e-4, (N, J, R, err)
+
+
 def test_noalloc_rejects_sizes_beyond_the_static_array():
     from paper_2305_18376_gb300 import _native
     lib = _native.load()
