@@ -75,6 +75,12 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-k0-max", type=int, default=1000)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serve-profile", action="store_true",
+                    help="per-kernel profile of every serving model (adds events and host work)")
+    ap.add_argument("--serve-precisions", default="f16x3,fp64")
+    ap.add_argument("--serve-init-iters", type=int, default=5,
+                    help="static ALS iterations of each stream's initial fit (untimed); Algorithm 1 "
+                         "does not fix the scale of S_k against V, and a poorly fitted start drifts")
     return ap.parse_args()
 
 
@@ -160,10 +166,8 @@ def algorithmic(kernel: str, plan: dict, N: int, K_all: int, J: int, R: int, tsi
     if kernel == "k_f_tc":               # X read, Ũ fragment blocks (16 rows each) read
         nt = -(-R // 8)
         return cr * J * isize + -(-cr // 16) * (512 * nt + 16), 2 * cr * J * R
-    if kernel == "k_f_umma":             # X read, Ũ TF32 blocks (32 rows, 8 KB each) read
-        return cr * J * isize + -(-cr // 32) * 8192, 2 * cr * J * R
-    if kernel == "k_utilde_tf32":        # U read, Ũ TF32 blocks written
-        return cr * R * 4 + -(-cr // 32) * 8192, cr * R
+    if kernel == "k_f_umma":             # X read, U rows read (Ũ = U ∘ w built in the kernel)
+        return cr * J * isize + cr * R * 4, 2 * cr * J * R
     if kernel == "k_utilde":             # U read, U ∘ w written (rank padded to 8)
         return cr * R * 4 + cr * (-(-R // 8) * 8) * 4, cr * R
     if kernel == "k_xv":
@@ -821,14 +825,14 @@ def run_lambda_sweep(a):
                       "precision": a.precision, "lambda": res}))
 
 
-def _replay_requests(load, s, b0, pool, K0, tdt, Request):
+def _replay_requests(load, s, b0, pool, K0, tdt, Request, init_iters):
     """Stream s's requests: its initial fit, then one update per arrival,
     replaying the pool of planted batches in turn.  Old slices keep their
     ids (the pool's old ids exist by the time a batch is replayed); new
     slices are renumbered to follow the stream's current slice count."""
     import numpy as np
     reqs = [Request(stream=s, arrival=0.0, kind="init", slice_ids=b0.slice_ids.numpy(),
-                    row_ptr=b0.row_ptr.numpy(), X=b0.X, init_iters=1, rows=b0.n_rows)]
+                    row_ptr=b0.row_ptr.numpy(), X=b0.X, init_iters=init_iters, rows=b0.n_rows)]
     K = K0
     i = 0
     for (t_arr, s2, _) in load.arrivals:
@@ -870,13 +874,15 @@ def run_serving(a):
                                   f"{a.serve_rate:g}/s for {a.serve_seconds:g} s, each batch touching a "
                                   "fraction U(0,1] of the slices with U{1..256} rows plus U{0..50} new "
                                   "slices; batches replayed from a pool of 3 per stream, device-resident"}}
-    for prec, tdt, idt in (("f16x3", torch.float32, "f32"), ("fp64", torch.float64, "f64")):
+    precs = [p for p in (("f16x3", torch.float32, "f32"), ("fp64", torch.float64, "f64"))
+             if p[0] in a.serve_precisions.split(",")]
+    for prec, tdt, idt in precs:
         specs, reqs_init, reqs_upd, V0 = {}, [], [], {}
         for s, w in enumerate(load.streams):
             ps = PlantedStream(scaled(w, steps=3), device="cuda", dtype=tdt)
             b0 = ps.batch(0)
             pool = [ps.batch(t) for t in range(1, 4)]
-            reqs, K_end = _replay_requests(load, s, b0, pool, w.K0, tdt, Request)
+            reqs, K_end = _replay_requests(load, s, b0, pool, w.K0, tdt, Request, a.serve_init_iters)
             reqs_init.append(reqs[0])
             reqs_upd.extend(reqs[1:])
             specs[s] = dict(J=w.J, R=w.R, lam=w.lam, precision=prec, input_dtype=idt,
@@ -885,10 +891,23 @@ def run_serving(a):
                             max_segments=max(b.slice_ids.numel() for b in [b0] + pool) + 8)
             V0[s] = np.random.default_rng(s).random((w.J, w.R))
         torch.cuda.synchronize()
-        counters = {}
+        counters, profiles = {}, {}
+
+        def prepare(s, m):
+            m.set_factors(V0[s])
+            if a.serve_profile:
+                m.profile(True)
+
+        def retire(s, m):
+            V, W = m.factors()
+            counters.setdefault(s, (m.counters(), m.K, float(np.abs(W).max()), float(np.abs(V).max())))
+            if a.serve_profile:
+                rep = m.profile_report()
+                top = sorted(rep.items(), key=lambda kv: -kv[1][1])[:6]
+                profiles[s] = {k: round(ms, 3) for k, (n, ms) in top}
+
         loop = ServingLoop(specs, int(a.serve_budget_gb * 1e9), max_inflight=max(2, a.serve_streams),
-                           prepare=lambda s, m: m.set_factors(V0[s]),
-                           on_retire=lambda s, m: counters.setdefault(s, (m.counters(), m.K)))
+                           prepare=prepare, on_retire=retire)
         loop.run(reqs_init, realtime=False)
         torch.cuda.synchronize()
         loop.run(reqs_upd, realtime=True)
@@ -903,13 +922,16 @@ def run_serving(a):
             if not rs:
                 continue
             svc = np.array([r.done - r.admitted for r in rs]) * 1e3
+            iss = np.array([r.issue_s for r in rs]) * 1e3
             lat = np.array([r.latency for r in rs]) * 1e3
-            (timeouts, fallbacks), K_end = counters.get(s, ((None, None), None))
+            (timeouts, fallbacks), K_end, wmax, vmax = counters.get(s, ((None, None), None, None, None))
             per.append({"stream": s, "J": w.J, "R": w.R, "K0": w.K0, "K_end": K_end,
                         "updates": len(rs), "rows": int(sum(r.rows for r in rs)),
                         "service_ms_median": float(np.median(svc)), "service_ms_max": float(svc.max()),
-                        "latency_ms_max": float(lat.max()), "wait_timeouts": timeouts,
-                        "fp64_fallback_solves": fallbacks})
+                        "latency_ms_max": float(lat.max()), "issue_ms_median": float(np.median(iss)),
+                        "issue_ms_max": float(iss.max()), "wait_timeouts": timeouts,
+                        "fp64_fallback_solves": fallbacks, "max_abs_W": wmax, "max_abs_V": vmax,
+                        "profile_ms": profiles.get(s)})
         summ["per_stream"] = per
         out["mixed" if prec == "f16x3" else "fp64"] = summ
         del reqs_init, reqs_upd
@@ -926,6 +948,9 @@ def main():
     elif a.lambda_sweep:
         run_lambda_sweep(a)
     elif a.serving:
+        # load every kernel at context creation, so that no request pays a
+        # kernel's first-use load while others run
+        os.environ.setdefault("CUDA_MODULE_LOADING", "EAGER")
         run_serving(a)
     else:
         run_ours(a)

@@ -321,8 +321,6 @@ static dash_status init_alloc(dash_model *m) {
     DALLOC(m->xq_bexp, 4, "Q_V fragment scale");
     if (m->xu_nst > 0) {
         DALLOC(m->qv_slabs, (size_t)xu_slabs((int)J) * XU_SLAB_BYTES, "Q_V TF32 slabs");
-        m->ub_blocks = Nm / 32 + 2;
-        DALLOC(m->ub_tf32, (size_t)m->ub_blocks * FB_UBLK, "U o w TF32 blocks");
     }
     if (m->fused_ok) {
         DALLOC(m->Ut, (size_t)(Nm / 16 + 2) * ft_ublk((R + 7) / 8) * 4, "U o w fragments");

@@ -24,7 +24,7 @@ enum KernelKind {
     KK_Q_BEGIN, KK_Q_AROWS, KK_Q_Y, KK_Q_LT, KK_Q_H, KK_Q_VPART, KK_Q_V, KK_Q_PW, KK_Q_W,
     KK_Q_OUT, KK_Q_FIT, KK_QLT_QR, KK_QLT_PRE, KK_QLT_PASS, KK_QLT_TAIL,
     KK_XQ_PREP, KK_XQ_TC, KK_F_TC, KK_UTILDE, KK_XQ_WAIT, KK_XQ_BUSY, KK_FT_WAIT, KK_FT_BUSY,
-    KK_QV_TF32, KK_XQ_UMMA, KK_UTILDE_TF32, KK_F_UMMA, KK_FIT_LAMBDA,
+    KK_QV_TF32, KK_XQ_UMMA, KK_F_UMMA, KK_FIT_LAMBDA,
     KK_XU_WAIT_P, KK_XU_WAIT_M, KK_XU_WAIT_C, KK_XU_WAIT_E, KK_XU_CYCLES,
     KK_HOST_PLAN, KK_HOST_WAIT, KK_HOST_LAUNCH, KK_COUNT
 };
@@ -38,7 +38,7 @@ static const char *const kKernelNames[KK_COUNT] = {
     "k_q_begin_new", "k_q_arows", "k_q_y", "k_q_lt", "k_q_h", "k_q_vpart", "k_q_v", "k_q_pw",
     "k_q_w", "k_q_out", "k_q_fit", "k_q_lt.qr", "k_q_lt.fp32_pass", "k_q_lt.passes",
     "k_q_lt.tail", "k_xq_bfrag", "k_xq_tc", "k_f_tc", "k_utilde", "k_xq_tc.wait", "k_xq_tc.loop",
-    "k_f_tc.wait", "k_f_tc.loop", "k_qv_tf32", "k_xq_umma", "k_utilde_tf32", "k_f_umma", "k_fit_lambda",
+    "k_f_tc.wait", "k_f_tc.loop", "k_qv_tf32", "k_xq_umma", "k_f_umma", "k_fit_lambda",
     "k_xq_umma.producer_wait", "k_xq_umma.mma_wait", "k_xq_umma.converter_wait", "k_xq_umma.epilogue_wait",
     "k_xq_umma.cta", "host.plan", "host.wait_previous", "host.launch"};
 
@@ -156,8 +156,6 @@ struct dash_model {
     // depth for this J (0: the shape takes the warp-level kernel)
     float *qv_slabs = nullptr;
     int xu_nst = 0;
-    float *ub_tf32 = nullptr;         // Ũ blocks of the tcgen05 F pass (k_utilde_tf32)
-    int64_t ub_blocks = 0;            // blocks that buffer holds
     long long wait_limit = 2000000000LL;   // cycles before a bounded device wait gives up
     int inject_wait_fault = 0;        // test hook: the next tcgen05 X·Q_V pass skips one copy
     int64_t K_prev = 0;               // slices before the last update (restored if it is dropped)

@@ -169,11 +169,16 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
             // register-resident one-sided Jacobi: FP32 sweeps, E re-orthogonalised
             // to the working type, then sweeps in the working type
             if (!std::is_same<S, float>::value) {
-                warp_eig_os<float, S>(Lw, Ew, nullptr, R, ld, 8, 1e-6f);
+                // stops after the sweep that started below sqrt(1e-6)/2: the
+                // quadratic step takes it to FP32's noise level
+                warp_eig_os<float, S>(Lw, Ew, nullptr, R, ld, 8, 1e-6f, 5e-4f);
                 warp_newton_schulz2<S>(Ew, Gw, Mw, R, ld);
             }
             if (q.phase) { const long long c1 = clock64(); pc[1] += c1 - c0k; c0k = c1; }
-            warp_eig_os<S, S>(Lw, Ew, mu, R, ld, passes, jac_tol);
+            // working-type sweeps; the double-float ones stop after the sweep that
+            // started below sqrt(tol)/2 (quadratic convergence)
+            warp_eig_os<S, S>(Lw, Ew, mu, R, ld, passes, jac_tol,
+                              std::is_same<S, df>::value ? 0.5f * sqrtf(jac_tol) : 0.f);
             if (q.phase) { const long long c1 = clock64(); pc[2] += c1 - c0k; c0k = c1; }
         } else {
             // FP32 pre-pass (float scratch in G and M), then the working-type passes
@@ -250,20 +255,39 @@ constexpr int QZ_RC = 32;     // Q rows staged per pass
 
 template <typename T>
 __host__ __device__ inline size_t q_y_smem(int R) {
-    return ((size_t)QZ_JC * R + (size_t)QZ_RC * R + (size_t)R * (QZ_JC + 1) + (size_t)R * R) * sizeof(T);
+    const size_t RM = R <= 32 ? 32 : 64;
+    return (RM * RM + (size_t)QZ_RC * RM + (size_t)QZ_JC * R + (size_t)R * (QZ_JC + 1)) * sizeof(T);
+}
+
+// n consecutive values from 16-byte aligned shared memory, as 16-byte loads.
+template <int n>
+__device__ __forceinline__ void ld_shared_vec(const float *p, float (&v)[n]) {
+#pragma unroll
+    for (int u = 0; u < n; u += 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p + u);
+        v[u] = t.x; v[u + 1] = t.y; v[u + 2] = t.z; v[u + 3] = t.w;
+    }
+}
+template <int n>
+__device__ __forceinline__ void ld_shared_vec(const double *p, double (&v)[n]) {
+#pragma unroll
+    for (int u = 0; u < n; u += 2) {
+        const double2 t = *reinterpret_cast<const double2 *>(p + u);
+        v[u] = t.x; v[u + 1] = t.y;
+    }
 }
 
 template <typename TI, typename T, int RM>
-__global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI *__restrict__ X,
+__global__ void __launch_bounds__(QZ_THREADS, RM <= 32 ? 2 : 1) k_q_y(BatchDev b, QDev q, const TI *__restrict__ X,
                                                     const T *__restrict__ Qrows, T *__restrict__ Y,
                                                     const T *__restrict__ VT, double *__restrict__ MHpart,
                                                     double *__restrict__ WWpart) {
     extern __shared__ unsigned char qy_raw[];
     const int R = q.R, J = q.J, tid = threadIdx.x;
-    T *Vs = reinterpret_cast<T *>(qy_raw);           // QZ_JC × R
-    T *Qs = Vs + QZ_JC * R;                          // QZ_RC × R
-    T *Ys = Qs + QZ_RC * R;                          // R × (QZ_JC + 1)
-    T *Cs = Ys + R * (QZ_JC + 1);                    // R × R   λ C_k
+    T *Cs = reinterpret_cast<T *>(qy_raw);           // RM × RM  λ C_k (permuted, below)
+    T *Qs = Cs + RM * RM;                            // QZ_RC × RM  Q rows (permuted)
+    T *Vs = Qs + QZ_RC * RM;                         // QZ_JC × R
+    T *Ys = Vs + QZ_JC * R;                          // R × (QZ_JC + 1)
     const int jj = tid % QZ_JC, rg = tid / QZ_JC;
     const int nq = (R + 3) / 4;
     constexpr int NQ = RM / 4;                        // rows of Y per thread
@@ -275,8 +299,14 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI
         const int t = b.tslot[k];
         T *Yk = Y + (int64_t)k * R * J;
         __syncthreads();
-        for (int e = tid; e < R * R; e += QZ_THREADS)
-            Cs[e] = q.lam == 0.0 ? T(0) : (T)(q.lam * q.C[(int64_t)k * R * R + e]);
+        // λC_k permuted so that a thread's NQ rows r = rg + 4u of column p are
+        // contiguous: Cs[(p·4 + rg)·NQ + u] = λC_k[rg + 4u][p] (zero past R)
+        for (int e = tid; e < RM * RM; e += QZ_THREADS) {
+            const int p = e / RM, rg2 = (e % RM) / NQ, u = e % NQ;
+            const int r = rg2 + 4 * u;
+            Cs[e] = (q.lam == 0.0 || r >= R || p >= R) ? T(0)
+                                                        : (T)(q.lam * q.C[(int64_t)k * R * R + r * R + p]);
+        }
         double yv[NP];
 #pragma unroll
         for (int u = 0; u < NP; ++u) yv[u] = 0.0;
@@ -295,12 +325,13 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI
             __syncthreads();
             T acc[NQ];
 #pragma unroll
-            for (int u = 0; u < NQ; ++u) {
-                const int r = rg + 4 * u;
-                T a = T(0);
-                if (u < nq && r < R)
-                    for (int p = 0; p < R; ++p) a += Cs[r * R + p] * Ys[p * (QZ_JC + 1) + jj];
-                acc[u] = a;
+            for (int u = 0; u < NQ; ++u) acc[u] = T(0);
+            for (int p = 0; p < R; ++p) {
+                const T y = Ys[p * (QZ_JC + 1) + jj];
+                T cv[NQ];
+                ld_shared_vec(Cs + (p * 4 + rg) * NQ, cv);   // warp-uniform: broadcasts
+#pragma unroll
+                for (int u = 0; u < NQ; ++u) acc[u] += cv[u] * y;
             }
             if (t >= 0) {
                 for (int si = b.tseg_ptr[t]; si < b.tseg_ptr[t + 1]; ++si) {
@@ -309,16 +340,20 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_y(BatchDev b, QDev q, const TI
                     for (int64_t c0 = r0; c0 < r1; c0 += QZ_RC) {
                         const int nr = (int)(r1 - c0 < QZ_RC ? r1 - c0 : QZ_RC);
                         __syncthreads();
-                        for (int e = tid; e < nr * R; e += QZ_THREADS) Qs[e] = Qrows[c0 * R + e];
+                        // the same permutation: Qs[(i·4 + rg)·NQ + u] = Q(c0 + i, rg + 4u)
+                        for (int e = tid; e < nr * RM; e += QZ_THREADS) {
+                            const int i = e / RM, rg2 = (e % RM) / NQ, u = e % NQ;
+                            const int r = rg2 + 4 * u;
+                            Qs[e] = r < R ? Qrows[(c0 + i) * R + r] : T(0);
+                        }
                         __syncthreads();
                         if (j < J) {
                             for (int i = 0; i < nr; ++i) {
                                 const T x = (T)X[(c0 + i) * J + j];
+                                T qv[NQ];
+                                ld_shared_vec(Qs + (i * 4 + rg) * NQ, qv);
 #pragma unroll
-                                for (int u = 0; u < NQ; ++u) {
-                                    const int r = rg + 4 * u;
-                                    if (u < nq && r < R) acc[u] += Qs[i * R + r] * x;
-                                }
+                                for (int u = 0; u < NQ; ++u) acc[u] += qv[u] * x;
                             }
                         }
                     }

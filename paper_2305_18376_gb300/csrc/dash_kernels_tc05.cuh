@@ -7,11 +7,10 @@
 //              columns, rows 32-63 the small parts; zero past J or R)
 //   k_xq_umma  P' = X·Q_V for every general row, the ‖X‖² partials and each
 //              row's max-|x| exponent
-//   k_utilde_tf32  Ũ = U ∘ w_k,new (the U_k,new S_k,new of Eq. 20) split
-//              into TF32 big + small parts, per 32-row block in the
-//              swizzled K-major layout of the F pass's B operand
 //   k_f_umma   per-chunk partials of F_inc = Σ_rows X(i,:)ᵀ Ũ(i,:) (P5,
-//              Eq. 20) on tcgen05 MMAs, A = Xᵀ from tensor memory
+//              Eq. 20) on tcgen05 MMAs, A = Xᵀ from tensor memory, B = Ũ =
+//              U ∘ w_k,new (the U_k,new S_k,new of Eq. 20) built per stage in
+//              shared memory from U and the new weights
 //
 // Products.  x = big(x) + small(x) + O(2^-22 x): big(x) the TF32 value the
 // tensor core takes from x's FP32 bits in shared memory (truncation), small(x)
@@ -408,15 +407,16 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
 // the strided index of X, so X enters as A = Xᵀ held in tensor memory (lane =
 // column j of the CTA's 128-column tile, TMEM column = row), written there by
 // converter warps that read each staged row block column by column; B = Ũᵀ
-// (rank columns as MMA N, rows as K) comes from k_utilde_tf32 already split
-// and swizzled.  Per 32-row stage and k-step of 8 rows:
+// (rank columns as MMA N, rows as K) is built in each stage's shared memory
+// by two builder warps from U and w_k,new, split and swizzled.  Per 32-row
+// block and k-step of 8 rows:
 //   D[:, 0:64]  (+)= big(X)ᵀ · [big(Ũ) | small(Ũ)]     (M=128, N=64)
 //   D[:, 32:64]  += small(X)ᵀ · big(Ũ)                   (M=128, N=32)
 // Every stage accumulates into a fresh accumulator of a ring of FB_NACC in
 // tensor memory (4 k-steps each), which the epilogue warps add to FP32
 // register sums (main + correction added in FP32, rounded to nearest): the
 // same split of the sum as the X·Q_V pass.
-constexpr int FB_THREADS = 320;
+constexpr int FB_THREADS = 384;
 constexpr int FB_ROWS = 64;                    // rows per stage
 constexpr int FB_XSTAGE = FB_ROWS * 128 * 4;   // 64 rows × 128 columns of X
 constexpr int FB_UBLK = 64 * 128;              // Ũ block: 64 rank rows × 32 rows
@@ -428,46 +428,10 @@ constexpr int FB_TMEM_COLS = 512;              // accumulators 0-127, A slots fr
 
 __host__ __device__ inline size_t fb_smem() { return 1024 + (size_t)FB_NST * FB_STAGE + 512; }
 
-// Ũ(g, r) = U(row(g), r)·w_k,new(r) (FP32 product with the FP32 copy of the
-// new weights) for general rows g, split into big + small and written per
-// 32-row block G at Ub + G·FB_UBLK: rank row r (big) and 32 + r (small), K
-// position g mod 32, 128-byte swizzled.  Rows past N_gen and ranks past R
-// are zero (the F pass reads whole stages of two blocks: launch an even
-// number of blocks).  One CTA of 256 threads per block.
-static __global__ void __launch_bounds__(256) k_utilde_tf32(BatchDev b, int R, const float *__restrict__ U,
-                                                           const float *__restrict__ Wf, float *__restrict__ Ub,
-                                                           int64_t n_blocks, int *err) {
-    __shared__ float t[32][33];
-    const int64_t G = blockIdx.x;
-    if (G >= n_blocks) {                        // index self-check (the whole block)
-        if (threadIdx.x == 0) tc05_check_failed(err, 201);
-        return;
-    }
-    const int64_t run0 = run0_of(b);
-    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
-        const int i = e / 32, r = e % 32;           // row in block, rank column
-        const int64_t g = 32 * G + i;
-        float v = 0.f;
-        if (g < b.N_gen && r < R) {
-            const int64_t row = gen_row_fast(b, run0, g);
-            const int k = __ldcg(b.row_slice + row);
-            v = __ldcg(U + row * R + r) * __ldcg(Wf + (int64_t)k * R + r);
-        }
-        t[i][r] = v;
-    }
-    __syncthreads();
-    char *blk = reinterpret_cast<char *>(Ub) + (size_t)G * FB_UBLK;
-    for (int e = threadIdx.x; e < 64 * 32; e += 256) {
-        const int n = e / 32, i = e % 32;           // rank row of the block, row in block
-        const float u = t[i][n & 31];
-        const float big = tf32_rn(u);
-        *reinterpret_cast<float *>(blk + umma::swz(n, i)) = n < 32 ? big : tf32_rn(u - big);
-    }
-}
-
 struct FbArgs {
-    const float *Ub;         // k_utilde_tf32 blocks
-    int64_t n_ub_blocks;     // blocks written by k_utilde_tf32 for this pass
+    BatchDev b;              // the batch: general row → batch row → slice
+    const float *U;          // U_k,new rows (batch row order, R per row)
+    const float *Wf;         // FP32 copy of the new weights w_k,new (K×R)
     int64_t n_part;          // partial slots available in Fpart
     float *Fpart;            // per row chunk: J×R FP32 partial
     int *err;
@@ -478,9 +442,18 @@ struct FbArgs {
 };
 
 // CTA (c, t): rows [c·rows_per_cta, ...) of the general rows, columns
-// [128t, 128t + 128).  Warps: 0 producer (TMA box of 32 rows × 128 columns,
-// no swizzle, plus the Ũ block by bulk copy), 1 MMA issuer, 2-5 converters
-// (thread = column j = TMEM lane), 6-9 epilogue (thread = column j).
+// [128t, 128t + 128).  Warps: 0 producer (TMA box of 64 rows × 128 columns,
+// no swizzle), 1 MMA issuer, 2-5 converters (thread = column j = TMEM lane),
+// 6-9 epilogue (thread = column j), 10-11 Ũ builders (warp 10 + h builds the
+// stage's 32-row block h; thread = row).  full[s] completes on the X bytes
+// and the two builders' arrivals.
+//
+// Ũ(g, r) = U(row(g), r)·w_k,new(r), the FP32 product with the FP32 copy of
+// the new weights, split into big = TF32(Ũ) and small = TF32(Ũ − big) and
+// stored per 32-row block at rank row r (big) and 32 + r (small), K position
+// g mod 32, 128-byte swizzled; rows past N_gen and ranks past R are zero.  A
+// builder loads its rows before it waits for the stage to be free, so the
+// loads overlap the wait.
 static __global__ void __launch_bounds__(FB_THREADS, 1)
     k_f_umma(const __grid_constant__ CUtensorMap tmX, FbArgs a) {
     extern __shared__ uint8_t fb_raw[];
@@ -497,7 +470,7 @@ static __global__ void __launch_bounds__(FB_THREADS, 1)
     const int j0 = 128 * blockIdx.y;
     if (threadIdx.x == 0) {
         for (int s = 0; s < FB_NST; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], 3);
             mbar_init(&conv[s], 4);
             mbar_init(&empty[s], 1);
         }
@@ -523,14 +496,12 @@ static __global__ void __launch_bounds__(FB_THREADS, 1)
                 if (u > 0 && !umma::wait_or_abort(&empty[s], (uint32_t)(u - 1) & 1u, abort_f, a.err, a.wait_limit))
                     break;
                 uint8_t *st = sm + (size_t)s * FB_STAGE;
-                const int64_t blk = g0 / 32 + 2 * i;
-                if (blk + 1 >= a.n_ub_blocks || g0 + FB_ROWS * i >= a.N_gen || j0 >= a.J) {
+                if (g0 + FB_ROWS * i >= a.N_gen || j0 >= a.J) {
                     tc05_check_failed(a.err, 301);   // stage skipped: its waits run out
                     break;
                 }
-                mbar_expect_tx(&full[s], FB_STAGE);
+                mbar_expect_tx(&full[s], FB_XSTAGE);
                 umma::tma_load_2d(st, &tmX, j0, (int)(g0 + FB_ROWS * i), &full[s]);
-                bulk_g2s(st + FB_XSTAGE, a.Ub + (size_t)blk * (FB_UBLK / 4), 2 * FB_UBLK, &full[s]);
                 ++issued;
             }
             for (int i = issued - 1; i >= 0 && i >= issued - FB_NST; --i) {
@@ -596,7 +567,7 @@ static __global__ void __launch_bounds__(FB_THREADS, 1)
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&conv[s]);
         }
-    } else {
+    } else if (warp < 10) {
         // ---- epilogue: thread = column jl ----
         const int q = warp & 3, jl = 32 * q + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
@@ -641,6 +612,55 @@ static __global__ void __launch_bounds__(FB_THREADS, 1)
 #pragma unroll
             for (int r = 0; r < 32; ++r)
                 if (r < a.R) out[r] = tot[r];
+        }
+    } else {
+        // ---- Ũ builders: warp 10 + h, thread = row 32h + lane of a stage ----
+        const int h = warp - 10;
+        const int64_t run0 = run0_of(a.b);
+        const bool vec = (a.R & 3) == 0;
+        for (int i = 0; i < nstage; ++i) {
+            const int s = i % FB_NST, u = i / FB_NST;
+            const int64_t g = g0 + (int64_t)FB_ROWS * i + 32 * h + lane;
+            float v[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) v[r] = 0.f;
+            if (g < a.N_gen) {
+                const int64_t row = gen_row_fast(a.b, run0, g);
+                const int k = __ldcg(a.b.row_slice + row);
+                const float *ur = a.U + row * a.R;
+                const float *wr = a.Wf + (int64_t)k * a.R;
+                if (vec) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (4 * q < a.R) {
+                            const float4 x = __ldcg(reinterpret_cast<const float4 *>(ur) + q);
+                            const float4 w = __ldcg(reinterpret_cast<const float4 *>(wr) + q);
+                            v[4 * q] = x.x * w.x;
+                            v[4 * q + 1] = x.y * w.y;
+                            v[4 * q + 2] = x.z * w.z;
+                            v[4 * q + 3] = x.w * w.w;
+                        }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 32; ++r)
+                        if (r < a.R) v[r] = __ldcg(ur + r) * __ldcg(wr + r);
+                }
+            }
+            if (u > 0) {
+                const bool ok = umma::wait_or_abort(&empty[s], (uint32_t)(u - 1) & 1u, abort_f, a.err, a.wait_limit);
+                if (!__all_sync(0xffffffffu, ok)) break;
+            }
+            uint8_t *blk = sm + (size_t)s * FB_STAGE + FB_XSTAGE + (size_t)h * FB_UBLK;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const float big = tf32_rn(v[r]);
+                *reinterpret_cast<float *>(blk + umma::swz(r, lane)) = big;
+                *reinterpret_cast<float *>(blk + umma::swz(32 + r, lane)) = tf32_rn(v[r] - big);
+            }
+            // the MMAs read these stores through the async proxy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&full[s]);
         }
     }
     umma::fence_before();

@@ -227,19 +227,15 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     // F partials of the general rows
     int nfb = 0;
     if (Ng > 0 && tc05) {
-        // Ũ = U ∘ w_new as TF32 blocks, then the F partials on tcgen05 MMAs:
+        // the F partials on tcgen05 MMAs, Ũ = U ∘ w_new built in the kernel:
         // about one CTA per SM, row chunks × 128-column tiles
-        const int64_t n_ub = 2 * ((Ng + FB_ROWS - 1) / FB_ROWS);
-        if (n_ub > m->ub_blocks) return fail(m, DASH_ECUDA, "internal: F-pass blocks exceed their buffer");
-        LAUNCH(KK_UTILDE_TF32, k_utilde_tf32<<<(unsigned)n_ub, 256, 0, st>>>(b, R, (const float *)m->U, m->Wf,
-                                                                            m->ub_tf32, m->ub_blocks, m->d_err));
         const int nmt = (J + 127) / 128;
         nfb = std::max(1, m->n_sm / nmt);
         const int64_t rpc = ((Ng + nfb - 1) / nfb + FB_ROWS - 1) / FB_ROWS * FB_ROWS;
         nfb = (int)((Ng + rpc - 1) / rpc);
         if (g_f + nfb > m->n_fb_max) return fail(m, DASH_ECUDA, "internal: F partials exceed their buffer");
-        FbArgs fb{m->ub_tf32, n_ub, (int64_t)(m->n_fb_max - g_f), (float *)m->Fpart + (size_t)g_f * J * R, m->d_err,
-                  Ng, rpc, J, R, m->wait_limit};
+        FbArgs fb{b, (const float *)m->U, m->Wf, (int64_t)(m->n_fb_max - g_f),
+                  (float *)m->Fpart + (size_t)g_f * J * R, m->d_err, Ng, rpc, J, R, m->wait_limit};
         CK(cudaFuncSetAttribute(k_f_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem()));
         LAUNCH(KK_F_UMMA, k_f_umma<<<dim3(nfb, nmt), FB_THREADS, fb_smem(), st>>>(tmxf, fb));
         m->prof.ft_warps = (double)nfb * nmt * (FB_THREADS / 32);

@@ -46,9 +46,12 @@ static dash_status launch_lt(dash_model *m, const BatchDev &b, const QDev &q, co
     const int nw = q_lt_warps<S>(R);
     const size_t smem = (size_t)nw * q_lt_warp_bytes<S>(R);
     const int grid = std::max(1, std::min((b.K_all + nw - 1) / nw, 4 * m->n_sm));
-    // rotation threshold on |γ|/√(αβ): a few units of the working type's roundoff
+    // rotation threshold on |γ|/√(αβ): FP64 and FP32 a few units of their
+    // roundoff; double-float 1e-10, four orders below what one FP32 rounding
+    // of the mixed path's inputs moves the eigenvectors by on these slices
+    // (its sweeps also stop early once a sweep starts below sqrt(1e-10)/2)
     const float jtol = std::is_same<S, double>::value ? 1e-15f
-                     : std::is_same<S, float>::value ? 3e-7f : 1e-13f;
+                     : std::is_same<S, float>::value ? 3e-7f : 1e-10f;
     CK(cudaFuncSetAttribute(k_q_lt<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     m->prof.q_lt_warps = (double)grid * nw;
     LAUNCH(KK_Q_LT, (k_q_lt<S, T><<<grid, 32 * nw, smem, m->stream>>>(b, q, A, Qrows, mode, 6, jtol)));

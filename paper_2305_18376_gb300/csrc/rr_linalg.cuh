@@ -369,13 +369,17 @@ __device__ void warp_newton_schulz2(S *E, S *Gs, S *Ms, int R, int ld) {
 // The lower lane of the pair computes t (in FP32: the angle need only be
 // close, the pair (c, s) in W is exactly orthogonal) and passes it to its
 // partner, so both apply one rotation.  Sweeps stop when every
-// |γ| <= tol·sqrt(αβ) or after max_sweeps.  On exit the columns of G are
+// |γ| <= tol·sqrt(αβ) or after max_sweeps, or (stop > 0) after a sweep whose
+// largest rotated cosine was <= stop: cyclic Jacobi converges quadratically
+// near the end, so a sweep that starts at cosines δ leaves O(δ²), below tol
+// when stop <= sqrt(tol)/2, and the confirming sweep is skipped.  On exit the columns of G are
 // orthogonal: E (smem, S) holds the eigenvectors and mu[c] = |g_c|² (S)
 // the eigenvalues.  Rotating G itself, never forming LᵀL, keeps the
 // relative accuracy of one-sided Jacobi (Demmel and Veselić 1992).  L (smem,
 // S, upper triangular) is read only.  Returns the sweeps run.
 template <class W, class S>
-__device__ int warp_eig_os(const S *L, S *E, S *mu, int R, int ld, int max_sweeps, float tol) {
+__device__ int warp_eig_os(const S *L, S *E, S *mu, int R, int ld, int max_sweeps, float tol,
+                            float stop = 0.f) {
     using O = RT<W>;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -407,17 +411,25 @@ __device__ int warp_eig_os(const S *L, S *E, S *mu, int R, int ld, int max_sweep
         float off = 0.f;
         for (int m = 1; m < 32; ++m) {
             const int p = lane ^ m;
-            W dot = O::zero(), nn = O::zero();
+            // γ in the working type, in two interleaved chains (ILP); the
+            // norms only steer the angle and the skip tests, which run in
+            // FP32, so they are summed in FP32 from the leading parts
+            W dot0 = O::zero(), dot1 = O::zero();
+            float nnf = 0.f;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const W gp = O::shfl_xor(g[i], m);
-                dot = O::fma(dot, g[i], gp);
-                nn = O::fma(nn, g[i], g[i]);
+            for (int i = 0; i < 32; i += 2) {
+                const W gp0 = O::shfl_xor(g[i], m);
+                const W gp1 = O::shfl_xor(g[i + 1], m);
+                dot0 = O::fma(dot0, g[i], gp0);
+                dot1 = O::fma(dot1, g[i + 1], gp1);
+                nnf = fmaf(O::hi(g[i]), O::hi(g[i]), nnf);
+                nnf = fmaf(O::hi(g[i + 1]), O::hi(g[i + 1]), nnf);
             }
-            const float np = __shfl_xor_sync(full, O::hi(nn), m);
+            const W dot = O::add(dot0, dot1);
+            const float np = __shfl_xor_sync(full, nnf, m);
             const bool lo = lane < p;
             float t = 0.f;
-            const float al = O::hi(nn), be = np;
+            const float al = nnf, be = np;
             if (lo && act && p < R && al > flo && be > flo) {   // this lane is i, the partner j
                 const float ga = O::hi(dot);
                 const float sc = sqrtf(al) * sqrtf(be);
@@ -452,7 +464,10 @@ __device__ int warp_eig_os(const S *L, S *E, S *mu, int R, int ld, int max_sweep
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) off = fmaxf(off, __shfl_xor_sync(full, off, o));
-        if (off == 0.f) break;
+        if (off <= stop) {
+            ++sweep;
+            break;
+        }
     }
     W nn = O::zero();
 #pragma unroll

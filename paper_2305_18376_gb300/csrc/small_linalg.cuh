@@ -78,7 +78,19 @@ __device__ inline void warp_cholesky_solve(const double *L, int n, int ld, doubl
 // eigenvectors (A_in = E diag(A_out) Eᵀ).  Off-diagonal entries of A are
 // destroyed.  Rotations follow the symmetric Schur 2×2 step of Golub and
 // Van Loan (Matrix Computations, §8.5).
-__device__ inline void warp_jacobi_eig(double *A, double *E, int n, int ld, int max_sweeps = 50) {
+//
+// A pair (p, q) is rotated only while |a_pq| > 1e-15·sqrt(|a_pp a_qq|), the
+// relative threshold of Demmel and Veselić ("Jacobi's method is more
+// accurate than QR", SIAM J. Matrix Anal. Appl. 13, 1992), which stops at
+// rounding level; and not when both a_pp and a_qq are below tiny_abs (for a
+// PSD matrix |a_pq| <= sqrt(a_pp a_qq) then, so the pair's eigenvalues stay
+// below 2·tiny_abs: callers pass a quarter of their pseudo-inverse cut, and
+// such a pair is dropped whichever way it is rotated).  The sweeps stop at
+// the first one that rotates nothing.  A threshold below the unit roundoff
+// never stops on a rank-deficient matrix: the rotations keep refilling the
+// zeroed entries at rounding level.
+__device__ inline void warp_jacobi_eig(double *A, double *E, int n, int ld, double tiny_abs = 0.0,
+                                       int max_sweeps = 50) {
     const int lane = threadIdx.x & 31;
     for (int i = lane; i < n * n; i += 32) {
         const int r = i / n, c = i % n;
@@ -95,6 +107,7 @@ __device__ inline void warp_jacobi_eig(double *A, double *E, int n, int ld, int 
         off = warp_sum(off);
         dia = warp_sum(dia);
         if (off <= 1e-32 * dia || off == 0.0) break;
+        int rotated = 0;
         for (int p = 0; p < n - 1; ++p) {
             for (int q = p + 1; q < n; ++q) {
                 __syncwarp();
@@ -102,9 +115,11 @@ __device__ inline void warp_jacobi_eig(double *A, double *E, int n, int ld, int 
                 const double app = A[p * ld + p];
                 const double aqq = A[q * ld + q];
                 if (fabs(apq) <= 1e-300 ||
-                    fabs(apq) <= 1e-18 * sqrt(fabs(app) * fabs(aqq))) {
+                    fabs(apq) <= 1e-15 * sqrt(fabs(app) * fabs(aqq)) ||
+                    (fabs(app) <= tiny_abs && fabs(aqq) <= tiny_abs)) {
                     continue;
                 }
+                ++rotated;
                 const double theta = (aqq - app) / (2.0 * apq);
                 const double t = (theta >= 0.0 ? 1.0 : -1.0) /
                                  (fabs(theta) + sqrt(1.0 + theta * theta));
@@ -132,6 +147,7 @@ __device__ inline void warp_jacobi_eig(double *A, double *E, int n, int ld, int 
             }
         }
         __syncwarp();
+        if (rotated == 0) break;
     }
     __syncwarp();
 }
@@ -204,10 +220,10 @@ __device__ inline void warp_cholesky_inverse(const double *L, int n, int ld, dou
 __device__ inline void warp_psd_pinv(double *A, double *E, double *f, double *out, int n,
                                      int ld, double rtol, int power, bool try_cholesky) {
     const int lane = threadIdx.x & 31;
+    double md = 0.0;
+    for (int i = lane; i < n; i += 32) md = fmax(md, fabs(A[i * ld + i]));
+    md = warp_max(md);
     if (power == 1 && try_cholesky) {
-        double md = 0.0;
-        for (int i = lane; i < n; i += 32) md = fmax(md, fabs(A[i * ld + i]));
-        md = warp_max(md);
         for (int i = lane; i < n * n; i += 32) E[(i / n) * ld + (i % n)] = A[(i / n) * ld + (i % n)];
         __syncwarp();
         if (md > 0.0 && warp_cholesky(E, n, ld, 100.0 * rtol * md)) {
@@ -225,7 +241,8 @@ __device__ inline void warp_psd_pinv(double *A, double *E, double *f, double *ou
             return;
         }
     }
-    warp_jacobi_eig(A, E, n, ld);
+    // both powers drop the eigenvalues <= rtol·max
+    warp_jacobi_eig(A, E, n, ld, 0.25 * rtol * md);
     warp_spectral_weights(A, n, ld, rtol, power, f);
     warp_spectral_apply(E, f, n, ld, out);
 }
@@ -246,7 +263,7 @@ __device__ inline int warp_psd_solve(double *A, double *L, double *E, double *b,
         warp_cholesky_solve(L, n, ld, b);
         return 0;
     }
-    warp_jacobi_eig(A, E, n, ld);
+    warp_jacobi_eig(A, E, n, ld, 0.25 * rtol * md);
     warp_spectral_weights(A, n, ld, rtol, 1, f);
     // x = E diag(f) Eᵀ b, using L's first row as scratch for y = Eᵀ b
     double *y = L;

@@ -47,6 +47,7 @@ class Request:
     rows: int = 0
     admitted: Optional[float] = None
     done: Optional[float] = None
+    issue_s: Optional[float] = None    # host time spent issuing it (append + update calls)
 
     @property
     def latency(self) -> Optional[float]:
@@ -184,6 +185,7 @@ class ServingLoop:
                     continue
                 r.admitted = self.clock() - t0
                 self._issue(self.models[s], r)
+                r.issue_s = self.clock() - t0 - r.admitted
                 inflight[s] = r
                 blocked.add(s)
                 self.events.append((r.admitted, "admit", s))

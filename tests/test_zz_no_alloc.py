@@ -69,26 +69,31 @@ def test_noalloc_f_increment_matches_update():
         m.close()
 
 
-def _f_inc_definition(X, U, seg_row, seg_slice, W):
-    """Σ_k X_k,newᵀ U_k,new S_k (Eq. 20's new term) in FP64, row by row."""
-    F = np.zeros((X.shape[1], U.shape[1]))
+def _oracle_f_inc(X, U, seg_row, seg_slice, W):
+    """Σ_k X_k,newᵀ U_k,new S_k (Eq. 20's new term) from the oracle: the rows
+    grouped by slice and passed to init_helpers_p, whose F is that sum
+    (Eq. 8 has the same form)."""
+    rows = {}
     for s in range(len(seg_slice)):
-        r0, r1 = seg_row[s], seg_row[s + 1]
-        F += X[r0:r1].T @ (U[r0:r1] * W[seg_slice[s]])
-    return F
+        rows.setdefault(int(seg_slice[s]), []).append((seg_row[s], seg_row[s + 1]))
+    ks = sorted(rows)
+    Xk = [np.concatenate([X[a:b] for a, b in rows[k]]) for k in ks]
+    Uk = [np.concatenate([U[a:b] for a, b in rows[k]]) for k in ks]
+    Wk = np.stack([W[k] for k in ks])
+    return O.init_helpers_p(Xk, Uk, Wk, np.zeros((X.shape[1], U.shape[1]))).F
 
 
 def test_noalloc_large_then_small_call_on_a_side_stream():
     """A call with every one of the 64 row chunks and J·R = 2^15 (R = 64, the
     largest rank), then a call with fewer rows, another J and R: each equals
-    the FP64 definition of F_inc (FP32 products: 1e-4), so nothing the first
+    the oracle's F_inc (FP32 products: 1e-4), so nothing the first
     call left in the shared array reaches the second.  Both on a non-default
     stream."""
     from paper_2305_18376_gb300 import _native
     lib = _native.load()
     rng = np.random.default_rng(5)
     side = torch.cuda.Stream()
-    for (N, J, R, n_seg) in ((60000, 512, 64, 700), (900, 70, 7, 40)):
+    for (N, J, R, n_seg) in ((8192, 512, 64, 120), (900, 70, 7, 40)):
         cuts = np.sort(rng.choice(np.arange(1, N), n_seg - 1, replace=False))
         seg_row = np.concatenate([[0], cuts, [N]]).astype(np.int64)
         seg_slice = rng.integers(0, 3 * n_seg, n_seg).astype(np.int32)
@@ -106,7 +111,7 @@ def test_noalloc_large_then_small_call_on_a_side_stream():
                                                 C.c_void_p(side.cuda_stream))
             assert stat == 0
             side.synchronize()
-        want = _f_inc_definition(X.astype(np.float64), U.astype(np.float64), seg_row, seg_slice, W)
+        want = _oracle_f_inc(X.astype(np.float64), U.astype(np.float64), seg_row, seg_slice, W)
         err = float(np.max(np.abs(out.cpu().numpy() - want)) / np.max(np.abs(want)))
         assert err <= 1e-4, (N, J, R, err)
 
