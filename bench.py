@@ -161,8 +161,11 @@ def algorithmic(kernel: str, plan: dict, N: int, K_all: int, J: int, R: int, tsi
     cr, gr = plan.get("chunk_rows", 0), plan.get("general_rows", 0)
     if kernel == "k_rows_fused":         # one read of every tile row, U written
         return tr * J * isize + tr * R * 4 + ts * per_slice, 4 * tr * J * R
-    if kernel in ("k_xq_tc", "k_xq_umma"):   # X read, P' written (chunked-path rows)
-        return cr * J * isize + cr * R * 4, 2 * cr * J * R
+    if kernel in ("k_xq_tc", "k_xq_umma"):   # X read, P' (mode Q: P) written
+        n = cr + gr
+        return n * J * isize + n * R * 4, 2 * n * J * R
+    if kernel == "k_q_arows":            # P and A rows, R values each (W rows from L2)
+        return 2 * N * R * tsize, 2 * N * R * R
     if kernel == "k_f_tc":               # X read, Ũ fragment blocks (16 rows each) read
         nt = -(-R // 8)
         return cr * J * isize + -(-cr // 16) * (512 * nt + 16), 2 * cr * J * R

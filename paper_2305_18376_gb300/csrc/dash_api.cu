@@ -396,7 +396,11 @@ static dash_status init_check(dash_model *m) {
     }
     m->fused_ok = m->df_state && c.input_dtype == DASH_F32 && c.R <= FU_RP &&
                   c.J <= FU_WARPS * FU_JG && (c.J % 4) == 0 && c.mode == DASH_MODE_P;
-    m->xu_nst = (m->fused_ok && c.precision == DASH_PREC_F16X3 && c.R <= 32) ? xu_stages(c.J) : 0;
+    // the tcgen05 X·Q_V pass (mode P) or X·V pass (mode Q): FP32 input, mixed
+    // products, R <= 32, 16-byte rows
+    const bool xu_shape = c.input_dtype == DASH_F32 && c.precision == DASH_PREC_F16X3 && c.R <= 32 &&
+                          (c.J % 4) == 0;
+    m->xu_nst = ((m->fused_ok || c.mode == DASH_MODE_Q) && xu_shape) ? xu_stages(c.J) : 0;
     m->st.J = c.J;
     m->st.R = c.R;
     m->st.lam = c.lambda;

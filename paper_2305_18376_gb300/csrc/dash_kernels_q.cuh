@@ -89,7 +89,33 @@ __global__ void k_q_begin_new(double *W, double *Lraw, double *Eraw, double *Bhr
     Y[(int64_t)k * R * J + e] = T(0);
 }
 
-// Q1: A_new = P S_k Hᵀ, one thread per entry.
+// Q1 for R <= 32: A_new = P S_k Hᵀ, one warp per row (grid-stride).  Lane s
+// forms P(i, s)·w_k(s) in T, and lane r sums those products against H(r, :)
+// (staged in shared memory in T, transposed, padded) through shuffles.
+template <typename T>
+__global__ void __launch_bounds__(256) k_q_arows_w(int64_t N, int R, const int *__restrict__ row_slice,
+                                                   const T *__restrict__ P, const double *__restrict__ W,
+                                                   const double *__restrict__ H, T *__restrict__ A) {
+    __shared__ T Ht[32 * 33];                      // Ht[s·33 + r] = H(r, s)
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+        const int s2 = e / 32, r = e % 32;
+        Ht[s2 * 33 + r] = (r < R && s2 < R) ? (T)H[r * R + s2] : T(0);
+    }
+    __syncthreads();
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int64_t step = (int64_t)gridDim.x * wpb;
+    for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < N; i += step) {
+        const int k = row_slice[i];
+        const T ps = lane < R ? P[i * R + lane] * (T)W[(int64_t)k * R + lane] : T(0);
+        T a = T(0);
+#pragma unroll
+        for (int s2 = 0; s2 < 32; ++s2) a += __shfl_sync(full, ps, s2) * Ht[s2 * 33 + lane];
+        if (lane < R) A[i * R + lane] = a;
+    }
+}
+
+// Q1 for R > 32: A_new = P S_k Hᵀ, one thread per entry.
 template <typename T>
 __global__ void k_q_arows(int64_t N, int R, const int *__restrict__ row_slice,
                           const T *__restrict__ P, const double *__restrict__ W,
@@ -172,7 +198,10 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
                 // stops after the sweep that started below sqrt(1e-6)/2: the
                 // quadratic step takes it to FP32's noise level
                 warp_eig_os<float, S>(Lw, Ew, nullptr, R, ld, 8, 1e-6f, 5e-4f);
-                warp_newton_schulz2<S>(Ew, Gw, Mw, R, ld);
+                // double-float: one step (the FP32 sweeps leave EᵀE − I at a few
+                // 1e-6; one step takes it to about 1e-11, below the sweeps' 1e-10
+                // target); FP64: two
+                warp_newton_schulz<S>(Ew, Gw, Mw, R, ld, std::is_same<S, df>::value ? 1 : 2);
             }
             if (q.phase) { const long long c1 = clock64(); pc[1] += c1 - c0k; c0k = c1; }
             // working-type sweeps; the double-float ones stop after the sweep that

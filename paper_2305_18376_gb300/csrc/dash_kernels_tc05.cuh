@@ -408,7 +408,7 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
 // column j of the CTA's 128-column tile, TMEM column = row), written there by
 // converter warps that read each staged row block column by column; B = Ũᵀ
 // (rank columns as MMA N, rows as K) is built in each stage's shared memory
-// by two builder warps from U and w_k,new, split and swizzled.  Per 32-row
+// by builder warps from U and w_k,new, split and swizzled.  Per 32-row
 // block and k-step of 8 rows:
 //   D[:, 0:64]  (+)= big(X)ᵀ · [big(Ũ) | small(Ũ)]     (M=128, N=64)
 //   D[:, 32:64]  += small(X)ᵀ · big(Ũ)                   (M=128, N=32)
@@ -585,15 +585,20 @@ static __global__ void __launch_bounds__(FB_THREADS, 1)
                 break;
             }
             umma::fence_after();
-            uint32_t mn[32], cr[32];
-            umma::tmem_ld32(lane_base + (uint32_t)ab * 64u, mn);
-            umma::tmem_ld32(lane_base + (uint32_t)ab * 64u + 32u, cr);
-            umma::tmem_ld_wait();
+            // 16 rank columns at a time (main and correction), which keeps the
+            // register count within the 448-thread block's share
+#pragma unroll
+            for (int c0 = 0; c0 < 32; c0 += 16) {
+                uint32_t mn[16], cr[16];
+                umma::tmem_ld16(lane_base + (uint32_t)ab * 64u + (uint32_t)c0, mn);
+                umma::tmem_ld16(lane_base + (uint32_t)ab * 64u + 32u + (uint32_t)c0, cr);
+                umma::tmem_ld_wait();
+#pragma unroll
+                for (int r = 0; r < 16; ++r) acc[c0 + r] += __uint_as_float(mn[r]) + __uint_as_float(cr[r]);
+            }
             umma::fence_before();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&acce[ab]);
-#pragma unroll
-            for (int r = 0; r < 32; ++r) acc[r] += __uint_as_float(mn[r]) + __uint_as_float(cr[r]);
             if ((i + 1) % FB_FLUSH == 0) {
 #pragma unroll
                 for (int r = 0; r < 32; ++r) {
@@ -614,38 +619,59 @@ static __global__ void __launch_bounds__(FB_THREADS, 1)
                 if (r < a.R) out[r] = tot[r];
         }
     } else {
-        // ---- Ũ builders: warp 10 + h, thread = row 32h + lane of a stage ----
+        // ---- Ũ builders: warp 10 + h, thread = row 32h + lane of a stage.
+        // Software-pipelined so that no global load sits on the critical
+        // path: the batch row and slice of stage i + 2 and the U and w_new
+        // rows of stage i + 1 are fetched while stage i is stored. ----
         const int h = warp - 10;
         const int64_t run0 = run0_of(a.b);
         const bool vec = (a.R & 3) == 0;
+        auto locate = [&](int i, int64_t &row, int &k) {
+            const int64_t g = g0 + (int64_t)FB_ROWS * i + 32 * h + lane;
+            row = -1;
+            k = 0;
+            if (i < nstage && g < a.N_gen) {
+                row = gen_row_fast(a.b, run0, g);
+                k = __ldcg(a.b.row_slice + row);
+            }
+        };
+        float x[32], wv[32];
+        auto fetch = [&](int64_t row, int k) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) x[r] = wv[r] = 0.f;
+            if (row < 0) return;
+            const float *ur = a.U + row * a.R;
+            const float *wr = a.Wf + (int64_t)k * a.R;
+            if (vec) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (4 * q < a.R) {
+                        const float4 u4 = __ldcg(reinterpret_cast<const float4 *>(ur) + q);
+                        const float4 w4 = __ldcg(reinterpret_cast<const float4 *>(wr) + q);
+                        x[4 * q] = u4.x; x[4 * q + 1] = u4.y; x[4 * q + 2] = u4.z; x[4 * q + 3] = u4.w;
+                        wv[4 * q] = w4.x; wv[4 * q + 1] = w4.y; wv[4 * q + 2] = w4.z; wv[4 * q + 3] = w4.w;
+                    }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 32; ++r)
+                    if (r < a.R) {
+                        x[r] = __ldcg(ur + r);
+                        wv[r] = __ldcg(wr + r);
+                    }
+            }
+        };
+        int64_t row_a, row_b;
+        int k_a, k_b;
+        locate(0, row_a, k_a);
+        fetch(row_a, k_a);
+        locate(1, row_b, k_b);
         for (int i = 0; i < nstage; ++i) {
             const int s = i % FB_NST, u = i / FB_NST;
-            const int64_t g = g0 + (int64_t)FB_ROWS * i + 32 * h + lane;
             float v[32];
 #pragma unroll
-            for (int r = 0; r < 32; ++r) v[r] = 0.f;
-            if (g < a.N_gen) {
-                const int64_t row = gen_row_fast(a.b, run0, g);
-                const int k = __ldcg(a.b.row_slice + row);
-                const float *ur = a.U + row * a.R;
-                const float *wr = a.Wf + (int64_t)k * a.R;
-                if (vec) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        if (4 * q < a.R) {
-                            const float4 x = __ldcg(reinterpret_cast<const float4 *>(ur) + q);
-                            const float4 w = __ldcg(reinterpret_cast<const float4 *>(wr) + q);
-                            v[4 * q] = x.x * w.x;
-                            v[4 * q + 1] = x.y * w.y;
-                            v[4 * q + 2] = x.z * w.z;
-                            v[4 * q + 3] = x.w * w.w;
-                        }
-                } else {
-#pragma unroll
-                    for (int r = 0; r < 32; ++r)
-                        if (r < a.R) v[r] = __ldcg(ur + r) * __ldcg(wr + r);
-                }
-            }
+            for (int r = 0; r < 32; ++r) v[r] = x[r] * wv[r];
+            fetch(row_b, k_b);                  // stage i + 1
+            locate(i + 2, row_b, k_b);
             if (u > 0) {
                 const bool ok = umma::wait_or_abort(&empty[s], (uint32_t)(u - 1) & 1u, abort_f, a.err, a.wait_limit);
                 if (!__all_sync(0xffffffffu, ok)) break;

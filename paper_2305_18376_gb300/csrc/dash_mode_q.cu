@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "dash_host.cuh"
+#include "dash_tmap.cuh"
 
 namespace dash {
 
@@ -77,11 +78,39 @@ static dash_status launch_update_q(dash_model *m, const BatchDev &b, const void 
     }
     if (N > 0) {
         LAUNCH(KK_ROWMAP, k_rowmap<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(b));
-        const int n_xn = (int)((N + XV_ROWS - 1) / XV_ROWS);
-        LAUNCH(KK_XV, (k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, b, J, R, (const T *)m->VT, (T *)m->P,
-                                                         m->xn_part)));
-        LAUNCH(KK_Q_AROWS, (k_q_arows<T><<<(unsigned)((N * R + 255) / 256), 256, 0, st>>>(
-                               N, R, b.row_slice, (const T *)m->P, m->st.W, m->qH, A)));
+        // P = X V: on tcgen05 MMAs (the mode-P X·Q_V pass with V's TF32 slabs
+        // in place of Q_V's) when the batch's rows form one run from row 0,
+        // else the SIMT kernel
+        bool tc05 = false;
+        if constexpr (std::is_same<T, float>::value && std::is_same<TI, float>::value) {
+            CUtensorMap tmx;
+            if (m->xu_nst > 0 && b.n_runs == 1 && m->h_run_row0[0] == 0 && b.N_gen == N)
+                tc05 = x_tensor_map(&tmx, (const float *)X, J, N, 32, 128, true);
+            if (tc05) {
+                const int nslab = xu_slabs(J);
+                LAUNCH(KK_QV_TF32, k_qv_tf32<<<(nslab * 2048 + 255) / 256, 256, 0, st>>>(
+                                       (const float *)m->VT, J, R, m->qv_slabs));
+                const int n_xn = (int)std::min<int64_t>(m->n_sm, (N + 127) / 128);
+                XuArgs xa{m->qv_slabs, (float *)m->P, m->xn_part, m->d_err, N, 0, J, R, m->xu_nst,
+                          m->wait_limit, 0, nullptr};
+                const size_t smem = xu_smem(J, m->xu_nst);
+                CK(cudaFuncSetAttribute(k_xq_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                LAUNCH(KK_XQ_UMMA, k_xq_umma<<<n_xn, XU_THREADS, smem, st>>>(tmx, xa));
+            }
+        }
+        if (!tc05) {
+            const int n_xn = (int)((N + XV_ROWS - 1) / XV_ROWS);
+            LAUNCH(KK_XV, (k_xv<TI, T><<<n_xn, 256, 0, st>>>(X, b, J, R, (const T *)m->VT, (T *)m->P,
+                                                             m->xn_part)));
+        }
+        if (R <= 32) {
+            const unsigned ga = (unsigned)std::min<int64_t>((N + 7) / 8, (int64_t)m->n_sm * 16);
+            LAUNCH(KK_Q_AROWS, (k_q_arows_w<T><<<ga, 256, 0, st>>>(N, R, b.row_slice, (const T *)m->P,
+                                                                    m->st.W, m->qH, A)));
+        } else {
+            LAUNCH(KK_Q_AROWS, (k_q_arows<T><<<(unsigned)((N * R + 255) / 256), 256, 0, st>>>(
+                                   N, R, b.row_slice, (const T *)m->P, m->st.W, m->qH, A)));
+        }
     }
     dash_status s = launch_lt<S, T>(m, b, q, A, Qrows, 0);
     if (s) return s;

@@ -328,13 +328,14 @@ __device__ void warp_eig_prepass_f32(const S *L, S *E, float *Lf, float *Ef, flo
     }
 }
 
-// Two Newton–Schulz steps E ← E (3I − EᵀE)/2 re-orthogonalise E to the
-// precision of S (each step squares EᵀE − I).  Gs, Ms: R×ld S scratch.
+// Newton–Schulz steps E ← E (3I − EᵀE)/2 re-orthogonalise E (each step
+// squares EᵀE − I: from the few 1e-6 FP32 sweeps leave, one step reaches
+// about 1e-11, two the precision of S).  Gs, Ms: R×ld S scratch.
 template <class S>
-__device__ void warp_newton_schulz2(S *E, S *Gs, S *Ms, int R, int ld) {
+__device__ void warp_newton_schulz(S *E, S *Gs, S *Ms, int R, int ld, int steps) {
     using O = RT<S>;
     const int lane = threadIdx.x & 31;
-    for (int step = 0; step < 2; ++step) {
+    for (int step = 0; step < steps; ++step) {
         for (int b = lane; b < R; b += 32)
             for (int a = 0; a < R; ++a) {
                 S acc = O::zero();
