@@ -401,6 +401,7 @@ static dash_status init_check(dash_model *m) {
     const bool xu_shape = c.input_dtype == DASH_F32 && c.precision == DASH_PREC_F16X3 && c.R <= 32 &&
                           (c.J % 4) == 0;
     m->xu_nst = ((m->fused_ok || c.mode == DASH_MODE_Q) && xu_shape) ? xu_stages(c.J) : 0;
+    m->xr_nst = m->xu_nst > 0 ? xr_stages(c.J) : 0;
     m->st.J = c.J;
     m->st.R = c.R;
     m->st.lam = c.lambda;

@@ -156,6 +156,7 @@ struct dash_model {
     // depth for this J (0: the shape takes the warp-level kernel)
     float *qv_slabs = nullptr;
     int xu_nst = 0;
+    int xr_nst = 0;                   // X ring depth of k_xq_umma_rq (0: Q_V does not fit)
     long long wait_limit = 2000000000LL;   // cycles before a bounded device wait gives up
     int inject_wait_fault = 0;        // test hook: the next tcgen05 X·Q_V pass skips one copy
     int64_t K_prev = 0;               // slices before the last update (restored if it is dropped)

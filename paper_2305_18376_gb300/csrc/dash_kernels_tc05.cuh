@@ -94,9 +94,10 @@ static_assert(XU_EPI_GROUPS == 1 || 256 + XU_MAX_STAGES * 64 <= (int)XU_HAND_COL
 // small part would keep only 2^-21.
 __device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 __device__ __forceinline__ float tf32_rn(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    // round the magnitude at bit 13, half away from zero (the rounding of
+    // cvt.rna.tf32.f32), in two integer operations on the full-rate ALU; a
+    // carry out of the mantissa moves into the exponent, as it should
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // Q_V slabs of J columns: one per 32 columns, rounded up to whole stages of
@@ -393,6 +394,280 @@ static __global__ void __launch_bounds__(XU_THREADS, 1)
     if (threadIdx.x == 0) {
         double sum = 0.0;
         for (int q = 0; q < 4 * XU_CONV_GROUPS; ++q) sum += red[q];
+        a.xn_part[blockIdx.x] = sum;
+        if (a.pc) atomicAdd(&a.pc[4], (unsigned long long)(clock64() - c_start));
+    }
+    if (warp == 0) {
+        umma::fence_after();
+        umma::tmem_free(tmem, XU_TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_xq_umma_rq: the same P' = X·Q_V (and the same MMAs in the same order, so
+// the same bits) with all of Q_V's slabs resident in shared memory, which
+// lets a stage's X be released as soon as the converters have read it.  In
+// k_xq_umma a stage holds its X until the MMAs that read big(X) from shared
+// memory complete, so a ring slot is held for TMA latency + conversion +
+// MMA + commit, and the ring turnover caps the pass near 4.7 TB/s.  Here the
+// converters write both parts, big(X) (the TF32 truncation) and small(X), to
+// one of two tensor-memory A buffers and release the X slot at once; the MMAs
+// read A from tensor memory and B (Q_V) from the resident slabs.  Fits when
+// the slabs and two X stages fit the 227 KB per-CTA limit (J <= 640).
+//
+// One persistent CTA per SM, 10 warps: 0 TMA producer (the Q_V slabs once,
+// then two 128×32 X boxes per stage), 1 MMA issuer, 2-5 converters (thread =
+// tile row r = TMEM lane r; one group takes every stage, so no converter can
+// run ahead of another on a barrier; eight warps, one box each, measured
+// 4 % slower), 6-9 epilogue (as in k_xq_umma).  Tensor memory:
+// accumulators in columns 0-255 (two stages of two 64-column boxes), A
+// buffers in 256-511 (per buffer and box: big in 32 columns, small in the
+// next 32).  Barriers: full[s] (X landed), xfree[s] (X read), afull[b] /
+// afree[b] (A buffer written / its MMAs done), accf / acce as in k_xq_umma.
+constexpr int XR_THREADS = 320;
+constexpr int XR_MAX_STAGES = 6;
+__host__ __device__ inline size_t xr_smem(int J, int nst) {
+    return 1024 + (size_t)xu_slabs(J) * XU_SLAB_BYTES + (size_t)nst * XU_XBYTES + 512;
+}
+// X ring depth of k_xq_umma_rq for J columns (0: the slabs and two stages do
+// not fit).
+inline int xr_stages(int J) {
+    const size_t cap = 232448;
+    for (int nst = XR_MAX_STAGES; nst >= 2; --nst)
+        if (xr_smem(J, nst) <= cap) return nst;
+    return 0;
+}
+
+static __global__ void __launch_bounds__(XR_THREADS, 1)
+    k_xq_umma_rq(const __grid_constant__ CUtensorMap tmX, XuArgs a) {
+    extern __shared__ uint8_t xr_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(xr_raw) + 1023) & ~(uintptr_t)1023);
+    const int nslab = xu_slabs(a.J), nst = a.nst;
+    const int nstg = nslab / 2;                        // stages per tile (64 columns each)
+    uint8_t *sQ = sm;                                  // resident Q_V slabs
+    uint8_t *sX = sQ + (size_t)nslab * XU_SLAB_BYTES;  // X ring: two boxes per stage
+    uint64_t *full = reinterpret_cast<uint64_t *>(sX + (size_t)nst * XU_XBYTES);
+    uint64_t *xfree = full + nst;
+    uint64_t *afull = xfree + nst, *afree = afull + 2;
+    uint64_t *accf = afree + 2, *acce = accf + XU_NACC, *qfull = acce + XU_NACC, *done = qfull + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_f = reinterpret_cast<volatile int *>(tslot + 1);
+    double *red = reinterpret_cast<double *>(tslot + 2);      // one per converter warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n_tiles = (a.N_gen + 127) / 128;
+    const int my_nt = blockIdx.x < n_tiles ? (int)((n_tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    const int total = my_nt * nstg;
+    const long long c_start = xu_clk(a.pc);
+    long long c_wait = 0;
+    if (threadIdx.x == 0) {
+        for (int s2 = 0; s2 < nst; ++s2) {
+            mbar_init(&full[s2], 1);
+            mbar_init(&xfree[s2], 4);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&afull[b], 4);
+            mbar_init(&afree[b], 1);
+        }
+        for (int b = 0; b < XU_NACC; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
+        mbar_init(qfull, 1);
+        mbar_init(done, 1);
+        *abort_f = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, XU_TMEM_COLS);
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    const uint32_t tmem = *tslot;
+    if (warp == 0) {
+        // ---- TMA producer ----
+        if (lane == 0) {
+            int issued = 0;
+            mbar_expect_tx(qfull, (uint32_t)nslab * XU_SLAB_BYTES);
+            for (int q = 0; q < nslab; ++q)
+                bulk_g2s(sQ + (size_t)q * XU_SLAB_BYTES, a.qv_slabs + (size_t)q * (XU_SLAB_BYTES / 4),
+                         XU_SLAB_BYTES, qfull);
+            for (int it = 0; it < total; ++it) {
+                const int s2 = it % nst, u = it / nst;
+                const long long w0 = xu_clk(a.pc);
+                if (u > 0 && !umma::wait_or_abort(&xfree[s2], (uint32_t)(u - 1) & 1u, abort_f, a.err, a.wait_limit))
+                    break;
+                c_wait += xu_clk(a.pc) - w0;
+                const int64_t tile = blockIdx.x + (int64_t)(it / nstg) * gridDim.x;
+                const int kk = it % nstg;
+                uint8_t *st = sX + (size_t)s2 * XU_XBYTES;
+                mbar_expect_tx(&full[s2], XU_XBYTES);
+                if (tile * 128 >= a.N_gen || 64 * kk >= a.J + 64) {
+                    tc05_check_failed(a.err, 111);
+                } else if (!(a.skip_first_copy && blockIdx.x == 0 && it == 0)) {
+                    umma::tma_load_2d(st, &tmX, 64 * kk, (int)(tile * 128), &full[s2]);
+                    umma::tma_load_2d(st + XU_BOX_BYTES, &tmX, 64 * kk + 32, (int)(tile * 128), &full[s2]);
+                }
+                ++issued;
+            }
+            // copies still in flight land before the CTA exits
+            {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(qfull, 0) && clock64() - t0 < a.wait_limit) {
+                }
+            }
+            for (int it = issued - 1; it >= 0 && it >= issued - nst; --it) {
+                const int s2 = it % nst, u = it / nst;
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&full[s2], (uint32_t)u & 1u) && clock64() - t0 < a.wait_limit) {
+                }
+            }
+            if (a.pc) atomicAdd(&a.pc[0], (unsigned long long)c_wait);
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ----
+        if (lane == 0 && total > 0) {
+            constexpr uint32_t id64 = umma::idesc_tf32(128, 64, 0, 0);
+            constexpr uint32_t id32 = umma::idesc_tf32(128, 32, 0, 0);
+            const uint32_t sq0 = smem_u32(sQ);
+            bool ok = umma::wait_or_abort(qfull, 0u, abort_f, a.err, a.wait_limit);
+            for (int it = 0; ok && it < total; ++it) {
+                const int b = it & 1, ub = it >> 1;
+                const int kk = it % nstg;
+                const int ab = it % XU_NACC, v = it / XU_NACC;
+                const long long w0 = xu_clk(a.pc);
+                if (v > 0 && !umma::wait_or_abort(&acce[ab], (uint32_t)(v - 1) & 1u, abort_f, a.err, a.wait_limit))
+                    break;
+                if (!umma::wait_or_abort(&afull[b], (uint32_t)ub & 1u, abort_f, a.err, a.wait_limit)) break;
+                c_wait += xu_clk(a.pc) - w0;
+                umma::fence_after();
+                const uint32_t abuf = tmem + 256u + 128u * (uint32_t)b;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t dcol = tmem + (uint32_t)ab * 128u + 64u * h;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t bd = umma::sdesc_sw128(
+                            sq0 + (uint32_t)(2 * kk + h) * XU_SLAB_BYTES + 32u * k, 16, 1024);
+                        umma::mma_ts(dcol, abuf + 64u * h + 8u * k, bd, id64, k != 0);
+                        umma::mma_ts(dcol + 32u, abuf + 64u * h + 32u + 8u * k, bd, id32, 1u);
+                    }
+                }
+                umma::commit(&afree[b]);
+                umma::commit(&accf[ab]);
+            }
+            // every MMA issued has completed before the tensor memory is freed
+            umma::commit(done);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(done, 0) && clock64() - t0 < a.wait_limit) {
+            }
+            if (a.pc) atomicAdd(&a.pc[1], (unsigned long long)c_wait);
+        }
+    } else if (warp < 6) {
+        // ---- converters: every stage in order; thread = tile row r, TMEM lane r ----
+        const int q = warp & 3, r = 32 * q + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+        double xn = 0.0;
+        for (int it = 0; it < total; ++it) {
+            const int s2 = it % nst, u = it / nst;
+            const int b = it & 1, ub = it >> 1;
+            const long long w0 = xu_clk(a.pc);
+            bool ok = umma::wait_or_abort(&full[s2], (uint32_t)u & 1u, abort_f, a.err, a.wait_limit);
+            if (ok && ub > 0) ok = umma::wait_or_abort(&afree[b], (uint32_t)(ub - 1) & 1u, abort_f, a.err, a.wait_limit);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            c_wait += xu_clk(a.pc) - w0;
+            umma::fence_after();
+            float xs = 0.f;
+            uint32_t bg[2][32], sl[2][32];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint8_t *row = sX + (size_t)s2 * XU_XBYTES + (size_t)h * XU_BOX_BYTES + (size_t)r * 128;
+#pragma unroll
+                for (int c4 = 0; c4 < 8; ++c4) {
+                    const float4 x = *reinterpret_cast<const float4 *>(row + ((c4 ^ (r & 7)) << 4));
+                    const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        xs = fmaf(xv[e], xv[e], xs);
+                        const float big = tf32_trunc(xv[e]);
+                        bg[h][4 * c4 + e] = __float_as_uint(big);
+                        sl[h][4 * c4 + e] = __float_as_uint(tf32_rn(xv[e] - big));
+                    }
+                }
+            }
+            // the stage's X is in registers: its slot can be refilled
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&xfree[s2]);
+            const uint32_t abuf = lane_base + 256u + 128u * (uint32_t)b;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                umma::tmem_st32(abuf + 64u * h, bg[h]);
+                umma::tmem_st32(abuf + 64u * h + 32u, sl[h]);
+            }
+            xn += (double)xs;
+            umma::tmem_st_wait();
+            umma::fence_before();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&afull[b]);
+        }
+        xn = warp_sum(xn);
+        if (lane == 0) red[warp - 2] = xn;
+        if (a.pc && lane == 0) atomicAdd(&a.pc[2], (unsigned long long)c_wait);
+    } else {
+        // ---- epilogue: thread = tile row r ----
+        const int q = warp & 3, r = 32 * q + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+        bool dead = false;
+        for (int tc = 0; tc < my_nt && !dead; ++tc) {
+            float acc[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+            for (int kk = 0; kk < nstg; ++kk) {
+                const int it = tc * nstg + kk;
+                const int ab = it % XU_NACC, v = it / XU_NACC;
+                const long long w0 = xu_clk(a.pc);
+                const bool ok = umma::wait_or_abort(&accf[ab], (uint32_t)v & 1u, abort_f, a.err, a.wait_limit);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    dead = true;
+                    break;
+                }
+                c_wait += xu_clk(a.pc) - w0;
+                umma::fence_after();
+                // per box: main terms (columns 0-31), then corrections (32-63),
+                // 16 columns at a time
+#pragma unroll
+                for (int q4 = 0; q4 < 8; ++q4) {
+                    uint32_t t[16];
+                    umma::tmem_ld16(lane_base + (uint32_t)ab * 128u + 16u * q4, t);
+                    umma::tmem_ld_wait();
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) acc[16 * (q4 & 1) + c] += __uint_as_float(t[c]);
+                }
+                umma::fence_before();
+                __syncwarp();
+                if (lane == 0) umma::mbar_arrive(&acce[ab]);
+            }
+            if (dead) break;
+            const int64_t g = (blockIdx.x + (int64_t)tc * gridDim.x) * 128 + r;
+            if (g < a.N_gen) {
+                float *p = a.P + (a.row0 + g) * a.R;
+                if ((a.R & 3) == 0) {
+#pragma unroll
+                    for (int c = 0; c < 32; c += 4)
+                        if (c < a.R)
+                            *reinterpret_cast<float4 *>(p + c) = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c)
+                        if (c < a.R) p[c] = acc[c];
+                }
+            }
+        }
+        if (a.pc && lane == 0) atomicAdd(&a.pc[3], (unsigned long long)c_wait);
+    }
+    umma::fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int q = 0; q < 4; ++q) sum += red[q];
         a.xn_part[blockIdx.x] = sum;
         if (a.pc) atomicAdd(&a.pc[4], (unsigned long long)(clock64() - c_start));
     }

@@ -102,13 +102,21 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
             LAUNCH(KK_QV_TF32, k_qv_tf32<<<(nslab * 2048 + 255) / 256, 256, 0, st>>>(m->QV, J, R, m->qv_slabs));
             n_xn = (int)std::min<int64_t>(m->n_sm, (Ng + 127) / 128);
             XuArgs xa{m->qv_slabs, (float *)m->P, m->xn_part + g_f, m->d_err, Ng, m->h_run_row0[0],
-                      J, R, m->xu_nst, m->wait_limit, m->inject_wait_fault,
+                      J, R, m->xr_nst > 0 ? m->xr_nst : m->xu_nst, m->wait_limit, m->inject_wait_fault,
                       m->prof.on ? m->prof.d_phase + 15 : nullptr};
             m->inject_wait_fault = 0;
-            const size_t smem = xu_smem(J, m->xu_nst);
-            CK(cudaFuncSetAttribute(k_xq_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            LAUNCH(KK_XQ_UMMA, k_xq_umma<<<n_xn, XU_THREADS, smem, st>>>(tmx, xa));
-            m->prof.xq_warps = (double)n_xn * (XU_THREADS / 32);
+            if (m->xr_nst > 0) {
+                // Q_V resident in shared memory, X released after conversion
+                const size_t smem = xr_smem(J, m->xr_nst);
+                CK(cudaFuncSetAttribute(k_xq_umma_rq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                LAUNCH(KK_XQ_UMMA, k_xq_umma_rq<<<n_xn, XR_THREADS, smem, st>>>(tmx, xa));
+                m->prof.xq_warps = (double)n_xn * (XR_THREADS / 32);
+            } else {
+                const size_t smem = xu_smem(J, m->xu_nst);
+                CK(cudaFuncSetAttribute(k_xq_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                LAUNCH(KK_XQ_UMMA, k_xq_umma<<<n_xn, XU_THREADS, smem, st>>>(tmx, xa));
+                m->prof.xq_warps = (double)n_xn * (XU_THREADS / 32);
+            }
             m->prof.xu_ctas = n_xn;
         } else if (split) {
             // P' = X Q_V on the tensor cores, Q_V pre-split into fragments

@@ -91,11 +91,17 @@ static dash_status launch_update_q(dash_model *m, const BatchDev &b, const void 
                 LAUNCH(KK_QV_TF32, k_qv_tf32<<<(nslab * 2048 + 255) / 256, 256, 0, st>>>(
                                        (const float *)m->VT, J, R, m->qv_slabs));
                 const int n_xn = (int)std::min<int64_t>(m->n_sm, (N + 127) / 128);
-                XuArgs xa{m->qv_slabs, (float *)m->P, m->xn_part, m->d_err, N, 0, J, R, m->xu_nst,
-                          m->wait_limit, 0, nullptr};
-                const size_t smem = xu_smem(J, m->xu_nst);
-                CK(cudaFuncSetAttribute(k_xq_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                LAUNCH(KK_XQ_UMMA, k_xq_umma<<<n_xn, XU_THREADS, smem, st>>>(tmx, xa));
+                XuArgs xa{m->qv_slabs, (float *)m->P, m->xn_part, m->d_err, N, 0, J, R,
+                          m->xr_nst > 0 ? m->xr_nst : m->xu_nst, m->wait_limit, 0, nullptr};
+                if (m->xr_nst > 0) {
+                    const size_t smem = xr_smem(J, m->xr_nst);
+                    CK(cudaFuncSetAttribute(k_xq_umma_rq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                    LAUNCH(KK_XQ_UMMA, k_xq_umma_rq<<<n_xn, XR_THREADS, smem, st>>>(tmx, xa));
+                } else {
+                    const size_t smem = xu_smem(J, m->xu_nst);
+                    CK(cudaFuncSetAttribute(k_xq_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                    LAUNCH(KK_XQ_UMMA, k_xq_umma<<<n_xn, XU_THREADS, smem, st>>>(tmx, xa));
+                }
             }
         }
         if (!tc05) {
