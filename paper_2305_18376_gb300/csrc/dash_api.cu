@@ -90,10 +90,17 @@ static void prof_collect(dash_model *m) {
             // thread per CTA; converters and epilogue: summed over their
             // warps) and each CTA's lifetime, reported per CTA
             for (int i = 0; i < 5; ++i) {
-                const double nw = i == 2 ? 4.0 * XU_CONV_GROUPS : (i == 3 ? 4.0 * XU_EPI_GROUPS : 1.0);
+                const double nw = i == 2 ? m->prof.xu_conv_warps : (i == 3 ? 4.0 * XU_EPI_GROUPS : 1.0);
                 const double per = (m->prof.xu_ctas > 0 ? m->prof.xu_ctas : 1.0) * nw;
                 m->prof.ms[KK_XU_WAIT_P + i] += (double)c[15 + i] / per / m->prof.clock_khz;
                 if (c[15 + i]) m->prof.launches[KK_XU_WAIT_P + i] += 1;
+            }
+            // k_big_c: cycles per phase of the slice finish, summed over its
+            // warps, reported per warp
+            for (int i = 0; i < 6; ++i) {
+                const double per = m->prof.bc_warps > 0 ? m->prof.bc_warps : 1.0;
+                m->prof.ms[KK_BC_DSUM + i] += (double)c[20 + i] / per / m->prof.clock_khz;
+                if (c[20 + i]) m->prof.launches[KK_BC_DSUM + i] += 1;
             }
             cudaMemset(m->prof.d_phase, 0, sizeof c);
         }

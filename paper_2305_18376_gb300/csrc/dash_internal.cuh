@@ -26,6 +26,7 @@ enum KernelKind {
     KK_XQ_PREP, KK_XQ_TC, KK_F_TC, KK_UTILDE, KK_XQ_WAIT, KK_XQ_BUSY, KK_FT_WAIT, KK_FT_BUSY,
     KK_QV_TF32, KK_XQ_UMMA, KK_F_UMMA, KK_FIT_LAMBDA,
     KK_XU_WAIT_P, KK_XU_WAIT_M, KK_XU_WAIT_C, KK_XU_WAIT_E, KK_XU_CYCLES,
+    KK_BC_DSUM, KK_BC_DUPD, KK_BC_CHOL, KK_BC_SOLVE, KK_BC_RESID, KK_BC_GSHARE,
     KK_HOST_PLAN, KK_HOST_WAIT, KK_HOST_LAUNCH, KK_COUNT
 };
 static const char *const kKernelNames[KK_COUNT] = {
@@ -40,7 +41,8 @@ static const char *const kKernelNames[KK_COUNT] = {
     "k_q_lt.tail", "k_xq_bfrag", "k_xq_tc", "k_f_tc", "k_utilde", "k_xq_tc.wait", "k_xq_tc.loop",
     "k_f_tc.wait", "k_f_tc.loop", "k_qv_tf32", "k_xq_umma", "k_f_umma", "k_fit_lambda",
     "k_xq_umma.producer_wait", "k_xq_umma.mma_wait", "k_xq_umma.converter_wait", "k_xq_umma.epilogue_wait",
-    "k_xq_umma.cta", "host.plan", "host.wait_previous", "host.launch"};
+    "k_xq_umma.cta", "k_big_c.dsum", "k_big_c.d_update", "k_big_c.cholesky", "k_big_c.solves",
+    "k_big_c.residual", "k_big_c.g_share", "host.plan", "host.wait_previous", "host.launch"};
 
 struct Profiler {
     bool on = false;
@@ -56,10 +58,12 @@ struct Profiler {
     double q_lt_warps = 0.0;    // warps of the last profiled k_q_lt launch
     double xq_warps = 0.0, ft_warps = 0.0;   // warps of the streaming kernels' last launch
     double xu_ctas = 0.0;                     // CTAs of the last k_xq_umma launch
+    double xu_conv_warps = 8.0;               // its converter warps per CTA
+    double bc_warps = 0.0;                    // warps of the last k_big_c launch
     std::chrono::steady_clock::time_point t_plan0;   // start of the current batch's planning
 };
 
-constexpr int kPhaseSlots = 20;        // in-kernel cycle counters of the profiler
+constexpr int kPhaseSlots = 26;        // in-kernel cycle counters of the profiler
 // device error slots: [0] timed-out waits, [1] FP64 fallback solves,
 // [2] non-finite slice results, [3] this update abandoned, [4] failed index
 // self-checks of the tcgen05 kernels, [5] the first failed check's code

@@ -1258,6 +1258,18 @@ static __device__ __forceinline__ double big_c_fallback(const FusedArgs &a, cons
 // FU_LD).  Called by all 32 lanes of a warp.
 __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &bg, int f,
                                              float *Lw, float *gsm, double *wsp) {
+    // optional phase clock (profiling, lane 0 adds each phase's cycles):
+    // ΔD sums, c/D update, factorisation, triangular solves, refinement
+    // residual, W write and G share
+    unsigned long long *const pc = a.phase_cycles;
+    long long t_ph = pc ? clock64() : 0;
+    auto mark = [&](int i) {
+        if (pc) {
+            const long long t = clock64();
+            if ((threadIdx.x & 31) == 0) atomicAdd(pc + i, (unsigned long long)(t - t_ph));
+            t_ph = t;
+        }
+    };
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int R = a.R;
@@ -1270,20 +1282,31 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
     float2 *D2 = reinterpret_cast<float2 *>(Dk);
     const df lamdf = df_from_double(a.lam);
     const bool keep_old = a.lam != 0.0;
-    // ΔD row `lane` (its column: ΔD is symmetric) and Δc[lane]
-    float dd[FU_RP];
-#pragma unroll
-    for (int q = 0; q < FU_RP; ++q) dd[q] = 0.f;
+    // ΔD column `lane` (= row `lane`: ΔD is symmetric) into the warp's shared
+    // block Lw, eight rows at a time (each entry summed over the chunks in
+    // order), and Δc[lane]; Lw takes the Cholesky factor later
     float dc = 0.f;
-    for (int c = c0; c < c1; ++c) {
-        const float *in = bg.dpart + (size_t)c * cst;
-        if (act) {
+    __syncwarp();
 #pragma unroll
-            for (int q = 0; q < FU_RP; ++q)
-                if (q < R) dd[q] += in[q * R + lane];
-            dc += in[R * R + lane];
-        }
+    for (int q0 = 0; q0 < FU_RP; q0 += 8) {
+        float sd[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sd[u] = 0.f;
+        if (q0 < R)
+            for (int c = c0; c < c1; ++c) {
+                const float *in = bg.dpart + (size_t)c * cst;
+                if (act) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (q0 + u < R) sd[u] += in[(q0 + u) * R + lane];
+                    if (q0 == 0) dc += in[R * R + lane];
+                }
+            }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) Lw[(q0 + u) * FU_LD + lane] = sd[u];
     }
+    __syncwarp();
+    mark(0);
     df cnew = {0.f, 0.f};
     if (act) {
         const df cold = a.c[(int64_t)k * R + lane];
@@ -1306,7 +1329,7 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
             row[r] = 0.f;
             if (r < R && act) {
                 const df dn = df_add(keep_old ? df_mul(lamdf, df{dold[u].x, dold[u].y}) : df{0.f, 0.f},
-                                     df_make(dd[r]));
+                                     df_make(Lw[r * FU_LD + lane]));
                 D2[r * R + lane] = make_float2(dn.hi, dn.lo);
                 const float2 g = __ldg(G2 + r * R + lane);
                 row[r] = df_mul(df{g.x, g.y}, dn).hi;
@@ -1315,6 +1338,7 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
         }
     }
     const float amax = warp_max_f(fabsf(mydiag));
+    mark(1);
     // right-looking Cholesky of A (hi parts), lane l = row l
     const float tol = 1e-6f * amax;
     bool ok = amax > 0.f;
@@ -1333,6 +1357,7 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
             row[q] = fmaf(-lij, lqj, row[q]);
         }
     }
+    mark(2);
     df x = {0.f, 0.f};
     if (ok) {
         __syncwarp();
@@ -1340,6 +1365,7 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
         for (int j = 0; j < FU_RP; ++j) Lw[lane * FU_LD + j] = row[j];
         __syncwarp();
         const float x0 = chol_solve_smem(Lw, myinv, act, cnew.hi);
+        mark(3);
         // one refinement step: res = c − A x0 in double-float, A re-formed
         // from the D_k just written
         df res = cnew;
@@ -1353,9 +1379,11 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
                 res = df_sub(res, df_mul_f(av, xr));
             }
         }
+        mark(4);
         const float dx = chol_solve_smem(Lw, myinv, act, res.hi);
         x = df_add(df_make(x0), df_make(dx));
         ok = __all_sync(full, isfinite(x.hi));
+        mark(3);
     }
     double wnew_d;
     if (ok) {
@@ -1387,6 +1415,7 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
         }
     }
     __syncwarp();
+    mark(5);
 }
 
 // Three CTAs of eight warps per SM (at most 80 registers a thread); each warp

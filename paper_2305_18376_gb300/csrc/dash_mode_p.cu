@@ -111,11 +111,13 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
                 CK(cudaFuncSetAttribute(k_xq_umma_rq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 LAUNCH(KK_XQ_UMMA, k_xq_umma_rq<<<n_xn, XR_THREADS, smem, st>>>(tmx, xa));
                 m->prof.xq_warps = (double)n_xn * (XR_THREADS / 32);
+                m->prof.xu_conv_warps = 4.0;
             } else {
                 const size_t smem = xu_smem(J, m->xu_nst);
                 CK(cudaFuncSetAttribute(k_xq_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 LAUNCH(KK_XQ_UMMA, k_xq_umma<<<n_xn, XU_THREADS, smem, st>>>(tmx, xa));
                 m->prof.xq_warps = (double)n_xn * (XU_THREADS / 32);
+                m->prof.xu_conv_warps = 4.0 * XU_CONV_GROUPS;
             }
             m->prof.xu_ctas = n_xn;
         } else if (split) {
@@ -185,7 +187,10 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
                 // kBigCBlocksPerSM CTAs fit on an SM
                 CK(cudaFuncSetAttribute(k_big_c, cudaFuncAttributePreferredSharedMemoryCarveout,
                                         (int)cudaSharedmemCarveoutMaxShared));
+                fa.phase_cycles = m->prof.on && m->prof.d_phase ? m->prof.d_phase + 20 : nullptr;
                 LAUNCH(KK_BIG_C, k_big_c<<<nsb, 256, 0, st>>>(fa, bg, m->Gpart + (size_t)g_f * R * R));
+                fa.phase_cycles = nullptr;
+                m->prof.bc_warps = (double)nsb * 8;
             }
             finished = true;
         }
