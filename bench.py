@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--serve-profile", action="store_true",
                     help="per-kernel profile of every serving model (adds events and host work)")
     ap.add_argument("--serve-precisions", default="f16x3,fp64")
-    ap.add_argument("--serve-init-iters", type=int, default=5,
+    ap.add_argument("--serve-init-iters", type=int, default=10,
                     help="static ALS iterations of each stream's initial fit (untimed); Algorithm 1 "
                          "does not fix the scale of S_k against V, and a poorly fitted start drifts")
     return ap.parse_args()
@@ -399,9 +399,17 @@ def run_ours(a):
         q_init_s = time.perf_counter() - t1
     del b0
     torch.cuda.empty_cache()
-    for b in batches[: a.warmup]:
+    # the last warm-up update runs with the in-kernel phase clocks (extra
+    # work inside the kernels), so the timed updates carry only the events
+    phase_rep = {}
+    for i, b in enumerate(batches[: a.warmup]):
+        if i == a.warmup - 1 and not a.graph:
+            m.profile(True, phases=True)
         m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X)
     m.sync()
+    if a.warmup > 0 and not a.graph:
+        phase_rep = {k: v for k, v in m.profile_report().items() if "." in k and not k.startswith("host.")}
+        m.profile(False)
     snap = m.get_state_p() if (rank == 0 and not a.no_fp64) else None
     timed = batches[a.warmup:]
     # ---- timed region (device-resident inputs) ----------------------------
@@ -430,6 +438,7 @@ def run_ours(a):
     clocks = sampler.stop()
     launches = m.launch_count() - l0
     timeouts, fallbacks = m.counters()
+    tune = m.autotune_result()
     prof = m.profile_report()
     m.profile(False)
     elapsed = e_start.elapsed_time(e_end) / 1e3
@@ -531,6 +540,8 @@ def run_ours(a):
     K_all = w.K0 + w.new_slices_per_step * (a.warmup + len(timed))
     # the dominant kernel: by time, among launched kernels (not the in-kernel
     # phase counters "kernel.phase" nor the host timers "host.*")
+    prof = {k: v for k, v in prof.items() if "." not in k or k.startswith("host.")}
+    prof.update(phase_rep)           # phase clocks: one (warm-up) update
     launched = {k: v for k, v in prof.items() if "." not in k}
     top = max(launched.items(), key=lambda kv: kv[1][1]) if launched else None
     roof = None
@@ -588,6 +599,7 @@ def run_ours(a):
             "kernels": kernels, "mode_q": mode_q, "cpu_baseline": cpu, "clocks": clocks,
             "init_seconds": init_s, "src_sha": src_hash(),
             "diagnostics": {"wait_timeouts": timeouts, "fp64_fallback_solves": fallbacks},
+            "xq_autotune": tune,
         }
         print(json.dumps(line), flush=True)
         if a.profile_out:
@@ -610,7 +622,7 @@ def measure_mode_q(a, w, mq, batches, stream, K_total, step_rows, max_seg, pk, i
     mq.sync()
     snap = None if a.no_fp64 else mq.get_state_q()
     timed = batches[1:1 + n_t]
-    mq.profile(True)
+    mq.profile(True, phases=True)   # k_q_lt's phase clocks: a few clock reads per slice
     evs = []
     torch.cuda.nvtx.range_push("dash_q_timed")    # ncu --nvtx-include dash_q_timed/
     for b in timed:
@@ -891,7 +903,8 @@ def run_serving(a):
             specs[s] = dict(J=w.J, R=w.R, lam=w.lam, precision=prec, input_dtype=idt,
                             max_slices=K_end + 8,
                             max_rows=max([b0.n_rows] + [b.n_rows for b in pool]) + 16,
-                            max_segments=max(b.slice_ids.numel() for b in [b0] + pool) + 8)
+                            max_segments=max(b.slice_ids.numel() for b in [b0] + pool) + 8,
+                            max_staged_rows=1)          # batches are device-resident: read in place
             V0[s] = np.random.default_rng(s).random((w.J, w.R))
         torch.cuda.synchronize()
         counters, profiles = {}, {}
@@ -911,10 +924,12 @@ def run_serving(a):
 
         loop = ServingLoop(specs, int(a.serve_budget_gb * 1e9), max_inflight=max(2, a.serve_streams),
                            prepare=prepare, on_retire=retire)
-        loop.run(reqs_init, realtime=False)
+        loop.run(reqs_init, realtime=False, final=False)   # fitted models stay for their updates
         torch.cuda.synchronize()
         loop.run(reqs_upd, realtime=True)
         summ = latency_summary(reqs_upd)
+        summ["failed_requests"] = sum(1 for r in reqs_upd if r.failed)
+        summ["failed_streams"] = sorted(loop.failed)
         summ["peak_resident_gb"] = loop.peak_resident / 1e9
         loop.close()
         # per stream: queueing (arrival to admission) against service (admission
@@ -934,6 +949,7 @@ def run_serving(a):
                         "latency_ms_max": float(lat.max()), "issue_ms_median": float(np.median(iss)),
                         "issue_ms_max": float(iss.max()), "wait_timeouts": timeouts,
                         "fp64_fallback_solves": fallbacks, "max_abs_W": wmax, "max_abs_V": vmax,
+                        "failed": loop.failed.get(s),
                         "profile_ms": profiles.get(s)})
         summ["per_stream"] = per
         out["mixed" if prec == "f16x3" else "fp64"] = summ

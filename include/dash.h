@@ -308,6 +308,10 @@ dash_status dash_last_update_ms(const dash_model *m, float *ms);
  * on this model since dash_init.  With profiling on, every launch is
  * bracketed by CUDA events on the model's stream and its device time is
  * accumulated per kernel kind (enabling resets the counters).
+ * dash_profile_enable(): 0 off, 1 the per-launch events, 2 the events plus
+ * in-kernel phase clocks of the streaming and slice-finish kernels (extra
+ * work inside the kernels: for breakdowns, not for timing); DASH_EINVAL
+ * otherwise.
  * dash_profile_get() reads kind i < dash_profile_kinds(): its name, the
  * launches and the total milliseconds since profiling was enabled; it
  * synchronises the stream.  *name points to static storage. */
@@ -381,6 +385,22 @@ dash_status dash_inject_wait_fault(dash_model *m);
  * in-place updates (either pointer may be NULL).  Synchronises the stream. */
 dash_status dash_set_graph(dash_model *m, int32_t on);
 dash_status dash_graph_stats(const dash_model *m, int64_t *instantiations, int64_t *updates);
+
+/* Autotuning of the X·Q_V pass (the paper has no counterpart: a choice
+ * between kernels that compute the same bits).  With it on (the default),
+ * the first mode-P update that runs the tcgen05 X·Q_V pass times every
+ * variant on its own batch (the resident-Q_V kernel at each ring depth from
+ * 2 to the deepest that fits, then the kernel that streams the Q_V slabs
+ * with each stage), keeps the fastest for the rest of the model's life and
+ * synchronises the stream once.  Skipped while graph updates are on (the
+ * first update after they are turned off tunes).  Results are bit-identical whichever variant runs.
+ * dash_autotune_result(): candidates timed (0 before tuning), the index of
+ * the one kept (-1 before), whether the kept kernel is the resident-Q_V one,
+ * its ring depth, and the candidates' times in ms (ms: 8 floats; unused
+ * entries 0).  Any pointer may be NULL.  DASH_EINVAL for a bad switch. */
+dash_status dash_set_autotune(dash_model *m, int32_t on);
+dash_status dash_autotune_result(const dash_model *m, int32_t *n_candidates, int32_t *chosen,
+                                 int32_t *resident, int32_t *ring, float *ms);
 
 /* Measured FP64 FMA rate of the current device (FMAs per second; one FMA is
  * two flops): independent FMA chains on every SM, best of three timed runs

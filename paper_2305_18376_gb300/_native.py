@@ -89,6 +89,9 @@ SIGNATURES = [
     ("dash_set_wait_limit", C.c_int, [P, I64]),
     ("dash_inject_wait_fault", C.c_int, [P]),
     ("dash_graph_stats", C.c_int, [P, PI64, PI64]),
+    ("dash_set_autotune", C.c_int, [P, I32]),
+    ("dash_autotune_result", C.c_int, [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
 ]
 
 
@@ -220,6 +223,17 @@ class DashModel:
         a, b = C.c_int64(), C.c_int64()
         self._ck(self._lib.dash_graph_stats(self._h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def set_autotune(self, on: bool) -> None:
+        self._ck(self._lib.dash_set_autotune(self._h, 1 if on else 0))
+
+    def autotune_result(self) -> dict:
+        """{candidates, chosen, resident, ring, ms} of the X·Q_V autotuning."""
+        n, c, r, g = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        ms = (C.c_float * 8)()
+        self._ck(self._lib.dash_autotune_result(self._h, C.byref(n), C.byref(c), C.byref(r), C.byref(g), ms))
+        return {"candidates": n.value, "chosen": c.value, "resident": bool(r.value), "ring": g.value,
+                "ms": [float(ms[i]) for i in range(n.value)]}
 
     def set_weighted_norm(self, xx: float) -> None:
         self._ck(self._lib.dash_set_weighted_norm(self._h, float(xx)))
@@ -355,8 +369,10 @@ class DashModel:
     def launch_count(self) -> int:
         return int(self._lib.dash_launch_count(self._h))
 
-    def profile(self, on: bool = True):
-        self._ck(self._lib.dash_profile_enable(self._h, 1 if on else 0))
+    def profile(self, on: bool = True, phases: bool = False):
+        """Per-launch event timing (on), plus in-kernel phase clocks (phases:
+        extra work inside the kernels, for breakdowns rather than timing)."""
+        self._ck(self._lib.dash_profile_enable(self._h, (2 if phases else 1) if on else 0))
 
     def profile_report(self) -> dict:
         """{kernel: (launches, total ms)} since profiling was enabled."""

@@ -128,8 +128,10 @@ extern "C" dash_status dash_profile_enable(dash_model *m, int32_t on) {
         }
         cudaGetLastError();
     }
+    if (on < 0 || on > 2) return fail(m, DASH_EINVAL, "profiling level must be 0, 1 or 2");
     prof_collect(m);
     m->prof.on = on != 0;
+    m->prof.phases = on == 2;
     for (int i = 0; i < KK_COUNT; ++i) {
         m->prof.ms[i] = 0.0;
         m->prof.launches[i] = 0;
@@ -877,6 +879,25 @@ extern "C" dash_status dash_set_graph(dash_model *m, int32_t on) {
         cudaGraphExecDestroy(m->gexec);
         m->gexec = nullptr;
     }
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_set_autotune(dash_model *m, int32_t on) {
+    if (!m) return DASH_EINVAL;
+    if (on != 0 && on != 1) return fail(m, DASH_EINVAL, "autotune switch must be 0 or 1");
+    m->autotune = on != 0;
+    return DASH_OK;
+}
+
+extern "C" dash_status dash_autotune_result(const dash_model *m, int32_t *n_candidates, int32_t *chosen,
+                                            int32_t *resident, int32_t *ring, float *ms) {
+    if (!m) return DASH_EINVAL;
+    if (n_candidates) *n_candidates = m->xu_tuned ? m->xu_tune_n : 0;
+    if (chosen) *chosen = m->xu_tuned ? m->xu_tune_best : -1;
+    if (resident) *resident = m->xr_nst > 0 ? 1 : 0;
+    if (ring) *ring = m->xr_nst > 0 ? m->xr_nst : m->xu_nst;
+    if (ms)
+        for (int i = 0; i < 8; ++i) ms[i] = (m->xu_tuned && i < m->xu_tune_n) ? m->xu_tune_ms[i] : 0.f;
     return DASH_OK;
 }
 

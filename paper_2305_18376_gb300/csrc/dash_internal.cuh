@@ -46,6 +46,7 @@ static const char *const kKernelNames[KK_COUNT] = {
 
 struct Profiler {
     bool on = false;
+    bool phases = false;                      // in-kernel phase clocks (level 2)
     int64_t launches_total = 0;
     int64_t launches[KK_COUNT] = {};
     double ms[KK_COUNT] = {};
@@ -161,6 +162,14 @@ struct dash_model {
     float *qv_slabs = nullptr;
     int xu_nst = 0;
     int xr_nst = 0;                   // X ring depth of k_xq_umma_rq (0: Q_V does not fit)
+    // autotuning of the X·Q_V pass on the first update that runs it: the
+    // resident-Q_V kernel at each ring depth that fits and the streamed-slab
+    // kernel, all computing the same bits; the fastest is kept
+    bool autotune = true;
+    bool xu_tuned = false;
+    int xu_tune_n = 0;                // candidates timed
+    float xu_tune_ms[8] = {};         // their times (ms), in candidate order
+    int xu_tune_best = -1;            // index of the one kept
     long long wait_limit = 2000000000LL;   // cycles before a bounded device wait gives up
     int inject_wait_fault = 0;        // test hook: the next tcgen05 X·Q_V pass skips one copy
     int64_t K_prev = 0;               // slices before the last update (restored if it is dropped)

@@ -351,6 +351,7 @@ __device__ __forceinline__ float slice_finish(const FusedArgs &a, int k, const f
     }
     if (act) a.W[(int64_t)k * R + lane] = wnew_d;
     if (act && a.Wf) a.Wf[(int64_t)k * R + lane] = (float)wnew_d;
+    if (act && !isfinite(wnew_d)) atomicAdd(a.err + 2, 1);   // reported as DASH_ENUMERIC
     const float wnew = (float)wnew_d;
 #pragma unroll
     for (int q = 0; q < FU_RP; ++q) {
@@ -1393,6 +1394,7 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
     }
     if (act) a.W[(int64_t)k * R + lane] = wnew_d;
     if (act && a.Wf) a.Wf[(int64_t)k * R + lane] = (float)wnew_d;
+    if (act && !isfinite(wnew_d)) atomicAdd(a.err + 2, 1);   // reported as DASH_ENUMERIC
     const float wnew = (float)wnew_d;
     // S_k ΔD S_k, row `lane`, into the warp's G block: ΔD summed again
 #pragma unroll 1

@@ -561,7 +561,7 @@ template <typename T>
 __global__ void k_vupdate(const double *__restrict__ F, const double *__restrict__ GP,
                           const double *__restrict__ Finc, int J, int R, double *__restrict__ V,
                           T *__restrict__ VT, double *__restrict__ cross_part,
-                          const int *__restrict__ abandoned) {
+                          const int *__restrict__ abandoned, int *nonfinite) {
     if (abandoned && *abandoned) return;
     __shared__ double red[8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -573,6 +573,7 @@ __global__ void k_vupdate(const double *__restrict__ F, const double *__restrict
             for (int r = 0; r < R; ++r) v += F[(int64_t)j * R + r] * GP[r * R + q];
             V[(int64_t)j * R + q] = v;
             VT[(int64_t)j * R + q] = (T)v;
+            if (nonfinite && !isfinite(v)) atomicAdd(nonfinite, 1);   // reported as DASH_ENUMERIC
             if (Finc) cr += v * Finc[(int64_t)j * R + q];
         }
     }

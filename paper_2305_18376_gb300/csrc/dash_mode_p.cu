@@ -14,6 +14,54 @@
 
 namespace dash {
 
+// Time the X·Q_V pass variants once on this batch and keep the fastest: the
+// resident-Q_V kernel at every ring depth from 2 to the deepest that fits,
+// then the streamed-slab kernel.  Every variant writes the same P' and ‖X‖²
+// partials (the same MMAs in the same order), so the last one launched
+// leaves correct outputs either way.  Synchronises the stream once.
+static dash_status autotune_xq(dash_model *m, const CUtensorMap &tmx, XuArgs xa, int n_xn, cudaStream_t st) {
+    const int J = m->cfg.J;
+    struct Cand { bool rq; int nst; };
+    Cand c[8];
+    int nc = 0;
+    for (int d = 2; d <= xr_stages(J) && nc < 7; ++d) c[nc++] = {true, d};
+    if (m->xu_nst > 0) c[nc++] = {false, m->xu_nst};
+    m->xu_tuned = true;
+    m->xu_tune_n = nc;
+    if (nc < 2) {
+        m->xu_tune_best = nc - 1;
+        return DASH_OK;
+    }
+    cudaEvent_t ev[16];
+    for (int i = 0; i < 2 * nc; ++i) CK(cudaEventCreate(&ev[i]));
+    for (int i = 0; i < nc; ++i) {
+        xa.nst = c[i].nst;
+        CK(cudaEventRecord(ev[2 * i], st));
+        if (c[i].rq) {
+            const size_t smem = xr_smem(J, c[i].nst);
+            CK(cudaFuncSetAttribute(k_xq_umma_rq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            LAUNCH(KK_XQ_UMMA, k_xq_umma_rq<<<n_xn, XR_THREADS, smem, st>>>(tmx, xa));
+        } else {
+            const size_t smem = xu_smem(J, c[i].nst);
+            CK(cudaFuncSetAttribute(k_xq_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            LAUNCH(KK_XQ_UMMA, k_xq_umma<<<n_xn, XU_THREADS, smem, st>>>(tmx, xa));
+        }
+        CK(cudaEventRecord(ev[2 * i + 1], st));
+    }
+    CK(cudaEventSynchronize(ev[2 * nc - 1]));
+    int best = 0;
+    for (int i = 0; i < nc; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+        m->xu_tune_ms[i] = ms;
+        if (ms < m->xu_tune_ms[best]) best = i;
+    }
+    for (int i = 0; i < 2 * nc; ++i) cudaEventDestroy(ev[i]);
+    m->xu_tune_best = best;
+    m->xr_nst = c[best].rq ? c[best].nst : 0;
+    return DASH_OK;
+}
+
 template <typename TI, typename T>
 static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void *Xv, double lam,
                                    bool begin_new) {
@@ -67,7 +115,7 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
             fa.xn_part = m->xn_part;
             fa.wsp = m->wsp;
             fa.err = m->d_err;
-            fa.phase_cycles = m->prof.on ? m->prof.d_phase : nullptr;
+            fa.phase_cycles = m->prof.phases && m->prof.d_phase ? m->prof.d_phase : nullptr;
             const size_t smem = fu_smem_bytes(J);
             if (m->cfg.precision == DASH_PREC_F16X3) {
                 CK(cudaFuncSetAttribute(k_rows_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -103,8 +151,12 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
             n_xn = (int)std::min<int64_t>(m->n_sm, (Ng + 127) / 128);
             XuArgs xa{m->qv_slabs, (float *)m->P, m->xn_part + g_f, m->d_err, Ng, m->h_run_row0[0],
                       J, R, m->xr_nst > 0 ? m->xr_nst : m->xu_nst, m->wait_limit, m->inject_wait_fault,
-                      m->prof.on ? m->prof.d_phase + 15 : nullptr};
+                      m->prof.phases && m->prof.d_phase ? m->prof.d_phase + 15 : nullptr};
             m->inject_wait_fault = 0;
+            if (m->autotune && !m->xu_tuned && !m->use_graph && xa.skip_first_copy == 0) {
+                if (dash_status e = autotune_xq(m, tmx, xa, n_xn, st)) return e;
+                xa.nst = m->xr_nst > 0 ? m->xr_nst : m->xu_nst;
+            }
             if (m->xr_nst > 0) {
                 // Q_V resident in shared memory, X released after conversion
                 const size_t smem = xr_smem(J, m->xr_nst);
@@ -133,7 +185,7 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
             LAUNCH(KK_XQ_TC, k_xq_tc<<<n_xn, XQ_THREADS, smem, st>>>((const float *)X, b, J, R, m->xq_frag,
                                                                      m->xq_bexp, (float *)m->P,
                                                                      m->xn_part + g_f, m->xe, m->d_err,
-                                                                     m->prof.on ? m->prof.d_phase + 11 : nullptr));
+                                                                     m->prof.phases && m->prof.d_phase ? m->prof.d_phase + 11 : nullptr));
             m->prof.xq_warps = (double)n_xn * XQ_WARPS;
         } else {
             n_xn = (int)((Ng + XV_ROWS - 1) / XV_ROWS);
@@ -187,7 +239,7 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
                 // kBigCBlocksPerSM CTAs fit on an SM
                 CK(cudaFuncSetAttribute(k_big_c, cudaFuncAttributePreferredSharedMemoryCarveout,
                                         (int)cudaSharedmemCarveoutMaxShared));
-                fa.phase_cycles = m->prof.on && m->prof.d_phase ? m->prof.d_phase + 20 : nullptr;
+                fa.phase_cycles = m->prof.phases && m->prof.d_phase ? m->prof.d_phase + 20 : nullptr;
                 LAUNCH(KK_BIG_C, k_big_c<<<nsb, 256, 0, st>>>(fa, bg, m->Gpart + (size_t)g_f * R * R));
                 fa.phase_cycles = nullptr;
                 m->prof.bc_warps = (double)nsb * 8;
@@ -232,7 +284,7 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
         const float *Xf = (const float *)X;
         m->prof.ft_warps = (double)grid.x * grid.y * FT_WARPS;
         const unsigned nug = (unsigned)((Ng + 127) / 128);
-        unsigned long long *pc = m->prof.on ? m->prof.d_phase + 13 : nullptr;
+        unsigned long long *pc = m->prof.phases && m->prof.d_phase ? m->prof.d_phase + 13 : nullptr;
         switch (NT) {
 #define FTC(n)                                                                                       \
     case n:                                                                                          \
@@ -266,7 +318,7 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
                                                                   m->d_err + 3));
     if (dash_status e = launch_pinv(m, s.G, m->GP, nullptr, m->d_err + 3)) return e;
     LAUNCH(KK_VUPDATE, k_vupdate<T><<<(J + 7) / 8, 256, 0, st>>>(s.F, m->GP, m->Finc, J, R, s.V, (T *)m->VT,
-                                               m->cross_part, m->d_err + 3));
+                                               m->cross_part, m->d_err + 3, m->d_err + 2));
     LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(s.V, J, R, s.Gam, m->d_err + 3));
     if (dash_status e = launch_pinv(m, s.Gam, s.GamP, s.gam_ok, m->d_err + 3)) return e;
     LAUNCH(KK_FITNESS, k_fitness<<<1, 32, 0, st>>>(m->xn_part, g_f + n_xn, m->cross_part, (J + 7) / 8, s.Gam, m->Ginc, R,

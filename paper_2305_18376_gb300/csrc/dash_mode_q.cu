@@ -29,7 +29,7 @@ static QDev make_qdev(dash_model *m, double lam) {
     q.C = m->qC;
     q.Gam = m->st.Gam;
     q.err = m->d_err;
-    q.phase = m->prof.on && m->prof.d_phase ? m->prof.d_phase + 7 : nullptr;
+    q.phase = m->prof.phases && m->prof.d_phase ? m->prof.d_phase + 7 : nullptr;
     return q;
 }
 

@@ -48,6 +48,7 @@ class Request:
     admitted: Optional[float] = None
     done: Optional[float] = None
     issue_s: Optional[float] = None    # host time spent issuing it (append + update calls)
+    failed: Optional[str] = None       # why it was not served (its stream's numerics failed)
 
     @property
     def latency(self) -> Optional[float]:
@@ -56,6 +57,9 @@ class Request:
 
 class ServingError(RuntimeError):
     pass
+
+
+NUMERIC_FAILURE = 5    # DASH_ENUMERIC: a non-finite value reached a stream's factors
 
 
 class ServingLoop:
@@ -92,8 +96,10 @@ class ServingLoop:
         self.resident = 0
         self.peak_resident = 0
         self.retired: List[int] = []
-        self.events: List[tuple] = []      # (time, "admit"|"done"|"create"|"retire", stream)
+        self.events: List[tuple] = []      # (time, "admit"|"done"|"create"|"retire"|"fail", stream)
+        self.failed: Dict[int, str] = {}   # streams stopped by a numerical failure
         self._t0 = clock()
+        self._final = True
 
     # ---- model residency ---------------------------------------------------
     def _retire(self, s: int, now: float):
@@ -108,6 +114,8 @@ class ServingLoop:
     def _make_room(self, need: int, left: Dict[int, int], busy: set, now: float) -> bool:
         if self.resident + need <= self.budget:
             return True
+        if not self._final:
+            return False
         for s in sorted(self.models):
             if self.resident + need <= self.budget:
                 break
@@ -138,21 +146,34 @@ class ServingLoop:
     # ---- issue ---------------------------------------------------------------
     @staticmethod
     def _issue(m, r: Request):
-        m.append_batch(np.asarray(r.slice_ids), np.asarray(r.row_ptr), r.X)
+        ids, rp = np.asarray(r.slice_ids), np.asarray(r.row_ptr)
+        if r.kind not in ("init", "update"):
+            raise ValueError(f"unknown request kind {r.kind!r}")
+        if getattr(r.X, "is_cuda", False):
+            # a device-resident batch is read in place (no staging copy)
+            if r.kind == "init":
+                m.fit_initial_device(ids, rp, r.X, r.init_iters)
+            else:
+                m.update_device(ids, rp, r.X)
+            return
+        m.append_batch(ids, rp, r.X)
         if r.kind == "init":
             m.fit_initial(r.init_iters)
-        elif r.kind == "update":
-            m.update()
         else:
-            raise ValueError(f"unknown request kind {r.kind!r}")
+            m.update()
 
     # ---- the loop ------------------------------------------------------------
-    def run(self, requests: List[Request], realtime: bool = True) -> List[Request]:
+    def run(self, requests: List[Request], realtime: bool = True, final: bool = True) -> List[Request]:
         """Serve `requests` (any order; taken by arrival time, ties in list
         order).  realtime=False lets every request arrive at once (a burst),
         which keeps the admission order and makes the loop's work
-        independent of the host's speed.  Returns the requests with their
-        admission and completion times filled in."""
+        independent of the host's speed.  final=False keeps every model
+        resident at the end (no retirement during this run), for streams
+        whose later requests come in a later run; a request that does not
+        fit then waits for room, and ServingError is raised if none can be
+        made.  Returns the requests with their admission and completion times
+        filled in."""
+        self._final = final
         order = sorted(range(len(requests)), key=lambda i: (requests[i].arrival, i))
         pending = collections.deque(requests[i] for i in order)
         left: Dict[int, int] = collections.Counter(r.stream for r in requests)
@@ -178,13 +199,26 @@ class ServingLoop:
             keep: List[Request] = []
             for r in waiting:
                 s = r.stream
+                if s in self.failed:                    # its stream stopped: not served
+                    r.failed = self.failed[s]
+                    left[s] -= 1
+                    progressed = True
+                    continue
                 if (len(inflight) >= self.max_inflight or s in blocked or s in inflight
                         or not self._ensure_model(s, left, set(inflight), now)):
                     blocked.add(s)
                     keep.append(r)
                     continue
                 r.admitted = self.clock() - t0
-                self._issue(self.models[s], r)
+                try:
+                    self._issue(self.models[s], r)
+                except Exception as e:          # a stream's numerics failed: stop that stream only
+                    if getattr(e, "status", None) != NUMERIC_FAILURE:
+                        raise
+                    self._fail_stream(s, str(e), r, pending, left, now)
+                    blocked.add(s)
+                    progressed = True
+                    continue
                 r.issue_s = self.clock() - t0 - r.admitted
                 inflight[s] = r
                 blocked.add(s)
@@ -197,6 +231,23 @@ class ServingLoop:
                 if self.poll_sleep:
                     time.sleep(self.poll_sleep)
         return requests
+
+    def _fail_stream(self, s: int, why: str, r: Request, pending, left, now: float):
+        """Mark stream s failed: this request and every later one of the
+        stream are not served; its model is closed (its state is not
+        trustworthy) and its memory released."""
+        self.failed[s] = why
+        r.failed = why
+        left[s] -= 1
+        for q in list(pending):
+            if q.stream == s:
+                q.failed = why
+                left[s] -= 1
+                pending.remove(q)
+        m = self.models.pop(s)
+        m.close()
+        self.resident -= self.model_bytes.pop(s)
+        self.events.append((now, "fail", s))
 
     def close(self):
         """Hand every resident model to on_retire, then free it."""

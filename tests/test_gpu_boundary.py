@@ -7,7 +7,9 @@ oracle and against themselves:
 * n_sweeps = 2: two passes of Algorithm 1 per update with the old helpers
   held fixed, against O.dash_update_p(..., n_sweeps=2);
 * dash_fitness_lambda: the λ-weighted fitness of every absorbed row against
-  the oracle's definition over the stored rows.
+  the oracle's definition over the stored rows;
+* the X·Q_V autotuning: the same bits with it on and off, and a valid choice;
+* a bounded wait that runs out drops the update and keeps the state.
 """
 import os
 
@@ -187,3 +189,37 @@ def test_timed_out_wait_drops_the_update_and_keeps_the_state():
     st2, _ = O.dash_update_p(st, segs_np(b, torch.float32), b.n_new, w.lam)
     compare_state_p(m.get_state_p(), st2, TOL["f16x3"], "after the dropped update")
     m.close()
+
+
+def test_autotuned_xq_pass_gives_the_same_bits():
+    """Two models on the same c4-shaped stream, one autotuning its X·Q_V pass
+    on the first update and one with autotuning off: the states after two
+    updates are bit-identical, the tuner timed every variant and kept one
+    of them, and the later update did not tune again."""
+    w = workload("c4", K0=400, steps=2, init_rows=("uniform", 40, 200), new_slices_per_step=4)
+    s = PlantedStream(w)
+    b0 = s.batch(0)
+    st = oracle_fit_p(segs_np(b0, torch.float32), np.random.default_rng(3).random((w.J, w.R)), 2)
+    from paper_2305_18376_gb300 import DashModel
+    batches = [s.batch(t) for t in (1, 2)]
+    states = []
+    for tune in (True, False):
+        m = DashModel(w.J, w.R, w.lam, precision="f16x3", input_dtype="f32", max_slices=w.K0 + 64,
+                      max_rows=max(b.n_rows for b in batches) + 16, max_segments=4096, max_staged_rows=1)
+        m.set_autotune(tune)
+        m.set_state_p(st.V, st.W, st.c, st.D, st.F, st.G)
+        for b in batches:
+            m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), b.X.float().cuda())
+        r = m.autotune_result()
+        if tune:
+            assert r["candidates"] >= 2, r
+            assert 0 <= r["chosen"] < r["candidates"], r
+            assert all(ms > 0 for ms in r["ms"]), r
+            assert r["ring"] >= 2, r
+            print("  autotune:", r)
+        else:
+            assert r["candidates"] == 0 and r["chosen"] == -1, r
+        states.append(m.get_state_p())
+        m.close()
+    for k in states[0]:
+        assert np.array_equal(states[0][k], states[1][k]), k

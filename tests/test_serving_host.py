@@ -8,9 +8,14 @@ import pytest
 from paper_2305_18376_gb300.serving import Request, ServingError, ServingLoop, latency_summary
 
 
+class NumericFailure(RuntimeError):
+    status = 5
+
+
 class FakeModel:
-    def __init__(self, J, R, lam, nbytes=0, polls=2, **kw):
+    def __init__(self, J, R, lam, nbytes=0, polls=2, fail_at=None, **kw):
         self.J, self.R, self.nbytes, self.polls = J, R, nbytes, polls
+        self.fail_at = fail_at
         self.busy = 0
         self.work = []
         self.closed = False
@@ -27,6 +32,8 @@ class FakeModel:
         self.busy = self.polls
 
     def update(self):
+        if self.fail_at is not None and sum(w[0] == "update" for w in self.work) == self.fail_at:
+            raise NumericFailure("non-finite factors")
         self.work.append(("update",))
         self.busy = self.polls
 
@@ -131,3 +138,37 @@ def test_latency_summary():
     assert out["requests"] == 2 and out["rows"] == 40
     assert out["p50_ms"] == pytest.approx(750.0)
     assert out["rows_per_s"] == pytest.approx(20.0)
+
+
+def test_non_final_run_keeps_models_for_the_next_run():
+    """A run with final=False retires nothing, so a stream fitted in it keeps
+    its model for its updates in the next run; a request that cannot fit
+    without retiring is an error instead of a silent restart."""
+    loop, retired = _loop({0: 40, 1: 40}, budget=100)
+    loop.run([_req(0, 0.0, "init"), _req(1, 0.0, "init")], realtime=False, final=False)
+    assert not retired and set(loop.models) == {0, 1}
+    m0 = loop.models[0]
+    loop.run([_req(0, 0.0), _req(1, 0.0)], realtime=False)
+    assert loop.models.get(0, m0) is m0 or retired.get(0) is m0
+    assert [w[0] for w in m0.work] == ["append", "init", "append", "update"]
+    loop2, retired2 = _loop({0: 60, 1: 60}, budget=100)
+    with pytest.raises(ServingError):
+        loop2.run([_req(0, 0.0, "init"), _req(1, 0.0, "init")], realtime=False, final=False)
+
+
+def test_a_numerical_failure_stops_only_its_stream():
+    """A stream whose update reports a non-finite state (DASH_ENUMERIC) is
+    stopped: that request and its later ones are marked failed, its model
+    is closed and its memory released; the other streams are served."""
+    specs = {0: dict(J=2, R=1, lam=1.0, nbytes=10, polls=1, fail_at=1),
+             1: dict(J=2, R=1, lam=1.0, nbytes=10, polls=1)}
+    loop = ServingLoop(specs, 100, 4, factory=FakeModel, bytes_of=lambda spec: spec["nbytes"],
+                       poll_sleep=0)
+    reqs = [_req(0, 0.0, "init"), _req(1, 0.0, "init")]
+    reqs += [_req(s, 0.001 * t) for t in range(1, 5) for s in (0, 1)]
+    loop.run(reqs, realtime=False)
+    ok0 = [r for r in reqs if r.stream == 0 and r.kind == "update"]
+    assert [r.done is not None for r in ok0] == [True, False, False, False]
+    assert all(r.failed for r in ok0[1:]) and 0 in loop.failed
+    assert all(r.done is not None and not r.failed for r in reqs if r.stream == 1)
+    assert 0 not in loop.models and loop.resident == loop.model_bytes.get(1, 0)
