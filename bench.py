@@ -936,7 +936,7 @@ def run_serving(a):
         # to completion), and the numerical counters
         per = []
         for s, w in enumerate(load.streams):
-            rs = [r for r in reqs_upd if r.stream == s]
+            rs = [r for r in reqs_upd if r.stream == s and r.done is not None]
             if not rs:
                 continue
             svc = np.array([r.done - r.admitted for r in rs]) * 1e3

@@ -388,8 +388,8 @@ dash_status dash_graph_stats(const dash_model *m, int64_t *instantiations, int64
 
 /* Autotuning of the X·Q_V pass (the paper has no counterpart: a choice
  * between kernels that compute the same bits).  With it on (the default),
- * the first mode-P update that runs the tcgen05 X·Q_V pass times every
- * variant on its own batch (the resident-Q_V kernel at each ring depth from
+ * the first mode-P update that runs the tcgen05 X·Q_V pass runs every
+ * variant once and then times it on its own batch (the resident-Q_V kernel at each ring depth from
  * 2 to the deepest that fits, then the kernel that streams the Q_V slabs
  * with each stage), keeps the fastest for the rest of the model's life and
  * synchronises the stream once.  Skipped while graph updates are on (the

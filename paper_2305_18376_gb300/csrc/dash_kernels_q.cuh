@@ -138,8 +138,10 @@ __global__ void k_q_arows(int64_t N, int R, const int *__restrict__ row_slice,
 //   mode 1 (prepare): E_k and B_k^{1/2} from a loaded L_k (cold start).
 template <class S>
 __host__ __device__ inline size_t q_lt_warp_bytes(int R) {
+    // R <= 32: L, E and one scratch block (G, the rotations, T_k); larger R
+    // also needs M for the Gram-Jacobi
     const int ld = q_ld(R);
-    return (size_t)4 * R * ld * sizeof(S) + (size_t)3 * R * sizeof(S);
+    return (size_t)(R <= 32 ? 3 : 4) * R * ld * sizeof(S) + (size_t)3 * R * sizeof(S);
 }
 
 template <class S, typename T>
@@ -153,8 +155,11 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
     S *Lw = reinterpret_cast<S *>(base);
     S *Ew = Lw + R * ld;
     S *Gw = Ew + R * ld;      // G, the rotations, then T_k
-    S *Mw = Gw + R * ld;      // M, then B_old^{1/2}, B_new^{1/2}, staged A rows
-    S *mu = Mw + R * ld;
+    // R > 32: M, then B_old^{1/2}, B_new^{1/2}, staged A rows.  R <= 32 has no
+    // fourth block: after the eigen-decomposition L_k (already written out)
+    // is dead and its block takes those roles.
+    S *Mw = R <= 32 ? Lw : Gw + R * ld;
+    S *mu = (R <= 32 ? Gw : Mw) + R * ld;
     S *finv = mu + R;
     S *fsq = finv + R;
     const int chunk = R < 32 ? R : 32;      // A rows per QR step (staged in Gw)
@@ -201,7 +206,7 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
                 // double-float: one step (the FP32 sweeps leave EᵀE − I at a few
                 // 1e-6; one step takes it to about 1e-11, below the sweeps' 1e-10
                 // target); FP64: two
-                warp_newton_schulz<S>(Ew, Gw, Mw, R, ld, std::is_same<S, df>::value ? 1 : 2);
+                warp_newton_schulz_reg<S>(Ew, Gw, R, ld, std::is_same<S, df>::value ? 1 : 2);
             }
             if (q.phase) { const long long c1 = clock64(); pc[1] += c1 - c0k; c0k = c1; }
             // working-type sweeps; the double-float ones stop after the sweep that

@@ -358,6 +358,40 @@ __device__ void warp_newton_schulz(S *E, S *Gs, S *Ms, int R, int ld, int steps)
     }
 }
 
+// warp_newton_schulz for R <= 32 with one shared scratch block: lane c holds
+// column c of P = EᵀE in registers, writes column c of E (3I − P)/2 to Es,
+// and Es is copied back to E.  The same arithmetic as warp_newton_schulz.
+template <class S>
+__device__ void warp_newton_schulz_reg(S *E, S *Es, int R, int ld, int steps) {
+    using O = RT<S>;
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < R;
+    for (int step = 0; step < steps; ++step) {
+        S p[32];
+#pragma unroll
+        for (int a = 0; a < 32; ++a) {
+            S acc = O::zero();
+            if (act && a < R)
+                for (int i = 0; i < R; ++i) acc = O::fma(acc, E[i * ld + a], E[i * ld + lane]);
+            p[a] = acc;
+        }
+        if (act)
+            for (int r = 0; r < R; ++r) {
+                S acc = O::zero();
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (k < R) {
+                        const S pk = (k == lane) ? O::sub(O::from_f(3.f), p[k]) : O::sub(O::zero(), p[k]);
+                        acc = O::fma(acc, E[r * ld + k], pk);
+                    }
+                Es[r * ld + lane] = O::mulf(acc, 0.5f);
+            }
+        __syncwarp();
+        for (int i = lane; i < R * R; i += 32) E[(i / R) * ld + (i % R)] = Es[(i / R) * ld + (i % R)];
+        __syncwarp();
+    }
+}
+
 // One-sided (Hestenes) Jacobi for the eigen-decomposition of B = LᵀL, R <= 32,
 // register-resident: lane c holds column c of G = L·E and of E in the
 // working type W (S, or float for a cheap first pass).  A sweep pairs every
