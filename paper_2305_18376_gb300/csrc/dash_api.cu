@@ -573,6 +573,8 @@ static dash_status refresh_gamma(dash_model *m) {
         LAUNCH(KK_CAST, k_cast<float><<<(n + 255) / 256, 256, 0, m->stream>>>(m->st.V, (float *)m->VT, n));
     LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, m->stream>>>(m->st.V, J, R, m->st.Gam, nullptr));
     if (dash_status e = launch_pinv(m, m->st.Gam, m->st.GamP, m->st.gam_ok, nullptr)) return e;
+    m->gamp_fresh = true;
+    m->vqr_fresh = false;
     int ok = 0;
     CK(cudaMemcpyAsync(&ok, m->st.gam_ok, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
     CK(cudaStreamSynchronize(m->stream));

@@ -92,6 +92,12 @@ struct dash_model {
     bool fused_ok = false;            // shapes the fused row kernel supports
     int n_sm = 1;
     bool gam_ok_host = false;         // mirror of the device flag (Γ nonsingular)
+    // which outputs derived from the current Γ are up to date: the Cholesky
+    // QR of V (R_V, R_V⁻ᵀ, Γ in double-float; the mixed path computes it at
+    // the end of each update) and Γ⁺ (the FP64 path, and the general kernel
+    // when a mixed update takes it)
+    bool vqr_fresh = false;
+    bool gamp_fresh = true;
     int64_t K = 0;                    // slices in the model
     bool v_set = false;
 

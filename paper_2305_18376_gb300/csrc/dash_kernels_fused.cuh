@@ -989,8 +989,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1) k_rows_fused(FusedArgs a) {
 }
 
 // V = Q_V R_V from Γ = VᵀV = R_VᵀR_V (Cholesky, FP64, one warp): R_V (upper),
-// L⁻¹ = R_V⁻ᵀ (lower) in FP64 and FP32, and Γ in double-float.  Clears
-// *gam_ok when Γ is not safely positive definite (the same test as Γ⁺).
+// L⁻¹ = R_V⁻ᵀ (lower) in FP64 and FP32, and Γ in double-float.  Sets *gam_ok
+// to whether Γ is safely positive definite (the same test as Γ⁺).
 static __global__ void k_vqr(const double *__restrict__ Gam, int R, double rtol, double *__restrict__ RV,
                       double *__restrict__ Linv, float *__restrict__ LinvF, df *__restrict__ Gdf,
                       int *__restrict__ gam_ok) {
@@ -1006,10 +1006,8 @@ static __global__ void k_vqr(const double *__restrict__ Gam, int R, double rtol,
     for (int i = lane; i < R; i += 32) md = fmax(md, fabs(L[i * ld + i]));
     md = warp_max(md);
     const bool ok = md > 0.0 && warp_cholesky(L, R, ld, 100.0 * rtol * md);
-    if (!ok) {
-        if (lane == 0) *gam_ok = 0;
-        return;
-    }
+    if (lane == 0) *gam_ok = ok ? 1 : 0;
+    if (!ok) return;
     for (int i = lane; i < R; i += 32) rinv[i] = 1.0 / L[i * ld + i];
     __syncwarp();
     // lane c: column c of L⁻¹ by forward substitution (no divisions in the loop)

@@ -85,9 +85,14 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     int g_f = 0;
     if constexpr (std::is_same<T, float>::value && std::is_same<TI, float>::value) {
         if (m->fused_active) {
-            const size_t qsm = (size_t)(2 * R * (R + 1) + R + 1) * 8;
-            LAUNCH(KK_VTILDE, k_vqr<<<1, 32, qsm, st>>>(s.Gam, R, m->rtol, m->RV, m->Linv, m->GPf,
-                                                        m->Gdf, s.gam_ok));
+            // the Cholesky QR of V: computed at the end of the previous update
+            // unless the state was set since
+            if (!m->vqr_fresh) {
+                const size_t qsm = (size_t)(2 * R * (R + 1) + R + 1) * 8;
+                LAUNCH(KK_VTILDE, k_vqr<<<1, 32, qsm, st>>>(s.Gam, R, m->rtol, m->RV, m->Linv, m->GPf,
+                                                            m->Gdf, s.gam_ok));
+                m->vqr_fresh = true;
+            }
             LAUNCH(KK_QV, k_qv<<<(J + 7) / 8, 256, 0, st>>>(s.V, m->Linv, J, R, m->QV));
         }
         if (m->fused_active && m->n_tiles > 0) {
@@ -251,6 +256,11 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
         }
     }
     if (!finished) {
+        // the general kernel reads Γ⁺
+        if (!m->gamp_fresh) {
+            if (dash_status e = launch_pinv(m, s.Gam, s.GamP, s.gam_ok, nullptr)) return e;
+            m->gamp_fresh = true;
+        }
         // per-slice work for slices the fused kernel did not finish
         const int nw = sl_warps(R);
         const size_t smem = (size_t)nw * sl_warp_doubles(R) * 8;
@@ -323,7 +333,19 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
     LAUNCH(KK_VUPDATE, k_vupdate<T><<<(J + 7) / 8, 256, 0, st>>>(s.F, m->GP, m->Finc, J, R, s.V, (T *)m->VT,
                                                m->cross_part, m->d_err + 3, m->d_err + 2));
     LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(s.V, J, R, s.Gam, m->d_err + 3));
-    if (dash_status e = launch_pinv(m, s.Gam, s.GamP, s.gam_ok, m->d_err + 3)) return e;
+    if (m->fused_ok) {
+        // mixed path: the Cholesky QR of the new V for the next update (it also
+        // decides whether Γ is nonsingular); Γ⁺ only if an update needs it
+        const size_t qsm = (size_t)(2 * R * (R + 1) + R + 1) * 8;
+        LAUNCH(KK_VTILDE, k_vqr<<<1, 32, qsm, st>>>(s.Gam, R, m->rtol, m->RV, m->Linv, m->GPf, m->Gdf,
+                                                    s.gam_ok));
+        m->vqr_fresh = true;
+        m->gamp_fresh = false;
+    } else {
+        if (dash_status e = launch_pinv(m, s.Gam, s.GamP, s.gam_ok, m->d_err + 3)) return e;
+        m->gamp_fresh = true;
+        m->vqr_fresh = false;
+    }
     LAUNCH(KK_FITNESS, k_fitness<<<1, 32, 0, st>>>(m->xn_part, g_f + n_xn, m->cross_part, (J + 7) / 8, s.Gam, m->Ginc, R,
                                 s.gam_ok, m->fit));
     CK(cudaMemcpyAsync(m->h_fit, m->fit, 4 * 8, cudaMemcpyDeviceToHost, st));

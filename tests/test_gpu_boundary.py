@@ -9,7 +9,9 @@ oracle and against themselves:
 * dash_fitness_lambda: the λ-weighted fitness of every absorbed row against
   the oracle's definition over the stored rows;
 * the X·Q_V autotuning: the same bits with it on and off, and a valid choice;
-* a bounded wait that runs out drops the update and keeps the state.
+* a bounded wait that runs out drops the update and keeps the state;
+* a non-finite input value reaches the factors and is reported as
+  DASH_ENUMERIC.
 """
 import os
 
@@ -223,3 +225,30 @@ def test_autotuned_xq_pass_gives_the_same_bits():
         m.close()
     for k in states[0]:
         assert np.array_equal(states[0][k], states[1][k]), k
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f16x3"])
+def test_non_finite_state_is_reported(prec):
+    """A batch with a NaN in X makes the new V non-finite (mode P): the
+    library reports DASH_ENUMERIC at the next read of the state and at the
+    next update, instead of returning NaN factors silently."""
+    from paper_2305_18376_gb300 import DashError, DashModel
+    w = tiny(K0=20, J=32, R=4, steps=2, sigma=0.05, lam=0.9)
+    s = PlantedStream(w)
+    b0 = s.batch(0)
+    _, tdt = (("f64", torch.float64) if prec == "fp64" else ("f32", torch.float32))
+    st = oracle_fit_p(segs_np(b0, tdt), np.random.default_rng(2).random((w.J, w.R)), 2)
+    m = _model(w, prec)
+    m.set_state_p(st.V, st.W, st.c, st.D, st.F, st.G)
+    b = s.batch(1)
+    X = b.X.to(tdt).clone()
+    X[0, 0] = float("nan")
+    m.update_device(b.slice_ids.numpy(), b.row_ptr.numpy(), X.cuda())
+    with pytest.raises(DashError) as e:
+        m.get_state_p()
+    assert e.value.status == 5, e.value
+    b2 = s.batch(2)
+    with pytest.raises(DashError) as e:
+        m.update_device(b2.slice_ids.numpy(), b2.row_ptr.numpy(), b2.X.to(tdt).cuda())
+    assert e.value.status == 5, e.value
+    m.close()
