@@ -1331,7 +1331,9 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
                                      df_make(Lw[r * FU_LD + lane]));
                 D2[r * R + lane] = make_float2(dn.hi, dn.lo);
                 const float2 g = __ldg(G2 + r * R + lane);
-                row[r] = df_mul(df{g.x, g.y}, dn).hi;
+                // the leading part only, for the FP32 factorisation (the refinement
+                // re-forms the product in double-float)
+                row[r] = fmaf(g.x, dn.hi, fmaf(g.x, dn.lo, g.y * dn.hi));
                 if (r == lane) mydiag = row[r];
             }
         }
