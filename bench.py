@@ -516,13 +516,16 @@ def run_ours(a):
         erows = 0
         b, hx = hosts[0]
         m.append_batch(b.slice_ids.numpy(), b.row_ptr.numpy(), hx)
+        step_s = []
         for i in range(len(timed)):
             b, hx = hosts[i % len(hosts)]
+            ts0 = time.perf_counter()
             m.update()
             if i + 1 < len(timed):                # the next step's copy overlaps this update
                 nb, nhx = hosts[(i + 1) % len(hosts)]
                 m.append_batch(nb.slice_ids.numpy(), nb.row_ptr.numpy(), nhx)
             m.fitness()                           # D2H read of the step's result
+            step_s.append(time.perf_counter() - ts0)
             h2d += hx.numel() * hx.element_size() + 16 * b.slice_ids.numel()
             d2h += 24
             erows += b.n_rows
@@ -533,7 +536,11 @@ def run_ours(a):
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             et = float(tt.item())
         e2e = {"value": erows * world / et, "unit": "rows/s",
-               "h2d_bytes_per_step": h2d // len(timed), "d2h_bytes_per_step": d2h // len(timed)}
+               "h2d_bytes_per_step": h2d // len(timed), "d2h_bytes_per_step": d2h // len(timed),
+               # host time per step (each step waits for its own copy): the
+               # median is the steady state, the maximum shows slow copies
+               "step_ms_p50": statistics.median(step_s) * 1e3, "step_ms_max": max(step_s) * 1e3,
+               "h2d_gbs_at_p50": h2d / len(timed) / statistics.median(step_s) / 1e9}
     # ---- roofline of the dominant kernel ------------------------------------
     pk, pk_kind = peaks()
     Nm = int(statistics.mean(b.n_rows for b in timed))

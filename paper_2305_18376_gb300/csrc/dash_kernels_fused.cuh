@@ -56,6 +56,8 @@ struct FusedArgs {
     const float *X;
     int J, R;
     double lam, rtol;
+    float lam_hi, lam_lo;     // λ as double-float (lam_hi + lam_lo)
+    int lam_on;               // λ != 0: the old summaries are kept
     const float *V32;         // Q_V (J×R, FP32): V = Q_V R_V with orthonormal Q_V
     const float *GPf;         // R_V⁻ᵀ (R×R, FP32, lower triangular)
     const double *RV;         // R_V (R×R, FP64, upper triangular)
@@ -1226,7 +1228,7 @@ __device__ __forceinline__ float chol_solve_smem(const float *Lw, float myinv, b
 
 // FP64 pseudo-inverse solve of W(k,:) (rare: the FP32 factor broke down):
 // A = Γ ∗ D_k, b = c_k.  Returns w_k,new[lane].
-static __device__ __forceinline__ double big_c_fallback(const FusedArgs &a, const df *Dk, df cnew, double *wsp) {
+static __device__ __noinline__ double big_c_fallback(const FusedArgs &a, const df *Dk, df cnew, double *wsp) {
     const int lane = threadIdx.x & 31;
     const int R = a.R;
     double *Aw = wsp, *Lf = Aw + R * (R + 1), *Ew = Lf + R * (R + 1);
@@ -1279,8 +1281,8 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
     const float2 *G2 = reinterpret_cast<const float2 *>(a.Gdf);
     df *Dk = a.D + (int64_t)k * R * R;
     float2 *D2 = reinterpret_cast<float2 *>(Dk);
-    const df lamdf = df_from_double(a.lam);
-    const bool keep_old = a.lam != 0.0;
+    const df lamdf{a.lam_hi, a.lam_lo};
+    const bool keep_old = a.lam_on != 0;
     // ΔD column `lane` (= row `lane`: ΔD is symmetric) into the warp's shared
     // block Lw, eight rows at a time (each entry summed over the chunks in
     // order), and Δc[lane]; Lw takes the Cholesky factor later
@@ -1309,7 +1311,7 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
     df cnew = {0.f, 0.f};
     if (act) {
         const df cold = a.c[(int64_t)k * R + lane];
-        cnew = df_add(keep_old ? df_mul(lamdf, cold) : df{0.f, 0.f}, df_make(dc));
+        cnew = keep_old ? df_add_f(df_mul(lamdf, cold), dc) : df_make(dc);
         a.c[(int64_t)k * R + lane] = cnew;
     }
     // D_k ← λD_k + ΔD and row `lane` of A = Γ ∗ D_k (hi parts); rows and
@@ -1327,8 +1329,8 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
             const int r = r0 + u;
             row[r] = 0.f;
             if (r < R && act) {
-                const df dn = df_add(keep_old ? df_mul(lamdf, df{dold[u].x, dold[u].y}) : df{0.f, 0.f},
-                                     df_make(Lw[r * FU_LD + lane]));
+                const float dd = Lw[r * FU_LD + lane];
+                const df dn = keep_old ? df_add_f(df_mul(lamdf, df{dold[u].x, dold[u].y}), dd) : df_make(dd);
                 D2[r * R + lane] = make_float2(dn.hi, dn.lo);
                 const float2 g = __ldg(G2 + r * R + lane);
                 // the leading part only, for the FP32 factorisation (the refinement
@@ -1367,22 +1369,30 @@ __device__ __forceinline__ void big_c_finish(const FusedArgs &a, const BigArgs &
         __syncwarp();
         const float x0 = chol_solve_smem(Lw, myinv, act, cnew.hi);
         mark(3);
-        // one refinement step: res = c − A x0 in double-float, A re-formed
-        // from the D_k just written
-        df res = cnew;
+        // one refinement step: res = c − A x0 with A re-formed from the D_k
+        // just written (A(lane, r) = ph + pl, ph = Γ.hi·D.hi, pl its error
+        // and cross terms).  The sum is carried as s + e, Ogita, Rump and
+        // Oishi's Dot2: each ph·x_r and each addition split error-free, the
+        // errors and pl·x_r summed in FP32, so s + e is the residual as if
+        // formed in twice the working precision.
+        float s = cnew.hi, e = cnew.lo;
 #pragma unroll 4
         for (int r = 0; r < R; ++r) {
             const float xr = __shfl_sync(full, x0, r);
             if (act) {
                 const float2 g = __ldg(G2 + r * R + lane);
                 const float2 d = D2[r * R + lane];
-                const df av = df_mul(df{g.x, g.y}, df{d.x, d.y});
-                res = df_sub(res, df_mul_f(av, xr));
+                const float ph = g.x * d.x;
+                const float pl = fmaf(g.x, d.y, fmaf(g.y, d.x, fmaf(g.x, d.x, -ph)));
+                const df q = two_prod(ph, xr);
+                const df t = two_sum(s, -q.hi);
+                s = t.hi;
+                e = fmaf(-pl, xr, __fsub_rn(__fadd_rn(e, t.lo), q.lo));
             }
         }
         mark(4);
-        const float dx = chol_solve_smem(Lw, myinv, act, res.hi);
-        x = df_add(df_make(x0), df_make(dx));
+        const float dx = chol_solve_smem(Lw, myinv, act, __fadd_rn(s, e));
+        x = two_sum(x0, dx);
         ok = __all_sync(full, isfinite(x.hi));
         mark(3);
     }
@@ -1453,11 +1463,12 @@ static __global__ void __launch_bounds__(256, kBigCBlocksPerSM) k_big_c(FusedArg
         big_c_finish(a, bg, f, Lw_all[warp], G_all[warp], wsp);
     }
     __syncthreads();
+    // the eight warp partials summed in double-float, one conversion to FP64
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
         const int r = e / R, q = e % R;
-        double s = 0.0;
-        for (int w = 0; w < FU_WARPS; ++w) s += (double)G_all[w][r * FU_LD + q];
-        Gpart_out[(int64_t)blockIdx.x * R * R + e] = s;
+        df s = df_make(G_all[0][r * FU_LD + q]);
+        for (int w = 1; w < FU_WARPS; ++w) s = df_add_f(s, G_all[w][r * FU_LD + q]);
+        Gpart_out[(int64_t)blockIdx.x * R * R + e] = df_to_double(s);
     }
 }
 

@@ -102,6 +102,9 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
             fa.J = J;
             fa.R = R;
             fa.lam = lam;
+            fa.lam_hi = (float)lam;
+            fa.lam_lo = (float)(lam - (double)fa.lam_hi);
+            fa.lam_on = lam != 0.0;
             fa.rtol = m->rtol;
             fa.V32 = m->QV;
             fa.GPf = m->GPf;
@@ -210,6 +213,9 @@ static dash_status launch_update_p(dash_model *m, const BatchDev &b, const void 
             fa.J = J;
             fa.R = R;
             fa.lam = lam;
+            fa.lam_hi = (float)lam;
+            fa.lam_lo = (float)(lam - (double)fa.lam_hi);
+            fa.lam_on = lam != 0.0;
             fa.rtol = m->rtol;
             fa.Gdf = m->Gdf;
             fa.GPf = m->GPf;

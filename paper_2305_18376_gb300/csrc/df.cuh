@@ -46,6 +46,14 @@ __device__ __forceinline__ df df_add(df a, df b) {
     return fast_two_sum(s.hi, s.lo);
 }
 
+// a + b with b a single FP32 number: one TwoSum, the low part added, one
+// Fast2Sum (the double-float + float sum of the same collection)
+__device__ __forceinline__ df df_add_f(df a, float b) {
+    df s = two_sum(a.hi, b);
+    s.lo = __fadd_rn(s.lo, a.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
 
 __device__ __forceinline__ df df_mul(df a, df b) {
