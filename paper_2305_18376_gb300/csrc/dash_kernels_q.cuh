@@ -311,12 +311,73 @@ __device__ __forceinline__ void ld_shared_vec(const double *p, double (&v)[n]) {
     }
 }
 
+// The (r, s) pairs of an R×R result that the QZ_THREADS threads of a CTA
+// split among themselves.  With R a multiple of 4, thread t owns runs of four
+// consecutive s, s = 4·(t mod R/4) + i, in the rows r = ⌊t / (R/4)⌋ + g·ρ
+// (ρ = ⌊QZ_THREADS / (R/4)⌋ rows per pass), pair index u = 4g + i; otherwise
+// the pairs e = t + u·QZ_THREADS, r = e / R, s = e mod R.  False past the
+// matrix.
+__device__ __forceinline__ bool qz_pair(int R, int u, int &r, int &s) {
+    const int t = threadIdx.x;
+    if ((R & 3) == 0) {
+        const int tpr = R >> 2, rpp = QZ_THREADS / tpr;
+        r = t / tpr + (u >> 2) * rpp;
+        s = ((t % tpr) << 2) + (u & 3);
+        return t < tpr * rpp && r < R;
+    }
+    const int e = t + u * QZ_THREADS;
+    r = e / R;
+    s = e % R;
+    return e < R * R;
+}
+
+// yv[u] += Σ_c Ys[r][c]·Vs[c][s] over one column chunk for the thread's pairs
+// (qz_pair), each sum taken in c order in the product type.  Ys is R ×
+// (QZ_JC + 1), Vs is QZ_JC × R; with R a multiple of 4 a run of four s is one
+// vector load of the Vs row (16-byte aligned: the Vs base is, and the row
+// pitch is R entries).
+template <typename T, int NP>
+__device__ __forceinline__ void qz_yv_chunk(const T *Ys, const T *Vs, int R, double (&yv)[NP]) {
+    const int t = threadIdx.x;
+    if ((R & 3) == 0) {
+        const int tpr = R >> 2, rpp = QZ_THREADS / tpr;
+        if (t >= tpr * rpp) return;
+        const int s0 = (t % tpr) << 2;
+#pragma unroll
+        for (int g = 0; g < NP / 4; ++g) {
+            const int r = t / tpr + g * rpp;
+            if (r < R) {
+                T a[4] = {T(0), T(0), T(0), T(0)};
+                for (int c = 0; c < QZ_JC; ++c) {
+                    const T y = Ys[r * (QZ_JC + 1) + c];
+                    T v[4];
+                    ld_shared_vec(Vs + c * R + s0, v);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a[i] += y * v[i];
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) yv[4 * g + i] += (double)a[i];
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int u = 0; u < NP; ++u) {
+        int r, s2;
+        if (qz_pair(R, u, r, s2)) {
+            T a = T(0);
+            for (int c = 0; c < QZ_JC; ++c) a += Ys[r * (QZ_JC + 1) + c] * Vs[c * R + s2];
+            yv[u] += (double)a;
+        }
+    }
+}
+
 template <typename TI, typename T, int RM>
 __global__ void __launch_bounds__(QZ_THREADS, RM <= 32 ? 2 : 1) k_q_y(BatchDev b, QDev q, const TI *__restrict__ X,
                                                     const T *__restrict__ Qrows, T *__restrict__ Y,
                                                     const T *__restrict__ VT, double *__restrict__ MHpart,
                                                     double *__restrict__ WWpart) {
-    extern __shared__ unsigned char qy_raw[];
+    extern __shared__ __align__(16) unsigned char qy_raw[];
     const int R = q.R, J = q.J, tid = threadIdx.x;
     T *Cs = reinterpret_cast<T *>(qy_raw);           // RM × RM  λ C_k (permuted, below)
     T *Qs = Cs + RM * RM;                            // QZ_RC × RM  Q rows (permuted)
@@ -382,12 +443,21 @@ __global__ void __launch_bounds__(QZ_THREADS, RM <= 32 ? 2 : 1) k_q_y(BatchDev b
                         }
                         __syncthreads();
                         if (j < J) {
-                            for (int i = 0; i < nr; ++i) {
-                                const T x = (T)X[(c0 + i) * J + j];
-                                T qv[NQ];
-                                ld_shared_vec(Qs + (i * 4 + rg) * NQ, qv);
+                            // four rows' loads in flight at a time
+                            for (int i0 = 0; i0 < nr; i0 += 4) {
+                                T xv[4];
 #pragma unroll
-                                for (int u = 0; u < NQ; ++u) acc[u] += qv[u] * x;
+                                for (int i = 0; i < 4; ++i)
+                                    xv[i] = i0 + i < nr ? (T)X[(c0 + i0 + i) * J + j] : T(0);
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) {
+                                    if (i0 + i < nr) {
+                                        T qv[NQ];
+                                        ld_shared_vec(Qs + ((i0 + i) * 4 + rg) * NQ, qv);
+#pragma unroll
+                                        for (int u = 0; u < NQ; ++u) acc[u] += qv[u] * xv[i];
+                                    }
+                                }
                             }
                         }
                     }
@@ -404,23 +474,13 @@ __global__ void __launch_bounds__(QZ_THREADS, RM <= 32 ? 2 : 1) k_q_y(BatchDev b
             }
             __syncthreads();
             // YV partial over this column chunk: thread owns pairs (r, s)
-#pragma unroll
-            for (int u = 0; u < NP; ++u) {
-                const int e = tid + u * QZ_THREADS;
-                if (e < R * R) {
-                    const int r = e / R, s2 = e % R;
-                    T a = T(0);
-                    for (int c = 0; c < QZ_JC; ++c) a += Ys[r * (QZ_JC + 1) + c] * Vs[c * R + s2];
-                    yv[u] += (double)a;
-                }
-            }
+            qz_yv_chunk(Ys, Vs, R, yv);
         }
         const double *wk = q.W + (int64_t)k * R;
 #pragma unroll
         for (int u = 0; u < NP; ++u) {
-            const int e = tid + u * QZ_THREADS;
-            if (e < R * R) {
-                const int r = e / R, s2 = e % R;
+            int r, s2;
+            if (qz_pair(R, u, r, s2)) {
                 mh[u] += yv[u] * wk[s2];
                 ww[u] += wk[r] * wk[s2];
             }
@@ -428,10 +488,10 @@ __global__ void __launch_bounds__(QZ_THREADS, RM <= 32 ? 2 : 1) k_q_y(BatchDev b
     }
 #pragma unroll
     for (int u = 0; u < NP; ++u) {
-        const int e = tid + u * QZ_THREADS;
-        if (e < R * R) {
-            MHpart[(int64_t)blockIdx.x * R * R + e] = mh[u];
-            WWpart[(int64_t)blockIdx.x * R * R + e] = ww[u];
+        int r, s2;
+        if (qz_pair(R, u, r, s2)) {
+            MHpart[(int64_t)blockIdx.x * R * R + r * R + s2] = mh[u];
+            WWpart[(int64_t)blockIdx.x * R * R + r * R + s2] = ww[u];
         }
     }
 }
@@ -485,33 +545,52 @@ constexpr int QV_THREADS = 128;
 template <typename T, int RM>
 __global__ void __launch_bounds__(QV_THREADS) k_q_vpart(int K_all, QDev q, const T *__restrict__ Y,
                                                         double *__restrict__ slots) {
-    __shared__ T Hs[RM * RM];
-    const int R = q.R, J = q.J, tid = threadIdx.x;
-    for (int e = tid; e < R * R; e += QV_THREADS) Hs[e] = (T)q.H[e];
+    __shared__ __align__(16) T Hs[RM * RM];           // H, row pitch RM, zero-padded
+    const int R = q.R, J = q.J, tid = threadIdx.x, lane = tid & 31;
+    for (int e = tid; e < RM * RM; e += QV_THREADS) {
+        const int r = e / RM, s2 = e % RM;
+        Hs[e] = (r < R && s2 < R) ? (T)q.H[r * R + s2] : T(0);
+    }
     __syncthreads();
     double *sl = slots + (size_t)blockIdx.x * J * R;
-    for (int j = tid; j < J; j += QV_THREADS) {
+    // every lane of a warp takes every column pass (the weights are shared by
+    // shuffles); lanes past J only skip their loads and stores
+    for (int j0 = 0; j0 < J; j0 += QV_THREADS) {
+        const int j = j0 + tid;
+        const bool on = j < J;
         T acc[RM];
 #pragma unroll
         for (int s2 = 0; s2 < RM; ++s2) acc[s2] = T(0);
         for (int k = blockIdx.x; k < K_all; k += gridDim.x) {
-            const T *Yk = Y + (int64_t)k * R * J + j;
+            const T *Yk = Y + (int64_t)k * R * J + (on ? j : 0);
+            // w_k in the product type, entry s on lane s mod 32 (converted once)
             const double *wk = q.W + (int64_t)k * R;
+            const T w0 = lane < R ? (T)wk[lane] : T(0);
+            const T w1 = (RM > 32 && lane + 32 < R) ? (T)wk[lane + 32] : T(0);
             T t[RM];
 #pragma unroll
             for (int s2 = 0; s2 < RM; ++s2) t[s2] = T(0);
             for (int r = 0; r < R; ++r) {
-                const T y = Yk[(int64_t)r * J];
+                const T y = on ? Yk[(int64_t)r * J] : T(0);
 #pragma unroll
-                for (int s2 = 0; s2 < RM; ++s2) t[s2] += y * Hs[r * R + s2];
+                for (int s0 = 0; s0 < RM; s0 += 4) {
+                    T h[4];
+                    ld_shared_vec(Hs + r * RM + s0, h);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) t[s0 + i] += y * h[i];
+                }
             }
 #pragma unroll
-            for (int s2 = 0; s2 < RM; ++s2)
-                if (s2 < R) acc[s2] += (T)wk[s2] * t[s2];
+            for (int s2 = 0; s2 < RM; ++s2) {
+                const T w = __shfl_sync(0xffffffffu, s2 < 32 ? w0 : w1, s2 & 31);
+                if (s2 < R) acc[s2] += w * t[s2];
+            }
         }
+        if (on) {
 #pragma unroll
-        for (int s2 = 0; s2 < RM; ++s2)
-            if (s2 < R) sl[(int64_t)j * R + s2] = (double)acc[s2];
+            for (int s2 = 0; s2 < RM; ++s2)
+                if (s2 < R) sl[(int64_t)j * R + s2] = (double)acc[s2];
+        }
     }
 }
 
@@ -561,7 +640,7 @@ template <typename T>
 __global__ void __launch_bounds__(QZ_THREADS) k_q_w(int K_all, QDev q, const T *__restrict__ Y,
                                                     const T *__restrict__ VT,
                                                     const double *__restrict__ PW) {
-    extern __shared__ unsigned char qw_raw[];
+    extern __shared__ __align__(16) unsigned char qw_raw[];
     const int R = q.R, J = q.J, tid = threadIdx.x;
     T *Vs = reinterpret_cast<T *>(qw_raw);            // QZ_JC × R
     T *Ys = Vs + QZ_JC * R;                           // R × (QZ_JC + 1)
@@ -584,21 +663,12 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_w(int K_all, QDev q, const T *
                 Ys[r * (QZ_JC + 1) + c] = jc + c < J ? Yk[(int64_t)r * J + jc + c] : T(0);
             }
             __syncthreads();
-#pragma unroll
-            for (int v = 0; v < 16; ++v) {
-                const int e = tid + v * QZ_THREADS;
-                if (e < R * R) {
-                    const int r = e / R, s = e % R;
-                    T a = T(0);
-                    for (int c = 0; c < QZ_JC; ++c) a += Ys[r * (QZ_JC + 1) + c] * Vs[c * R + s];
-                    yv[v] += (double)a;
-                }
-            }
+            qz_yv_chunk(Ys, Vs, R, yv);
         }
 #pragma unroll
         for (int v = 0; v < 16; ++v) {
-            const int e = tid + v * QZ_THREADS;
-            if (e < R * R) red[e] = q.H[e] * yv[v];
+            int r, s;
+            if (qz_pair(R, v, r, s)) red[r * R + s] = q.H[r * R + s] * yv[v];
         }
         __syncthreads();
         for (int r = tid; r < R; r += QZ_THREADS) {
@@ -661,6 +731,13 @@ __global__ void __launch_bounds__(256) k_q_out(int64_t N, QDev q, const int *__r
             }
             __syncwarp();
             const TI *xr = X + row * J + jb;
+            // FP32 data and products: the lane's share of the row is summed in
+            // double-float (x − x̂ exactly by TwoSum, each square split by
+            // TwoProduct, each addition by TwoSum) and added to the FP64 totals
+            // once per row, so the FP64 pipe sees four additions per row, not
+            // five operations per entry
+            constexpr bool f32 = std::is_same<T, float>::value && std::is_same<TI, float>::value;
+            df rs = {0.f, 0.f}, xs = {0.f, 0.f};
             for (int j0 = 4 * lane; j0 < Jc && jb + j0 < J; j0 += 128) {
                 T h0 = T(0), h1 = T(0), h2 = T(0), h3 = T(0);
                 for (int s2 = 0; s2 < R; ++s2) {
@@ -675,12 +752,27 @@ __global__ void __launch_bounds__(256) k_q_out(int64_t N, QDev q, const int *__r
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (jb + j0 + u < J) {
-                        const double x = (double)xr[j0 + u];
-                        const double d = x - (double)hh[u];
-                        res += d * d;
-                        xn += x * x;
+                        if constexpr (f32) {
+                            const float x = (float)xr[j0 + u];
+                            const df d = two_sum(x, -(float)hh[u]);     // x − x̂ exactly
+                            const df p = two_prod(d.hi, d.hi);
+                            const df t = two_sum(rs.hi, p.hi);
+                            rs = {t.hi, __fadd_rn(rs.lo, __fadd_rn(t.lo, fmaf(2.f * d.hi, d.lo, p.lo)))};
+                            const df px = two_prod(x, x);
+                            const df tx = two_sum(xs.hi, px.hi);
+                            xs = {tx.hi, __fadd_rn(xs.lo, __fadd_rn(tx.lo, px.lo))};
+                        } else {
+                            const double x = (double)xr[j0 + u];
+                            const double d = x - (double)hh[u];
+                            res += d * d;
+                            xn += x * x;
+                        }
                     }
                 }
+            }
+            if constexpr (f32) {
+                res += (double)rs.hi + (double)rs.lo;
+                xn += (double)xs.hi + (double)xs.lo;
             }
         }
     }
