@@ -26,7 +26,7 @@ enum KernelKind {
     KK_XQ_PREP, KK_XQ_TC, KK_F_TC, KK_UTILDE, KK_XQ_WAIT, KK_XQ_BUSY, KK_FT_WAIT, KK_FT_BUSY,
     KK_QV_TF32, KK_XQ_UMMA, KK_F_UMMA, KK_FIT_LAMBDA,
     KK_XU_WAIT_P, KK_XU_WAIT_M, KK_XU_WAIT_C, KK_XU_WAIT_E, KK_XU_CYCLES,
-    KK_BC_DSUM, KK_BC_DUPD, KK_BC_CHOL, KK_BC_SOLVE, KK_BC_RESID, KK_BC_GSHARE,
+    KK_BC_DSUM, KK_BC_DUPD, KK_BC_CHOL, KK_BC_SOLVE, KK_BC_RESID, KK_BC_GSHARE, KK_Q_PSUM,
     KK_HOST_PLAN, KK_HOST_WAIT, KK_HOST_LAUNCH, KK_COUNT
 };
 static const char *const kKernelNames[KK_COUNT] = {
@@ -42,7 +42,7 @@ static const char *const kKernelNames[KK_COUNT] = {
     "k_f_tc.wait", "k_f_tc.loop", "k_qv_tf32", "k_xq_umma", "k_f_umma", "k_fit_lambda",
     "k_xq_umma.producer_wait", "k_xq_umma.mma_wait", "k_xq_umma.converter_wait", "k_xq_umma.epilogue_wait",
     "k_xq_umma.cta", "k_big_c.dsum", "k_big_c.d_update", "k_big_c.cholesky", "k_big_c.solves",
-    "k_big_c.residual", "k_big_c.g_share", "host.plan", "host.wait_previous", "host.launch"};
+    "k_big_c.residual", "k_big_c.g_share", "k_q_psum", "host.plan", "host.wait_previous", "host.launch"};
 
 struct Profiler {
     bool on = false;

@@ -496,6 +496,19 @@ __global__ void __launch_bounds__(QZ_THREADS, RM <= 32 ? 2 : 1) k_q_y(BatchDev b
     }
 }
 
+// Sums of per-CTA FP64 partials, in place: parts[e] = Σ_{p < nb} parts[p·n + e]
+// for e < n, each entry by one thread in the order p = 0, 1, ... (so the
+// result has the bits of a sequential sum).  Entry e is read and written by
+// its own thread only, so the in-place write is race-free.
+static __global__ void k_q_psum(double *__restrict__ parts, int nb, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int p = 0; p < nb; ++p) a += parts[(int64_t)p * n + e];
+        parts[e] = a;
+    }
+}
+
 // H = MH (Γ ∗ WᵀW)⁺ and PV = (HᵀH ∗ WᵀW)⁺, one warp; WW (R×R) is kept.
 static __global__ void k_q_h(const double *__restrict__ MHpart, const double *__restrict__ WWpart, int nb,
                       QDev q, double *__restrict__ WW, double *__restrict__ PV) {
@@ -694,13 +707,13 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_w(int K_all, QDev q, const T *
 template <typename T>
 __host__ __device__ inline int q_out_chunk(int R, int J) {
     const int Jp = ((J + 127) / 128) * 128;
-    int cap = (int)((190 * 1024) / ((size_t)R * sizeof(T)) / 128) * 128;
+    int cap = (int)((190 * 1024 - (size_t)R * R * sizeof(T)) / ((size_t)R * sizeof(T)) / 128) * 128;
     if (cap < 128) cap = 128;
     return Jp < cap ? Jp : cap;
 }
 template <typename T>
 __host__ __device__ inline size_t q_out_smem(int R, int J) {
-    return ((size_t)R * q_out_chunk<T>(R, J) + 8 * 64) * sizeof(T);
+    return ((size_t)R * q_out_chunk<T>(R, J) + 8 * 64 + (size_t)R * R) * sizeof(T);
 }
 
 template <typename TI, typename T>
@@ -713,6 +726,8 @@ __global__ void __launch_bounds__(256) k_q_out(int64_t N, QDev q, const int *__r
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     T *Vt = reinterpret_cast<T *>(qo_raw);                     // R × Jc, Vt[s][j] = V[j0 + j][s]
     T *zs = Vt + (size_t)R * Jc + (size_t)wid * 64;            // per warp z
+    T *Hs = Vt + (size_t)R * Jc + 8 * 64;                      // H in the product type
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) Hs[e] = (T)q.H[e];
     double res = 0.0, xn = 0.0;
     for (int jb = 0; jb < J; jb += Jc) {
         __syncthreads();
@@ -726,7 +741,7 @@ __global__ void __launch_bounds__(256) k_q_out(int64_t N, QDev q, const int *__r
             __syncwarp();
             for (int s2 = lane; s2 < R; s2 += 32) {
                 T a = T(0);
-                for (int r = 0; r < R; ++r) a += Qrows[row * R + r] * (T)q.H[r * R + s2];
+                for (int r = 0; r < R; ++r) a += Qrows[row * R + r] * Hs[r * R + s2];
                 zs[s2] = a * (T)q.W[(int64_t)k * R + s2];
             }
             __syncwarp();

@@ -138,14 +138,26 @@ static dash_status launch_update_q(dash_model *m, const BatchDev &b, const void 
     }
     const int ld = R + 1;
     if (sweep) {
-        LAUNCH(KK_Q_H, (k_q_h<<<1, 32, (size_t)(4 * R * ld + R) * 8, st>>>(m->qMH, m->qWWp, gy, q,
+        // the per-CTA partials summed across SMs first (one warp summing them
+        // serially was latency-bound), then H and the pseudo-inverses
+        const int nyb = b.K_all > 0 ? gy : 1;
+        if (nyb > 1) {
+            const int g = (int)std::min<int64_t>(((int64_t)R * R + 255) / 256, m->n_sm);
+            LAUNCH(KK_Q_PSUM, (k_q_psum<<<g, 256, 0, st>>>(m->qMH, nyb, (int64_t)R * R)));
+            LAUNCH(KK_Q_PSUM, (k_q_psum<<<g, 256, 0, st>>>(m->qWWp, nyb, (int64_t)R * R)));
+        }
+        LAUNCH(KK_Q_H, (k_q_h<<<1, 32, (size_t)(4 * R * ld + R) * 8, st>>>(m->qMH, m->qWWp, 1, q,
                                                                              m->qWW, m->qPV)));
         const int gv = std::max(1, std::min(b.K_all, m->q_vslots));
         if (R <= 32)
             LAUNCH(KK_Q_VPART, (k_q_vpart<T, 32><<<gv, QV_THREADS, 0, st>>>(b.K_all, q, Y, m->qslots)));
         else
             LAUNCH(KK_Q_VPART, (k_q_vpart<T, 64><<<gv, QV_THREADS, 0, st>>>(b.K_all, q, Y, m->qslots)));
-        LAUNCH(KK_Q_V, (k_q_v<T><<<(J + 7) / 8, 256, 0, st>>>(m->qslots, gv, m->qPV, J, R, m->st.V,
+        if (gv > 1) {
+            const int g = (int)std::min<int64_t>(((int64_t)J * R + 255) / 256, 2 * m->n_sm);
+            LAUNCH(KK_Q_PSUM, (k_q_psum<<<g, 256, 0, st>>>(m->qslots, gv, (int64_t)J * R)));
+        }
+        LAUNCH(KK_Q_V, (k_q_v<T><<<(J + 7) / 8, 256, 0, st>>>(m->qslots, 1, m->qPV, J, R, m->st.V,
                                                                (T *)m->VT)));
         LAUNCH(KK_GAMMA, k_gamma<<<(R * R + 7) / 8, 256, 0, st>>>(m->st.V, J, R, m->st.Gam, nullptr));
         LAUNCH(KK_Q_PW, (k_q_pw<<<1, 32, (size_t)(3 * R * ld + R) * 8, st>>>(q, m->qPW)));
