@@ -285,12 +285,13 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
 // column jc+jj and the rows r ≡ rg (mod 4).
 constexpr int QZ_THREADS = 256;
 constexpr int QZ_JC = 64;
+constexpr int QZ_JC2 = 2 * QZ_JC;   // k_q_y: columns per pass (two per thread, QZ_JC apart)
 constexpr int QZ_RC = 32;     // Q rows staged per pass
 
 template <typename T>
 __host__ __device__ inline size_t q_y_smem(int R) {
     const size_t RM = R <= 32 ? 32 : 64;
-    return (RM * RM + (size_t)QZ_RC * RM + (size_t)QZ_JC * R + (size_t)R * (QZ_JC + 1)) * sizeof(T);
+    return (RM * RM + (size_t)QZ_RC * RM + (size_t)QZ_JC2 * R + (size_t)R * (QZ_JC2 + 1)) * sizeof(T);
 }
 
 // n consecutive values from 16-byte aligned shared memory, as 16-byte loads.
@@ -337,7 +338,8 @@ __device__ __forceinline__ bool qz_pair(int R, int u, int &r, int &s) {
 // vector load of the Vs row (16-byte aligned: the Vs base is, and the row
 // pitch is R entries).
 template <typename T, int NP>
-__device__ __forceinline__ void qz_yv_chunk(const T *Ys, const T *Vs, int R, double (&yv)[NP]) {
+__device__ __forceinline__ void qz_yv_chunk(const T *Ys, const T *Vs, int R, double (&yv)[NP],
+                                            int ypitch = QZ_JC + 1) {
     const int t = threadIdx.x;
     if ((R & 3) == 0) {
         const int tpr = R >> 2, rpp = QZ_THREADS / tpr;
@@ -349,7 +351,7 @@ __device__ __forceinline__ void qz_yv_chunk(const T *Ys, const T *Vs, int R, dou
             if (r < R) {
                 T a[4] = {T(0), T(0), T(0), T(0)};
                 for (int c = 0; c < QZ_JC; ++c) {
-                    const T y = Ys[r * (QZ_JC + 1) + c];
+                    const T y = Ys[r * ypitch + c];
                     T v[4];
                     ld_shared_vec(Vs + c * R + s0, v);
 #pragma unroll
@@ -366,7 +368,7 @@ __device__ __forceinline__ void qz_yv_chunk(const T *Ys, const T *Vs, int R, dou
         int r, s2;
         if (qz_pair(R, u, r, s2)) {
             T a = T(0);
-            for (int c = 0; c < QZ_JC; ++c) a += Ys[r * (QZ_JC + 1) + c] * Vs[c * R + s2];
+            for (int c = 0; c < QZ_JC; ++c) a += Ys[r * ypitch + c] * Vs[c * R + s2];
             yv[u] += (double)a;
         }
     }
@@ -381,10 +383,12 @@ __global__ void __launch_bounds__(QZ_THREADS, RM <= 32 ? 2 : 1) k_q_y(BatchDev b
     const int R = q.R, J = q.J, tid = threadIdx.x;
     T *Cs = reinterpret_cast<T *>(qy_raw);           // RM × RM  λ C_k (permuted, below)
     T *Qs = Cs + RM * RM;                            // QZ_RC × RM  Q rows (permuted)
-    T *Vs = Qs + QZ_RC * RM;                         // QZ_JC × R
-    T *Ys = Vs + QZ_JC * R;                          // R × (QZ_JC + 1)
+    T *Vs = Qs + QZ_RC * RM;                         // QZ_JC2 × R
+    T *Ys = Vs + QZ_JC2 * R;                         // R × (QZ_JC2 + 1)
+    constexpr int YP = QZ_JC2 + 1;                   // Ys pitch
     const int jj = tid % QZ_JC, rg = tid / QZ_JC;
     const int nq = (R + 3) / 4;
+    const bool lam_on = q.lam != 0.0;
     constexpr int NQ = RM / 4;                        // rows of Y per thread
     constexpr int NP = (RM * RM + QZ_THREADS - 1) / QZ_THREADS;   // (r, s) pairs per thread
     double mh[NP], ww[NP];
@@ -399,34 +403,40 @@ __global__ void __launch_bounds__(QZ_THREADS, RM <= 32 ? 2 : 1) k_q_y(BatchDev b
         for (int e = tid; e < RM * RM; e += QZ_THREADS) {
             const int p = e / RM, rg2 = (e % RM) / NQ, u = e % NQ;
             const int r = rg2 + 4 * u;
-            Cs[e] = (q.lam == 0.0 || r >= R || p >= R) ? T(0)
+            Cs[e] = (!lam_on || r >= R || p >= R) ? T(0)
                                                         : (T)(q.lam * q.C[(int64_t)k * R * R + r * R + p]);
         }
         double yv[NP];
 #pragma unroll
         for (int u = 0; u < NP; ++u) yv[u] = 0.0;
-        for (int jc = 0; jc < J; jc += QZ_JC) {
-            const int j = jc + jj;
+        // columns in passes of QZ_JC2: a thread owns columns j0 = jc + jj and
+        // j1 = j0 + QZ_JC, each summed exactly as a single column would be
+        for (int jc = 0; jc < J; jc += QZ_JC2) {
+            const int j0 = jc + jj, j1 = j0 + QZ_JC;
             __syncthreads();
-            for (int e = tid; e < QZ_JC * R; e += QZ_THREADS) {
-                const int j2 = jc + e / R;
-                Vs[e] = j2 < J ? VT[(int64_t)j2 * R + (e % R)] : T(0);
+            // rows jc.. of Vᵀ's J×R layout are one contiguous block
+            const int vlim = (J - jc < QZ_JC2 ? J - jc : QZ_JC2) * R;
+            for (int e = tid; e < QZ_JC2 * R; e += QZ_THREADS) {
+                Vs[e] = e < vlim ? VT[(int64_t)jc * R + e] : T(0);
             }
             // old Y chunk → Ys (all R rows, needed by every output row)
-            for (int e = tid; e < R * QZ_JC; e += QZ_THREADS) {
-                const int r = e / QZ_JC, c = e % QZ_JC;
-                Ys[r * (QZ_JC + 1) + c] = (q.lam != 0.0 && jc + c < J) ? Yk[(int64_t)r * J + jc + c] : T(0);
+            for (int e = tid; e < R * QZ_JC2; e += QZ_THREADS) {
+                const int r = e / QZ_JC2, c = e % QZ_JC2;
+                Ys[r * YP + c] = (lam_on && jc + c < J) ? Yk[(int64_t)r * J + jc + c] : T(0);
             }
             __syncthreads();
-            T acc[NQ];
+            T acc[NQ], acc1[NQ];
 #pragma unroll
-            for (int u = 0; u < NQ; ++u) acc[u] = T(0);
+            for (int u = 0; u < NQ; ++u) { acc[u] = T(0); acc1[u] = T(0); }
             for (int p = 0; p < R; ++p) {
-                const T y = Ys[p * (QZ_JC + 1) + jj];
+                const T y = Ys[p * YP + jj], y1 = Ys[p * YP + jj + QZ_JC];
                 T cv[NQ];
                 ld_shared_vec(Cs + (p * 4 + rg) * NQ, cv);   // warp-uniform: broadcasts
 #pragma unroll
-                for (int u = 0; u < NQ; ++u) acc[u] += cv[u] * y;
+                for (int u = 0; u < NQ; ++u) {
+                    acc[u] += cv[u] * y;
+                    acc1[u] += cv[u] * y1;
+                }
             }
             if (t >= 0) {
                 for (int si = b.tseg_ptr[t]; si < b.tseg_ptr[t + 1]; ++si) {
@@ -442,20 +452,28 @@ __global__ void __launch_bounds__(QZ_THREADS, RM <= 32 ? 2 : 1) k_q_y(BatchDev b
                             Qs[e] = r < R ? Qrows[(c0 + i) * R + r] : T(0);
                         }
                         __syncthreads();
-                        if (j < J) {
-                            // four rows' loads in flight at a time
+                        if (j0 < J) {
+                            // four rows' loads in flight at a time, both columns
+                            const TI *xb = X + c0 * J;
+                            const bool on1 = j1 < J;
                             for (int i0 = 0; i0 < nr; i0 += 4) {
-                                T xv[4];
+                                T xv[4], xw[4];
 #pragma unroll
-                                for (int i = 0; i < 4; ++i)
-                                    xv[i] = i0 + i < nr ? (T)X[(c0 + i0 + i) * J + j] : T(0);
+                                for (int i = 0; i < 4; ++i) {
+                                    const bool in = i0 + i < nr;
+                                    xv[i] = in ? (T)xb[(int64_t)(i0 + i) * J + j0] : T(0);
+                                    xw[i] = in && on1 ? (T)xb[(int64_t)(i0 + i) * J + j1] : T(0);
+                                }
 #pragma unroll
                                 for (int i = 0; i < 4; ++i) {
                                     if (i0 + i < nr) {
                                         T qv[NQ];
                                         ld_shared_vec(Qs + ((i0 + i) * 4 + rg) * NQ, qv);
 #pragma unroll
-                                        for (int u = 0; u < NQ; ++u) acc[u] += qv[u] * xv[i];
+                                        for (int u = 0; u < NQ; ++u) {
+                                            acc[u] += qv[u] * xv[i];
+                                            acc1[u] += qv[u] * xw[i];
+                                        }
                                     }
                                 }
                             }
@@ -468,13 +486,17 @@ __global__ void __launch_bounds__(QZ_THREADS, RM <= 32 ? 2 : 1) k_q_y(BatchDev b
             for (int u = 0; u < NQ; ++u) {
                 const int r = rg + 4 * u;
                 if (u < nq && r < R) {
-                    if (j < J) Yk[(int64_t)r * J + j] = acc[u];
-                    Ys[r * (QZ_JC + 1) + jj] = j < J ? acc[u] : T(0);
+                    if (j0 < J) Yk[(int64_t)r * J + j0] = acc[u];
+                    if (j1 < J) Yk[(int64_t)r * J + j1] = acc1[u];
+                    Ys[r * YP + jj] = j0 < J ? acc[u] : T(0);
+                    Ys[r * YP + jj + QZ_JC] = j1 < J ? acc1[u] : T(0);
                 }
             }
             __syncthreads();
-            // YV partial over this column chunk: thread owns pairs (r, s)
-            qz_yv_chunk(Ys, Vs, R, yv);
+            // YV partial, one sum per half of the pass (as per QZ_JC-column
+            // chunk): thread owns pairs (r, s)
+            qz_yv_chunk(Ys, Vs, R, yv, YP);
+            if (jc + QZ_JC < J) qz_yv_chunk(Ys + QZ_JC, Vs + QZ_JC * R, R, yv, YP);
         }
         const double *wk = q.W + (int64_t)k * R;
 #pragma unroll
@@ -667,9 +689,10 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_w(int K_all, QDev q, const T *
         for (int v = 0; v < 16; ++v) yv[v] = 0.0;
         for (int jc = 0; jc < J; jc += QZ_JC) {
             __syncthreads();
+            // rows jc.. of Vᵀ's J×R layout are one contiguous block
+            const int vlim = (J - jc < QZ_JC ? J - jc : QZ_JC) * R;
             for (int e = tid; e < QZ_JC * R; e += QZ_THREADS) {
-                const int j2 = jc + e / R;
-                Vs[e] = j2 < J ? VT[(int64_t)j2 * R + (e % R)] : T(0);
+                Vs[e] = e < vlim ? VT[(int64_t)jc * R + e] : T(0);
             }
             for (int e = tid; e < R * QZ_JC; e += QZ_THREADS) {
                 const int r = e / QZ_JC, c = e % QZ_JC;
