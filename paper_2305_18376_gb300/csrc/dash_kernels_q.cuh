@@ -668,7 +668,7 @@ static __global__ void k_q_pw(QDev q, double *__restrict__ PW) {
 // One CTA per slice; Y_k V in column chunks.
 template <typename T>
 __host__ __device__ inline size_t q_w_smem(int R) {
-    return ((size_t)QZ_JC * R + (size_t)R * (QZ_JC + 1)) * sizeof(T) + (size_t)(64 + R * R) * 8 + 16;
+    return ((size_t)QZ_JC2 * R + (size_t)R * (QZ_JC2 + 1)) * sizeof(T) + (size_t)(64 + R * R) * 8 + 16;
 }
 
 template <typename T>
@@ -677,9 +677,10 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_w(int K_all, QDev q, const T *
                                                     const double *__restrict__ PW) {
     extern __shared__ __align__(16) unsigned char qw_raw[];
     const int R = q.R, J = q.J, tid = threadIdx.x;
-    T *Vs = reinterpret_cast<T *>(qw_raw);            // QZ_JC × R
-    T *Ys = Vs + QZ_JC * R;                           // R × (QZ_JC + 1)
-    const size_t off = (((size_t)QZ_JC * R + (size_t)R * (QZ_JC + 1)) * sizeof(T) + 15) / 16 * 16;
+    constexpr int YP = QZ_JC2 + 1;                    // Ys pitch
+    T *Vs = reinterpret_cast<T *>(qw_raw);            // QZ_JC2 × R
+    T *Ys = Vs + QZ_JC2 * R;                          // R × (QZ_JC2 + 1)
+    const size_t off = (((size_t)QZ_JC2 * R + (size_t)R * YP) * sizeof(T) + 15) / 16 * 16;
     double *u = reinterpret_cast<double *>(qw_raw + off);   // 64
     double *red = u + 64;                                   // R × R
     for (int k = blockIdx.x; k < K_all; k += gridDim.x) {
@@ -687,19 +688,21 @@ __global__ void __launch_bounds__(QZ_THREADS) k_q_w(int K_all, QDev q, const T *
         double yv[16];
 #pragma unroll
         for (int v = 0; v < 16; ++v) yv[v] = 0.0;
-        for (int jc = 0; jc < J; jc += QZ_JC) {
+        // passes of QZ_JC2 columns, summed per half (QZ_JC columns) as before
+        for (int jc = 0; jc < J; jc += QZ_JC2) {
             __syncthreads();
             // rows jc.. of Vᵀ's J×R layout are one contiguous block
-            const int vlim = (J - jc < QZ_JC ? J - jc : QZ_JC) * R;
-            for (int e = tid; e < QZ_JC * R; e += QZ_THREADS) {
+            const int vlim = (J - jc < QZ_JC2 ? J - jc : QZ_JC2) * R;
+            for (int e = tid; e < QZ_JC2 * R; e += QZ_THREADS) {
                 Vs[e] = e < vlim ? VT[(int64_t)jc * R + e] : T(0);
             }
-            for (int e = tid; e < R * QZ_JC; e += QZ_THREADS) {
-                const int r = e / QZ_JC, c = e % QZ_JC;
-                Ys[r * (QZ_JC + 1) + c] = jc + c < J ? Yk[(int64_t)r * J + jc + c] : T(0);
+            for (int e = tid; e < R * QZ_JC2; e += QZ_THREADS) {
+                const int r = e / QZ_JC2, c = e % QZ_JC2;
+                Ys[r * YP + c] = jc + c < J ? Yk[(int64_t)r * J + jc + c] : T(0);
             }
             __syncthreads();
-            qz_yv_chunk(Ys, Vs, R, yv);
+            qz_yv_chunk(Ys, Vs, R, yv, YP);
+            if (jc + QZ_JC < J) qz_yv_chunk(Ys + QZ_JC, Vs + QZ_JC * R, R, yv, YP);
         }
 #pragma unroll
         for (int v = 0; v < 16; ++v) {
@@ -762,10 +765,19 @@ __global__ void __launch_bounds__(256) k_q_out(int64_t N, QDev q, const int *__r
         for (int64_t row = (int64_t)blockIdx.x * nw + wid; row < N; row += (int64_t)gridDim.x * nw) {
             const int k = row_slice[row];
             __syncwarp();
-            for (int s2 = lane; s2 < R; s2 += 32) {
-                T a = T(0);
-                for (int r = 0; r < R; ++r) a += Qrows[row * R + r] * Hs[r * R + s2];
-                zs[s2] = a * (T)q.W[(int64_t)k * R + s2];
+            // z = q H S_k: the row's q entries read once (lane l holds q_l and
+            // q_{l+32}) and broadcast by shuffles
+            {
+                const T qa = lane < R ? Qrows[row * R + lane] : T(0);
+                const T qb = lane + 32 < R ? Qrows[row * R + lane + 32] : T(0);
+                T a0 = T(0), a1 = T(0);
+                for (int r = 0; r < R; ++r) {
+                    const T qr = __shfl_sync(0xffffffffu, r < 32 ? qa : qb, r & 31);
+                    if (lane < R) a0 += qr * Hs[r * R + lane];
+                    if (lane + 32 < R) a1 += qr * Hs[r * R + lane + 32];
+                }
+                if (lane < R) zs[lane] = a0 * (T)q.W[(int64_t)k * R + lane];
+                if (lane + 32 < R) zs[lane + 32] = a1 * (T)q.W[(int64_t)k * R + lane + 32];
             }
             __syncwarp();
             const TI *xr = X + row * J + jb;
