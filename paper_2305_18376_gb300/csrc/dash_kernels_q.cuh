@@ -170,6 +170,13 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
     S *Bg = reinterpret_cast<S *>(q.Bh);
     long long pc[4] = {0, 0, 0, 0};
     for (int k = blockIdx.x * nw + wid; k < b.K_all; k += gridDim.x * nw) {
+        // the CTA's warps that have a slice this round take each phase (QR,
+        // FP32 sweeps, working-type sweeps, tail) together: a named barrier
+        // over exactly those warps between phases, so that the SM's
+        // instruction cache holds one phase's code at a time
+        const int kb = k - wid;
+        const int nact = b.K_all - kb < nw ? b.K_all - kb : nw;
+        auto phase_bar = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(32 * nact) : "memory"); };
         long long c0k = q.phase ? clock64() : 0;
         const int t = mode == 0 ? b.tslot[k] : -1;
         __syncwarp();
@@ -196,6 +203,7 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
         if (mode == 0)
             for (int i = lane; i < R * R; i += 32) Lg[k * RR + i] = Lw[(i / R) * ld + (i % R)];
         if (q.phase) { const long long c1 = clock64(); pc[0] += c1 - c0k; c0k = c1; }
+        phase_bar();
         if (R <= 32) {
             // register-resident one-sided Jacobi: FP32 sweeps, E re-orthogonalised
             // to the working type, then sweeps in the working type
@@ -209,11 +217,13 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
                 warp_newton_schulz_reg<S>(Ew, Gw, R, ld, std::is_same<S, df>::value ? 1 : 2);
             }
             if (q.phase) { const long long c1 = clock64(); pc[1] += c1 - c0k; c0k = c1; }
+            phase_bar();
             // working-type sweeps; the double-float ones stop after the sweep that
             // started below sqrt(tol)/2 (quadratic convergence)
             warp_eig_os<S, S>(Lw, Ew, mu, R, ld, passes, jac_tol,
                               std::is_same<S, df>::value ? 0.5f * sqrtf(jac_tol) : 0.f);
             if (q.phase) { const long long c1 = clock64(); pc[2] += c1 - c0k; c0k = c1; }
+            phase_bar();
         } else {
             // FP32 pre-pass (float scratch in G and M), then the working-type passes
             float *f0 = reinterpret_cast<float *>(Gw);
@@ -222,8 +232,10 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
                 warp_eig_prepass_f32<S>(Lw, Ew, f0, f0 + fs, f0 + 2 * fs, f0 + 3 * fs,
                                         reinterpret_cast<float *>(mu), Gw, Mw, R, ld, 6);
             if (q.phase) { const long long c1 = clock64(); pc[1] += c1 - c0k; c0k = c1; }
+            phase_bar();
             warp_eig_factor(Lw, Ew, Gw, Mw, mu, R, ld, passes, jac_tol, 40, 1e-7f);
             if (q.phase) { const long long c1 = clock64(); pc[2] += c1 - c0k; c0k = c1; }
+            phase_bar();
         }
         {
             // a non-finite factor or eigenvalue must not pass silently
