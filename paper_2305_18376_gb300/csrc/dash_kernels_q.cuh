@@ -211,6 +211,7 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
                 // stops after the sweep that started below sqrt(1e-6)/2: the
                 // quadratic step takes it to FP32's noise level
                 warp_eig_os<float, S>(Lw, Ew, nullptr, R, ld, 8, 1e-6f, 5e-4f);
+                phase_bar();
                 // double-float: one step (the FP32 sweeps leave EᵀE − I at a few
                 // 1e-6; one step takes it to about 1e-11, below the sweeps' 1e-10
                 // target); FP64: two
