@@ -170,7 +170,7 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
     S *Bg = reinterpret_cast<S *>(q.Bh);
     long long pc[4] = {0, 0, 0, 0};
     for (int k = blockIdx.x * nw + wid; k < b.K_all; k += gridDim.x * nw) {
-        // the CTA's warps that have a slice this round take each phase (QR,
+        // the CTA's warps that have a slice in this pass take each phase (QR,
         // FP32 sweeps, working-type sweeps, tail) together: a named barrier
         // over exactly those warps between phases, so that the SM's
         // instruction cache holds one phase's code at a time
