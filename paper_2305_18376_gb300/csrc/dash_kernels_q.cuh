@@ -171,9 +171,11 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
     long long pc[4] = {0, 0, 0, 0};
     for (int k = blockIdx.x * nw + wid; k < b.K_all; k += gridDim.x * nw) {
         // the CTA's warps that have a slice in this pass take each phase (QR,
-        // FP32 sweeps, working-type sweeps, tail) together: a named barrier
-        // over exactly those warps between phases, so that the SM's
-        // instruction cache holds one phase's code at a time
+        // FP32 sweeps, Newton–Schulz, working-type sweeps, tail) together: a
+        // named barrier over exactly those warps between phases, so that the
+        // SM's instruction cache holds one phase's unrolled code at a time.
+        // Every such warp runs the same sequence of barriers (no phase is
+        // skipped), and warps without a slice have left the loop.
         const int kb = k - wid;
         const int nact = b.K_all - kb < nw ? b.K_all - kb : nw;
         auto phase_bar = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(32 * nact) : "memory"); };
