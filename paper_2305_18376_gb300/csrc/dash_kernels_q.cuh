@@ -174,8 +174,8 @@ __global__ void k_q_lt(BatchDev b, QDev q, const T *__restrict__ A, T *__restric
         // FP32 sweeps, Newton–Schulz, working-type sweeps, tail) together: a
         // named barrier over exactly those warps between phases, so that the
         // SM's instruction cache holds one phase's unrolled code at a time.
-        // Every such warp runs the same sequence of barriers (no phase is
-        // skipped), and warps without a slice have left the loop.
+        // Every such warp runs the same barriers (none is data-dependent),
+        // and warps without a slice have left the loop.
         const int kb = k - wid;
         const int nact = b.K_all - kb < nw ? b.K_all - kb : nw;
         auto phase_bar = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(32 * nact) : "memory"); };
